@@ -1,0 +1,93 @@
+"""Residual and comparison helpers -- TEST INFRASTRUCTURE.
+
+The relative residual of an eigenvector v of (S, T) for (alpha, beta) is
+    ||beta S v - alpha T v||_inf / ((|beta| ||S||_inf + |alpha| ||T||_inf) ||v||_inf)
+(matrix infinity norms are maximum row sums, vector norms maximum moduli);
+Table 1 of the paper reports all vectors below 2u with this kind of measure.
+The acceptance bar used here is 100 n u, u = 2^-53.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U = 2.0 ** -53
+
+
+def column_kinds(blk, select=None):
+    """Kind and diagonal position of each output column.
+
+    Returns (kinds, pos): kinds[c] = 0 real, 1 first (real part) and 2 second
+    (imaginary part) column of a complex pair; pos[c] = diagonal row of the
+    block's first row.
+    """
+    blk = np.asarray(blk)
+    n = blk.size
+    kinds, pos = [], []
+    c = 0
+    while c < n:
+        sz = 2 if blk[c] == 1 else 1
+        sel = select is None or bool(select[c]) or (sz == 2 and bool(select[c + 1]))
+        if sel:
+            if sz == 1:
+                kinds.append(0)
+                pos.append(c)
+            else:
+                kinds += [1, 2]
+                pos += [c, c]
+        c += sz
+    return np.asarray(kinds, dtype=np.int64), np.asarray(pos, dtype=np.int64)
+
+
+def as_complex(V, kinds):
+    """One complex vector per eigenvector (pairs combined), with its column."""
+    out, cols = [], []
+    for c, k in enumerate(kinds):
+        if k == 0:
+            out.append(V[:, c].astype(complex))
+            cols.append(c)
+        elif k == 1:
+            out.append(V[:, c] + 1j * V[:, c + 1])
+            cols.append(c)
+    return out, cols
+
+
+def residuals(S, T, V, kinds, pos, a, b, beta):
+    """Relative residual of every eigenvector (one value per output column)."""
+    S = np.asarray(S)
+    T = np.asarray(T)
+    nS = np.abs(S).sum(axis=1).max()
+    nT = np.abs(T).sum(axis=1).max()
+    vecs, cols = as_complex(V, kinds)
+    res = np.zeros(len(kinds))
+    for z, c in zip(vecs, cols):
+        p = pos[c]
+        al = complex(a[p], b[p])
+        bt = beta[p]
+        r = bt * (S @ z) - al * (T @ z)
+        den = (abs(bt) * nS + abs(al) * nT) * np.abs(z).max()
+        val = np.abs(r).max() / den if den > 0 else np.inf
+        res[c] = val
+        if kinds[c] == 1:
+            res[c + 1] = val
+    return res
+
+
+def compare_normalised(Vref, Vgot, kinds):
+    """Largest componentwise |difference| after normalising ``Vgot`` at the
+    index where ``Vref`` has its largest modulus (near-ties in the maximum may
+    pick different indices on the two sides, so both are taken at the same
+    index).  Returns (max_err, per-vector errors)."""
+    ref, cols = as_complex(Vref, kinds)
+    got, _ = as_complex(Vgot, kinds)
+    errs = np.zeros(len(cols))
+    for q, (zr, zg) in enumerate(zip(ref, got)):
+        m = np.abs(zr)
+        istar = int(np.argmax(m))
+        d = zg[istar]
+        if d == 0 or not np.isfinite(d):
+            errs[q] = np.inf
+            continue
+        zg2 = zg / d
+        zr2 = zr / zr[istar]
+        errs[q] = np.abs(zg2 - zr2).max()
+    return (errs.max() if errs.size else 0.0), errs

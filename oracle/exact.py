@@ -1,0 +1,116 @@
+"""Exact brute force for tiny pencils -- TEST INFRASTRUCTURE.
+
+For a pencil whose entries are exact rationals (``pencilgen.exact_pencil``),
+the eigenvector of the eigenvalue lambda = alpha/beta is the kernel of
+M = beta*S - alpha*T (Section 2, the tall equation and its Lemma).  This
+module computes that kernel in exact arithmetic over the Gaussian rationals
+Q(i) by reduced row echelon form of the whole n x n matrix M: a general
+null-space computation, not the triangular substitution the method uses.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+
+class GQ:
+    """Gaussian rational re + i*im with Fraction parts."""
+    __slots__ = ("re", "im")
+
+    def __init__(self, re, im=0):
+        self.re = Fraction(re)
+        self.im = Fraction(im)
+
+    def __add__(self, o):
+        return GQ(self.re + o.re, self.im + o.im)
+
+    def __sub__(self, o):
+        return GQ(self.re - o.re, self.im - o.im)
+
+    def __mul__(self, o):
+        return GQ(self.re * o.re - self.im * o.im, self.re * o.im + self.im * o.re)
+
+    def __truediv__(self, o):
+        d = o.re * o.re + o.im * o.im
+        return GQ((self.re * o.re + self.im * o.im) / d, (self.im * o.re - self.re * o.im) / d)
+
+    def __neg__(self):
+        return GQ(-self.re, -self.im)
+
+    def is_zero(self):
+        return self.re == 0 and self.im == 0
+
+    def abs2(self):
+        return self.re * self.re + self.im * self.im
+
+    def to_complex(self):
+        return complex(float(self.re), float(self.im))
+
+
+def nullspace(M):
+    """Basis of the kernel of the square matrix M (list of lists of GQ)."""
+    n = len(M)
+    A = [row[:] for row in M]
+    pivots = []
+    r = 0
+    for col in range(n):
+        piv = None
+        for i in range(r, n):
+            if not A[i][col].is_zero():
+                piv = i
+                break
+        if piv is None:
+            continue
+        A[r], A[piv] = A[piv], A[r]
+        p = A[r][col]
+        A[r] = [x / p for x in A[r]]
+        for i in range(n):
+            if i != r and not A[i][col].is_zero():
+                f = A[i][col]
+                A[i] = [x - f * y for x, y in zip(A[i], A[r])]
+        pivots.append(col)
+        r += 1
+        if r == n:
+            break
+    free = [c for c in range(n) if c not in pivots]
+    basis = []
+    for fcol in free:
+        v = [GQ(0) for _ in range(n)]
+        v[fcol] = GQ(1)
+        for i, pc in enumerate(pivots):
+            v[pc] = -A[i][fcol]
+        basis.append(v)
+    return basis
+
+
+def exact_eigenvectors(ep):
+    """Normalised exact eigenvectors of an ``ExactPencil``.
+
+    Returns an n x n complex array V (column c of a 1x1 block holds the real
+    vector; for a 2x2 block starting at c, column c holds z for mu + i nu,
+    nu > 0, and column c+1 holds its conjugate) and the kernel dimensions.
+    Each vector is divided by its first entry of largest modulus.
+    """
+    n = len(ep.S)
+    V = np.zeros((n, n), dtype=complex)
+    dims = []
+    c = 0
+    while c < n:
+        sz = 2 if ep.block[c] == 1 else 1
+        lr, li = ep.lam[c]
+        alpha = GQ(lr, li)
+        M = [[GQ(ep.S[i][j]) - alpha * GQ(ep.T[i][j]) for j in range(n)] for i in range(n)]
+        basis = nullspace(M)
+        dims.append(len(basis))
+        v = basis[0]
+        best = max(x.abs2() for x in v)
+        istar = next(i for i, x in enumerate(v) if x.abs2() == best)
+        d = v[istar]
+        z = [x / d for x in v]
+        col = np.array([x.to_complex() for x in z])
+        V[:, c] = col
+        if sz == 2:
+            V[:, c + 1] = np.conj(col)
+        c += sz
+    return V, dims
