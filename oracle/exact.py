@@ -98,9 +98,13 @@ def exact_eigenvectors(ep):
     c = 0
     while c < n:
         sz = 2 if ep.block[c] == 1 else 1
-        lr, li = ep.lam[c]
-        alpha = GQ(lr, li)
-        M = [[GQ(ep.S[i][j]) - alpha * GQ(ep.T[i][j]) for j in range(n)] for i in range(n)]
+        if sz == 1:
+            # homogeneous pair (alpha, beta) = (S_cc, T_cc): also covers beta = 0
+            alpha, beta = GQ(ep.S[c][c]), GQ(ep.T[c][c])
+        else:
+            lr, li = ep.lam[c]
+            alpha, beta = GQ(lr, li), GQ(1)
+        M = [[beta * GQ(ep.S[i][j]) - alpha * GQ(ep.T[i][j]) for j in range(n)] for i in range(n)]
         basis = nullspace(M)
         dims.append(len(basis))
         v = basis[0]

@@ -26,7 +26,7 @@
  * Readings of points the paper leaves open (each is listed in the design doc):
  *   - Omega = 2^1022.  ProtectUpdate / ProtectDivision return a power of two
  *     2^-k, with k from exponent bounds (frexp); they satisfy the properties
- *     of Section 4 but may scale by up to 4x more than the minimum.
+ *     of Section 4 but may scale by up to 8x more than the minimum.
  *   - (alpha, beta): 1x1 block -> (S_cc, T_cc), sign chosen so beta >= 0;
  *     2x2 block (T_jj diagonal, positive) -> beta = 1, alpha = p + i q from
  *     the quadratic det(S_jj - lambda T_jj) = 0, q > 0.

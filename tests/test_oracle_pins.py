@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+* exact kernels of beta*S - alpha*T over the Gaussian rationals (brute force,
+  stored fixtures and fresh tiny pencils);
+* the eigenvalues the generator placed (independent of the oracle's formula);
+* the properties of ProtectDivision / ProtectUpdate (paper, Section 4),
+  checked in exact rational arithmetic;
+* special cases that reduce to library routines (T = I, scipy's QZ-based
+  generalized eigensolver) and to unit vectors (diagonal pencils);
+* the residual bar, conjugate-pair structure and zeros below the tip
+  (Section 2, Lemma);
+* robustness: on stress pencils the non-robust substitution overflows while
+  the oracle stays finite and records growth beyond the binary64 range.
+"""
+import glob
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import pencilgen
+from oracle import check, exact
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OMEGA = Fraction(2) ** 1022
+
+
+def _real_columns(Vc, kinds):
+    n = Vc.shape[0]
+    Vr = np.zeros((n, len(kinds)))
+    for c, k in enumerate(kinds):
+        if k == 0:
+            Vr[:, c] = Vc[:, c].real
+        elif k == 1:
+            Vr[:, c] = Vc[:, c].real
+            Vr[:, c + 1] = Vc[:, c].imag
+    return Vr
+
+
+# ---------------------------------------------------------------- exact pins
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(HERE, "golden", "exact_*.txt"))))
+def test_oracle_matches_golden_exact(path):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    S, T, block, Vx = mg.load(path)
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0 and m == S.shape[0]
+    kinds, pos = check.column_kinds(block)
+    err, _ = check.compare_normalised(_real_columns(Vx, kinds), V, kinds)
+    assert err <= 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_oracle_matches_fresh_exact(n):
+    worst = 0.0
+    for seed in range(12):
+        ep = pencilgen.exact_pencil(n, 100 + seed)
+        S, T = ep.as_float()
+        Vx, dims = exact.exact_eigenvectors(ep)
+        assert all(d == 1 for d in dims)
+        st, V, sc, m = oracle.evc(S, T)
+        assert st == 0
+        kinds, _ = check.column_kinds(ep.block)
+        err, _ = check.compare_normalised(_real_columns(Vx, kinds), V, kinds)
+        worst = max(worst, err)
+    assert worst <= 1e-13
+
+
+def test_oracle_first_max_normalisation_exact():
+    """The oracle puts exactly 1 at its largest-modulus entry and 0 below the tip."""
+    p = pencilgen.config_pencil(0, n=64)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    kinds, pos = check.column_kinds(p.block)
+    vecs, cols = check.as_complex(V, kinds)
+    for z, c in zip(vecs, cols):
+        mags = np.abs(z)
+        i = int(np.argmax(mags))
+        assert z[i] == 1.0
+        tip_last = pos[c] + (1 if kinds[c] == 1 else 0)
+        assert np.all(z[tip_last + 1:] == 0)
+
+
+# ------------------------------------------------------------ eigenvalues
+
+def test_eigpairs_match_generated_eigenvalues():
+    for seed, stress in ((1, False), (2, True)):
+        p = pencilgen.make_pencil(300, seed, stress=stress)
+        st, blk, a, b, beta, sigma = oracle.eigpairs(p.S, p.T)
+        assert st == 0
+        assert np.array_equal(blk, p.block)
+        lam = (a + 1j * b) / beta
+        first = np.flatnonzero(p.block != 2)
+        ref = p.lam_re[first] + 1j * p.lam_im[first]
+        assert np.all(np.abs(lam[first] - ref) <= 1e-12 * (1 + np.abs(ref)))
+        assert np.all(b[p.block == 1] > 0)
+        assert np.all(beta >= 0)
+
+
+def test_eigpairs_status_codes():
+    p = pencilgen.config_pencil(0, n=16)
+    i = int(np.flatnonzero(p.block == 1)[0])
+    S = p.S.copy(order="F")
+    S[i + 1, i] = -S[i + 1, i] * 0 + 1e-30 * np.sign(S[i, i + 1] or 1)  # 2x2 block with real eigenvalues
+    S[i, i + 1] = abs(S[i, i + 1])
+    S[i + 1, i] = abs(S[i + 1, i])
+    st, *_ = oracle.eigpairs(S, p.T)
+    assert st == oracle.ERR_NOT_SCHUR
+    T = p.T.copy(order="F")
+    T[i, i + 1] = 0.5                                            # T_jj not diagonal
+    st, *_ = oracle.eigpairs(p.S, T)
+    assert st == oracle.ERR_NOT_SCHUR
+    S = p.S.copy(order="F")
+    S[0, 5] = np.nan
+    st, *_ = oracle.eigpairs(S, p.T)
+    assert st == oracle.ERR_NONFINITE
+    S = p.S.copy(order="F")
+    T = p.T.copy(order="F")
+    j = int(np.flatnonzero(p.block == 0)[0])
+    S[j, j] = 0.0
+    T[j, j] = 0.0
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == oracle.ERR_INDEFINITE
+
+
+# ------------------------------------------------ ProtectUpdate / Division
+
+def _random_magnitudes(rng, count):
+    e = rng.integers(-1074, 1024, size=count)
+    m = rng.uniform(0.5, 1.0, size=count)
+    vals = np.ldexp(m, e)
+    vals = np.where(np.isfinite(vals), vals, np.finfo(float).max)
+    return vals
+
+
+def test_protect_update_properties():
+    rng = np.random.default_rng(7)
+    ys = _random_magnitudes(rng, 4000)
+    ts = _random_magnitudes(rng, 4000)
+    xs = _random_magnitudes(rng, 4000)
+    edge = [0.0, 5e-324, 2.2250738585072014e-308, 1.0, 2.0 ** 1022, np.finfo(float).max]
+    cases = list(zip(ys, ts, xs))
+    for y in edge:
+        for t in edge:
+            for x in edge:
+                cases.append((y, t, x))
+    for y, t, x in cases:
+        k = oracle.protect_upd(y, t, x)
+        assert k >= 0
+        val = Fraction(y) + Fraction(t) * Fraction(x)
+        assert val <= OMEGA * Fraction(2) ** k           # xi (y + t x) <= Omega, xi = 2^-k
+        if k > 0:                                        # at most 3 bits beyond the minimum
+            assert val > OMEGA * Fraction(2) ** (k - 4)
+
+
+def test_protect_division_properties():
+    rng = np.random.default_rng(8)
+    bs = _random_magnitudes(rng, 4000)
+    ts = _random_magnitudes(rng, 4000)
+    edge = [5e-324, 2.2250738585072014e-308, 1e-200, 1.0, 2.0 ** 1022]
+    cases = list(zip(bs, ts)) + [(b, t) for b in edge + [0.0] for t in edge]
+    for b, t in cases:
+        if b > 2.0 ** 1022:
+            continue                                     # precondition |b| <= Omega
+        k = oracle.protect_div(b, t)
+        assert k >= 0
+        assert Fraction(b) <= Fraction(t) * OMEGA * Fraction(2) ** k
+        if k > 0:
+            assert Fraction(b) > Fraction(t) * OMEGA * Fraction(2) ** (k - 3)
+
+
+def test_complex_division_accuracy_and_range():
+    rng = np.random.default_rng(9)
+    for _ in range(3000):
+        a = complex(*np.ldexp(rng.uniform(-1, 1, 2), rng.integers(-250, 250, 2)))
+        b = complex(*np.ldexp(rng.uniform(-1, 1, 2), rng.integers(-250, 250, 2)))
+        if b == 0:
+            continue
+        q = oracle.cdiv(a, b)
+        # exact quotient in rationals
+        ar, ai, br, bi = map(Fraction, (a.real, a.imag, b.real, b.imag))
+        d = br * br + bi * bi
+        qr = (ar * br + ai * bi) / d
+        qi = (ai * br - ar * bi) / d
+        mod = math.sqrt(float(qr * qr + qi * qi)) if (qr or qi) else 0.0
+        if mod == 0 or not math.isfinite(mod) or mod < 1e-290:
+            continue
+        err = math.hypot(q.real - float(qr), q.imag - float(qi))
+        assert err <= 8 * 2.0 ** -53 * mod
+    # extreme operands where the textbook formula overflows or underflows
+    q = oracle.cdiv(complex(1e300, 1e300), complex(1e300, 1e-300))
+    assert abs(q - complex(1, 1)) < 1e-15
+    q = oracle.cdiv(complex(1e-300, 1e-300), complex(1e-300, 2e-300))
+    assert abs(q - complex(0.6, -0.2)) < 1e-15
+
+
+# -------------------------------------------- special cases and invariants
+
+def test_identity_T_reduces_to_standard_eigenproblem():
+    import scipy.linalg as sl
+    p = pencilgen.config_pencil(0, n=120)
+    T = np.asfortranarray(np.eye(p.n))
+    S = p.S.copy(order="F")
+    # with T = I the diagonal blocks of S carry the eigenvalues directly
+    for i in range(p.n):
+        if p.block[i] == 0:
+            S[i, i] = p.lam_re[i]
+        elif p.block[i] == 1:
+            mu, nu = p.lam_re[i], p.lam_im[i]
+            S[i:i + 2, i:i + 2] = [[mu, nu], [-nu, mu]]
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0
+    w, VR = sl.eig(S)
+    st, blk, a, b, beta, _ = oracle.eigpairs(S, T)
+    kinds, pos = check.column_kinds(blk)
+    vecs, cols = check.as_complex(V, kinds)
+    worst = 0.0
+    for z, c in zip(vecs, cols):
+        lam = (a[pos[c]] + 1j * b[pos[c]]) / beta[pos[c]]
+        j = int(np.argmin(np.abs(w - lam)))
+        zr = VR[:, j]
+        i = int(np.argmax(np.abs(z)))
+        worst = max(worst, np.abs(zr / zr[i] - z).max())
+    assert worst < 1e-8
+
+
+def test_scipy_generalized_cross_check():
+    import scipy.linalg as sl
+    p = pencilgen.make_pencil(250, 31)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    w, VR = sl.eig(p.S, p.T)
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    vecs, cols = check.as_complex(V, kinds)
+    worst = 0.0
+    for z, c in zip(vecs, cols):
+        lam = (a[pos[c]] + 1j * b[pos[c]]) / beta[pos[c]]
+        j = int(np.argmin(np.abs(w - lam)))
+        zr = VR[:, j]
+        i = int(np.argmax(np.abs(z)))
+        worst = max(worst, np.abs(zr / zr[i] - z).max())
+    assert worst < 1e-8
+
+
+def test_diagonal_pencil_gives_unit_vectors():
+    n = 9
+    S = np.asfortranarray(np.diag(np.arange(1.0, n + 1)))
+    T = np.asfortranarray(np.eye(n))
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0
+    assert np.array_equal(V, np.eye(n))
+    assert np.all(sc == 0)
+
+
+def test_residual_and_pair_structure():
+    for n, seed in ((256, pencilgen.config_seed(0)), (500, 12)):
+        p = pencilgen.make_pencil(n, seed)
+        st, V, sc, m = oracle.evc(p.S, p.T, nthreads=4)
+        assert st == 0 and np.isfinite(V).all()
+        st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+        kinds, pos = check.column_kinds(blk)
+        res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta)
+        assert res.max() <= 100 * n * check.U
+        # the conjugate vector solves the conjugate problem, and [x y] has rank 2
+        for c in np.flatnonzero(kinds == 1)[:20]:
+            z = V[:, c] - 1j * V[:, c + 1]
+            al = complex(a[pos[c]], -b[pos[c]])
+            r = beta[pos[c]] * (p.S @ z) - al * (p.T @ z)
+            assert np.abs(r).max() <= 100 * n * check.U * (np.abs(p.S).sum(1).max() + abs(al) * np.abs(p.T).sum(1).max())
+            sv = np.linalg.svd(V[:, c:c + 2], compute_uv=False)
+            assert sv[1] > 1e-8 * sv[0]
+
+
+def test_selection_matches_full_and_closes_pairs():
+    p = pencilgen.config_pencil(0, n=100)
+    st, Vfull, scfull, m = oracle.evc(p.S, p.T)
+    sel = np.zeros(p.n, dtype=np.int32)
+    pairs = np.flatnonzero(p.block == 1)
+    ones = np.flatnonzero(p.block == 0)
+    sel[ones[::3]] = 1
+    sel[pairs[::2] + 1] = 1                       # second row only: the pair is selected
+    st, Vs, scs, ms = oracle.evc(p.S, p.T, select=sel)
+    assert st == 0
+    kinds, pos = check.column_kinds(p.block, sel)
+    assert ms == len(kinds)
+    expect = []
+    for c in range(p.n):
+        if p.block[c] == 0 and sel[c]:
+            expect.append(c)
+        elif p.block[c] == 1 and (sel[c] or sel[c + 1]):
+            expect += [c, c + 1]
+    assert np.array_equal(Vs, Vfull[:, expect])
+    assert np.array_equal(scs, scfull[expect])
+
+
+def test_unnormalised_output_represents_same_vectors():
+    p = pencilgen.config_pencil(0, n=80)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    st, W, e, m = oracle.evc(p.S, p.T, normalise=False)
+    kinds, _ = check.column_kinds(p.block)
+    err, _ = check.compare_normalised(V, W, kinds)
+    assert err < 1e-15
+    # scale of the normalised output is the growth exponent of the largest entry
+    for c, k in enumerate(kinds):
+        if k == 0:
+            assert sc[c] == e[c] + math.frexp(np.abs(W[:, c]).max())[1] - 1
+
+
+# --------------------------------------------------------------- stress
+
+def test_stress_plain_overflows_robust_finite():
+    p = pencilgen.make_pencil(600, pencilgen.config_seed(2), stress=True)
+    st, V, sc, m = oracle.evc(p.S, p.T, nthreads=4)
+    assert st == 0
+    assert np.isfinite(V).all()
+    assert sc.max() > 1023                      # growth beyond the binary64 range is represented
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta)
+    assert res.max() <= 100 * p.n * check.U
+    stp, Vp, scp, mp = oracle.evc(p.S, p.T, plain=True, normalise=False)
+    assert not np.isfinite(Vp).all()
+
+
+def test_infinite_eigenvalue_vector():
+    ep = pencilgen.exact_pencil(7, 44, two_by_two=False)
+    r = 3
+    ep.T[r][r] = Fraction(0)
+    ep.S[r][r] = Fraction(5, 4)
+    S, T = ep.as_float()
+    Vx, dims = exact.exact_eigenvectors(ep)
+    assert all(d == 1 for d in dims)
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0
+    kinds, _ = check.column_kinds(ep.block)
+    err, _ = check.compare_normalised(_real_columns(Vx, kinds), V, kinds)
+    assert err < 1e-13
+    # the vector of the infinite eigenvalue lies in the kernel of T
+    assert np.abs(T @ V[:, r]).max() < 1e-14
