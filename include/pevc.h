@@ -1,0 +1,153 @@
+/*
+ * pevc.h -- C ABI of the GB300 library for robust generalized eigenvectors
+ * of a real pencil (S, T) in generalized real Schur form.
+ *
+ * Method: Kjelgaard Mikkelsen & Myllykoski, "Parallel Robust Computation of
+ * Generalized Eigenvectors of Matrix Pencils" (PPAM 2019).  The library solves
+ * the homogeneous matrix equation S V D - T V B = 0 (Section 2.2) for all or
+ * selected eigenvectors with the blocked algorithm of Section 3 (Algorithm 1),
+ * made robust against overflow with augmented tiles -- a tile plus one
+ * power-of-two scale per eigenvector column -- and scale consolidation before
+ * every update (Section 4, Algorithms 2 and 3).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are binary64, column-major, with a leading dimension ld >= n.
+ *   - S is upper quasi-triangular with 1x1 and 2x2 diagonal blocks (a 2x2
+ *     block starts at row i when S[i+1,i] != 0); T is upper triangular and
+ *     each 2x2 diagonal block of T is diagonal with positive entries (the
+ *     standardised real Schur form of Section 2).  Entries strictly below the
+ *     first subdiagonal of S and below the diagonal of T are never read.
+ *   - Eigenvalues follow Section 2: (alpha, beta), alpha = a + i b, beta >= 0;
+ *     a 1x1 block gives (S_cc, T_cc), a 2x2 block gives beta = 1 and the root
+ *     a + i b, b > 0, of det(S_jj - lambda T_jj) = 0.  beta = 0 is an infinite
+ *     eigenvalue; alpha = beta = 0 is the indefinite case (an error when
+ *     selected).
+ *   - Output columns: a real eigenvalue gives one column, a complex pair two
+ *     consecutive columns (Re z, Im z) of the eigenvector z of a + i b with
+ *     b > 0 (the Lemma of Section 2.1).  Without a selection column c belongs
+ *     to diagonal position c and V is upper quasi-triangular; with a selection
+ *     the selected eigenvectors are packed in diagonal order.  Selecting
+ *     either row of a 2x2 block selects the pair (Section 5: the subset is
+ *     closed under complex conjugation).  Rows below an eigenvector's block
+ *     are written as zero.
+ *   - Normalisation (default): every vector is divided by its entry of
+ *     largest modulus (first index on ties), so that entry is exactly 1.
+ *     scale_out[c] is then the binary exponent of that entry's magnitude
+ *     relative to a tip of unit largest modulus, i.e. log2 of the growth.
+ *     With PEVC_NO_NORMALISE the columns are returned consolidated to one
+ *     power of two per column: the eigenvector is 2^scale_out[c] * V[:,c]
+ *     (the augmented representation of Section 4 with alpha = 2^-scale).
+ *   - Status: 0 success; -i means argument i is invalid (LAPACK INFO style,
+ *     counting the plan as argument 1); positive values are the PEVC_ERR_*
+ *     codes below.  On error V_out is unspecified.  No entry point aborts or
+ *     traps; device-side conditions are reported through the status.
+ */
+#ifndef PEVC_H
+#define PEVC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pevc_plan_s *pevc_plan_t;
+
+/* Arithmetic of the bulk updates (kernel 2 of Section 3). */
+#define PEVC_FP64 0          /* FP64 tensor-core updates (DMMA)                      */
+#define PEVC_SPLIT_BF16X3 1  /* BF16 x3 slice products + FP64 residual correction   */
+#define PEVC_SPLIT_FP8X4 2   /* FP8 E4M3 x4 slice products + FP64 residual correction */
+
+/* Plan / solve flags. */
+#define PEVC_NO_NORMALISE 1u   /* return consolidated columns and exponents      */
+#define PEVC_NO_CORRECTION 2u  /* split precisions: skip the correction sweep    */
+
+/* Status codes. */
+#define PEVC_SUCCESS 0
+#define PEVC_ERR_NOT_SCHUR 1    /* 2x2 block with real eigenvalues, adjacent 2x2 blocks,
+                                   or a 2x2 block of T that is not diagonal and positive */
+#define PEVC_ERR_NONFINITE 2    /* Inf or NaN among the entries of S or T that are read */
+#define PEVC_ERR_INDEFINITE 3   /* alpha = beta = 0 for a selected eigenvalue (Section 2) */
+#define PEVC_ERR_TIMEOUT 4      /* a bounded device wait ran out                         */
+#define PEVC_ERR_CUDA 5         /* a CUDA runtime call failed                            */
+#define PEVC_ERR_NOMEM 6        /* device or pinned host allocation failed               */
+#define PEVC_ERR_UNSUPPORTED 7  /* a requested feature is not available in this build    */
+
+/*
+ * pevc_plan -- create a plan that owns all device workspace for pencils of
+ * order up to n_max (and batches of up to batch_max pencils).
+ *   plan       out: the new plan (NULL on failure)
+ *   n_max      largest order a solve will use, >= 0
+ *   batch_max  largest batch count for pevc_solve_batched, >= 1
+ *   prec       PEVC_FP64, PEVC_SPLIT_BF16X3 or PEVC_SPLIT_FP8X4
+ *   tile       tile order (Section 5.1: tiles of S, T and V are conformal; a
+ *              tile boundary never splits a 2x2 block); 0 lets the autotuner
+ *              choose from n_max and prec; otherwise 32, 64, 96 or 128
+ *   flags      PEVC_NO_NORMALISE | PEVC_NO_CORRECTION
+ *   stream     cudaStream_t (as void*) on which every solve is ordered; NULL
+ *              is the legacy default stream
+ * The plan allocates with cudaMalloc; pevc_solve itself allocates nothing.
+ * Returns 0, -i, PEVC_ERR_NOMEM or PEVC_ERR_CUDA.
+ */
+int pevc_plan(pevc_plan_t *plan, int n_max, int batch_max, int prec, int tile,
+              unsigned flags, void *stream);
+
+/*
+ * pevc_solve -- all (select == NULL) or the selected eigenvectors of (S, T).
+ *   plan       a plan with n <= n_max
+ *   S, lds     device, n x n, read only (never modified; pre-scaling is done
+ *              on the eigenvalue pairs, which leaves the eigenvectors fixed)
+ *   T, ldt     device, n x n, read only
+ *   n          order, 0 <= n <= n_max
+ *   select     device int32[n] or NULL; nonzero selects an eigenvalue
+ *   V_out, ldv device, n x m_out, written (caller-owned; n x n suffices)
+ *   scale_out  device int32[m_out], written
+ *   m_out      host: number of columns written
+ * Stream-ordered on the plan's stream; the call reads the block structure
+ * back to the host once and synchronises on return (m_out and the status are
+ * final when it returns).  Deterministic: equal inputs give bitwise-equal
+ * outputs.
+ */
+int pevc_solve(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
+               const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
+
+/*
+ * pevc_solve_batched -- count independent pencils of (possibly) different
+ * orders, each as in pevc_solve.  Pointer arguments are host arrays of
+ * length count holding device pointers (select[i] may be NULL, select itself
+ * may be NULL for "all"); lds, ldt, n, ldv are host int arrays.  m_out and
+ * status are host int arrays of length count: status[i] is pencil i's own
+ * status, so one bad pencil does not stop the others.  Every n[i] must be
+ * <= n_max and count <= batch_max.  Returns 0 when the arguments are valid
+ * and every pencil was processed (check status[]), else -i or a PEVC_ERR_*.
+ */
+int pevc_solve_batched(pevc_plan_t plan, int count,
+                       const double *const *S, const int *lds,
+                       const double *const *T, const int *ldt, const int *n,
+                       const int32_t *const *select, double *const *V_out, const int *ldv,
+                       int32_t *const *scale_out, int *m_out, int *status);
+
+/* pevc_destroy -- free a plan and its workspace (NULL is accepted). */
+int pevc_destroy(pevc_plan_t plan);
+
+/* pevc_strerror -- static text for a status value. */
+const char *pevc_strerror(int code);
+
+/*
+ * pevc_plan_info -- the plan's resolved settings (after autotuning).
+ *   info  host int[8]: {tile, prec, n_max, batch_max, flags, device SM count,
+ *                       slices per operand (0 for FP64), correction sweeps}
+ */
+int pevc_plan_info(pevc_plan_t plan, int *info);
+
+/*
+ * pevc_last_stats -- host double[8] timing/work figures of the last solve on
+ * this plan: {total ms (device, CUDA events), prepass ms, dag ms, correction
+ * ms, postpass ms, tiles M, update launches, diag launches}.
+ */
+int pevc_last_stats(pevc_plan_t plan, double *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEVC_H */

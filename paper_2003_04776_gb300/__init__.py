@@ -1,0 +1,197 @@
+"""Python binding of libpevc (robust generalized eigenvectors on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libpevc.so``; PyTorch provides device memory and streams.  The
+functions ``pevc_plan``, ``pevc_solve``, ``pevc_solve_batched``,
+``pevc_destroy``, ``pevc_strerror``, ``pevc_plan_info`` and
+``pevc_last_stats`` mirror the C ABI of ``include/pevc.h`` one to one (raw
+pointers and sizes); ``Plan`` wraps them for torch tensors.
+
+There is no CPU fallback: importing this module fails loudly when the
+compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpevc.so")
+
+FP64 = 0
+SPLIT_BF16X3 = 1
+SPLIT_FP8X4 = 2
+PRECISIONS = {"fp64": FP64, "bf16x3": SPLIT_BF16X3, "fp8x4": SPLIT_FP8X4}
+
+NO_NORMALISE = 1
+NO_CORRECTION = 2
+
+SUCCESS = 0
+ERR_NOT_SCHUR = 1
+ERR_NONFINITE = 2
+ERR_INDEFINITE = 3
+ERR_TIMEOUT = 4
+ERR_CUDA = 5
+ERR_NOMEM = 6
+ERR_UNSUPPORTED = 7
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpevc.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python paper_2003_04776_gb300/build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _i, _u = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+_lib.pevc_plan.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _i, _u, _vp]
+_lib.pevc_plan.restype = _i
+_lib.pevc_solve.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
+_lib.pevc_solve.restype = _i
+_lib.pevc_solve_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pevc_solve_batched.restype = _i
+_lib.pevc_destroy.argtypes = [_vp]
+_lib.pevc_destroy.restype = _i
+_lib.pevc_strerror.argtypes = [_i]
+_lib.pevc_strerror.restype = ctypes.c_char_p
+_lib.pevc_plan_info.argtypes = [_vp, _vp]
+_lib.pevc_plan_info.restype = _i
+_lib.pevc_last_stats.argtypes = [_vp, _vp]
+_lib.pevc_last_stats.restype = _i
+
+EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
+           "pevc_plan_info", "pevc_last_stats")
+
+
+# ----------------------------------------------------------- raw C ABI names
+
+def pevc_plan(n_max: int, batch_max: int = 1, prec: int = FP64, tile: int = 0, flags: int = 0,
+              stream: int = 0):
+    """Returns (status, plan handle)."""
+    h = _vp()
+    st = _lib.pevc_plan(ctypes.byref(h), int(n_max), int(batch_max), int(prec), int(tile),
+                        int(flags), _vp(stream) if stream else None)
+    return st, h
+
+
+def pevc_solve(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, V: int, ldv: int,
+               scale: int):
+    """Raw pointers (device addresses as ints).  Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None,
+                         _vp(V), ldv, _vp(scale), ctypes.byref(m))
+    return st, m.value
+
+
+def pevc_solve_batched(plan, count, S, lds, T, ldt, n, select, V, ldv, scale):
+    """Lists of device addresses / ints.  Returns (status, m_out list, status list)."""
+    P = ctypes.c_void_p * max(count, 1)
+    I = ctypes.c_int * max(count, 1)
+    sel = None if select is None else P(*[_vp(x) if x else None for x in select])
+    m_out = I()
+    stat = I()
+    st = _lib.pevc_solve_batched(plan, count, P(*[_vp(x) for x in S]), I(*lds), P(*[_vp(x) for x in T]),
+                                 I(*ldt), I(*n), sel, P(*[_vp(x) for x in V]), I(*ldv),
+                                 P(*[_vp(x) for x in scale]), m_out, stat)
+    return st, list(m_out)[:count], list(stat)[:count]
+
+
+def pevc_destroy(plan) -> int:
+    return _lib.pevc_destroy(plan)
+
+
+def pevc_strerror(code: int) -> str:
+    return _lib.pevc_strerror(int(code)).decode()
+
+
+def pevc_plan_info(plan):
+    info = (ctypes.c_int * 8)()
+    st = _lib.pevc_plan_info(plan, info)
+    return st, list(info)
+
+
+def pevc_last_stats(plan):
+    stats = (ctypes.c_double * 8)()
+    st = _lib.pevc_last_stats(plan, stats)
+    return st, list(stats)
+
+
+# ------------------------------------------------------------ torch wrapper
+
+class PevcError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: status {code}: {pevc_strerror(code)}")
+
+
+def to_device_colmajor(A, device="cuda"):
+    """Column-major float64 copy of A on the device (a torch tensor whose
+    storage is A in column-major order, i.e. a row-major A^T)."""
+    import torch
+    if isinstance(A, np.ndarray):
+        t = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64).T))
+        return t.to(device)
+    if A.dtype != torch.float64:
+        A = A.double()
+    return A.t().contiguous().to(device)
+
+
+class Plan:
+    """A plan (device workspace for order <= n_max) bound to a torch stream."""
+
+    def __init__(self, n_max: int, prec="fp64", tile: int = 0, batch_max: int = 1,
+                 normalise: bool = True, correction: bool = True, stream=None):
+        import torch
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.flags = (0 if normalise else NO_NORMALISE) | (0 if correction else NO_CORRECTION)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = pevc_plan(n_max, batch_max, self.prec, tile, self.flags, self.stream.cuda_stream)
+        if st:
+            raise PevcError(st, "pevc_plan")
+        self.h = h
+        self.n_max = n_max
+
+    def close(self):
+        if getattr(self, "h", None):
+            pevc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return pevc_plan_info(self.h)[1]
+
+    @property
+    def stats(self):
+        return pevc_last_stats(self.h)[1]
+
+    def solve_colmajor(self, St, Tt, n, V, scale, select=None, lds=None, ldt=None, ldv=None):
+        """Device tensors already in column-major storage (see to_device_colmajor)."""
+        st, m = pevc_solve(self.h, St.data_ptr(), lds or max(n, 1), Tt.data_ptr(), ldt or max(n, 1), n,
+                           select.data_ptr() if select is not None else 0, V.data_ptr(),
+                           ldv or max(n, 1), scale.data_ptr())
+        return st, m
+
+    def solve(self, S, T, select=None, check: bool = True):
+        """Eigenvectors of (S, T) given as numpy arrays or torch tensors.
+
+        Returns (V as an n x m numpy array, scale int32[m], status)."""
+        import torch
+        n = int(S.shape[0])
+        St = to_device_colmajor(S)
+        Tt = to_device_colmajor(T)
+        V = torch.empty((max(n, 1), max(n, 1)), dtype=torch.float64, device="cuda")   # column-major storage
+        scale = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        sel = None
+        if select is not None:
+            sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
+        with torch.cuda.stream(self.stream):
+            st, m = self.solve_colmajor(St, Tt, n, V, scale, sel)
+        if check and st:
+            raise PevcError(st, "pevc_solve")
+        Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0))
+        return np.asfortranarray(Vh[:n, :m]), scale[:m].cpu().numpy(), st

@@ -1,0 +1,437 @@
+// api.cu -- the C ABI (include/pevc.h): plans, argument checks, the host-side
+// structure analysis (1x1 / 2x2 blocks, tile partition, output columns) and
+// the stage loop that walks the task graph of Algorithm 1 bottom-up.
+//
+// Task graph (Section 3, Algorithm 1; Section 5.3): for every block column j
+// a tip task on tile (j, j), then for i = j-1 .. 0 the updates of all tiles
+// above from tile (i+1, j) and the solve of tile (i, j).  The graph is the
+// disjoint union of one sub-graph per block column; here all block columns
+// advance together, one block row per stage from the bottom up:
+//   stage i:  solve tiles (i, j), j > i   ->   update tiles (k, j), k < i <= j
+// so every [S_ki T_ki] tile row panel is read once per stage for all columns.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "split.cuh"
+
+using namespace pevc;
+
+struct pevc_plan_s {
+  int dev = 0, nsm = 0;
+  int n_max = 0, batch_max = 1, prec = PEVC_FP64, tb = 64;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  int Mmax = 0;
+  // device workspace
+  double* Y = nullptr;
+  int* ex = nullptr;
+  double* nrm = nullptr;
+  int* EA = nullptr;
+  double* tcS = nullptr;
+  double* tcT = nullptr;
+  double* gmax = nullptr;
+  double* ca = nullptr;
+  double* cb = nullptr;
+  double* cbeta = nullptr;
+  signed char* blk = nullptr;
+  int* toff = nullptr;
+  int* cstart = nullptr;
+  int* ccol = nullptr;
+  signed char* kind = nullptr;
+  unsigned* status = nullptr;
+  double* subd = nullptr;
+  // pinned host staging
+  double* h_subd = nullptr;
+  int32_t* h_sel = nullptr;
+  signed char* h_blk = nullptr;
+  int* h_toff = nullptr;
+  int* h_cstart = nullptr;
+  int* h_ccol = nullptr;
+  signed char* h_kind = nullptr;
+  unsigned* h_status = nullptr;
+  cudaEvent_t ev[6] = {};
+  double stats[8] = {};
+  SplitWorkspace split;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return PEVC_ERR_NOMEM;
+  return PEVC_ERR_CUDA;
+}
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t _e = (call);                    \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+int status_from_bits(unsigned bits) {
+  if (bits & kStNonfinite) return PEVC_ERR_NONFINITE;
+  if (bits & kStNotSchur) return PEVC_ERR_NOT_SCHUR;
+  if (bits & kStIndefinite) return PEVC_ERR_INDEFINITE;
+  if (bits & kStTimeout) return PEVC_ERR_TIMEOUT;
+  return PEVC_SUCCESS;
+}
+
+// Autotuned tile order: small pencils want small tiles (enough tiles to fill
+// the GPU, short diagonal solves), large ones the largest tile (fewer stages,
+// larger updates).
+int choose_tile(int n_max, int prec) {
+  (void)prec;
+  if (n_max <= 256) return 32;
+  if (n_max <= 1024) return 64;
+  return 128;
+}
+
+template <typename Tp>
+int dalloc(Tp** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(Tp));
+  return e == cudaSuccess ? 0 : cuda_fail(e);
+}
+
+template <typename Tp>
+int halloc(Tp** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocHost((void**)p, count * sizeof(Tp));
+  return e == cudaSuccess ? 0 : cuda_fail(e);
+}
+
+void free_plan(pevc_plan_t p) {
+  if (!p) return;
+  void* dev[] = {p->Y, p->ex, p->nrm, p->EA, p->tcS, p->tcT, p->gmax, p->ca, p->cb, p->cbeta,
+                 p->blk, p->toff, p->cstart, p->ccol, p->kind, p->status, p->subd};
+  for (void* d : dev)
+    if (d) cudaFree(d);
+  void* host[] = {p->h_subd, p->h_sel, p->h_blk, p->h_toff, p->h_cstart, p->h_ccol, p->h_kind, p->h_status};
+  for (void* h : host)
+    if (h) cudaFreeHost(h);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  split_free(p->split);
+  delete p;
+}
+
+struct Structure {
+  int M = 0, m = 0;
+};
+
+// Host-side structure analysis: block pattern from the subdiagonal, tile
+// partition (Section 5.1: tiles of order tb, moved down by one row where a
+// boundary would split a 2x2 block), and the output columns grouped by the
+// row tile of their block (the column partition conforms to the row one).
+int analyse(pevc_plan_t p, int n, bool has_sel, Structure& st) {
+  for (int i = 0; i + 1 < n; ++i)
+    if (!std::isfinite(p->h_subd[i])) return PEVC_ERR_NONFINITE;
+  for (int i = 0; i < n; ++i) p->h_blk[i] = 0;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (p->h_subd[i] != 0.0) {
+      if (p->h_blk[i] != 0) return PEVC_ERR_NOT_SCHUR;
+      p->h_blk[i] = 1;
+      p->h_blk[i + 1] = 2;
+    }
+  }
+  int M = 0;
+  p->h_toff[0] = 0;
+  int off = 0;
+  while (off < n) {
+    int nxt = std::min(off + p->tb, n);
+    if (nxt < n && p->h_blk[nxt] == 2) --nxt;
+    if (M + 1 >= p->Mmax) return PEVC_ERR_CUDA;   // cannot happen: Mmax bounds ceil(n/(tb-1))
+    p->h_toff[++M] = nxt;
+    off = nxt;
+  }
+  int m = 0, tile = 0;
+  for (int j = 0; j <= M; ++j) p->h_cstart[j] = 0;
+  for (int c = 0; c < n; ++c) {
+    if (p->h_blk[c] == 2) continue;
+    const int sz = (p->h_blk[c] == 1) ? 2 : 1;
+    while (c >= p->h_toff[tile + 1]) {
+      ++tile;
+      p->h_cstart[tile] = m;
+    }
+    bool sel = !has_sel || p->h_sel[c] != 0 || (sz == 2 && p->h_sel[c + 1] != 0);
+    if (!sel) continue;
+    for (int u = 0; u < sz; ++u) {
+      p->h_ccol[m] = c + u;
+      p->h_kind[m] = (signed char)(sz == 1 ? 0 : 1 + u);
+      ++m;
+    }
+  }
+  while (tile < M) {
+    ++tile;
+    p->h_cstart[tile] = m;
+  }
+  st.M = M;
+  st.m = m;
+  return 0;
+}
+
+Problem make_problem(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n,
+                     const Structure& st) {
+  Problem P;
+  P.S = S;
+  P.T = T;
+  P.lds = lds;
+  P.ldt = ldt;
+  P.n = n;
+  P.blk = p->blk;
+  P.toff = p->toff;
+  P.cstart = p->cstart;
+  P.ccol = p->ccol;
+  P.kind = p->kind;
+  P.M = st.M;
+  P.m = st.m;
+  P.tb = p->tb;
+  P.ca = p->ca;
+  P.cb = p->cb;
+  P.cbeta = p->cbeta;
+  P.EA = p->EA;
+  P.tcS = p->tcS;
+  P.tcT = p->tcT;
+  P.gmax = p->gmax;
+  P.Y = p->Y;
+  P.ex = p->ex;
+  P.nrm = p->nrm;
+  P.status = p->status;
+  return P;
+}
+
+int read_status(pevc_plan_t p, unsigned* bits) {
+  CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  *bits = *p->h_status;
+  return 0;
+}
+
+int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n,
+              const int32_t* sel, double* V, int ldv, int32_t* scale, int* m_out) {
+  cudaStream_t s = p->stream;
+  *m_out = 0;
+  for (double& x : p->stats) x = 0.0;
+  if (n == 0) return 0;
+  CK(cudaEventRecord(p->ev[0], s));
+  // 1. block structure and selection to the host
+  CK(launch_gather_subdiag(S, lds, n, p->subd, s));
+  if (n > 1) CK(cudaMemcpyAsync(p->h_subd, p->subd, (size_t)(n - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (sel) CK(cudaMemcpyAsync(p->h_sel, sel, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  Structure st;
+  int rc = analyse(p, n, sel != nullptr, st);
+  if (rc) return rc;
+  *m_out = st.m;
+  // 2. structure to the device, pre-processing tasks
+  CK(cudaMemcpyAsync(p->blk, p->h_blk, (size_t)n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->toff, p->h_toff, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->cstart, p->h_cstart, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (st.m > 0) {
+    CK(cudaMemcpyAsync(p->ccol, p->h_ccol, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->kind, p->h_kind, (size_t)st.m, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(p->gmax, 0, sizeof(double), s));
+  Problem P = make_problem(p, S, lds, T, ldt, n, st);
+  CK(launch_prepass(P, s));
+  unsigned bits = 0;
+  if ((rc = read_status(p, &bits))) return rc;
+  if (bits) return status_from_bits(bits);
+  CK(cudaEventRecord(p->ev[1], s));
+  if (st.m == 0) {
+    CK(cudaEventRecord(p->ev[2], s));
+    CK(cudaEventRecord(p->ev[3], s));
+    CK(cudaEventRecord(p->ev[4], s));
+  } else {
+    CK(launch_init_state(P, s));
+    // 3. the task graph, bottom-up by block row
+    int nupd = 0, ndiag = 0;
+    if (p->prec == PEVC_FP64) {
+      CK(launch_diag(P, 0, true, s));
+      ++ndiag;
+      for (int i = st.M - 1; i >= 0; --i) {
+        if (i < st.M - 1) {
+          CK(launch_diag(P, i, false, s));
+          ++ndiag;
+        }
+        if (i > 0) {
+          CK(launch_update_f64(P, i, s));
+          ++nupd;
+        }
+      }
+      CK(cudaEventRecord(p->ev[2], s));
+      CK(cudaEventRecord(p->ev[3], s));
+    } else {
+      rc = split_solve(p->split, P, p->prec, (p->flags & PEVC_NO_CORRECTION) == 0, s, p->ev[2],
+                       p->ev[3], &nupd, &ndiag);
+      if (rc) return rc;
+    }
+    p->stats[6] = nupd;
+    p->stats[7] = ndiag;
+    // 4. post-processing: consistent scaling and normalisation
+    CK(launch_post(P, V, ldv, scale, (p->flags & PEVC_NO_NORMALISE) == 0, s));
+    CK(cudaEventRecord(p->ev[4], s));
+  }
+  if ((rc = read_status(p, &bits))) return rc;
+  float ms[4] = {0, 0, 0, 0};
+  cudaEventElapsedTime(&ms[0], p->ev[0], p->ev[4]);
+  cudaEventElapsedTime(&ms[1], p->ev[0], p->ev[1]);
+  cudaEventElapsedTime(&ms[2], p->ev[1], p->ev[2]);
+  cudaEventElapsedTime(&ms[3], p->ev[2], p->ev[3]);
+  p->stats[0] = ms[0];
+  p->stats[1] = ms[1];
+  p->stats[2] = ms[2];
+  p->stats[3] = ms[3];
+  float post = 0.0f;
+  cudaEventElapsedTime(&post, p->ev[3], p->ev[4]);
+  p->stats[4] = post;
+  p->stats[5] = st.M;
+  return status_from_bits(bits);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, unsigned flags,
+              void* stream) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (n_max < 0) return -2;
+  if (batch_max < 1) return -3;
+  if (prec != PEVC_FP64 && prec != PEVC_SPLIT_BF16X3 && prec != PEVC_SPLIT_FP8X4) return -4;
+  if (tile != 0 && tile != 32 && tile != 64 && tile != 96 && tile != 128) return -5;
+  if (flags & ~(PEVC_NO_NORMALISE | PEVC_NO_CORRECTION)) return -6;
+  pevc_plan_t p = new (std::nothrow) pevc_plan_s();
+  if (!p) return PEVC_ERR_NOMEM;
+  p->n_max = n_max;
+  p->batch_max = batch_max;
+  p->prec = prec;
+  p->flags = flags;
+  p->stream = (cudaStream_t)stream;
+  p->tb = tile ? tile : choose_tile(n_max, prec);
+  if (cudaGetDevice(&p->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess) {
+    delete p;
+    return PEVC_ERR_CUDA;
+  }
+  const int nm = std::max(n_max, 1);
+  p->Mmax = (nm + p->tb - 2) / (p->tb - 1) + 1;
+  const size_t M = (size_t)p->Mmax;
+  int rc = 0;
+  rc = rc ? rc : dalloc(&p->Y, M * (M + 1) / 2 * (size_t)p->tb * p->tb);
+  rc = rc ? rc : dalloc(&p->ex, M * nm);
+  rc = rc ? rc : dalloc(&p->nrm, M * nm);
+  rc = rc ? rc : dalloc(&p->EA, M * M);
+  rc = rc ? rc : dalloc(&p->tcS, nm);
+  rc = rc ? rc : dalloc(&p->tcT, nm);
+  rc = rc ? rc : dalloc(&p->gmax, 1);
+  rc = rc ? rc : dalloc(&p->ca, nm);
+  rc = rc ? rc : dalloc(&p->cb, nm);
+  rc = rc ? rc : dalloc(&p->cbeta, nm);
+  rc = rc ? rc : dalloc(&p->blk, nm);
+  rc = rc ? rc : dalloc(&p->toff, M + 1);
+  rc = rc ? rc : dalloc(&p->cstart, M + 1);
+  rc = rc ? rc : dalloc(&p->ccol, nm);
+  rc = rc ? rc : dalloc(&p->kind, nm);
+  rc = rc ? rc : dalloc(&p->status, 1);
+  rc = rc ? rc : dalloc(&p->subd, nm);
+  rc = rc ? rc : halloc(&p->h_subd, nm);
+  rc = rc ? rc : halloc(&p->h_sel, nm);
+  rc = rc ? rc : halloc(&p->h_blk, nm);
+  rc = rc ? rc : halloc(&p->h_toff, M + 1);
+  rc = rc ? rc : halloc(&p->h_cstart, M + 1);
+  rc = rc ? rc : halloc(&p->h_ccol, nm);
+  rc = rc ? rc : halloc(&p->h_kind, nm);
+  rc = rc ? rc : halloc(&p->h_status, 1);
+  for (auto& e : p->ev)
+    if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = PEVC_ERR_CUDA;
+  if (!rc && prec != PEVC_FP64) rc = split_alloc(p->split, n_max, p->tb, p->Mmax, prec);
+  if (rc) {
+    free_plan(p);
+    return rc;
+  }
+  *plan = p;
+  return 0;
+}
+
+int pevc_solve(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+               const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !V_out) return -8;
+  if (ldv < std::max(n, 1)) return -9;
+  if (n > 0 && !scale_out) return -10;
+  if (!m_out) return -11;
+  return solve_one(plan, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out);
+}
+
+int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, const int* lds,
+                       const double* const* T, const int* ldt, const int* n,
+                       const int32_t* const* select, double* const* V_out, const int* ldv,
+                       int32_t* const* scale_out, int* m_out, int* status) {
+  if (!plan) return -1;
+  if (count < 0 || count > plan->batch_max) return -2;
+  if (count > 0 && (!S || !lds || !T || !ldt || !n || !V_out || !ldv || !scale_out || !m_out || !status))
+    return -3;
+  for (int b = 0; b < count; ++b) {
+    status[b] = pevc_solve(plan, S[b], lds[b], T[b], ldt[b], n[b], select ? select[b] : nullptr,
+                           V_out[b], ldv[b], scale_out[b], &m_out[b]);
+    if (status[b] == PEVC_ERR_CUDA) return PEVC_ERR_CUDA;
+  }
+  return 0;
+}
+
+int pevc_destroy(pevc_plan_t plan) {
+  if (!plan) return 0;
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return 0;
+}
+
+const char* pevc_strerror(int code) {
+  switch (code) {
+    case PEVC_SUCCESS: return "success";
+    case PEVC_ERR_NOT_SCHUR: return "pencil is not in standardised real Schur form";
+    case PEVC_ERR_NONFINITE: return "Inf or NaN in the input";
+    case PEVC_ERR_INDEFINITE: return "indefinite eigenvalue (alpha = beta = 0) selected";
+    case PEVC_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PEVC_ERR_CUDA: return "CUDA runtime error";
+    case PEVC_ERR_NOMEM: return "out of memory";
+    case PEVC_ERR_UNSUPPORTED: return "unsupported feature";
+    default: return code < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+int pevc_plan_info(pevc_plan_t plan, int* info) {
+  if (!plan) return -1;
+  if (!info) return -2;
+  info[0] = plan->tb;
+  info[1] = plan->prec;
+  info[2] = plan->n_max;
+  info[3] = plan->batch_max;
+  info[4] = (int)plan->flags;
+  info[5] = plan->nsm;
+  info[6] = plan->prec == PEVC_FP64 ? 0 : (plan->prec == PEVC_SPLIT_BF16X3 ? 3 : 4);
+  info[7] = (plan->prec != PEVC_FP64 && !(plan->flags & PEVC_NO_CORRECTION)) ? 1 : 0;
+  return 0;
+}
+
+int pevc_last_stats(pevc_plan_t plan, double* stats) {
+  if (!plan) return -1;
+  if (!stats) return -2;
+  for (int q = 0; q < 8; ++q) stats[q] = plan->stats[q];
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// common.cuh -- internal definitions of the pevc CUDA library (sm_103a).
+//
+// Robustness arithmetic of Section 4 of Kjelgaard Mikkelsen & Myllykoski
+// (PPAM 2019): every stored tile column is an augmented column <alpha, x>
+// with alpha = 2^-e kept as a signed 32-bit exponent e (Section 5), so the
+// represented value is 2^e * x.  Omega = 2^1022.  All scale factors are
+// powers of two, so applying them is exact up to underflow.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pevc.h"
+
+namespace pevc {
+
+constexpr int kOmegaExp = 1022;        // Omega = 2^1022
+constexpr int kPrescaleExp = 1000;     // |beta| max|S|, (|a|+|b|) max|T| <= 2^1000
+constexpr int kExpZero = -(1 << 29);   // exponent of a tile column that is still zero
+constexpr int kMaxTile = 128;          // largest tile order
+
+// Device status bits (reduced to a PEVC_ERR_* value on the host).
+constexpr unsigned kStNotSchur = 1u;
+constexpr unsigned kStNonfinite = 2u;
+constexpr unsigned kStIndefinite = 4u;
+constexpr unsigned kStTimeout = 8u;
+
+// Smallest E with v < 2^E for finite v > 0 (ilogb is exact, also for
+// subnormals).
+__device__ __forceinline__ int exp_above(double v) { return ilogb(v) + 1; }
+
+// ProtectUpdate (Section 4, property 2) on exponent bounds: y, t, x >= 0 and
+// finite.  k >= 0 with 2^-k (y + t x) <= Omega.
+__device__ __forceinline__ int protect_update(double y, double t, double x) {
+  int top = INT32_MIN / 4;
+  if (y > 0.0) top = exp_above(y);
+  if (t > 0.0 && x > 0.0) top = max(top, exp_above(t) + exp_above(x));
+  int k = top + 1 - kOmegaExp;
+  return k > 0 ? k : 0;
+}
+
+// Same bound when t is already given as an exponent bound (t < 2^et).
+__device__ __forceinline__ int protect_update_e(int ey_or_min, int etx_or_min) {
+  int top = max(ey_or_min, etx_or_min);
+  int k = top + 1 - kOmegaExp;
+  return k > 0 ? k : 0;
+}
+
+// ProtectDivision (Section 4, property 1) for the numerator bound 2^sh * b
+// and denominator magnitude t > 0: k >= 0 with 2^-k 2^sh b <= t Omega.
+__device__ __forceinline__ int protect_division(double b, int sh, double t) {
+  if (!(b > 0.0)) return 0;
+  int k = exp_above(b) + sh - ilogb(t) - kOmegaExp;   // t >= 2^ilogb(t)
+  return k > 0 ? k : 0;
+}
+
+// Complex quotient (pr + i pi) = (ar + i ai) / (br + i bi): Smith (1962),
+// with Baudin & Smith's (2012) regrouping when the divisor-part ratio
+// underflows to zero.
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
+                                     double& pr, double& pi) {
+  if (fabs(br) >= fabs(bi)) {
+    const double rho = bi / br;
+    const double den = br + bi * rho;
+    if (rho != 0.0) {
+      pr = (ar + ai * rho) / den;
+      pi = (ai - ar * rho) / den;
+    } else {
+      pr = (ar + bi * (ai / br)) / den;
+      pi = (ai - bi * (ar / br)) / den;
+    }
+  } else {
+    const double rho = br / bi;
+    const double den = bi + br * rho;
+    if (rho != 0.0) {
+      pr = (ar * rho + ai) / den;
+      pi = (ai * rho - ar) / den;
+    } else {
+      pr = (br * (ar / bi) + ai) / den;
+      pi = (br * (ai / bi) - ar) / den;
+    }
+  }
+}
+
+__device__ __forceinline__ double cmag(double re, double im) { return fabs(re) + fabs(im); }
+
+// Largest of non-negative doubles via their bit patterns (monotone for x >= 0).
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
+}
+
+// Packed index of tile (k, j), k <= j, in the upper triangle of tiles.
+__host__ __device__ __forceinline__ long long tri_index(int k, int j) {
+  return (long long)j * (j + 1) / 2 + k;
+}
+
+// Everything a kernel needs to know about one pencil and its workspace.
+struct Problem {
+  // inputs
+  const double* S;
+  const double* T;
+  int lds, ldt, n;
+  // structure (device copies of host-computed arrays)
+  const signed char* blk;   // [n]  0 = 1x1, 1 = first row of 2x2, 2 = second row
+  const int* toff;          // [M+1] row offsets of the tiles
+  const int* cstart;        // [M+1] first output column of each column tile
+  const int* ccol;          // [m]   diagonal position of each output column
+  const signed char* kind;  // [m]   0 real, 1 Re of a pair, 2 Im of a pair
+  int M, m, tb;             // tile count, output columns, tile storage order
+  // eigenvalues per output column (pre-scaled)
+  double* ca;
+  double* cb;
+  double* cbeta;
+  // norms
+  int* EA;                  // [M*M] ||[S_kl T_kl]||_inf < 2^EA[k*M+l], k < l
+  double* tcS;              // [n] max |S_rc| over rows r of c's tile above c's block
+  double* tcT;              // [n]
+  double* gmax;             // [1] max |entry| of S, T over what is read
+  // augmented tiles
+  double* Y;                // tiles (k <= j), tb x tb column-major each
+  int* ex;                  // [M*m] exponent of column q in row tile k
+  double* nrm;              // [M*m] max |stored| of column q in row tile k
+  unsigned* status;         // device status bits
+};
+
+__device__ __forceinline__ double* tile_ptr(const Problem& P, int k, int j) {
+  return P.Y + tri_index(k, j) * (long long)P.tb * P.tb;
+}
+
+// ---- launchers (one translation unit each) ----
+cudaError_t launch_prepass(const Problem& P, cudaStream_t s);
+cudaError_t launch_init_state(const Problem& P, cudaStream_t s);
+cudaError_t launch_diag(const Problem& P, int i, bool tips, cudaStream_t s);
+cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s);
+cudaError_t launch_post(const Problem& P, double* V, int ldv, int32_t* scale, bool normalise,
+                        cudaStream_t s);
+cudaError_t launch_gather_subdiag(const double* S, int lds, int n, double* out, cudaStream_t s);
+
+}  // namespace pevc
