@@ -14,8 +14,16 @@ def _declared(header):
     return sorted(set(re.findall(r"\b(pevc_[a-z_]+)\s*\(", text)))
 
 
+def _builder():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("pevc_build", os.path.join(ROOT, "paper_2003_04776_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def test_library_builds_and_exports_declared_symbols():
-    from paper_2003_04776_gb300 import build as b
+    b = _builder()
     lib_path = b.build()
     names = _declared("pevc.h")
     assert {"pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror"} <= set(names)
@@ -36,7 +44,7 @@ def test_python_binding_mirrors_abi_names():
 
 
 def test_library_targets_sm103a_only():
-    from paper_2003_04776_gb300 import build as b
+    b = _builder()
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -106,11 +106,12 @@ def test_fp64_unnormalised_representation(pevc_lib):
         d = int(sc[c]) - int(sco[c])
         a = np.ldexp(V[:, c], d)
         assert np.allclose(a, Vo[:, c], rtol=0, atol=1e-10 * np.abs(Vo[:, c]).max())
-    # consolidated: the largest stored magnitude of each vector lies in [1, 2)
+    # consolidated to the exponent of the largest stored part: that part lies in
+    # [1, 2), so a complex entry's modulus lies in [1, 2*sqrt(2))
     vecs, cols = check.as_complex(V, kinds)
-    for z in vecs:
-        mx = np.abs(z).max()
-        assert 0.5 <= mx < 2.0 + 1e-12
+    for z, c in zip(vecs, cols):
+        mx = max(np.abs(z.real).max(), np.abs(z.imag).max())
+        assert 1.0 <= mx < 2.0
 
 
 def test_fp64_deterministic(pevc_lib):
