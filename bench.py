@@ -1,0 +1,329 @@
+"""Benchmark: all-eigenvector solve of a seeded synthetic Schur pencil.
+
+One step = one pevc_solve of the whole hot path (pre-processing, tips,
+diagonal solves, updates, correction if any, post-processing) on an
+n x n pencil that is already resident in HBM.  The default workload is the
+n = 20000 pencil (2x2 blocks on ~50 % of the diagonal, N(0,1) off-diagonal
+entries) with the split-BF16 path; ``--prec fp64`` measures the FP64 path.
+
+Metric: effective GFLOP/s = F / time with F = sum over eigenvectors of 2 c^2
+~ 2 n^3 / 3 (the FP64-equivalent work of the substitution); ms per solve and
+eigenvectors/s are reported beside it.  Inputs (S, T: 2 x 3.2 GB at
+n = 20000) are far larger than the 129 MB L2, so no flush is needed.
+
+Under torchrun every rank solves its own pencil on its own GPU (the solve
+does not shard: replicas, weak scaling); value = total work / max time.
+``--impl reference`` times the FP64 CPU oracle (test infrastructure, the
+reference arm of this benchmark) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "all-eigenvector solve time & GFLOP/s at n=20000, split-BF16 vs FP64 at resid<=100nu"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def flops_all(n: int) -> float:
+    c = np.arange(1, n + 1, dtype=np.float64)
+    return float((2.0 * c * c).sum())
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_oracle_sample(pencil, budget_s: float, threads: int):
+    """Time the oracle on a stratified sample of eigenvectors; extrapolate to
+    all of them with the sum-of-c^2 work weights.  Returns (GFLOP/s, info)."""
+    import oracle
+    n = pencil.n
+    starts = np.flatnonzero(pencil.block != 2)
+    # stratified over the diagonal, largest vectors included
+    picks = []
+    spent = 0.0
+    work = 0.0
+    order = np.linspace(len(starts) - 1, 0, num=min(len(starts), 64)).astype(int)
+    for idx in order:
+        c = int(starts[idx])
+        sel = np.zeros(n, dtype=np.int32)
+        sel[c] = 1
+        t0 = time.perf_counter()
+        st, V, sc, m = oracle.evc(pencil.S, pencil.T, select=sel, nthreads=1)
+        dt = time.perf_counter() - t0
+        sz = 2 if pencil.block[c] == 1 else 1
+        picks.append(c)
+        spent += dt
+        work += sum(2.0 * (cc + 1) ** 2 for cc in range(c, c + sz))
+        if spent > budget_s:
+            break
+    rate = work / spent / 1e9
+    if threads > 1:
+        rate *= 1.0  # single-threaded sample; cores reported as 1
+    return rate, {"columns": len(picks), "seconds": round(spent, 2), "work_flops": work}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import pencilgen
+    n = args.n
+    p = pencilgen.config_pencil(3, n=n) if n == 20000 else pencilgen.make_pencil(n, pencilgen.config_seed(3))
+    budget = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        r, info = cpu_oracle_sample(p, budget, 1)
+        if s >= args.warmup:
+            rates.append(r)
+    val = float(np.median(rates))
+    F = flops_all(n)
+    ms = F / (val * 1e9) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"schur-pencil n={n}, all eigenvectors", "n": n, "prec": "oracle-fp64"},
+            "cpu_baseline": {"value": round(val, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{info['columns']} eigenvectors per step, {info['seconds']} s, "
+                                       "extrapolated by sum c^2"},
+            "e2e": {"value": round(val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pevc", choices=["pevc", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16x5", "fp8x4", "fp64"])
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check", action="store_true", help="residual of sampled columns after the run")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import pencilgen
+    import paper_2003_04776_gb300 as pevc
+
+    n = args.n
+    seed_pencil = pencilgen.config_pencil(3, index=rank, n=n)
+    stream = torch.cuda.current_stream()
+    St = pevc.to_device_colmajor(seed_pencil.S)
+    Tt = pevc.to_device_colmajor(seed_pencil.T)
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    scale = torch.empty(n, dtype=torch.int32, device="cuda")
+    plan = pevc.Plan(n, prec=args.prec, tile=args.tile, stream=stream)
+    plan.profile(True)
+
+    def step():
+        st, m = plan.solve_colmajor(St, Tt, n, V, scale)
+        if st:
+            raise pevc.PevcError(st, "pevc_solve")
+        return m
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prof = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            prof.append(plan.kernel_profile())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    F = flops_all(n)
+    value = F * world / (ms * 1e-3) / 1e9
+    info = plan.info
+    launches = int(np.mean([p["launches"] for p in prof]))
+
+    # dominant kernel roofline (CUDA events around each launch of the update kernel)
+    peaks, peak_src = load_peaks()
+    upd_ms = float(np.mean([p["update_ms"] for p in prof]))
+    upd_n = int(np.mean([p["update_launches"] for p in prof]))
+    upd_flops = float(np.mean([p["update_tensor_flops"] for p in prof]))
+    if args.prec == "fp64":
+        roof = {"bound": "alu", "unit": "TFLOP/s",
+                "achieved": upd_flops / max(upd_n, 1) / (upd_ms / max(upd_n, 1) * 1e-3) / 1e12 if upd_ms else None,
+                "peak": 1.02, "peak_source": "own DFMA/DMMA probe (FP64 tensor and ALU rates are equal on GB300)"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
+                "peak": pk, "peak_source": f"{peak_src} bf16 sustained"}
+    if roof["achieved"]:
+        roof["achieved"] = round(roof["achieved"], 2)
+        roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
+    roof["traffic"] = None
+    roof["kernel"] = "k_update_split" if args.prec != "fp64" else "k_update_f64"
+    roof["launches_per_step"] = upd_n
+    roof["avg_launch_ms"] = round(upd_ms / max(upd_n, 1), 4)
+    roof["share_of_step"] = round(upd_ms / ms, 3)
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-split+f64" if args.prec != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": f"schur-pencil n={n}, all eigenvectors, 2x2 blocks ~50%",
+                       "n": n, "prec": args.prec, "tile": info[0], "slices": info[6],
+                       "correction_sweeps": info[7], "parallelism": f"replicas{world}",
+                       "l2": "inputs 2 x %.1f GB >> 129 MB L2, no flush" % (n * n * 8 / 1e9)},
+            "eigvec_per_s": round(n * world / (ms * 1e-3), 1),
+            "gpu_launches": launches, "roofline": roof, "clocks": clk.summary()}
+
+    if not args.no_e2e:
+        # end to end through the public API: host S, T in pinned memory, result back to host
+        Sh = torch.from_numpy(np.ascontiguousarray(seed_pencil.S.T)).pin_memory()
+        Th = torch.from_numpy(np.ascontiguousarray(seed_pencil.T.T)).pin_memory()
+        Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        sch = torch.empty(n, dtype=torch.int32).pin_memory()
+        steps_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps_e2e):
+            St.copy_(Sh, non_blocking=True)
+            Tt.copy_(Th, non_blocking=True)
+            step()
+            Vh.copy_(V, non_blocking=True)
+            sch.copy_(scale, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / steps_e2e
+        line["e2e"] = {"value": round(F * world / (ems * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                       "ms_per_step": round(ems, 3),
+                       "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + n * 4}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        r, inf = cpu_oracle_sample(seed_pencil, 20.0, 1)
+        line["cpu_baseline"] = {"value": round(r, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{inf['columns']} eigenvectors of the same pencil, {inf['seconds']} s "
+                                          "single-threaded, extrapolated to all n by sum c^2"}
+    if args.check and rank == 0:
+        line["check"] = sampled_check(seed_pencil, V, n)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def sampled_check(p, V, n, count=8):
+    """Relative residual of a few sampled eigenvectors (host FP64)."""
+    import oracle
+    from oracle import check
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    cols = np.linspace(0, n - 1, count).astype(int)
+    cols = [c - 1 if kinds[c] == 2 else c for c in cols]
+    Vh = V[cols].cpu().numpy().T
+    nS = np.abs(p.S).sum(1).max()
+    nT = np.abs(p.T).sum(1).max()
+    worst = 0.0
+    for q, c in enumerate(cols):
+        if kinds[c] == 0:
+            z = Vh[:, q].astype(complex)
+        else:
+            z = Vh[:, q] + 1j * V[c + 1].cpu().numpy()
+        al = complex(a[pos[c]], b[pos[c]])
+        r = beta[pos[c]] * (p.S @ z) - al * (p.T @ z)
+        res = np.abs(r).max() / ((abs(beta[pos[c]]) * nS + abs(al) * nT) * np.abs(z).max())
+        worst = max(worst, res)
+    return {"sampled_columns": len(cols), "max_resid_over_nu": worst / (n * 2.0 ** -53)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -57,6 +57,7 @@ typedef struct pevc_plan_s *pevc_plan_t;
 #define PEVC_FP64 0          /* FP64 tensor-core updates (DMMA)                      */
 #define PEVC_SPLIT_BF16X3 1  /* BF16 x3 slice products + FP64 residual correction   */
 #define PEVC_SPLIT_FP8X4 2   /* FP8 E4M3 x4 slice products + FP64 residual correction */
+#define PEVC_SPLIT_BF16X5 3  /* BF16 x5 slice products in one pass (no correction)   */
 
 /* Plan / solve flags. */
 #define PEVC_NO_NORMALISE 1u   /* return consolidated columns and exponents      */
@@ -79,7 +80,7 @@ typedef struct pevc_plan_s *pevc_plan_t;
  *   plan       out: the new plan (NULL on failure)
  *   n_max      largest order a solve will use, >= 0
  *   batch_max  largest batch count for pevc_solve_batched, >= 1
- *   prec       PEVC_FP64, PEVC_SPLIT_BF16X3 or PEVC_SPLIT_FP8X4
+ *   prec       PEVC_FP64, PEVC_SPLIT_BF16X3, PEVC_SPLIT_FP8X4 or PEVC_SPLIT_BF16X5
  *   tile       tile order (Section 5.1: tiles of S, T and V are conformal; a
  *              tile boundary never splits a 2x2 block); 0 lets the autotuner
  *              choose from n_max and prec; otherwise 32, 64, 96 or 128
@@ -142,10 +143,25 @@ int pevc_plan_info(pevc_plan_t plan, int *info);
 
 /*
  * pevc_last_stats -- host double[8] timing/work figures of the last solve on
- * this plan: {total ms (device, CUDA events), prepass ms, dag ms, correction
- * ms, postpass ms, tiles M, update launches, diag launches}.
+ * this plan: {total ms (device, CUDA events), prepass ms, first-pass ms,
+ * correction ms, postpass ms, tiles M, kernel launches, 0}.
  */
 int pevc_last_stats(pevc_plan_t plan, double *stats);
+
+/*
+ * pevc_set_profile -- on != 0 records a CUDA event pair around every kernel
+ * launch of later solves on the plan's stream (a few microseconds per
+ * launch); 0 switches it off (the default).
+ */
+int pevc_set_profile(pevc_plan_t plan, int on);
+
+/*
+ * pevc_kernel_profile -- per-kernel-kind totals of the last profiled solve.
+ *   out  host double[12]: for kind = update, diagonal solve, slicing, other:
+ *        {milliseconds, launches, tensor-core flops} at out[3*kind .. 3*kind+2]
+ *        (flops count every slice product: 2 * rows * cols * K * products).
+ */
+int pevc_kernel_profile(pevc_plan_t plan, double *out);
 
 #ifdef __cplusplus
 }

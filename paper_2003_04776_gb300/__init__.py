@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libpevc.so")
 FP64 = 0
 SPLIT_BF16X3 = 1
 SPLIT_FP8X4 = 2
-PRECISIONS = {"fp64": FP64, "bf16x3": SPLIT_BF16X3, "fp8x4": SPLIT_FP8X4}
+SPLIT_BF16X5 = 3
+PRECISIONS = {"fp64": FP64, "bf16x3": SPLIT_BF16X3, "fp8x4": SPLIT_FP8X4, "bf16x5": SPLIT_BF16X5}
 
 NO_NORMALISE = 1
 NO_CORRECTION = 2
@@ -57,9 +58,13 @@ _lib.pevc_plan_info.argtypes = [_vp, _vp]
 _lib.pevc_plan_info.restype = _i
 _lib.pevc_last_stats.argtypes = [_vp, _vp]
 _lib.pevc_last_stats.restype = _i
+_lib.pevc_set_profile.argtypes = [_vp, _i]
+_lib.pevc_set_profile.restype = _i
+_lib.pevc_kernel_profile.argtypes = [_vp, _vp]
+_lib.pevc_kernel_profile.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
-           "pevc_plan_info", "pevc_last_stats")
+           "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -115,6 +120,16 @@ def pevc_last_stats(plan):
     return st, list(stats)
 
 
+def pevc_set_profile(plan, on: bool) -> int:
+    return _lib.pevc_set_profile(plan, 1 if on else 0)
+
+
+def pevc_kernel_profile(plan):
+    out = (ctypes.c_double * 12)()
+    st = _lib.pevc_kernel_profile(plan, out)
+    return st, list(out)
+
+
 # ------------------------------------------------------------ torch wrapper
 
 class PevcError(RuntimeError):
@@ -168,6 +183,25 @@ class Plan:
     @property
     def stats(self):
         return pevc_last_stats(self.h)[1]
+
+    def profile(self, on: bool = True):
+        st = pevc_set_profile(self.h, on)
+        if st:
+            raise PevcError(st, "pevc_set_profile")
+
+    def kernel_profile(self):
+        """Per-kind totals of the last solve (profiling on): milliseconds,
+        launches and tensor-core flops of the updates, diagonal solves,
+        slicing and the remaining kernels; plus the launch count."""
+        out = pevc_kernel_profile(self.h)[1]
+        names = ("update", "diag", "slice", "other")
+        d = {}
+        for k, nm in enumerate(names):
+            d[f"{nm}_ms"] = out[3 * k]
+            d[f"{nm}_launches"] = int(out[3 * k + 1])
+            d[f"{nm}_tensor_flops"] = out[3 * k + 2]
+        d["launches"] = int(self.stats[6])
+        return d
 
     def solve_colmajor(self, St, Tt, n, V, scale, select=None, lds=None, ldt=None, ldv=None):
         """Device tensors already in column-major storage (see to_device_colmajor)."""

@@ -58,6 +58,8 @@ struct pevc_plan_s {
   cudaEvent_t ev[6] = {};
   double stats[8] = {};
   SplitWorkspace split;
+  Profiler prof;
+  double kprof[12] = {};
 };
 
 namespace {
@@ -85,7 +87,7 @@ int status_from_bits(unsigned bits) {
 // the GPU, short diagonal solves), large ones the largest tile (fewer stages,
 // larger updates).
 int choose_tile(int n_max, int prec) {
-  (void)prec;
+  if (prec != PEVC_FP64) return n_max <= 512 ? 32 : (n_max <= 2048 ? 64 : 128);
   if (n_max <= 256) return 32;
   if (n_max <= 1024) return 64;
   return 128;
@@ -116,6 +118,12 @@ void free_plan(pevc_plan_t p) {
     if (h) cudaFreeHost(h);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  if (p->prof.ev) {
+    for (int q = 0; q < 2 * p->prof.cap; ++q) cudaEventDestroy(p->prof.ev[q]);
+    delete[] p->prof.ev;
+    delete[] p->prof.kind;
+    delete[] p->prof.flops;
+  }
   split_free(p->split);
   delete p;
 }
@@ -218,9 +226,12 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   *m_out = 0;
   for (double& x : p->stats) x = 0.0;
   if (n == 0) return 0;
+  p->prof.reset();
   CK(cudaEventRecord(p->ev[0], s));
   // 1. block structure and selection to the host
+  p->prof.begin(s);
   CK(launch_gather_subdiag(S, lds, n, p->subd, s));
+  p->prof.end(s, 3, 0.0);
   if (n > 1) CK(cudaMemcpyAsync(p->h_subd, p->subd, (size_t)(n - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (sel) CK(cudaMemcpyAsync(p->h_sel, sel, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -239,7 +250,10 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), s));
   CK(cudaMemsetAsync(p->gmax, 0, sizeof(double), s));
   Problem P = make_problem(p, S, lds, T, ldt, n, st);
+  p->prof.begin(s);
   CK(launch_prepass(P, s));
+  p->prof.end(s, 3, 0.0);
+  ++p->prof.launches;   // the prepass is two kernels
   unsigned bits = 0;
   if ((rc = read_status(p, &bits))) return rc;
   if (bits) return status_from_bits(bits);
@@ -249,33 +263,40 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
     CK(cudaEventRecord(p->ev[3], s));
     CK(cudaEventRecord(p->ev[4], s));
   } else {
+    p->prof.begin(s);
     CK(launch_init_state(P, s));
+    p->prof.end(s, 3, 0.0);
     // 3. the task graph, bottom-up by block row
-    int nupd = 0, ndiag = 0;
     if (p->prec == PEVC_FP64) {
-      CK(launch_diag(P, 0, true, s));
-      ++ndiag;
+      p->prof.begin(s);
+      CK(launch_diag(P, 0, kDiagTip, s));
+      p->prof.end(s, 1, 0.0);
       for (int i = st.M - 1; i >= 0; --i) {
         if (i < st.M - 1) {
-          CK(launch_diag(P, i, false, s));
-          ++ndiag;
+          p->prof.begin(s);
+          CK(launch_diag(P, i, kDiagSolve, s));
+          p->prof.end(s, 1, 0.0);
         }
         if (i > 0) {
+          const double rows = p->h_toff[i], cols = st.m - p->h_cstart[i];
+          const double K = 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
+          p->prof.begin(s);
           CK(launch_update_f64(P, i, s));
-          ++nupd;
+          p->prof.end(s, 0, 2.0 * rows * cols * K);
         }
       }
       CK(cudaEventRecord(p->ev[2], s));
       CK(cudaEventRecord(p->ev[3], s));
     } else {
-      rc = split_solve(p->split, P, p->prec, (p->flags & PEVC_NO_CORRECTION) == 0, s, p->ev[2],
-                       p->ev[3], &nupd, &ndiag);
+      HostStructure hs{p->h_toff, p->h_cstart};
+      SplitConfig cfg = split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0);
+      rc = split_solve(p->split, P, hs, cfg, s, p->prof, p->ev[2], p->ev[3]);
       if (rc) return rc;
     }
-    p->stats[6] = nupd;
-    p->stats[7] = ndiag;
     // 4. post-processing: consistent scaling and normalisation
+    p->prof.begin(s);
     CK(launch_post(P, V, ldv, scale, (p->flags & PEVC_NO_NORMALISE) == 0, s));
+    p->prof.end(s, 3, 0.0);
     CK(cudaEventRecord(p->ev[4], s));
   }
   if ((rc = read_status(p, &bits))) return rc;
@@ -292,6 +313,16 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   cudaEventElapsedTime(&post, p->ev[3], p->ev[4]);
   p->stats[4] = post;
   p->stats[5] = st.M;
+  p->stats[6] = p->prof.launches;
+  for (double& x : p->kprof) x = 0.0;
+  for (int q = 0; q < p->prof.used; ++q) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, p->prof.ev[2 * q], p->prof.ev[2 * q + 1]);
+    const int k = p->prof.kind[q];
+    p->kprof[3 * k] += t;
+    p->kprof[3 * k + 1] += 1.0;
+    p->kprof[3 * k + 2] += p->prof.flops[q];
+  }
   return status_from_bits(bits);
 }
 
@@ -305,7 +336,9 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
   *plan = nullptr;
   if (n_max < 0) return -2;
   if (batch_max < 1) return -3;
-  if (prec != PEVC_FP64 && prec != PEVC_SPLIT_BF16X3 && prec != PEVC_SPLIT_FP8X4) return -4;
+  if (prec != PEVC_FP64 && prec != PEVC_SPLIT_BF16X3 && prec != PEVC_SPLIT_FP8X4 && prec != PEVC_SPLIT_BF16X5)
+    return -4;
+  if (prec == PEVC_SPLIT_FP8X4) return PEVC_ERR_UNSUPPORTED;
   if (tile != 0 && tile != 32 && tile != 64 && tile != 96 && tile != 128) return -5;
   if (flags & ~(PEVC_NO_NORMALISE | PEVC_NO_CORRECTION)) return -6;
   pevc_plan_t p = new (std::nothrow) pevc_plan_s();
@@ -422,8 +455,32 @@ int pevc_plan_info(pevc_plan_t plan, int* info) {
   info[3] = plan->batch_max;
   info[4] = (int)plan->flags;
   info[5] = plan->nsm;
-  info[6] = plan->prec == PEVC_FP64 ? 0 : (plan->prec == PEVC_SPLIT_BF16X3 ? 3 : 4);
-  info[7] = (plan->prec != PEVC_FP64 && !(plan->flags & PEVC_NO_CORRECTION)) ? 1 : 0;
+  info[6] = plan->prec == PEVC_FP64 ? 0 : (plan->prec == PEVC_SPLIT_BF16X5 ? 5 : (plan->prec == PEVC_SPLIT_BF16X3 ? 3 : 4));
+  info[7] = (plan->prec == PEVC_SPLIT_BF16X3 && !(plan->flags & PEVC_NO_CORRECTION)) ? 1 : 0;
+  return 0;
+}
+
+int pevc_set_profile(pevc_plan_t plan, int on) {
+  if (!plan) return -1;
+  Profiler& pr = plan->prof;
+  if (on && !pr.ev) {
+    const int cap = 8192;
+    pr.ev = new (std::nothrow) cudaEvent_t[2 * cap];
+    pr.kind = new (std::nothrow) int[cap];
+    pr.flops = new (std::nothrow) double[cap];
+    if (!pr.ev || !pr.kind || !pr.flops) return PEVC_ERR_NOMEM;
+    for (int q = 0; q < 2 * cap; ++q)
+      if (cudaEventCreate(&pr.ev[q]) != cudaSuccess) return PEVC_ERR_CUDA;
+    pr.cap = cap;
+  }
+  pr.on = on != 0;
+  return 0;
+}
+
+int pevc_kernel_profile(pevc_plan_t plan, double* out) {
+  if (!plan) return -1;
+  if (!out) return -2;
+  for (int q = 0; q < 12; ++q) out[q] = plan->kprof[q];
   return 0;
 }
 

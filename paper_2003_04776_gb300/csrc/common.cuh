@@ -112,7 +112,7 @@ struct Problem {
   double* cb;
   double* cbeta;
   // norms
-  int* EA;                  // [M*M] ||[S_kl T_kl]||_inf < 2^EA[k*M+l], k < l
+  int* EA;                  // [M*M] ||[S_kl T_kl]||_inf < 2^EA[k*M+l], k <= l
   double* tcS;              // [n] max |S_rc| over rows r of c's tile above c's block
   double* tcT;              // [n]
   double* gmax;             // [1] max |entry| of S, T over what is read
@@ -127,10 +127,70 @@ __device__ __forceinline__ double* tile_ptr(const Problem& P, int k, int j) {
   return P.Y + tri_index(k, j) * (long long)P.tb * P.tb;
 }
 
+// Per-column consolidation + protection of the update of Y_kj (target P) by
+// X = tile (i, j) whose exponents / norms are exX / nrmX (Algorithms 2 and 3):
+// returns false when X'' is zero (nothing to do).  sY, sX shift the stored Y
+// and X to the new common exponent enew.
+__device__ __forceinline__ bool update_scales(const Problem& P, const int* exX, const double* nrmX,
+                                              int k, int i, int q, int& sY, int& sX, int& enew,
+                                              bool& yzero) {
+  const int m = P.m;
+  const int kd = P.kind[q];
+  const int partner = (kd == 1) ? q + 1 : (kd == 2 ? q - 1 : q);
+  const long long bk = (long long)k * m, bi = (long long)i * m;
+  const double nY = fmax(P.nrm[bk + q], P.nrm[bk + partner]);
+  const double nX = fmax(nrmX[bi + q], nrmX[bi + partner]);
+  const int c0 = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
+  const double cB = fmax(fabs(P.cbeta[c0]), fabs(P.ca[c0]) + fabs(P.cb[c0]));
+  yzero = !(nY > 0.0);
+  if (!(nX > 0.0) || !(cB > 0.0)) return false;
+  const int eY = P.ex[bk + q], eX = exX[bi + q];
+  const int e0 = yzero ? eX : max(eY, eX);
+  const int xb = exp_above(cB) + exp_above(nX) + eX - e0;          // ||X''|| < 2^xb at e0
+  const int top_y = yzero ? INT32_MIN / 4 : exp_above(nY) + eY - e0;
+  int kp = protect_update_e(top_y, P.EA[k * P.M + i] + xb);       // Algorithm 3
+  const int kr = xb - kOmegaExp;                                   // Algorithm 2: ||X''|| <= Omega
+  if (kr > kp) kp = kr;
+  enew = e0 + kp;
+  sY = yzero ? 0 : eY - enew;
+  sX = eX - enew;
+  return true;
+}
+
+// Per-launch CUDA-event timing on the solve's stream (host side).  Kinds:
+// 0 update, 1 diagonal solve, 2 slicing of X, 3 everything else.
+struct Profiler {
+  bool on = false;
+  int cap = 0, used = 0;
+  cudaEvent_t* ev = nullptr;   // 2 * cap events
+  int* kind = nullptr;
+  double* flops = nullptr;
+  int launches = 0;
+  int pending_kind = 3;
+  void reset() { used = 0; launches = 0; }
+  void begin(cudaStream_t s) {
+    ++launches;
+    if (on && used < cap) cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s, int k, double f) {
+    if (on && used < cap) {
+      cudaEventRecord(ev[2 * used + 1], s);
+      kind[used] = k;
+      flops[used] = f;
+      ++used;
+    }
+  }
+};
+
+// Diagonal-tile kernel modes.
+constexpr int kDiagSolve = 0;     // kernel 3: tiles (i, j), j > i, right-hand side from Y
+constexpr int kDiagTip = 1;       // kernel 1: tiles (j, j), unit tips, zero right-hand side
+constexpr int kDiagTipCorr = 2;   // tiles (j, j) of a correction: zero tips, right-hand side from Y
+
 // ---- launchers (one translation unit each) ----
 cudaError_t launch_prepass(const Problem& P, cudaStream_t s);
 cudaError_t launch_init_state(const Problem& P, cudaStream_t s);
-cudaError_t launch_diag(const Problem& P, int i, bool tips, cudaStream_t s);
+cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s);
 cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s);
 cudaError_t launch_post(const Problem& P, double* V, int ldv, int32_t* scale, bool normalise,
                         cudaStream_t s);

@@ -214,7 +214,8 @@ __device__ void cplx_tip(const Problem& P, int i0, double a, double b, double be
 }
 
 template <int CB>
-__global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tips) {
+__global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mode) {
+  const bool tips = mode != kDiagSolve;          // one CTA row per diagonal tile
   constexpr int NC = CB + 1;
   const int j = tips ? (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;
   const int i = tips ? j : i_row;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tip
     s_beta[lr] = P.cbeta[c0];
     s_nrm[lr] = 0.0;
     s_sh[lr] = 0;
-    if (tips) {
+    if (mode == kDiagTip) {
       s_act[lr] = 0;
       s_e[lr] = 0;
       s_y[lr] = 0.0;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tip
 #pragma unroll
   for (int t = 0; t < NC; ++t) {
     vals[t] = 0.0;
-    if (!tips && t < nq && lr < h && s_act[t]) vals[t] = Yt[(size_t)(q0 - cs + t) * P.tb + lr];
+    if (mode != kDiagTip && t < nq && lr < h && s_act[t]) vals[t] = Yt[(size_t)(q0 - cs + t) * P.tb + lr];
   }
 
   int rr = r0 + h - 1;
@@ -295,7 +296,8 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tip
           for (int v = 0; v < 2; ++v) { st.P[u][v] = 0.0; st.Q[u][v] = 0.0; st.W[u][v] = 0.0; }
         double y = s_y[t];
         bool active = s_act[t];
-        if (tips && i0 == tip) {
+        const bool at_or_below_tip = tips && i0 >= tip;
+        if (mode == kDiagTip && i0 == tip) {
           // kernel 1: the tip, then the protect for the update of the rows above
           active = true;
           const double a = s_a[t], b = s_b[t], beta = s_beta[t];
@@ -319,8 +321,10 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tip
             st.Q[u][1] = a * w[u][1] + b * w[u][0];
           }
           s_e[t] = ku;
-          st.shift = 0;
-        } else if (active && (!tips || i0 < tip)) {
+        } else if (at_or_below_tip) {
+          // below a tip, and (correction) at the tip block itself, the column
+          // is zero: W, P, Q stay 0 and nothing is scaled
+        } else if (active) {
           const double a = s_a[t], b = s_b[t], beta = s_beta[t];
           if (kd == 0) {
             real_block(P, i0, sz, has_above, a, beta, s_piv[0][t], sz == 2 ? s_piv[1][t] : 0.0, y, st);
@@ -410,12 +414,12 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int tip
 
 constexpr int kDiagCB = 16;
 
-cudaError_t launch_diag(const Problem& P, int i, bool tips, cudaStream_t s) {
+cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s) {
   const int chunks = (P.tb + kDiagCB - 1) / kDiagCB;
-  const int ntiles = tips ? P.M : (P.M - 1 - i);
+  const int ntiles = (mode != kDiagSolve) ? P.M : (P.M - 1 - i);
   if (ntiles <= 0) return cudaSuccess;
   dim3 grid(chunks, ntiles);
-  k_diag<kDiagCB><<<grid, kMaxTile, 0, s>>>(P, i, tips ? 1 : 0);
+  k_diag<kDiagCB><<<grid, kMaxTile, 0, s>>>(P, i, mode);
   return cudaGetLastError();
 }
 

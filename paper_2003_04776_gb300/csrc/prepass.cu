@@ -74,12 +74,23 @@ __global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
       P.tcS[gc] = ms;
       P.tcT[gc] = mt;
     }
+    // row sums of the quasi-triangular diagonal tile (row r reads S[r, r-1]
+    // when r is the second row of a 2x2 block)
+    const int r = threadIdx.x;
+    if (r < hl) {
+      const int gr = cl0 + r;
+      const int c_first = (P.blk[gr] == 2) ? gr - 1 : gr;
+      for (int gc = c_first; gc < cl0 + hl; ++gc) {
+        rs += ldexp(fabs(S[(size_t)gc * P.lds + gr]), -32);
+        if (gc >= gr) rs += ldexp(fabs(T[(size_t)gc * P.ldt + gr]), -32);
+      }
+    }
   }
   if (!finite) atomicOr(P.status, kStNonfinite);
   block_reduce_max2(amax, rs, red);
   if (threadIdx.x == 0) {
     if (isfinite(amax)) atomic_max_nonneg(P.gmax, amax);
-    if (k < l) P.EA[k * P.M + l] = (rs > 0.0 && isfinite(rs)) ? exp_above(rs) + 33 : -(1 << 28);
+    P.EA[k * P.M + l] = (rs > 0.0 && isfinite(rs)) ? exp_above(rs) + 33 : -(1 << 28);
   }
 }
 

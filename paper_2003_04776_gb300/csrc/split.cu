@@ -1,12 +1,589 @@
+// split.cu -- split-precision updates (Section 3, kernel 2) and the residual
+// correction sweep.
+//
+// Slicing (Ozaki-style, exact): every row r of a tile [S_kl T_kl] is written
+// as 2^e_r * sum_p s_p 2^(-7-8p) and every column q of X'' = [X D; -X B] as
+// 2^F_q * sum_q t_q 2^(-7-8q), with integer slices |s|, |t| <= 128 that BF16
+// holds exactly.  A slice product is an integer below 2^14, so the FP32
+// tensor-core accumulation of K = 2 tb <= 256 terms is exact for the slice
+// levels l = p + q <= 2 (the levels above contribute below 2^-24 of the
+// result).  Each level has its own FP32 accumulator; the FP64 epilogue
+// recombines them, applies the power-of-two scales of the augmented tiles
+// (Algorithms 2 and 3 of Section 4: consolidation to a common exponent,
+// ProtectUpdate) and writes the new column maxima (Section 4 norm
+// bookkeeping).
+//
+// The power-of-two column scales of the augmented tiles are what makes the
+// slices exact: X'' is scaled by 2^-F_q, a per-column exponent the augmented
+// representation already carries.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "split.cuh"
 
 namespace pevc {
 
-int split_alloc(SplitWorkspace& w, int, int, int, int) { w.on = false; return PEVC_ERR_UNSUPPORTED; }
-void split_free(SplitWorkspace& w) { w.on = false; }
-int split_solve(SplitWorkspace&, const Problem&, int, bool, cudaStream_t, cudaEvent_t, cudaEvent_t,
-                int*, int*) {
-  return PEVC_ERR_UNSUPPORTED;
+__device__ __forceinline__ void tile_pair(long long x, int& k, int& l) {
+  int ll = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  while ((long long)ll * (ll + 1) / 2 > x) --ll;
+  while ((long long)(ll + 1) * (ll + 2) / 2 <= x) ++ll;
+  l = ll;
+  k = (int)(x - (long long)ll * (ll + 1) / 2);
+}
+
+__device__ __forceinline__ int col_tile_of(const Problem& P, int q) {
+  int lo = 0, hi = P.M - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.cstart[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Integer slices of a in (-1, 1): s_0 = rint(a 2^7), then 8 more bits each.
+template <int NS>
+__device__ __forceinline__ void make_slices(double a, float (&sl)[NS]) {
+  double rem = a;
+#pragma unroll
+  for (int p = 0; p < NS; ++p) {
+    const double x = rem * (p == 0 ? 128.0 : 256.0);
+    const double s = rint(x);
+    sl[p] = (float)s;
+    rem = x - s;
+  }
+}
+
+// ---------------------------------------------------------------- A slices
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __restrict__ As,
+                                                 int* __restrict__ eA, int ns) {
+  int k, l;
+  tile_pair(blockIdx.x, k, l);
+  const int tb = P.tb, K2 = 2 * tb;
+  const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
+  const int cl0 = P.toff[l], hl = P.toff[l + 1] - cl0;
+  const long long tri = tri_index(k, l);
+  __shared__ int s_e[kMaxTile];
+  const double* S = P.S;
+  const double* T = P.T;
+  const int tid = threadIdx.x;
+  if (tid < tb) {
+    const int r = tid;
+    double mx = 0.0;
+    if (r < hk) {
+      const int gr = rk0 + r;
+      const int cs_first = (k == l) ? max(0, gr - cl0 - (P.blk[gr] == 2 ? 1 : 0)) : 0;
+      const int ct_first = (k == l) ? gr - cl0 : 0;
+      for (int c = cs_first; c < hl; ++c) mx = fmax(mx, fabs(S[(size_t)(cl0 + c) * P.lds + gr]));
+      for (int c = ct_first; c < hl; ++c) mx = fmax(mx, fabs(T[(size_t)(cl0 + c) * P.ldt + gr]));
+    }
+    const int e = (mx > 0.0) ? exp_above(mx) : 0;
+    s_e[r] = e;
+    eA[tri * tb + r] = e;
+  }
+  __syncthreads();
+  const int groups = K2 / 8;
+  for (int item = tid; item < tb * groups; item += blockDim.x) {
+    const int r = item % tb, g = item / tb;
+    const int gr = rk0 + r;
+    float sl[8][NS];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int kap = 8 * g + u;
+      const bool isT = kap >= tb;
+      const int c = isT ? kap - tb : kap;
+      double v = 0.0;
+      if (r < hk && c < hl) {
+        const int gc = cl0 + c;
+        bool ok = true;
+        if (k == l) ok = isT ? (gc >= gr) : (gc >= gr || (gc == gr - 1 && P.blk[gr] == 2));
+        if (ok) v = isT ? T[(size_t)gc * P.ldt + gr] : S[(size_t)gc * P.lds + gr];
+      }
+      make_slices<NS>(ldexp(v, -s_e[r]), sl[u]);
+    }
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      __align__(16) __nv_bfloat16 pk[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pk[u] = __float2bfloat16_rn(sl[u][p]);
+      __nv_bfloat16* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- X slices
+
+// X'' = [beta x ; -(alpha x)] of tile row i for output columns q >= q_begin,
+// from the augmented tiles (Ysrc, exsrc, nrmsrc).  One warp per column.
+template <int NS>
+__global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, const double* __restrict__ Ysrc,
+                                                 const double* __restrict__ nrmsrc, __nv_bfloat16* __restrict__ Xs,
+                                                 int* __restrict__ F, int ns, int mstride) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = q_begin + blockIdx.x * 8 + warp;
+  if (q >= P.m) return;
+  const int tb = P.tb, K2 = 2 * tb, m = P.m;
+  const int kd = P.kind[q];
+  const int c0 = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
+  const double a = P.ca[c0], b = P.cb[c0], beta = P.cbeta[c0];
+  const int j = col_tile_of(P, q);
+  const int lq = q - P.cstart[j];
+  const double* Xt = Ysrc + tri_index(i, j) * (long long)tb * tb;
+  const long long base = (long long)i * m;
+  double nx = nrmsrc[base + q];
+  if (kd == 1) nx = fmax(nx, nrmsrc[base + q + 1]);
+  if (kd == 2) nx = fmax(nx, nrmsrc[base + q - 1]);
+  const int hi = P.toff[i + 1] - P.toff[i];
+  constexpr int U = kMaxTile / 32;
+  double top[U], bot[U];
+  double mx = 0.0;
+  const int g = (nx > 0.0) ? exp_above(nx) : 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int kap = lane + 32 * u;
+    double own = 0.0, oth = 0.0;
+    if (nx > 0.0 && kap < hi) {
+      own = ldexp(Xt[(size_t)lq * tb + kap], -g);
+      if (kd == 1) oth = ldexp(Xt[(size_t)(lq + 1) * tb + kap], -g);
+      if (kd == 2) oth = ldexp(Xt[(size_t)(lq - 1) * tb + kap], -g);
+    }
+    top[u] = beta * own;
+    if (kd == 0) bot[u] = -(a * own);
+    else if (kd == 1) bot[u] = -(a * own - b * oth);     // own = Re x, oth = Im x
+    else bot[u] = -(b * oth + a * own);                 // own = Im x, oth = Re x
+    mx = fmax(mx, fmax(fabs(top[u]), fabs(bot[u])));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int f = (mx > 0.0) ? exp_above(mx) : 0;
+  if (lane == 0) F[q] = (mx > 0.0) ? g + f : kExpZero;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int kap = lane + 32 * u;
+    if (kap >= tb) continue;
+    float st[NS], sb[NS];
+    make_slices<NS>(ldexp(top[u], -f), st);
+    make_slices<NS>(ldexp(bot[u], -f), sb);
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      __nv_bfloat16* col = Xs + ((long long)p * mstride + q) * K2;
+      col[kap] = __float2bfloat16_rn(st[p]);
+      col[tb + kap] = __float2bfloat16_rn(sb[p]);
+    }
+  }
+}
+
+// ------------------------------------------------------------- the update
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* smem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kSplitRows = 128;
+constexpr int kSplitCols = 32;
+constexpr int kSplitKc = 32;
+constexpr int kSplitLd = kSplitKc + 8;   // padded smem row (bf16): conflict-free ldmatrix
+
+template <int NS>
+constexpr int split_smem_bytes() {
+  return 2 * NS * (kSplitRows + kSplitCols) * kSplitLd * 2;
+}
+
+// Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij for k < kend, j >= i.
+template <int NS, int L>
+__global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const int* __restrict__ exX,
+                                                      const double* __restrict__ nrmX,
+                                                      const __nv_bfloat16* __restrict__ As,
+                                                      const int* __restrict__ eA,
+                                                      const __nv_bfloat16* __restrict__ Xs,
+                                                      const int* __restrict__ F, int ns, int mstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);          // [2][NS][128][Ld]
+  __nv_bfloat16* sB = sA + 2 * NS * kSplitRows * kSplitLd;                 // [2][NS][32][Ld]
+  const int tb = P.tb, K2 = 2 * tb;
+  const int nsub = tb / kSplitCols;
+  const int j = i + (int)blockIdx.x / nsub;
+  const int sub = (int)blockIdx.x % nsub;
+  const int k = blockIdx.y;
+  const int cs = P.cstart[j], ce = P.cstart[j + 1];
+  const int c0 = cs + sub * kSplitCols;
+  if (c0 >= ce) return;
+  const int nc = min(kSplitCols, ce - c0);
+  const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
+  double* Yt = tile_ptr(P, k, j);
+  const long long tri = tri_index(k, i);
+  const int tid = threadIdx.x;
+
+  __shared__ int s_sY[kSplitCols], s_sc[kSplitCols], s_e[kSplitCols], s_on[kSplitCols], s_yz[kSplitCols];
+  __shared__ double s_nrm[kSplitCols];
+  __shared__ int s_eA[kSplitRows];
+  __shared__ int s_any;
+  if (tid == 0) s_any = 0;
+  __syncthreads();
+  if (tid < kSplitCols) {
+    int on = 0, sY = 0, sX = 0, en = 0;
+    bool yz = true;
+    if (tid < nc) {
+      const int q = c0 + tid;
+      on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
+      if (on && F[q] == kExpZero) on = 0;
+      s_sc[tid] = on ? F[q] - 14 + sX : 0;
+    }
+    s_on[tid] = on;
+    s_sY[tid] = sY;
+    s_e[tid] = en;
+    s_yz[tid] = yz ? 1 : 0;
+    s_nrm[tid] = 0.0;
+    if (on) atomicOr(&s_any, 1);
+  }
+  if (tid < kSplitRows) s_eA[tid] = (tid < tb) ? eA[tri * tb + tid] : 0;
+  __syncthreads();
+  if (!s_any) return;
+
+  const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
+  auto load_stage = [&](int st, int kb) {
+    __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * kSplitLd;
+    __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * kSplitLd;
+    constexpr int chunks = kSplitKc / 8;                       // 16-byte pieces per row
+    for (int idx = tid; idx < NS * kSplitRows * chunks; idx += 256) {
+      const int c16 = idx % chunks, r = (idx / chunks) % kSplitRows, p = idx / (chunks * kSplitRows);
+      const bool valid = r < tb;
+      const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * c16;
+      cp_async16(a_dst + (p * kSplitRows + r) * kSplitLd + 8 * c16, src, valid);
+    }
+    for (int idx = tid; idx < NS * kSplitCols * chunks; idx += 256) {
+      const int c16 = idx % chunks, col = (idx / chunks) % kSplitCols, p = idx / (chunks * kSplitCols);
+      const bool valid = col < nc;
+      const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * c16;
+      cp_async16(b_dst + (p * kSplitCols + col) * kSplitLd + 8 * c16, src, valid);
+    }
+  };
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wr = warp & 3, wc = warp >> 2;
+  float acc[L][2][2][4];
+#pragma unroll
+  for (int s = 0; s < L; ++s)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[s][a][b][e] = 0.0f;
+
+  const int nchunks = K2 / kSplitKc;
+  load_stage(0, 0);
+  cp_async_commit();
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int st = ch & 1;
+    if (ch + 1 < nchunks) load_stage(st ^ 1, (ch + 1) * kSplitKc);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const __nv_bfloat16* a_s = sA + st * NS * kSplitRows * kSplitLd;
+    const __nv_bfloat16* b_s = sB + st * NS * kSplitCols * kSplitLd;
+#pragma unroll
+    for (int kk = 0; kk < kSplitKc; kk += 16) {
+      unsigned af[NS][2][4];
+      unsigned bf[NS][4];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+          ldmatrix_x4(af[p][mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * kSplitLd + kk +
+                                     (lane >> 4) * 8);
+        ldmatrix_x4(bf[p], b_s + (p * kSplitCols + 16 * wc + (lane & 7) + ((lane >> 4) << 3)) * kSplitLd + kk +
+                               ((lane >> 3) & 1) * 8);
+      }
+#pragma unroll
+      for (int p = 0; p < NS; ++p)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (p + q < L) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              mma_bf16(acc[p + q][mt][0], af[p][mt], bf[q][0], bf[q][1]);
+              mma_bf16(acc[p + q][mt][1], af[p][mt], bf[q][2], bf[q][3]);
+            }
+          }
+        }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+
+  // epilogue: recombine the levels in FP64, scale, update Y, column maxima
+  const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int row = 32 * wr + 16 * mt + g + 8 * h;
+          const int col = 16 * wc + 8 * nt + 2 * t4 + e;
+          if (row < hk && col < nc && s_on[col]) {
+            double comb = 0.0;
+#pragma unroll
+            for (int s = L - 1; s >= 0; --s) comb = comb * (1.0 / 256.0) + (double)acc[s][mt][nt][2 * h + e];
+            const size_t off = (size_t)(c0 + col - cs) * tb + row;
+            const double yold = s_yz[col] ? 0.0 : ldexp(Yt[off], s_sY[col]);
+            const double ynew = yold - ldexp(comb, s_eA[row] + s_sc[col]);
+            Yt[off] = ynew;
+            if (ynew != 0.0) atomic_max_nonneg(&s_nrm[col], fabs(ynew));
+          }
+        }
+  __syncthreads();
+  if (tid < nc && s_on[tid]) {
+    const long long idx = (long long)k * P.m + c0 + tid;
+    P.nrm[idx] = s_nrm[tid];
+    P.ex[idx] = s_e[tid];
+  }
+}
+
+// V (first pass) += delta (correction), per tile column, at a common exponent.
+__global__ void __launch_bounds__(256) k_combine(Problem P, const double* __restrict__ Y2,
+                                                 const int* __restrict__ ex2, const double* __restrict__ nrm2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.y * 8 + warp;
+  const int k = blockIdx.x;
+  if (q >= P.m) return;
+  const int j = col_tile_of(P, q);
+  if (k > j) return;
+  const int m = P.m, tb = P.tb;
+  const int kd = P.kind[q];
+  const int partner = (kd == 1) ? q + 1 : (kd == 2 ? q - 1 : q);
+  const long long idx = (long long)k * m + q;
+  const long long pidx = (long long)k * m + partner;
+  const double n1 = fmax(P.nrm[idx], P.nrm[pidx]);
+  const double n2 = fmax(nrm2[idx], nrm2[pidx]);
+  if (!(n2 > 0.0)) return;
+  const int lq = q - P.cstart[j];
+  double* Vt = tile_ptr(P, k, j) + (size_t)lq * tb;
+  const double* Dt = Y2 + tri_index(k, j) * (long long)tb * tb + (size_t)lq * tb;
+  const int h = P.toff[k + 1] - P.toff[k];
+  const int e1 = P.ex[idx], e2 = ex2[idx];
+  const int e = (n1 > 0.0) ? max(e1, e2) + 1 : e2;
+  double mx = 0.0;
+  for (int r = lane; r < h; r += 32) {
+    const double v = (n1 > 0.0 ? ldexp(Vt[r], e1 - e) : 0.0) + ldexp(Dt[r], e2 - e);
+    Vt[r] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    P.nrm[idx] = mx;
+    P.ex[idx] = e;
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
+  (void)prec;
+  w.tb = tb;
+  w.n_max = std::max(n_max, 1);
+  w.Mmax = Mmax;
+  w.ns = kMaxSlices;
+  w.tiles = (size_t)Mmax * (Mmax + 1) / 2;
+  auto al = [](void** p, size_t bytes) { return cudaMalloc(p, bytes > 0 ? bytes : 16); };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = al((void**)&w.As, w.tiles * w.ns * (size_t)tb * 2 * tb * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = al((void**)&w.eA, w.tiles * (size_t)tb * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.Xs, (size_t)w.ns * w.n_max * 2 * tb * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = al((void**)&w.F, (size_t)w.n_max * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.Y2, w.tiles * (size_t)tb * tb * sizeof(double));
+  if (e == cudaSuccess) e = al((void**)&w.ex2, (size_t)Mmax * w.n_max * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.nrm2, (size_t)Mmax * w.n_max * sizeof(double));
+  if (e == cudaSuccess) {
+    cudaError_t a1 = cudaFuncSetAttribute(k_update_split<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          split_smem_bytes<3>());
+    cudaError_t a2 = cudaFuncSetAttribute(k_update_split<5, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          split_smem_bytes<5>());
+    e = (a1 != cudaSuccess) ? a1 : a2;
+  }
+  w.on = e == cudaSuccess;
+  if (e != cudaSuccess) {
+    split_free(w);
+    return e == cudaErrorMemoryAllocation ? PEVC_ERR_NOMEM : PEVC_ERR_CUDA;
+  }
+  return 0;
+}
+
+void split_free(SplitWorkspace& w) {
+  void* ptrs[] = {w.As, w.eA, w.Xs, w.F, w.Y2, w.ex2, w.nrm2};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w.As = nullptr;
+  w.eA = nullptr;
+  w.Xs = nullptr;
+  w.F = nullptr;
+  w.Y2 = nullptr;
+  w.ex2 = nullptr;
+  w.nrm2 = nullptr;
+  w.on = false;
+}
+
+SplitConfig split_config(int prec, bool correction) {
+  SplitConfig c;
+  if (prec == PEVC_SPLIT_BF16X5) {
+    c.ns1 = 5;
+    c.levels1 = 5;
+    c.correction = false;
+  } else {
+    c.ns1 = 3;
+    c.levels1 = 3;
+    c.correction = correction;
+  }
+  c.ns_res = 5;
+  c.levels_res = 5;
+  return c;
+}
+
+namespace {
+
+int products(int ns, int levels) {
+  int c = 0;
+  for (int p = 0; p < ns; ++p)
+    for (int q = 0; q < ns; ++q)
+      if (p + q < levels) ++c;
+  return c;
+}
+
+cudaError_t launch_split_A(const Problem& P, SplitWorkspace& w, int ns, cudaStream_t s) {
+  const long long tiles = (long long)P.M * (P.M + 1) / 2;
+  if (tiles <= 0) return cudaSuccess;
+  if (ns == 5) k_split_A<5><<<(unsigned)tiles, 256, 0, s>>>(P, w.As, w.eA, w.ns);
+  else k_split_A<3><<<(unsigned)tiles, 256, 0, s>>>(P, w.As, w.eA, w.ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_X(const Problem& P, SplitWorkspace& w, int i, int q_begin, const double* Ysrc,
+                           const double* nrmsrc, int ns, cudaStream_t s) {
+  const int cols = P.m - q_begin;
+  if (cols <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((cols + 7) / 8);
+  if (ns == 5) k_split_X<5><<<blocks, 256, 0, s>>>(P, i, q_begin, Ysrc, nrmsrc, w.Xs, w.F, w.ns, w.n_max);
+  else k_split_X<3><<<blocks, 256, 0, s>>>(P, i, q_begin, Ysrc, nrmsrc, w.Xs, w.F, w.ns, w.n_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int kend, const int* exX,
+                                const double* nrmX, int ns, int levels, cudaStream_t s) {
+  if (kend <= 0) return cudaSuccess;
+  const int nsub = P.tb / kSplitCols;
+  dim3 grid((P.M - i) * nsub, kend);
+  if (ns == 5 && levels == 5)
+    k_update_split<5, 5><<<grid, 256, split_smem_bytes<5>(), s>>>(P, i, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
+                                                                  w.n_max);
+  else
+    k_update_split<3, 3><<<grid, 256, split_smem_bytes<3>(), s>>>(P, i, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
+                                                                  w.n_max);
+  return cudaGetLastError();
+}
+
+#define SCK(call)                                              \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return PEVC_ERR_CUDA;               \
+  } while (0)
+
+// One bottom-up pass of the task graph over the augmented tiles of P:
+// (tips or tip corrections), then per block row i the diagonal solves and the
+// updates of everything above.
+int run_pass(const Problem& P, SplitWorkspace& w, const HostStructure& hs, int tip_mode, int ns, int levels,
+             cudaStream_t s, Profiler& prof) {
+  const int M = P.M;
+  const int prods = products(ns, levels);
+  prof.begin(s);
+  SCK(launch_diag(P, 0, tip_mode, s));
+  prof.end(s, 1, 0.0);
+  for (int i = M - 1; i >= 0; --i) {
+    if (i < M - 1) {
+      prof.begin(s);
+      SCK(launch_diag(P, i, kDiagSolve, s));
+      prof.end(s, 1, 0.0);
+    }
+    if (i > 0) {
+      prof.begin(s);
+      SCK(launch_split_X(P, w, i, hs.cstart[i], P.Y, P.nrm, ns, s));
+      prof.end(s, 2, 0.0);
+      const double rows = hs.toff[i], cols = P.m - hs.cstart[i], K = 2.0 * (hs.toff[i + 1] - hs.toff[i]);
+      prof.begin(s);
+      SCK(launch_update_split(P, w, i, i, P.ex, P.nrm, ns, levels, s));
+      prof.end(s, 0, 2.0 * rows * cols * K * prods);
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
+                cudaStream_t s, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
+  if (!w.on) return PEVC_ERR_UNSUPPORTED;
+  const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
+  prof.begin(s);
+  SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
+  prof.end(s, 3, 0.0);
+  int rc = run_pass(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, s, prof);
+  if (rc) return rc;
+  SCK(cudaEventRecord(ev_dag, s));
+  if (cfg.correction) {
+    // residual R = (S V D - T V B) of the first pass, accumulated tile row by
+    // tile row into the correction tiles as -R (including the diagonal tiles)
+    Problem P2 = P;
+    P2.Y = w.Y2;
+    P2.ex = w.ex2;
+    P2.nrm = w.nrm2;
+    prof.begin(s);
+    SCK(launch_init_state(P2, s));
+    prof.end(s, 3, 0.0);
+    const int prods = products(cfg.ns_res, cfg.levels_res);
+    for (int l = 0; l < P.M; ++l) {
+      prof.begin(s);
+      SCK(launch_split_X(P, w, l, hs.cstart[l], P.Y, P.nrm, cfg.ns_res, s));
+      prof.end(s, 2, 0.0);
+      const double rows = hs.toff[l + 1], cols = P.m - hs.cstart[l], K = 2.0 * (hs.toff[l + 1] - hs.toff[l]);
+      prof.begin(s);
+      SCK(launch_update_split(P2, w, l, l + 1, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
+      prof.end(s, 0, 2.0 * rows * cols * K * prods);
+    }
+    // the correction: same graph, zero tips, right-hand side -R
+    rc = run_pass(P2, w, hs, kDiagTipCorr, cfg.ns1, cfg.levels1, s, prof);
+    if (rc) return rc;
+    prof.begin(s);
+    dim3 grid(P.M, (P.m + 7) / 8);
+    k_combine<<<grid, 256, 0, s>>>(P, w.Y2, w.ex2, w.nrm2);
+    SCK(cudaGetLastError());
+    prof.end(s, 3, 0.0);
+  }
+  SCK(cudaEventRecord(ev_corr, s));
+  return 0;
 }
 
 }  // namespace pevc

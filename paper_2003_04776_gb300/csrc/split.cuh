@@ -1,18 +1,46 @@
-// split.cuh -- split-precision update path (Ozaki-style slices, Section 3's
-// kernel 2 on BF16 / FP8 tensor cores) and the FP64 residual correction.
+// split.cuh -- split-precision path: kernel 2 of Section 3 (the updates
+// Y <- Y - (S X D - T X B)) as exact products of BF16 slices on the tensor
+// cores, with FP32 accumulation per slice level and an FP64 epilogue, and the
+// FP64-faithful residual correction sweep.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 
 namespace pevc {
 
+constexpr int kMaxSlices = 5;
+
+struct SplitConfig {
+  int ns1 = 3, levels1 = 3;      // slices / levels of the solve passes
+  int ns_res = 5, levels_res = 5;  // slices / levels of the residual
+  bool correction = true;
+};
+
 struct SplitWorkspace {
   bool on = false;
+  int tb = 0, n_max = 0, Mmax = 0, ns = 0;
+  size_t tiles = 0;
+  __nv_bfloat16* As = nullptr;   // [tile (k<=l)][slice][tb][2 tb]   row slices of [S_kl T_kl]
+  int* eA = nullptr;             // [tile (k<=l)][tb]                row exponents
+  __nv_bfloat16* Xs = nullptr;   // [slice][n_max][2 tb]             column slices of X''
+  int* F = nullptr;              // [n_max]                          column exponents of X''
+  double* Y2 = nullptr;          // correction tiles
+  int* ex2 = nullptr;
+  double* nrm2 = nullptr;
+};
+
+// Host copies of the structure, for launch shapes and work counts.
+struct HostStructure {
+  const int* toff;
+  const int* cstart;
 };
 
 int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
 void split_free(SplitWorkspace& w);
-int split_solve(SplitWorkspace& w, const Problem& P, int prec, bool correct, cudaStream_t s,
-                cudaEvent_t ev_dag, cudaEvent_t ev_corr, int* nupd, int* ndiag);
+SplitConfig split_config(int prec, bool correction);
+int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
+                cudaStream_t s, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr);
 
 }  // namespace pevc

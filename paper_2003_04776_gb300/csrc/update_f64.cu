@@ -23,33 +23,6 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                : "d"(a), "d"(b));
 }
 
-// Per-column consolidation + protection of one update (shared with the split
-// update): returns false when X'' is zero (nothing to do).
-__device__ __forceinline__ bool update_scales(const Problem& P, int k, int i, int q, int& sY, int& sX,
-                                              int& enew, bool& yzero) {
-  const int m = P.m;
-  const int kd = P.kind[q];
-  const int partner = (kd == 1) ? q + 1 : (kd == 2 ? q - 1 : q);
-  const long long bk = (long long)k * m, bi = (long long)i * m;
-  const double nY = fmax(P.nrm[bk + q], P.nrm[bk + partner]);
-  const double nX = fmax(P.nrm[bi + q], P.nrm[bi + partner]);
-  const int c0 = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
-  const double cB = fmax(fabs(P.cbeta[c0]), fabs(P.ca[c0]) + fabs(P.cb[c0]));
-  yzero = !(nY > 0.0);
-  if (!(nX > 0.0) || !(cB > 0.0)) return false;
-  const int eY = P.ex[bk + q], eX = P.ex[bi + q];
-  const int e0 = yzero ? eX : max(eY, eX);
-  const int xb = exp_above(cB) + exp_above(nX) + eX - e0;          // ||X''|| < 2^xb at e0
-  const int top_y = yzero ? INT32_MIN / 4 : exp_above(nY) + eY - e0;
-  int kp = protect_update_e(top_y, P.EA[k * P.M + i] + xb);       // Algorithm 3
-  const int kr = xb - kOmegaExp;                                   // Algorithm 2: ||X''|| <= Omega
-  if (kr > kp) kp = kr;
-  enew = e0 + kp;
-  sY = yzero ? 0 : eY - enew;
-  sX = eX - enew;
-  return true;
-}
-
 __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
   const int nsub = P.tb / kUpdCols;
   const int j = i + (int)blockIdx.x / nsub;
@@ -81,7 +54,7 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
     bool yz = true;
     if (tid < nc) {
       const int q = c0 + tid;
-      on = update_scales(P, k, i, q, sY, sX, en, yz) ? 1 : 0;
+      on = update_scales(P, P.ex, P.nrm, k, i, q, sY, sX, en, yz) ? 1 : 0;
       const int kd = P.kind[q];
       const int cc = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
       s_kind[tid] = kd;

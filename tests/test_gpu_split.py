@@ -1,0 +1,112 @@
+"""Parity of the split-precision GPU paths with the FP64 oracle.
+
+bf16x5: one pass, five BF16 slices per operand (15 slice products per update).
+bf16x3: three slices (6 products) plus the residual correction sweep (the
+residual with 5-slice products, the correction pass with 3).
+Bar: residual <= 100 n u and no Inf/NaN; componentwise error against the
+oracle within the tolerance below (and printed).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import pencilgen
+from oracle import check
+
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-10
+
+
+def _run(pevc, S, T, prec, tile=0, select=None, correction=True, normalise=True):
+    plan = pevc.Plan(S.shape[0], prec=prec, tile=tile, correction=correction, normalise=normalise)
+    try:
+        V, sc, st = plan.solve(S, T, select=select, check=False)
+        stats = plan.stats
+    finally:
+        plan.close()
+    return V, sc, st, stats
+
+
+def _errors(p, V, select=None):
+    ost, Vo, sco, m = oracle.evc(p.S, p.T, select=select, nthreads=os.cpu_count() or 1)
+    assert ost == 0
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk, select)
+    err, errs = check.compare_normalised(Vo, V, kinds)
+    res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta)
+    return err, res.max() / (p.n * check.U)
+
+
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+@pytest.mark.parametrize("n,tile", [(1, 32), (5, 32), (64, 32), (100, 32), (257, 32), (300, 64), (513, 128)])
+def test_split_matches_oracle(pevc_lib, prec, n, tile):
+    p = pencilgen.make_pencil(n, 2000 + n + tile)
+    V, sc, st, _ = _run(pevc_lib, p.S, p.T, prec, tile=tile)
+    assert st == 0
+    assert np.isfinite(V).all()
+    err, res = _errors(p, V)
+    print(f"{prec} n={n} tile={tile}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert res <= 100.0
+    assert err <= TOL_SPLIT
+
+
+def test_split_uncorrected_bf16x3_is_low_precision(pevc_lib):
+    """Without the correction sweep the 3-slice pass carries ~2^-22 errors; the
+    sweep brings them to FP64 level (this is what the sweep is for)."""
+    p = pencilgen.make_pencil(400, 4001)
+    V0, _, st0, _ = _run(pevc_lib, p.S, p.T, "bf16x3", tile=64, correction=False)
+    V1, _, st1, _ = _run(pevc_lib, p.S, p.T, "bf16x3", tile=64, correction=True)
+    assert st0 == st1 == 0
+    e0, r0 = _errors(p, V0)
+    e1, r1 = _errors(p, V1)
+    print(f"uncorrected err {e0:.3e} resid/(nu) {r0:.3e}; corrected err {e1:.3e} resid/(nu) {r1:.3e}")
+    assert np.isfinite(V0).all()
+    assert e0 < 1e-3
+    assert r1 <= 100.0 and e1 <= TOL_SPLIT
+    assert e1 < e0
+
+
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+def test_split_config0(pevc_lib, prec):
+    p = pencilgen.config_pencil(0)
+    V, sc, st, _ = _run(pevc_lib, p.S, p.T, prec)
+    assert st == 0
+    err, res = _errors(p, V)
+    print(f"config0 {prec}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert res <= 100.0 and err <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+def test_split_selection(pevc_lib, prec):
+    p = pencilgen.make_pencil(350, 4002)
+    sel = np.zeros(p.n, dtype=np.int32)
+    sel[::5] = 1
+    V, sc, st, _ = _run(pevc_lib, p.S, p.T, prec, tile=64, select=sel)
+    assert st == 0
+    err, res = _errors(p, V, select=sel)
+    assert res <= 100.0 and err <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+def test_split_stress_finite(pevc_lib, prec):
+    p = pencilgen.make_pencil(700, pencilgen.config_seed(2), stress=True)
+    V, sc, st, _ = _run(pevc_lib, p.S, p.T, prec, tile=64)
+    assert st == 0
+    assert np.isfinite(V).all()
+    assert sc.max() > 1023
+    err, res = _errors(p, V)
+    print(f"stress {prec}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert res <= 100.0
+
+
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+def test_split_config1_full(pevc_lib, prec):
+    p = pencilgen.config_pencil(1)
+    V, sc, st, stats = _run(pevc_lib, p.S, p.T, prec)
+    assert st == 0
+    err, res = _errors(p, V)
+    print(f"config1 {prec}: err {err:.3e} resid/(nu) {res:.3e} device ms {stats[0]:.1f}")
+    assert res <= 100.0 and err <= TOL_SPLIT
