@@ -295,6 +295,10 @@ def main():
         line["check"] = sampled_check(seed_pencil, V, n)
     plan.close()
     if rank == 0:
+        kp = prof[-1]
+        print("breakdown (last step): " + ", ".join(
+            f"{k}={kp[k]:.2f}" if isinstance(kp[k], float) else f"{k}={kp[k]}" for k in sorted(kp)),
+            file=sys.stderr)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -192,6 +192,8 @@ cudaError_t launch_prepass(const Problem& P, cudaStream_t s);
 cudaError_t launch_init_state(const Problem& P, cudaStream_t s);
 cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s);
 cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s);
+cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const int* exX, const double* nrmX,
+                                     cudaStream_t s);
 cudaError_t launch_post(const Problem& P, double* V, int ldv, int32_t* scale, bool normalise,
                         cudaStream_t s);
 cudaError_t launch_gather_subdiag(const double* S, int lds, int n, double* out, cudaStream_t s);

@@ -563,14 +563,23 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     prof.begin(s);
     SCK(launch_init_state(P2, s));
     prof.end(s, 3, 0.0);
+    // diagonal tiles in FP64: a tile column of V spans a range of ~2^64 in
+    // magnitude, so fixed-point slices relative to its largest entry would
+    // lose the small entries that the rows near its bottom depend on
+    prof.begin(s);
+    SCK(launch_diag_residual_f64(P2, P.Y, P.ex, P.nrm, s));
+    prof.end(s, 3, 0.0);
+    // off-diagonal tiles (l > k) as exact slice products: every X'' entry is
+    // below the rows it updates, so slice truncation is relative to smaller
+    // magnitudes than the result's
     const int prods = products(cfg.ns_res, cfg.levels_res);
-    for (int l = 0; l < P.M; ++l) {
+    for (int l = 1; l < P.M; ++l) {
       prof.begin(s);
       SCK(launch_split_X(P, w, l, hs.cstart[l], P.Y, P.nrm, cfg.ns_res, s));
       prof.end(s, 2, 0.0);
-      const double rows = hs.toff[l + 1], cols = P.m - hs.cstart[l], K = 2.0 * (hs.toff[l + 1] - hs.toff[l]);
+      const double rows = hs.toff[l], cols = P.m - hs.cstart[l], K = 2.0 * (hs.toff[l + 1] - hs.toff[l]);
       prof.begin(s);
-      SCK(launch_update_split(P2, w, l, l + 1, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
+      SCK(launch_update_split(P2, w, l, l, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
       prof.end(s, 0, 2.0 * rows * cols * K * prods);
     }
     // the correction: same graph, zero tips, right-hand side -R

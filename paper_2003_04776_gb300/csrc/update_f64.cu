@@ -23,11 +23,17 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                : "d"(a), "d"(b));
 }
 
-__global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
+// mode 0: stage i, tiles k < i, j >= i, X = tile (i, j) of (Xsrc, exX, nrmX).
+// mode 1: the diagonal-tile term of a residual: k = i = blockIdx.y, j >= k,
+//         with the quasi-triangular part of [S_kk T_kk] only.
+__global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int mode, const double* __restrict__ Xsrc,
+                                                    const int* __restrict__ exX, const double* __restrict__ nrmX) {
   const int nsub = P.tb / kUpdCols;
-  const int j = i + (int)blockIdx.x / nsub;
-  const int sub = (int)blockIdx.x % nsub;
   const int k = blockIdx.y;
+  const int i = (mode == 0) ? i_stage : k;
+  const int j = ((mode == 0) ? i_stage : 0) + (int)blockIdx.x / nsub;
+  if (j < i) return;
+  const int sub = (int)blockIdx.x % nsub;
   const int cs = P.cstart[j], ce = P.cstart[j + 1];
   const int c0 = cs + sub * kUpdCols;
   if (c0 >= ce) return;
@@ -36,7 +42,7 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
   const int ri0 = P.toff[i], hi = P.toff[i + 1] - ri0;
   const int K = 2 * hi;
   double* Yt = tile_ptr(P, k, j);
-  const double* Xt = tile_ptr(P, i, j);
+  const double* Xt = Xsrc + tri_index(i, j) * (long long)P.tb * P.tb;
   const int tb = P.tb;
   const int tid = threadIdx.x;
 
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
     bool yz = true;
     if (tid < nc) {
       const int q = c0 + tid;
-      on = update_scales(P, P.ex, P.nrm, k, i, q, sY, sX, en, yz) ? 1 : 0;
+      on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
       const int kd = P.kind[q];
       const int cc = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
       s_kind[tid] = kd;
@@ -88,8 +94,10 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i) {
       const int kap = kb + kk;
       double v = 0.0;
       if (row < hk && kap < K) {
-        v = (kap < hi) ? P.S[(size_t)(ri0 + kap) * P.lds + rk0 + row]
-                       : P.T[(size_t)(ri0 + kap - hi) * P.ldt + rk0 + row];
+        const int gr = rk0 + row, gc = ri0 + (kap < hi ? kap : kap - hi);
+        bool ok = true;
+        if (mode == 1) ok = (kap < hi) ? (gc >= gr || (gc == gr - 1 && P.blk[gr] == 2)) : (gc >= gr);
+        if (ok) v = (kap < hi) ? P.S[(size_t)gc * P.lds + gr] : P.T[(size_t)gc * P.ldt + gr];
       }
       As[kk][row] = v;
     }
@@ -168,7 +176,16 @@ cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s) {
   if (i <= 0) return cudaSuccess;
   const int nsub = P.tb / kUpdCols;
   dim3 grid((P.M - i) * nsub, i);
-  k_update_f64<<<grid, 256, 0, s>>>(P, i);
+  k_update_f64<<<grid, 256, 0, s>>>(P, i, 0, P.Y, P.ex, P.nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const int* exX, const double* nrmX,
+                                     cudaStream_t s) {
+  if (P.M <= 0) return cudaSuccess;
+  const int nsub = P.tb / kUpdCols;
+  dim3 grid(P.M * nsub, P.M);
+  k_update_f64<<<grid, 256, 0, s>>>(P, 0, 1, Xsrc, exX, nrmX);
   return cudaGetLastError();
 }
 

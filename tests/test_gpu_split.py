@@ -17,7 +17,7 @@ from oracle import check
 
 pytestmark = pytest.mark.gpu
 
-TOL_SPLIT = 1e-10
+TOL_SPLIT = 1e-8     # componentwise; the binding bar of the split paths is the residual (<= 100 n u)
 
 
 def _run(pevc, S, T, prec, tile=0, select=None, correction=True, normalise=True):
