@@ -84,6 +84,24 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
 
 __device__ __forceinline__ double cmag(double re, double im) { return fabs(re) + fabs(im); }
 
+// x * 2^e, exact up to underflow/overflow like ldexp.  Normal results are
+// formed by adding e to the exponent field with integer arithmetic (FP64
+// instructions are scarce on this GPU); zero, subnormal and out-of-range
+// cases take the library path.
+__device__ __forceinline__ double pow2_scale(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const int En = E + e;
+  if (E != 0 && E != 0x7ff && En > 0 && En < 0x7ff) return __longlong_as_double(b + ((long long)e << 52));
+  if (e == 0 || x == 0.0) return x;
+  return ldexp(x, e);
+}
+
+// |x| as an ordered integer key (non-negative doubles order like their bits).
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 // Largest of non-negative doubles via their bit patterns (monotone for x >= 0).
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));

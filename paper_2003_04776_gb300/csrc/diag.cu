@@ -48,7 +48,7 @@ __device__ void real_block(const Problem& P, int i0, int sz, bool has_above, dou
     const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + fabs(a) * fabs(t)), 0x1p-1022);
     if (fabs(p) < smin) p = copysign(smin, p);
     kd = protect_division(fabs(r0), 0, fabs(p));
-    if (kd) { r0 = ldexp(r0, -kd); y = ldexp(y, -kd); }
+    if (kd) { r0 = pow2_scale(r0, -kd); y = pow2_scale(y, -kd); }
     w0 = r0 / p;
   } else {
     double m[2][2];
@@ -78,7 +78,7 @@ __device__ void real_block(const Problem& P, int i0, int sz, bool has_above, dou
     double u22 = m[oi][oj] - l * m[pi][oj];
     if (fabs(u22) < smin) u22 = copysign(smin, u22);
     kd = protect_division(fmax(fabs(r0), fabs(r1)), 5, fabs(u22));
-    if (kd) { r0 = ldexp(r0, -kd); r1 = ldexp(r1, -kd); y = ldexp(y, -kd); }
+    if (kd) { r0 = pow2_scale(r0, -kd); r1 = pow2_scale(r1, -kd); y = pow2_scale(y, -kd); }
     const double rp = pi ? r1 : r0, ro = pi ? r0 : r1;
     const double xo = (ro - l * rp) / u22;
     const double xp = rp / piv - (m[pi][oj] / piv) * xo;
@@ -89,8 +89,8 @@ __device__ void real_block(const Problem& P, int i0, int sz, bool has_above, dou
   const double tn = upd_norm(P, i0, sz, beta, fabs(a));
   const double x = fmax(fabs(w0), fabs(w1));
   if (has_above) ku = protect_update(y, tn, x);
-  if (ku) { w0 = ldexp(w0, -ku); w1 = ldexp(w1, -ku); }
-  if (has_above) y = ldexp(y, -ku) + tn * ldexp(x, -ku);
+  if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); }
+  if (has_above) y = pow2_scale(y, -ku) + tn * pow2_scale(x, -ku);
   out.shift = kd + ku;
   out.W[0][0] = w0; out.W[1][0] = w1;
   out.P[0][0] = beta * w0; out.P[1][0] = beta * w1;
@@ -113,7 +113,7 @@ __device__ void cplx_block(const Problem& P, int i0, int sz, bool has_above, dou
     const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + amag * fabs(t)), 0x1p-1022);
     if (cmag(pr, pim) < smin) { pr = smin; pim = 0.0; }
     kd = protect_division(cmag(r0r, r0i), 1, cmag(pr, pim));
-    if (kd) { r0r = ldexp(r0r, -kd); r0i = ldexp(r0i, -kd); y = ldexp(y, -kd); }
+    if (kd) { r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd); y = pow2_scale(y, -kd); }
     cdiv(r0r, r0i, pr, pim, w0r, w0i);
   } else {
     double mr[2][2], mi[2][2];
@@ -149,9 +149,9 @@ __device__ void cplx_block(const Problem& P, int i0, int sz, bool has_above, dou
     if (cmag(ur, ui) < smin) { ur = smin; ui = 0.0; }
     kd = protect_division(fmax(cmag(r0r, r0i), cmag(r1r, r1i)), 5, cmag(ur, ui));
     if (kd) {
-      r0r = ldexp(r0r, -kd); r0i = ldexp(r0i, -kd);
-      r1r = ldexp(r1r, -kd); r1i = ldexp(r1i, -kd);
-      y = ldexp(y, -kd);
+      r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
+      r1r = pow2_scale(r1r, -kd); r1i = pow2_scale(r1i, -kd);
+      y = pow2_scale(y, -kd);
     }
     const double rpr = pi ? r1r : r0r, rpi = pi ? r1i : r0i;
     const double ror = pi ? r0r : r1r, roi = pi ? r0i : r1i;
@@ -170,10 +170,10 @@ __device__ void cplx_block(const Problem& P, int i0, int sz, bool has_above, dou
   const double x = fmax(cmag(w0r, w0i), cmag(w1r, w1i));
   if (has_above) ku = protect_update(y, tn, x);
   if (ku) {
-    w0r = ldexp(w0r, -ku); w0i = ldexp(w0i, -ku);
-    w1r = ldexp(w1r, -ku); w1i = ldexp(w1i, -ku);
+    w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
+    w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
   }
-  if (has_above) y = ldexp(y, -ku) + tn * ldexp(x, -ku);
+  if (has_above) y = pow2_scale(y, -ku) + tn * pow2_scale(x, -ku);
   out.shift = kd + ku;
   out.W[0][0] = w0r; out.W[0][1] = w0i; out.W[1][0] = w1r; out.W[1][1] = w1i;
   out.P[0][0] = beta * w0r; out.P[0][1] = beta * w0i;
@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
 #pragma unroll
           for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int v = 0; v < 2; ++v) w[u][v] = ku ? ldexp(w[u][v], -ku) : w[u][v];
-          y = has_above ? tn * ldexp(x, -ku) : 0.0;
+            for (int v = 0; v < 2; ++v) w[u][v] = ku ? pow2_scale(w[u][v], -ku) : w[u][v];
+          y = has_above ? tn * pow2_scale(x, -ku) : 0.0;
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             st.W[u][0] = w[u][0]; st.W[u][1] = w[u][1];
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
         if (t >= nq) break;
         const int sh = s_sh[t];
         double v = vals[t];
-        if (sh) v = ldexp(v, -sh);
+        if (sh) v = pow2_scale(v, -sh);
         if (inblk) {
           v = s_W[lr - li0][t];
         } else if (above) {

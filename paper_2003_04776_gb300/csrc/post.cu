@@ -73,10 +73,10 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
     const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
     const double* Yt = tile_ptr(P, k, j);
     for (int r = tid; r < h; r += blockDim.x) {
-      const double vr = ldexp(Yt[(size_t)lq * tb + r], sh);
+      const double vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
       double mg;
       if (pair) {
-        const double vi = ldexp(Yt[(size_t)(lq + 1) * tb + r], sh);
+        const double vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
         mg = hypot(vr, vi);
       } else {
         mg = fabs(vr);
@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
     const int sh = P.ex[idx] - eref;
     const double* Yt = tile_ptr(P, k, j);
     const int r = istar - P.toff[k];
-    dr = ldexp(Yt[(size_t)lq * tb + r], sh);
-    if (pair) di = ldexp(Yt[(size_t)(lq + 1) * tb + r], sh);
+    dr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
+    if (pair) di = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
   }
 
   // 3. write the column(s)
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
     for (int r = tid; r < h; r += blockDim.x) {
       double vr = 0.0, vi = 0.0;
       if (nv > 0.0) {
-        vr = ldexp(Yt[(size_t)lq * tb + r], sh);
-        if (pair) vi = ldexp(Yt[(size_t)(lq + 1) * tb + r], sh);
+        vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
+        if (pair) vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
       }
       if (normalise) {
         if (pair) {

@@ -41,18 +41,41 @@ __device__ __forceinline__ int col_tile_of(const Problem& P, int q) {
   return lo;
 }
 
-// Integer slices of a in (-1, 1): s_0 = rint(a 2^7), then 8 more bits each.
+// Slices of v relative to 2^e (|v| < 2^e): the balanced base-256 digits of
+// the integer round(v 2^(B - e)), B = 7 + 8 (NS - 1), so that
+//   v 2^-e = sum_p d_p 2^(-7 - 8p) + O(2^-B-1),   |d_p| <= 128.
+// Integer arithmetic on the binary64 fields only (exact).
 template <int NS>
-__device__ __forceinline__ void make_slices(double a, float (&sl)[NS]) {
-  double rem = a;
-#pragma unroll
-  for (int p = 0; p < NS; ++p) {
-    const double x = rem * (p == 0 ? 128.0 : 256.0);
-    const double s = rint(x);
-    sl[p] = (float)s;
-    rem = x - s;
+__device__ __forceinline__ void int_slices(double v, int e, int (&d)[NS]) {
+  constexpr int B = 7 + 8 * (NS - 1);
+  const long long bits = __double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7ff);
+  long long mant = bits & ((1ll << 52) - 1);
+  if (E != 0) mant |= 1ll << 52;
+  const int Eeff = E != 0 ? E : 1;
+  const int sh = Eeff - 1075 + B - e;
+  long long q;
+  if (mant == 0) {
+    q = 0;
+  } else if (sh >= 0) {
+    q = mant << sh;
+  } else if (-sh >= 60) {
+    q = 0;
+  } else {
+    const int r = -sh;
+    q = (mant + (1ll << (r - 1))) >> r;
   }
+  if (bits < 0) q = -q;
+#pragma unroll
+  for (int p = NS - 1; p >= 1; --p) {
+    const int dp = (int)(((q + 128) & 255) - 128);
+    d[p] = dp;
+    q = (q - dp) >> 8;
+  }
+  d[0] = (int)q;
 }
+
+__device__ __forceinline__ __nv_bfloat16 small_int_bf16(int x) { return __float2bfloat16_rn((float)x); }
 
 // ---------------------------------------------------------------- A slices
 
@@ -76,8 +99,10 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
       const int gr = rk0 + r;
       const int cs_first = (k == l) ? max(0, gr - cl0 - (P.blk[gr] == 2 ? 1 : 0)) : 0;
       const int ct_first = (k == l) ? gr - cl0 : 0;
-      for (int c = cs_first; c < hl; ++c) mx = fmax(mx, fabs(S[(size_t)(cl0 + c) * P.lds + gr]));
-      for (int c = ct_first; c < hl; ++c) mx = fmax(mx, fabs(T[(size_t)(cl0 + c) * P.ldt + gr]));
+      unsigned long long key = 0;
+      for (int c = cs_first; c < hl; ++c) key = max(key, abs_key(S[(size_t)(cl0 + c) * P.lds + gr]));
+      for (int c = ct_first; c < hl; ++c) key = max(key, abs_key(T[(size_t)(cl0 + c) * P.ldt + gr]));
+      mx = __longlong_as_double((long long)key);
     }
     const int e = (mx > 0.0) ? exp_above(mx) : 0;
     s_e[r] = e;
@@ -88,7 +113,7 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
   for (int item = tid; item < tb * groups; item += blockDim.x) {
     const int r = item % tb, g = item / tb;
     const int gr = rk0 + r;
-    float sl[8][NS];
+    int sl[8][NS];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int kap = 8 * g + u;
@@ -101,13 +126,13 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
         if (k == l) ok = isT ? (gc >= gr) : (gc >= gr || (gc == gr - 1 && P.blk[gr] == 2));
         if (ok) v = isT ? T[(size_t)gc * P.ldt + gr] : S[(size_t)gc * P.lds + gr];
       }
-      make_slices<NS>(ldexp(v, -s_e[r]), sl[u]);
+      int_slices<NS>(v, s_e[r], sl[u]);
     }
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
       __align__(16) __nv_bfloat16 pk[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) pk[u] = __float2bfloat16_rn(sl[u][p]);
+      for (int u = 0; u < 8; ++u) pk[u] = small_int_bf16(sl[u][p]);
       __nv_bfloat16* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
     }
@@ -140,37 +165,39 @@ __global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, 
   constexpr int U = kMaxTile / 32;
   double top[U], bot[U];
   double mx = 0.0;
+  unsigned long long key = 0;
   const int g = (nx > 0.0) ? exp_above(nx) : 0;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int kap = lane + 32 * u;
     double own = 0.0, oth = 0.0;
     if (nx > 0.0 && kap < hi) {
-      own = ldexp(Xt[(size_t)lq * tb + kap], -g);
-      if (kd == 1) oth = ldexp(Xt[(size_t)(lq + 1) * tb + kap], -g);
-      if (kd == 2) oth = ldexp(Xt[(size_t)(lq - 1) * tb + kap], -g);
+      own = pow2_scale(Xt[(size_t)lq * tb + kap], -g);
+      if (kd == 1) oth = pow2_scale(Xt[(size_t)(lq + 1) * tb + kap], -g);
+      if (kd == 2) oth = pow2_scale(Xt[(size_t)(lq - 1) * tb + kap], -g);
     }
     top[u] = beta * own;
     if (kd == 0) bot[u] = -(a * own);
     else if (kd == 1) bot[u] = -(a * own - b * oth);     // own = Re x, oth = Im x
     else bot[u] = -(b * oth + a * own);                 // own = Im x, oth = Re x
-    mx = fmax(mx, fmax(fabs(top[u]), fabs(bot[u])));
+    key = max(key, max(abs_key(top[u]), abs_key(bot[u])));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+  mx = __longlong_as_double((long long)key);
   const int f = (mx > 0.0) ? exp_above(mx) : 0;
   if (lane == 0) F[q] = (mx > 0.0) ? g + f : kExpZero;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int kap = lane + 32 * u;
     if (kap >= tb) continue;
-    float st[NS], sb[NS];
-    make_slices<NS>(ldexp(top[u], -f), st);
-    make_slices<NS>(ldexp(bot[u], -f), sb);
+    int st[NS], sb[NS];
+    int_slices<NS>(top[u], f, st);
+    int_slices<NS>(bot[u], f, sb);
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
       __nv_bfloat16* col = Xs + ((long long)p * mstride + q) * K2;
-      col[kap] = __float2bfloat16_rn(st[p]);
-      col[tb + kap] = __float2bfloat16_rn(sb[p]);
+      col[kap] = small_int_bf16(st[p]);
+      col[tb + kap] = small_int_bf16(sb[p]);
     }
   }
 }
@@ -203,25 +230,32 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 
 constexpr int kSplitRows = 128;
 constexpr int kSplitCols = 32;
-constexpr int kSplitKc = 32;
-constexpr int kSplitLd = kSplitKc + 8;   // padded smem row (bf16): conflict-free ldmatrix
+
+// K chunk per pipeline stage: 32 for up to 3 slices, 16 for 5 (so that two
+// CTAs fit in shared memory and one CTA's epilogue overlaps the other's MMAs).
+template <int NS>
+__host__ __device__ constexpr int split_kc() { return NS >= 5 ? 16 : 32; }
+template <int NS>
+__host__ __device__ constexpr int split_ld() { return split_kc<NS>() + 8; }   // padded smem row (bf16): conflict-free ldmatrix
 
 template <int NS>
 constexpr int split_smem_bytes() {
-  return 2 * NS * (kSplitRows + kSplitCols) * kSplitLd * 2;
+  return 2 * NS * (kSplitRows + kSplitCols) * split_ld<NS>() * 2;
 }
 
 // Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij for k < kend, j >= i.
 template <int NS, int L>
-__global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const int* __restrict__ exX,
-                                                      const double* __restrict__ nrmX,
-                                                      const __nv_bfloat16* __restrict__ As,
-                                                      const int* __restrict__ eA,
-                                                      const __nv_bfloat16* __restrict__ Xs,
-                                                      const int* __restrict__ F, int ns, int mstride) {
+__global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, const int* __restrict__ exX,
+                                                         const double* __restrict__ nrmX,
+                                                         const __nv_bfloat16* __restrict__ As,
+                                                         const int* __restrict__ eA,
+                                                         const __nv_bfloat16* __restrict__ Xs,
+                                                         const int* __restrict__ F, int ns, int mstride) {
+  constexpr int KC = split_kc<NS>();
+  constexpr int LD = split_ld<NS>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);          // [2][NS][128][Ld]
-  __nv_bfloat16* sB = sA + 2 * NS * kSplitRows * kSplitLd;                 // [2][NS][32][Ld]
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);    // [2][NS][128][LD]
+  __nv_bfloat16* sB = sA + 2 * NS * kSplitRows * LD;                 // [2][NS][32][LD]
   const int tb = P.tb, K2 = 2 * tb;
   const int nsub = tb / kSplitCols;
   const int j = i + (int)blockIdx.x / nsub;
@@ -237,7 +271,7 @@ __global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const in
   const int tid = threadIdx.x;
 
   __shared__ int s_sY[kSplitCols], s_sc[kSplitCols], s_e[kSplitCols], s_on[kSplitCols], s_yz[kSplitCols];
-  __shared__ double s_nrm[kSplitCols];
+  __shared__ unsigned long long s_key[kSplitCols];
   __shared__ int s_eA[kSplitRows];
   __shared__ int s_any;
   if (tid == 0) s_any = 0;
@@ -249,13 +283,13 @@ __global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const in
       const int q = c0 + tid;
       on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
       if (on && F[q] == kExpZero) on = 0;
-      s_sc[tid] = on ? F[q] - 14 + sX : 0;
+      s_sc[tid] = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
     }
     s_on[tid] = on;
     s_sY[tid] = sY;
     s_e[tid] = en;
     s_yz[tid] = yz ? 1 : 0;
-    s_nrm[tid] = 0.0;
+    s_key[tid] = 0ull;
     if (on) atomicOr(&s_any, 1);
   }
   if (tid < kSplitRows) s_eA[tid] = (tid < tb) ? eA[tri * tb + tid] : 0;
@@ -264,20 +298,20 @@ __global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const in
 
   const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
   auto load_stage = [&](int st, int kb) {
-    __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * kSplitLd;
-    __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * kSplitLd;
-    constexpr int chunks = kSplitKc / 8;                       // 16-byte pieces per row
+    __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * LD;
+    __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * LD;
+    constexpr int chunks = KC / 8;                        // 16-byte pieces per row
     for (int idx = tid; idx < NS * kSplitRows * chunks; idx += 256) {
       const int c16 = idx % chunks, r = (idx / chunks) % kSplitRows, p = idx / (chunks * kSplitRows);
       const bool valid = r < tb;
       const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * c16;
-      cp_async16(a_dst + (p * kSplitRows + r) * kSplitLd + 8 * c16, src, valid);
+      cp_async16(a_dst + (p * kSplitRows + r) * LD + 8 * c16, src, valid);
     }
     for (int idx = tid; idx < NS * kSplitCols * chunks; idx += 256) {
       const int c16 = idx % chunks, col = (idx / chunks) % kSplitCols, p = idx / (chunks * kSplitCols);
       const bool valid = col < nc;
       const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * c16;
-      cp_async16(b_dst + (p * kSplitCols + col) * kSplitLd + 8 * c16, src, valid);
+      cp_async16(b_dst + (p * kSplitCols + col) * LD + 8 * c16, src, valid);
     }
   };
 
@@ -293,74 +327,88 @@ __global__ void __launch_bounds__(256) k_update_split(Problem P, int i, const in
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[s][a][b][e] = 0.0f;
 
-  const int nchunks = K2 / kSplitKc;
+  const int nchunks = K2 / KC;
   load_stage(0, 0);
   cp_async_commit();
   for (int ch = 0; ch < nchunks; ++ch) {
     const int st = ch & 1;
-    if (ch + 1 < nchunks) load_stage(st ^ 1, (ch + 1) * kSplitKc);
+    if (ch + 1 < nchunks) load_stage(st ^ 1, (ch + 1) * KC);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    const __nv_bfloat16* a_s = sA + st * NS * kSplitRows * kSplitLd;
-    const __nv_bfloat16* b_s = sB + st * NS * kSplitCols * kSplitLd;
+    const __nv_bfloat16* a_s = sA + st * NS * kSplitRows * LD;
+    const __nv_bfloat16* b_s = sB + st * NS * kSplitCols * LD;
 #pragma unroll
-    for (int kk = 0; kk < kSplitKc; kk += 16) {
-      unsigned af[NS][2][4];
+    for (int kk = 0; kk < KC; kk += 16) {
       unsigned bf[NS][4];
 #pragma unroll
+      for (int q = 0; q < NS; ++q)
+        ldmatrix_x4(bf[q], b_s + (q * kSplitCols + 16 * wc + (lane & 7) + ((lane >> 4) << 3)) * LD + kk +
+                               ((lane >> 3) & 1) * 8);
+#pragma unroll
       for (int p = 0; p < NS; ++p) {
+        unsigned af[2][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
-          ldmatrix_x4(af[p][mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * kSplitLd + kk +
-                                     (lane >> 4) * 8);
-        ldmatrix_x4(bf[p], b_s + (p * kSplitCols + 16 * wc + (lane & 7) + ((lane >> 4) << 3)) * kSplitLd + kk +
-                               ((lane >> 3) & 1) * 8);
-      }
-#pragma unroll
-      for (int p = 0; p < NS; ++p)
+          ldmatrix_x4(af[mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * LD + kk + (lane >> 4) * 8);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
           if (p + q < L) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-              mma_bf16(acc[p + q][mt][0], af[p][mt], bf[q][0], bf[q][1]);
-              mma_bf16(acc[p + q][mt][1], af[p][mt], bf[q][2], bf[q][3]);
+              mma_bf16(acc[p + q][mt][0], af[mt], bf[q][0], bf[q][1]);
+              mma_bf16(acc[p + q][mt][1], af[mt], bf[q][2], bf[q][3]);
             }
           }
         }
+      }
     }
     __syncthreads();
   }
   cp_async_wait<0>();
 
-  // epilogue: recombine the levels in FP64, scale, update Y, column maxima
+  // epilogue: recombine the (integer-valued) levels exactly as one integer,
+  // one conversion to FP64, power-of-two scales by exponent arithmetic, one
+  // FP64 subtraction per element; column maxima by integer keys
   const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int e = 0; e < 2; ++e) {
+      const int col = 16 * wc + 8 * nt + 2 * t4 + e;
+      const bool con = col < nc && s_on[col];
+      unsigned long long key = 0;
+      if (con) {
+        const int sY = s_sY[col], sc = s_sc[col];
+        const bool yz = s_yz[col] != 0;
+        double* ycol = Yt + (size_t)(c0 + col - cs) * tb;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int row = 32 * wr + 16 * mt + g + 8 * h;
-          const int col = 16 * wc + 8 * nt + 2 * t4 + e;
-          if (row < hk && col < nc && s_on[col]) {
-            double comb = 0.0;
+          for (int h = 0; h < 2; ++h) {
+            const int row = 32 * wr + 16 * mt + g + 8 * h;
+            if (row < hk) {
+              long long t = 0;
 #pragma unroll
-            for (int s = L - 1; s >= 0; --s) comb = comb * (1.0 / 256.0) + (double)acc[s][mt][nt][2 * h + e];
-            const size_t off = (size_t)(c0 + col - cs) * tb + row;
-            const double yold = s_yz[col] ? 0.0 : ldexp(Yt[off], s_sY[col]);
-            const double ynew = yold - ldexp(comb, s_eA[row] + s_sc[col]);
-            Yt[off] = ynew;
-            if (ynew != 0.0) atomic_max_nonneg(&s_nrm[col], fabs(ynew));
+              for (int s = 0; s < L; ++s) t = (t << 8) + (long long)__float2int_rn(acc[s][mt][nt][2 * h + e]);
+              const double prod = pow2_scale((double)t, s_eA[row] + sc);
+              const double yold = yz ? 0.0 : pow2_scale(ycol[row], sY);
+              const double ynew = yold - prod;
+              ycol[row] = ynew;
+              key = max(key, abs_key(ynew));
+            }
           }
-        }
+      }
+      // reduce over the 8 lanes (g) that share this column
+      key = max(key, __shfl_xor_sync(0xffffffffu, key, 4));
+      key = max(key, __shfl_xor_sync(0xffffffffu, key, 8));
+      key = max(key, __shfl_xor_sync(0xffffffffu, key, 16));
+      if (con && g == 0 && key) atomicMax(&s_key[col], key);
+    }
   __syncthreads();
   if (tid < nc && s_on[tid]) {
     const long long idx = (long long)k * P.m + c0 + tid;
-    P.nrm[idx] = s_nrm[tid];
+    P.nrm[idx] = __longlong_as_double((long long)s_key[tid]);
     P.ex[idx] = s_e[tid];
   }
 }
@@ -390,7 +438,7 @@ __global__ void __launch_bounds__(256) k_combine(Problem P, const double* __rest
   const int e = (n1 > 0.0) ? max(e1, e2) + 1 : e2;
   double mx = 0.0;
   for (int r = lane; r < h; r += 32) {
-    const double v = (n1 > 0.0 ? ldexp(Vt[r], e1 - e) : 0.0) + ldexp(Dt[r], e2 - e);
+    const double v = (n1 > 0.0 ? pow2_scale(Vt[r], e1 - e) : 0.0) + pow2_scale(Dt[r], e2 - e);
     Vt[r] = v;
     mx = fmax(mx, fabs(v));
   }

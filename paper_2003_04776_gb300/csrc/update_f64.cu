@@ -110,19 +110,19 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int 
         const int sx = s_sX[col];
         const int kd = s_kind[col];
         if (kap < hi) {
-          v = s_beta[col] * ldexp(Xt[(size_t)lq * tb + kap], sx);
+          v = s_beta[col] * pow2_scale(Xt[(size_t)lq * tb + kap], sx);
         } else {
           const int kp = kap - hi;
           const double a = s_a[col], b = s_b[col];
           if (kd == 0) {
-            v = -a * ldexp(Xt[(size_t)lq * tb + kp], sx);
+            v = -a * pow2_scale(Xt[(size_t)lq * tb + kp], sx);
           } else if (kd == 1) {
-            const double xr = ldexp(Xt[(size_t)lq * tb + kp], sx);
-            const double xi = ldexp(Xt[(size_t)(lq + 1) * tb + kp], sx);
+            const double xr = pow2_scale(Xt[(size_t)lq * tb + kp], sx);
+            const double xi = pow2_scale(Xt[(size_t)(lq + 1) * tb + kp], sx);
             v = -(a * xr - b * xi);
           } else {
-            const double xr = ldexp(Xt[(size_t)(lq - 1) * tb + kp], sx);
-            const double xi = ldexp(Xt[(size_t)lq * tb + kp], sx);
+            const double xr = pow2_scale(Xt[(size_t)(lq - 1) * tb + kp], sx);
+            const double xi = pow2_scale(Xt[(size_t)lq * tb + kp], sx);
             v = -(b * xr + a * xi);
           }
         }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int 
         const int col = 16 * wc + 8 * b + 2 * t4 + e;
         if (row < hk && col < nc && s_on[col]) {
           const size_t off = (size_t)(c0 + col - cs) * tb + row;
-          const double yold = s_yz[col] ? 0.0 : ldexp(Yt[off], s_sY[col]);
+          const double yold = s_yz[col] ? 0.0 : pow2_scale(Yt[off], s_sY[col]);
           const double ynew = yold - acc[a][b][e];
           Yt[off] = ynew;
           if (ynew != 0.0) atomic_max_nonneg(&s_nrm[col], fabs(ynew));
