@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sched.cuh"
 #include "split.cuh"
 
 using namespace pevc;
@@ -60,6 +61,9 @@ struct pevc_plan_s {
   SplitWorkspace split;
   Profiler prof;
   double kprof[12] = {};
+  cudaStream_t aux = nullptr;
+  cudaEvent_t* sev = nullptr;   // 2 * Mmax scheduling events
+  bool lookahead = true;
 };
 
 namespace {
@@ -125,6 +129,12 @@ void free_plan(pevc_plan_t p) {
     delete[] p->prof.flops;
   }
   split_free(p->split);
+  if (p->sev) {
+    for (int q = 0; q < 2 * p->Mmax; ++q)
+      if (p->sev[q]) cudaEventDestroy(p->sev[q]);
+    delete[] p->sev;
+  }
+  if (p->aux) cudaStreamDestroy(p->aux);
   delete p;
 }
 
@@ -267,30 +277,41 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
     CK(launch_init_state(P, s));
     p->prof.end(s, 3, 0.0);
     // 3. the task graph, bottom-up by block row
+    SchedContext sc{p->aux, p->sev, p->lookahead};
     if (p->prec == PEVC_FP64) {
-      p->prof.begin(s);
-      CK(launch_diag(P, 0, kDiagTip, s));
-      p->prof.end(s, 1, 0.0);
-      for (int i = st.M - 1; i >= 0; --i) {
-        if (i < st.M - 1) {
-          p->prof.begin(s);
-          CK(launch_diag(P, i, kDiagSolve, s));
-          p->prof.end(s, 1, 0.0);
+      struct F64Ops : StageOps {
+        const Problem& P;
+        pevc_plan_t p;
+        F64Ops(const Problem& P_, pevc_plan_t p_) : P(P_), p(p_) {}
+        cudaError_t tips(cudaStream_t st) override {
+          p->prof.begin(st);
+          cudaError_t e = launch_diag(P, 0, kDiagTip, st);
+          p->prof.end(st, 1, 0.0);
+          return e;
         }
-        if (i > 0) {
-          const double rows = p->h_toff[i], cols = st.m - p->h_cstart[i];
+        cudaError_t diag(int i, cudaStream_t st) override {
+          p->prof.begin(st);
+          cudaError_t e = launch_diag(P, i, kDiagSolve, st);
+          p->prof.end(st, 1, 0.0);
+          return e;
+        }
+        cudaError_t prep(int, cudaStream_t) override { return cudaSuccess; }
+        cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t st) override {
+          const double rows = p->h_toff[k_hi] - p->h_toff[k_lo], cols = P.m - p->h_cstart[i];
           const double K = 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
-          p->prof.begin(s);
-          CK(launch_update_f64(P, i, s));
-          p->prof.end(s, 0, 2.0 * rows * cols * K);
+          p->prof.begin(st);
+          cudaError_t e = launch_update_f64(P, i, k_lo, k_hi, st);
+          p->prof.end(st, 0, 2.0 * rows * cols * K);
+          return e;
         }
-      }
+      } ops(P, p);
+      CK(walk_dag(st.M, ops, s, sc.aux, sc.ev, sc.lookahead));
       CK(cudaEventRecord(p->ev[2], s));
       CK(cudaEventRecord(p->ev[3], s));
     } else {
       HostStructure hs{p->h_toff, p->h_cstart};
       SplitConfig cfg = split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0);
-      rc = split_solve(p->split, P, hs, cfg, s, p->prof, p->ev[2], p->ev[3]);
+      rc = split_solve(p->split, P, hs, cfg, s, sc, p->prof, p->ev[2], p->ev[3]);
       if (rc) return rc;
     }
     // 4. post-processing: consistent scaling and normalisation
@@ -385,6 +406,13 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
   rc = rc ? rc : halloc(&p->h_status, 1);
   for (auto& e : p->ev)
     if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = PEVC_ERR_CUDA;
+  if (!rc && cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess) rc = PEVC_ERR_CUDA;
+  if (!rc) {
+    p->sev = new (std::nothrow) cudaEvent_t[2 * p->Mmax]();
+    if (!p->sev) rc = PEVC_ERR_NOMEM;
+    for (int q = 0; !rc && q < 2 * p->Mmax; ++q)
+      if (cudaEventCreateWithFlags(&p->sev[q], cudaEventDisableTiming) != cudaSuccess) rc = PEVC_ERR_CUDA;
+  }
   if (!rc && prec != PEVC_FP64) rc = split_alloc(p->split, n_max, p->tb, p->Mmax, prec);
   if (rc) {
     free_plan(p);

@@ -209,7 +209,7 @@ constexpr int kDiagTipCorr = 2;   // tiles (j, j) of a correction: zero tips, ri
 cudaError_t launch_prepass(const Problem& P, cudaStream_t s);
 cudaError_t launch_init_state(const Problem& P, cudaStream_t s);
 cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s);
-cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s);
+cudaError_t launch_update_f64(const Problem& P, int i, int k_lo, int k_hi, cudaStream_t s);
 cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const int* exX, const double* nrmX,
                                      cudaStream_t s);
 cudaError_t launch_post(const Problem& P, double* V, int ldv, int32_t* scale, bool normalise,

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 
+#include "sched.cuh"
 #include "split.cuh"
 
 namespace pevc {
@@ -243,9 +244,9 @@ constexpr int split_smem_bytes() {
   return 2 * NS * (kSplitRows + kSplitCols) * split_ld<NS>() * 2;
 }
 
-// Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij for k < kend, j >= i.
+// Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij for k_lo <= k < k_lo + gridDim.y, j >= i.
 template <int NS, int L>
-__global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, const int* __restrict__ exX,
+__global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k_lo, const int* __restrict__ exX,
                                                          const double* __restrict__ nrmX,
                                                          const __nv_bfloat16* __restrict__ As,
                                                          const int* __restrict__ eA,
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, const
   const int nsub = tb / kSplitCols;
   const int j = i + (int)blockIdx.x / nsub;
   const int sub = (int)blockIdx.x % nsub;
-  const int k = blockIdx.y;
+  const int k = k_lo + (int)blockIdx.y;
   const int cs = P.cstart[j], ce = P.cstart[j + 1];
   const int c0 = cs + sub * kSplitCols;
   if (c0 >= ce) return;
@@ -540,19 +541,61 @@ cudaError_t launch_split_X(const Problem& P, SplitWorkspace& w, int i, int q_beg
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int kend, const int* exX,
+cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                                 const double* nrmX, int ns, int levels, cudaStream_t s) {
-  if (kend <= 0) return cudaSuccess;
+  if (k_hi <= k_lo) return cudaSuccess;
   const int nsub = P.tb / kSplitCols;
-  dim3 grid((P.M - i) * nsub, kend);
+  dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   if (ns == 5 && levels == 5)
-    k_update_split<5, 5><<<grid, 256, split_smem_bytes<5>(), s>>>(P, i, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
-                                                                  w.n_max);
+    k_update_split<5, 5><<<grid, 256, split_smem_bytes<5>(), s>>>(P, i, k_lo, exX, nrmX, w.As, w.eA, w.Xs, w.F,
+                                                                  w.ns, w.n_max);
   else
-    k_update_split<3, 3><<<grid, 256, split_smem_bytes<3>(), s>>>(P, i, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
-                                                                  w.n_max);
+    k_update_split<3, 3><<<grid, 256, split_smem_bytes<3>(), s>>>(P, i, k_lo, exX, nrmX, w.As, w.eA, w.Xs, w.F,
+                                                                  w.ns, w.n_max);
   return cudaGetLastError();
 }
+
+
+// One bottom-up pass of the task graph over the augmented tiles of P: tips
+// (or tip corrections), then per block row the diagonal solves and the sliced
+// updates of everything above, walked with lookahead (sched.cuh).
+struct SplitOps : StageOps {
+  const Problem& P;
+  SplitWorkspace& w;
+  const HostStructure& hs;
+  int tip_mode, ns, levels, prods;
+  Profiler& prof;
+  SplitOps(const Problem& P_, SplitWorkspace& w_, const HostStructure& hs_, int tip_mode_, int ns_, int levels_,
+           Profiler& prof_)
+      : P(P_), w(w_), hs(hs_), tip_mode(tip_mode_), ns(ns_), levels(levels_), prods(products(ns_, levels_)),
+        prof(prof_) {}
+  cudaError_t tips(cudaStream_t s) override {
+    prof.begin(s);
+    cudaError_t e = launch_diag(P, 0, tip_mode, s);
+    prof.end(s, 1, 0.0);
+    return e;
+  }
+  cudaError_t diag(int i, cudaStream_t s) override {
+    prof.begin(s);
+    cudaError_t e = launch_diag(P, i, kDiagSolve, s);
+    prof.end(s, 1, 0.0);
+    return e;
+  }
+  cudaError_t prep(int i, cudaStream_t s) override {
+    prof.begin(s);
+    cudaError_t e = launch_split_X(P, w, i, hs.cstart[i], P.Y, P.nrm, ns, s);
+    prof.end(s, 2, 0.0);
+    return e;
+  }
+  cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t s) override {
+    const double rows = hs.toff[k_hi] - hs.toff[k_lo], cols = P.m - hs.cstart[i];
+    const double K = 2.0 * (hs.toff[i + 1] - hs.toff[i]);
+    prof.begin(s);
+    cudaError_t e = launch_update_split(P, w, i, k_lo, k_hi, P.ex, P.nrm, ns, levels, s);
+    prof.end(s, 0, 2.0 * rows * cols * K * prods);
+    return e;
+  }
+};
 
 #define SCK(call)                                              \
   do {                                                         \
@@ -560,46 +603,19 @@ cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int 
     if (_e != cudaSuccess) return PEVC_ERR_CUDA;               \
   } while (0)
 
-// One bottom-up pass of the task graph over the augmented tiles of P:
-// (tips or tip corrections), then per block row i the diagonal solves and the
-// updates of everything above.
-int run_pass(const Problem& P, SplitWorkspace& w, const HostStructure& hs, int tip_mode, int ns, int levels,
-             cudaStream_t s, Profiler& prof) {
-  const int M = P.M;
-  const int prods = products(ns, levels);
-  prof.begin(s);
-  SCK(launch_diag(P, 0, tip_mode, s));
-  prof.end(s, 1, 0.0);
-  for (int i = M - 1; i >= 0; --i) {
-    if (i < M - 1) {
-      prof.begin(s);
-      SCK(launch_diag(P, i, kDiagSolve, s));
-      prof.end(s, 1, 0.0);
-    }
-    if (i > 0) {
-      prof.begin(s);
-      SCK(launch_split_X(P, w, i, hs.cstart[i], P.Y, P.nrm, ns, s));
-      prof.end(s, 2, 0.0);
-      const double rows = hs.toff[i], cols = P.m - hs.cstart[i], K = 2.0 * (hs.toff[i + 1] - hs.toff[i]);
-      prof.begin(s);
-      SCK(launch_update_split(P, w, i, i, P.ex, P.nrm, ns, levels, s));
-      prof.end(s, 0, 2.0 * rows * cols * K * prods);
-    }
-  }
-  return 0;
-}
-
 }  // namespace
 
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
-                cudaStream_t s, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
+                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
   const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
   prof.begin(s);
   SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
   prof.end(s, 3, 0.0);
-  int rc = run_pass(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, s, prof);
-  if (rc) return rc;
+  {
+    SplitOps ops(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, prof);
+    SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+  }
   SCK(cudaEventRecord(ev_dag, s));
   if (cfg.correction) {
     // residual R = (S V D - T V B) of the first pass, accumulated tile row by
@@ -627,12 +643,14 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
       prof.end(s, 2, 0.0);
       const double rows = hs.toff[l], cols = P.m - hs.cstart[l], K = 2.0 * (hs.toff[l + 1] - hs.toff[l]);
       prof.begin(s);
-      SCK(launch_update_split(P2, w, l, l, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
+      SCK(launch_update_split(P2, w, l, 0, l, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
       prof.end(s, 0, 2.0 * rows * cols * K * prods);
     }
     // the correction: same graph, zero tips, right-hand side -R
-    rc = run_pass(P2, w, hs, kDiagTipCorr, cfg.ns1, cfg.levels1, s, prof);
-    if (rc) return rc;
+    {
+      SplitOps ops(P2, w, hs, kDiagTipCorr, cfg.ns1, cfg.levels1, prof);
+      SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+    }
     prof.begin(s);
     dim3 grid(P.M, (P.m + 7) / 8);
     k_combine<<<grid, 256, 0, s>>>(P, w.Y2, w.ex2, w.nrm2);

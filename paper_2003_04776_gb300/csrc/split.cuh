@@ -37,10 +37,16 @@ struct HostStructure {
   const int* cstart;
 };
 
+struct SchedContext {
+  cudaStream_t aux = nullptr;   // second stream for the lookahead solves
+  cudaEvent_t* ev = nullptr;    // 2 * Mmax events
+  bool lookahead = true;
+};
+
 int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
-                cudaStream_t s, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr);
+                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr);
 
 }  // namespace pevc

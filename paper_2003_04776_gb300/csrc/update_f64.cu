@@ -26,10 +26,11 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 // mode 0: stage i, tiles k < i, j >= i, X = tile (i, j) of (Xsrc, exX, nrmX).
 // mode 1: the diagonal-tile term of a residual: k = i = blockIdx.y, j >= k,
 //         with the quasi-triangular part of [S_kk T_kk] only.
-__global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int mode, const double* __restrict__ Xsrc,
-                                                    const int* __restrict__ exX, const double* __restrict__ nrmX) {
+__global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int k_lo, int mode,
+                                                    const double* __restrict__ Xsrc, const int* __restrict__ exX,
+                                                    const double* __restrict__ nrmX) {
   const int nsub = P.tb / kUpdCols;
-  const int k = blockIdx.y;
+  const int k = k_lo + (int)blockIdx.y;
   const int i = (mode == 0) ? i_stage : k;
   const int j = ((mode == 0) ? i_stage : 0) + (int)blockIdx.x / nsub;
   if (j < i) return;
@@ -172,11 +173,11 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int 
   }
 }
 
-cudaError_t launch_update_f64(const Problem& P, int i, cudaStream_t s) {
-  if (i <= 0) return cudaSuccess;
+cudaError_t launch_update_f64(const Problem& P, int i, int k_lo, int k_hi, cudaStream_t s) {
+  if (k_hi <= k_lo) return cudaSuccess;
   const int nsub = P.tb / kUpdCols;
-  dim3 grid((P.M - i) * nsub, i);
-  k_update_f64<<<grid, 256, 0, s>>>(P, i, 0, P.Y, P.ex, P.nrm);
+  dim3 grid((P.M - i) * nsub, k_hi - k_lo);
+  k_update_f64<<<grid, 256, 0, s>>>(P, i, k_lo, 0, P.Y, P.ex, P.nrm);
   return cudaGetLastError();
 }
 
@@ -185,7 +186,7 @@ cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const
   if (P.M <= 0) return cudaSuccess;
   const int nsub = P.tb / kUpdCols;
   dim3 grid(P.M * nsub, P.M);
-  k_update_f64<<<grid, 256, 0, s>>>(P, 0, 1, Xsrc, exX, nrmX);
+  k_update_f64<<<grid, 256, 0, s>>>(P, 0, 0, 1, Xsrc, exX, nrmX);
   return cudaGetLastError();
 }
 
