@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "sched.cuh"
 #include "split.cuh"
@@ -475,6 +476,12 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
                                           split_smem_bytes<5>());
     e = (a1 != cudaSuccess) ? a1 : a2;
   }
+  if (e == cudaSuccess && update_tc_setup() != 0) e = cudaErrorInvalidValue;
+  {
+    // PEVC_UPDATE_KERNEL=mma selects the legacy mma.sync update (comparisons)
+    const char* sel = getenv("PEVC_UPDATE_KERNEL");
+    w.use_tc = !(sel && sel[0] == 'm');
+  }
   w.on = e == cudaSuccess;
   if (e != cudaSuccess) {
     split_free(w);
@@ -544,6 +551,7 @@ cudaError_t launch_split_X(const Problem& P, SplitWorkspace& w, int i, int q_beg
 cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                                 const double* nrmX, int ns, int levels, cudaStream_t s) {
   if (k_hi <= k_lo) return cudaSuccess;
+  if (w.use_tc) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, s);
   const int nsub = P.tb / kSplitCols;
   dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   if (ns == 5 && levels == 5)

@@ -29,6 +29,7 @@ struct SplitWorkspace {
   double* Y2 = nullptr;          // correction tiles
   int* ex2 = nullptr;
   double* nrm2 = nullptr;
+  bool use_tc = true;            // tcgen05 update kernel (else the mma.sync one)
 };
 
 // Host copies of the structure, for launch shapes and work counts.
@@ -44,6 +45,9 @@ struct SchedContext {
 };
 
 int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
+int update_tc_setup();
+cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
+                             const double* nrmX, int ns, int levels, cudaStream_t s);
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
