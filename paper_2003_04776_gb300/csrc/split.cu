@@ -478,9 +478,9 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
   }
   if (e == cudaSuccess && update_tc_setup() != 0) e = cudaErrorInvalidValue;
   {
-    // PEVC_UPDATE_KERNEL=mma selects the legacy mma.sync update (comparisons)
+    // update kernel: mma.sync (default) or tcgen05 (PEVC_UPDATE_KERNEL=tc)
     const char* sel = getenv("PEVC_UPDATE_KERNEL");
-    w.use_tc = !(sel && sel[0] == 'm');
+    w.use_tc = sel && sel[0] == 't';
   }
   w.on = e == cudaSuccess;
   if (e != cudaSuccess) {
