@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
       __align__(16) __nv_bfloat16 pk[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) pk[u] = small_int_bf16(sl[u][p]);
-      __nv_bfloat16* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
+      __nv_bfloat16* dst = As + (((tri * ns + p) * (K2 / 8) + g) * tb + r) * 8ll;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
     }
   }
@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, 
     int_slices<NS>(bot[u], f, sb);
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-      __nv_bfloat16* col = Xs + ((long long)p * mstride + q) * K2;
-      col[kap] = small_int_bf16(st[p]);
-      col[tb + kap] = small_int_bf16(sb[p]);
+      const long long gt = (long long)p * (K2 / 8) + kap / 8, gb = (long long)p * (K2 / 8) + (tb + kap) / 8;
+      Xs[(gt * mstride + q) * 8 + (kap & 7)] = small_int_bf16(st[p]);
+      Xs[(gb * mstride + q) * 8 + ((tb + kap) & 7)] = small_int_bf16(sb[p]);
     }
   }
 }
@@ -298,21 +298,23 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
   __syncthreads();
   if (!s_any) return;
 
+  // slices are stored core-matrix-major: [slice][k group of 8][row or column][8]
   const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
   auto load_stage = [&](int st, int kb) {
     __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * LD;
     __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * LD;
     constexpr int chunks = KC / 8;                        // 16-byte pieces per row
     for (int idx = tid; idx < NS * kSplitRows * chunks; idx += 256) {
-      const int c16 = idx % chunks, r = (idx / chunks) % kSplitRows, p = idx / (chunks * kSplitRows);
+      const int r = idx % kSplitRows, c16 = (idx / kSplitRows) % chunks, p = idx / (chunks * kSplitRows);
       const bool valid = r < tb;
-      const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * c16;
+      const __nv_bfloat16* src = Abase + (((long long)p * (K2 / 8) + kb / 8 + c16) * tb + (valid ? r : 0)) * 8;
       cp_async16(a_dst + (p * kSplitRows + r) * LD + 8 * c16, src, valid);
     }
     for (int idx = tid; idx < NS * kSplitCols * chunks; idx += 256) {
-      const int c16 = idx % chunks, col = (idx / chunks) % kSplitCols, p = idx / (chunks * kSplitCols);
+      const int col = idx % kSplitCols, c16 = (idx / kSplitCols) % chunks, p = idx / (chunks * kSplitCols);
       const bool valid = col < nc;
-      const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * c16;
+      const __nv_bfloat16* src =
+          Xs + (((long long)p * (K2 / 8) + kb / 8 + c16) * mstride + c0 + (valid ? col : 0)) * 8;
       cp_async16(b_dst + (p * kSplitCols + col) * LD + 8 * c16, src, valid);
     }
   };
@@ -476,7 +478,21 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
                                           split_smem_bytes<5>());
     e = (a1 != cudaSuccess) ? a1 : a2;
   }
+  w.max_chunks = w.n_max / 48 + Mmax + 1;
+  if (e == cudaSuccess) e = al((void**)&w.chunk_c0_48, (size_t)w.max_chunks * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.chunk_j_48, (size_t)w.max_chunks * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.chunk_c0_64, (size_t)w.max_chunks * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.chunk_j_64, (size_t)w.max_chunks * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w.h_chunk_first48, (size_t)(Mmax + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w.h_chunk_first64, (size_t)(Mmax + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w.h_chunks, (size_t)4 * w.max_chunks * sizeof(int));
+  if (e == cudaSuccess) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
   if (e == cudaSuccess && update_tc_setup() != 0) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess && make_tensor_maps(w) != 0) e = cudaErrorInvalidValue;
   {
     // update kernel: mma.sync (default) or tcgen05 (PEVC_UPDATE_KERNEL=tc)
     const char* sel = getenv("PEVC_UPDATE_KERNEL");
@@ -491,9 +507,14 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
 }
 
 void split_free(SplitWorkspace& w) {
-  void* ptrs[] = {w.As, w.eA, w.Xs, w.F, w.Y2, w.ex2, w.nrm2};
+  void* ptrs[] = {w.As, w.eA, w.Xs, w.F, w.Y2, w.ex2, w.nrm2, w.chunk_c0_48, w.chunk_j_48, w.chunk_c0_64, w.chunk_j_64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  void* hp[] = {w.h_chunk_first48, w.h_chunk_first64, w.h_chunks};
+  for (void* p : hp)
+    if (p) cudaFreeHost(p);
+  w.chunk_c0_48 = w.chunk_j_48 = w.chunk_c0_64 = w.chunk_j_64 = nullptr;
+  w.h_chunk_first48 = w.h_chunk_first64 = w.h_chunks = nullptr;
   w.As = nullptr;
   w.eA = nullptr;
   w.Xs = nullptr;
@@ -616,6 +637,27 @@ struct SplitOps : StageOps {
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
+  if (w.use_tc) {
+    // output column chunks (width 48 and 64) inside every column tile
+    int* h48c = w.h_chunks;
+    int* h48j = h48c + w.max_chunks;
+    int* h64c = h48j + w.max_chunks;
+    int* h64j = h64c + w.max_chunks;
+    int n48 = 0, n64 = 0;
+    for (int j = 0; j < P.M; ++j) {
+      w.h_chunk_first48[j] = n48;
+      w.h_chunk_first64[j] = n64;
+      for (int c = hs.cstart[j]; c < hs.cstart[j + 1]; c += 48) { h48c[n48] = c; h48j[n48] = j; ++n48; }
+      for (int c = hs.cstart[j]; c < hs.cstart[j + 1]; c += 64) { h64c[n64] = c; h64j[n64] = j; ++n64; }
+    }
+    w.h_chunk_first48[P.M] = n48;
+    w.h_chunk_first64[P.M] = n64;
+    if (n48 > w.max_chunks || n64 > w.max_chunks) return PEVC_ERR_CUDA;
+    SCK(cudaMemcpyAsync(w.chunk_c0_48, h48c, (size_t)n48 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCK(cudaMemcpyAsync(w.chunk_j_48, h48j, (size_t)n48 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCK(cudaMemcpyAsync(w.chunk_c0_64, h64c, (size_t)n64 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCK(cudaMemcpyAsync(w.chunk_j_64, h64j, (size_t)n64 * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
   const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
   prof.begin(s);
   SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));

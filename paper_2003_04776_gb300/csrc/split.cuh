@@ -30,6 +30,20 @@ struct SplitWorkspace {
   int* ex2 = nullptr;
   double* nrm2 = nullptr;
   bool use_tc = true;            // tcgen05 update kernel (else the mma.sync one)
+  int nsm = 0;
+  // TMA tensor maps over As and Xs (CUtensorMap storage: 128 bytes, 64-aligned)
+  alignas(64) unsigned char tmA[128];
+  alignas(64) unsigned char tmB48[128];
+  alignas(64) unsigned char tmB64[128];
+  // output column chunks of width 48 / 64 inside each column tile (per solve)
+  int* chunk_c0_48 = nullptr;
+  int* chunk_j_48 = nullptr;
+  int* chunk_c0_64 = nullptr;
+  int* chunk_j_64 = nullptr;
+  int* h_chunk_first48 = nullptr;   // host [Mmax + 1]
+  int* h_chunk_first64 = nullptr;
+  int* h_chunks = nullptr;          // host staging
+  int max_chunks = 0;
 };
 
 // Host copies of the structure, for launch shapes and work counts.
@@ -46,6 +60,7 @@ struct SchedContext {
 
 int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
 int update_tc_setup();
+int make_tensor_maps(SplitWorkspace& w);
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                              const double* nrmX, int ns, int levels, cudaStream_t s);
 void split_free(SplitWorkspace& w);

@@ -1,238 +1,350 @@
 // update_tc.cu -- the split-precision update (Section 3, kernel 2) on the
-// fifth-generation tensor cores:
+// fifth-generation tensor cores, fed by TMA:
 //     Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij,   k in [k_lo, k_hi), j >= i,
-// with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).  One CTA
-// (4 warps) owns 128 rows x 64 columns.  Every slice product p x q with
-// p + q < L is a tcgen05.mma (M=128, N=64, K=16, BF16 in, FP32 out) into the
-// accumulator of its level p + q, held in tensor memory; one thread issues the
-// MMAs, cp.async double-buffers the K chunks in the canonical K-major layout,
-// an mbarrier per buffer reports MMA completion (every wait is bounded and
-// reports PEVC_ERR_TIMEOUT through the status word).  The epilogue reads the
-// level accumulators with tcgen05.ld, combines them exactly as one integer and
-// applies the augmented-tile scales (Algorithms 2 and 3 of Section 4) with
-// one FP64 conversion and one FP64 subtraction per element.
+// with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).
+//
+// Persistent, warp-specialised CTA of 6 warps:
+//   warp 0   TMA producer: 3-D tensor-map boxes (8 elements x rows x K groups)
+//            land directly in the canonical K-major core-matrix layout;
+//   warp 1   tensor-memory owner and MMA issuer: every slice product p x q
+//            with p + q < L is a tcgen05.mma (M=128, N=NCOL, K=16, BF16 in,
+//            FP32 out) into the accumulator of its level p + q;
+//   warps 2-5 epilogue: tcgen05.ld of the level accumulators, exact integer
+//            recombination, augmented-tile scales (Algorithms 2 and 3 of
+//            Section 4), one FP64 conversion and one FP64 subtraction per
+//            element, new column maxima.
+// Shared-memory stages form an mbarrier ring (full / empty); the level
+// accumulators are double-buffered in tensor memory so that the epilogue of
+// one output tile overlaps the MMAs of the next.  Every wait is bounded: a
+// wait that runs out sets PEVC_ERR_TIMEOUT in the status word and the CTA
+// winds down (all roles run out of bounded waits, tensor memory is freed).
+#include <cuda.h>
+
 #include "split.cuh"
 #include "tc.cuh"
 
 namespace pevc {
 
-constexpr int kTcRows = 128;
-constexpr int kTcCols = 64;
-constexpr int kTcKc = 32;                              // K per pipeline stage
-constexpr int kTcLboA = (kTcRows / 8) * 128;           // bytes between K-adjacent core matrices (A)
-constexpr int kTcLboB = (kTcCols / 8) * 128;           // (B)
-constexpr int kTcSbo = 128;                            // bytes between M/N-adjacent core matrices
-constexpr int kTcSliceA = (kTcKc / 8) * kTcLboA;       // one slice of one stage
-constexpr int kTcSliceB = (kTcKc / 8) * kTcLboB;
-constexpr long kTcWaitLimit = 1L << 22;
+constexpr int kTmRows = 128;
+constexpr int kTmKc = 32;                        // K per stage
+constexpr int kTmGroups = kTmKc / 8;             // core-matrix columns per stage
+constexpr int kTmLboA = kTmRows * 16;            // bytes between K-adjacent core matrices of A
+constexpr int kTmSbo = 128;                      // bytes between M/N-adjacent core matrices
+constexpr long kTmWait = 1L << 22;
 
-template <int NS>
-__host__ __device__ constexpr int tc_stage_bytes() { return NS * (kTcSliceA + kTcSliceB); }
-template <int NS>
-__host__ __device__ constexpr int tc_smem_bytes() { return 2 * tc_stage_bytes<NS>(); }
-template <int L>
-__host__ __device__ constexpr uint32_t tc_tmem_cols() {
-  return (L * kTcCols <= 32) ? 32 : (L * kTcCols <= 64) ? 64 : (L * kTcCols <= 128) ? 128 : (L * kTcCols <= 256) ? 256 : 512;
+template <int NS, int NCOL>
+struct TmGeom {
+  static constexpr int lbo_b = NCOL * 16;
+  static constexpr int slice_a = kTmGroups * kTmLboA;
+  static constexpr int slice_b = kTmGroups * lbo_b;
+  static constexpr int stage = NS * (slice_a + slice_b);
+  static constexpr int stages = (NS >= 5) ? 3 : 4;
+  static constexpr int smem = stages * stage + 1024;   // + barriers
+};
+
+template <int L, int NCOL>
+__host__ __device__ constexpr uint32_t tm_tmem_cols() {
+  return (2 * L * NCOL <= 128) ? 128 : (2 * L * NCOL <= 256) ? 256 : 512;
 }
 
-template <int NS, int L>
-__global__ void __launch_bounds__(128) k_update_tc(Problem P, int i, int k_lo, const int* __restrict__ exX,
-                                                   const double* __restrict__ nrmX,
-                                                   const __nv_bfloat16* __restrict__ As,
-                                                   const int* __restrict__ eA,
-                                                   const __nv_bfloat16* __restrict__ Xs,
-                                                   const int* __restrict__ F, int ns, int mstride) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)));
+}
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;\n" ::); }
+
+struct TmTiles {
+  const int* chunk_c0;   // first output column of every column chunk (global list)
+  const int* chunk_j;    // its column tile
+  int chunk_first;       // first chunk of column tile i
+  int nchunks;           // chunks of column tiles >= i
+  int k_lo, nk;
+};
+
+template <int NS, int L, int NCOL>
+__global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
+                                                       const double* __restrict__ nrmX, const int* __restrict__ eA,
+                                                       const int* __restrict__ F, int ns,
+                                                       const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB) {
+  using G = TmGeom<NS, NCOL>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int tb = P.tb, K2 = 2 * tb;
-  const int nsub = (tb + kTcCols - 1) / kTcCols;
-  const int j = i + (int)blockIdx.x / nsub;
-  const int sub = (int)blockIdx.x % nsub;
-  const int k = k_lo + (int)blockIdx.y;
-  const int cs = P.cstart[j], ce = P.cstart[j + 1];
-  const int c0 = cs + sub * kTcCols;
-  if (c0 >= ce) return;
-  const int nc = min(kTcCols, ce - c0);
-  const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
-  double* Yt = tile_ptr(P, k, j);
-  const long long tri = tri_index(k, i);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::stages * G::stage);
+  uint64_t* empty = full + G::stages;
+  uint64_t* tfull = empty + G::stages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  __shared__ int s_on[2][NCOL], s_sY[2][NCOL], s_sc[2][NCOL], s_e[2][NCOL], s_yz[2][NCOL];
+  __shared__ unsigned long long s_key[2][NCOL];
+  __shared__ int s_fail, s_stop;
+  volatile int* fail = &s_fail;
+
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tb = P.tb, K2 = 2 * tb;
+  const int nkc = K2 / kTmKc;
+  const int total = tt.nk * tt.nchunks;
+  constexpr uint32_t kCols = tm_tmem_cols<L, NCOL>();
+  constexpr uint32_t kTx = (uint32_t)G::stage;
 
-  __shared__ int s_sY[kTcCols], s_sc[kTcCols], s_e[kTcCols], s_on[kTcCols], s_yz[kTcCols];
-  __shared__ unsigned long long s_key[kTcCols];
-  __shared__ int s_eA[kTcRows];
-  __shared__ int s_any, s_fail;
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar[2];
-
-  if (tid == 0) { s_any = 0; s_fail = 0; }
-  __syncthreads();
-  if (tid < kTcCols) {
-    int on = 0, sY = 0, sX = 0, en = 0;
-    bool yz = true;
-    if (tid < nc) {
-      const int q = c0 + tid;
-      on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
-      if (on && F[q] == kExpZero) on = 0;
-      s_sc[tid] = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
-    }
-    s_on[tid] = on;
-    s_sY[tid] = sY;
-    s_e[tid] = en;
-    s_yz[tid] = yz ? 1 : 0;
-    s_key[tid] = 0ull;
-    if (on) atomicOr(&s_any, 1);
-  }
-  s_eA[tid] = (tid < tb) ? eA[tri * tb + tid] : 0;
-  __syncthreads();
-  if (!s_any) return;
-
-  constexpr uint32_t kCols = tc_tmem_cols<L>();
-  if (warp == 0) tc_alloc(&s_tmem, kCols);
   if (tid == 0) {
-    mbar_init(&s_mbar[0], 1);
-    mbar_init(&s_mbar[1], 1);
+    for (int s = 0; s < G::stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    s_fail = 0;
+    s_stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
+  if (warp == 1) tc_alloc(tmem_slot, kCols);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = s_tmem;
+  const uint32_t tmem = *tmem_slot;
 
-  const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
-  auto load_stage = [&](int st, int kb) {
-    unsigned char* a_dst = smem + st * tc_stage_bytes<NS>();
-    unsigned char* b_dst = a_dst + NS * kTcSliceA;
-    constexpr int groups = kTcKc / 8;
-    for (int idx = tid; idx < NS * kTcRows * groups; idx += 128) {
-      const int g = idx % groups, r = (idx / groups) % kTcRows, p = idx / (groups * kTcRows);
-      const bool valid = r < tb;
-      const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * g;
-      cp_async16_zfill(a_dst + p * kTcSliceA + g * kTcLboA + (r >> 3) * kTcSbo + (r & 7) * 16, src, valid);
-    }
-    for (int idx = tid; idx < NS * kTcCols * groups; idx += 128) {
-      const int g = idx % groups, col = (idx / groups) % kTcCols, p = idx / (groups * kTcCols);
-      const bool valid = col < nc;
-      const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * g;
-      cp_async16_zfill(b_dst + p * kTcSliceB + g * kTcLboB + (col >> 3) * kTcSbo + (col & 7) * 16, src, valid);
-    }
-  };
-
-  constexpr uint32_t idesc = idesc_bf16_f32(kTcRows, kTcCols);
-  const int nchunks = K2 / kTcKc;
-  uint32_t started = 0;   // levels whose accumulator already holds data (issuing thread only)
-  bool ok = true;
-  load_stage(0, 0);
-  cp_async_commit_group();
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int st = ch & 1;
-    if (ch + 1 < nchunks) {
-      if (ch >= 1) {   // the buffer of chunk ch+1 was read by the MMAs of chunk ch-1
-        if (!mbar_wait_bounded(&s_mbar[st ^ 1], ((ch - 1) >> 1) & 1, kTcWaitLimit)) {
-          atomicExch(&s_fail, 1);
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
+        const int k = tt.k_lo + t / tt.nchunks;
+        const int ch = tt.chunk_first + t % tt.nchunks;
+        const int c0 = tt.chunk_c0[ch];
+        const int a_plane = (int)(tri_index(k, i) * ns);
+        for (int kc = 0; kc < nkc; ++kc) {
+          if (!mbar_wait_bounded(&empty[s], ph ^ 1u, kTmWait)) { *fail = 1; break; }
+          mbar_expect_tx(&full[s], kTx);
+          unsigned char* a_dst = smem + s * G::stage;
+          unsigned char* b_dst = a_dst + NS * G::slice_a;
+          for (int p = 0; p < NS; ++p) {
+            tma_load_4d(a_dst + p * G::slice_a, &tmA, 0, 0, kc * kTmGroups, a_plane + p, &full[s]);
+            tma_load_4d(b_dst + p * G::slice_b, &tmB, 0, c0, kc * kTmGroups, p, &full[s]);
+          }
+          if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
       }
-      load_stage(st ^ 1, (ch + 1) * kTcKc);
     }
-    cp_async_commit_group();
-    cp_async_wait_group<1>();
-    fence_async_smem();
-    __syncthreads();
-    if (s_fail) { ok = false; break; }
-    if (tid == 0) {
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(kTmRows, NCOL);
+      int s = 0, buf = 0;
+      uint32_t ph = 0, aph = 0;
+      for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
+        if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, kTmWait)) { *fail = 1; break; }
+        tc_fence_after();
+        const uint32_t acc0 = tmem + (uint32_t)(buf * L * NCOL);
+        uint32_t started = 0;
+        for (int kc = 0; kc < nkc; ++kc) {
+          if (!mbar_wait_bounded(&full[s], ph, kTmWait)) { *fail = 1; break; }
+          tc_fence_after();
+          const uint32_t a_base = smem_addr(smem + s * G::stage);
+          const uint32_t b_base = a_base + NS * G::slice_a;
+#pragma unroll
+          for (int kk = 0; kk < kTmKc / 16; ++kk)
+#pragma unroll
+            for (int p = 0; p < NS; ++p)
+#pragma unroll
+              for (int q = 0; q < NS; ++q)
+                if (p + q < L) {
+                  const uint64_t ad = smem_desc(a_base + p * G::slice_a + kk * 2 * kTmLboA, kTmLboA, kTmSbo);
+                  const uint64_t bd = smem_desc(b_base + q * G::slice_b + kk * 2 * G::lbo_b, G::lbo_b, kTmSbo);
+                  tc_mma_bf16(acc0 + (uint32_t)((p + q) * NCOL), ad, bd, idesc, (started >> (p + q)) & 1u);
+                  started |= 1u << (p + q);
+                }
+          tc_commit(&empty[s]);             // frees the stage once these MMAs completed
+          if (++s == G::stages) { s = 0; ph ^= 1u; }
+        }
+        if (*fail) break;
+        tc_commit(&tfull[buf]);             // the tile's accumulators are complete
+        buf ^= 1;
+        if (buf == 0) aph ^= 1u;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int et = tid - 64;                          // 0..127
+    const int quarter = warp & 3;                     // tensor-memory lane quarter of this warp
+    const int row = 32 * quarter + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      // a uniform stop decision for the four epilogue warps
+      if (et == 0) s_stop = *fail;
+      epi_barrier();
+      if (s_stop) break;
+      const int k = tt.k_lo + t / tt.nchunks;
+      const int ch = tt.chunk_first + t % tt.nchunks;
+      const int j = tt.chunk_j[ch];
+      const int c0 = tt.chunk_c0[ch];
+      const int cs = P.cstart[j];
+      const int nc = min(NCOL, P.cstart[j + 1] - c0);
+      const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
+      double* Yt = tile_ptr(P, k, j);
+      // per-column consolidation + protection while the MMAs run
+      if (et < NCOL) {
+        int on = 0, sY = 0, sX = 0, en = 0;
+        bool yz = true;
+        if (et < nc) {
+          const int q = c0 + et;
+          on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
+          if (on && F[q] == kExpZero) on = 0;
+          s_sc[buf][et] = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
+        }
+        s_on[buf][et] = on;
+        s_sY[buf][et] = sY;
+        s_e[buf][et] = en;
+        s_yz[buf][et] = yz ? 1 : 0;
+        s_key[buf][et] = 0ull;
+      }
+      const int erow = (row < tb) ? eA[tri_index(k, i) * tb + row] : 0;
+      epi_barrier();
+      const bool ok = mbar_wait_bounded(&tfull[buf], aph, kTmWait);
+      if (!ok) *fail = 1;
       tc_fence_after();
-      const uint32_t a_base = smem_addr(smem + st * tc_stage_bytes<NS>());
-      const uint32_t b_base = a_base + NS * kTcSliceA;
+      if (ok) {
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * L * NCOL);
+        for (int cb = 0; cb < NCOL; cb += 16) {
+          uint32_t lv[L][16];
 #pragma unroll
-      for (int kk = 0; kk < kTcKc / 16; ++kk) {
+          for (int s = 0; s < L; ++s) tc_ld16(lane_base + (uint32_t)(s * NCOL + cb), lv[s]);
+          tc_wait_ld();
 #pragma unroll
-        for (int p = 0; p < NS; ++p)
+          for (int u = 0; u < 16; ++u) {
+            const int col = cb + u;
+            const bool con = col < nc && s_on[buf][col];
+            unsigned long long key = 0;
+            if (con && row < hk) {
+              long long tv = 0;
 #pragma unroll
-          for (int q = 0; q < NS; ++q) {
-            if (p + q < L) {
-              const int s = p + q;
-              const uint64_t ad = smem_desc(a_base + p * kTcSliceA + kk * 2 * kTcLboA, kTcLboA, kTcSbo);
-              const uint64_t bd = smem_desc(b_base + q * kTcSliceB + kk * 2 * kTcLboB, kTcLboB, kTcSbo);
-              tc_mma_bf16(tmem + s * kTcCols, ad, bd, idesc, (started >> s) & 1u);
-              started |= 1u << s;
+              for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
+              double* ycol = Yt + (size_t)(c0 + col - cs) * tb;
+              const double prod = pow2_scale((double)tv, erow + s_sc[buf][col]);
+              const double yold = s_yz[buf][col] ? 0.0 : pow2_scale(ycol[row], s_sY[buf][col]);
+              const double ynew = yold - prod;
+              ycol[row] = ynew;
+              key = abs_key(ynew);
+            }
+            if (con) {
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+              if (lane == 0 && key) atomicMax(&s_key[buf][col], key);
             }
           }
-      }
-      tc_commit(&s_mbar[st]);
-    }
-  }
-  cp_async_wait_group<0>();
-  if (ok) {
-    const int last = nchunks - 1;
-    if (!mbar_wait_bounded(&s_mbar[last & 1], (last >> 1) & 1, kTcWaitLimit)) atomicExch(&s_fail, 1);
-  }
-  tc_fence_after();
-  __syncthreads();
-  const bool good = ok && !s_fail;
-
-  if (good) {
-    const int row = 32 * warp + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int cb = 0; cb < kTcCols; cb += 16) {
-      uint32_t lv[L][16];
-#pragma unroll
-      for (int s = 0; s < L; ++s) tc_ld16(lane_base + s * kTcCols + cb, lv[s]);
-      tc_wait_ld();
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int col = cb + u;
-        unsigned long long key = 0;
-        const bool con = col < nc && s_on[col];
-        if (con && row < hk) {
-          long long t = 0;
-#pragma unroll
-          for (int s = 0; s < L; ++s) t = (t << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
-          double* ycol = Yt + (size_t)(c0 + col - cs) * tb;
-          const double prod = pow2_scale((double)t, s_eA[row] + s_sc[col]);
-          const double yold = s_yz[col] ? 0.0 : pow2_scale(ycol[row], s_sY[col]);
-          const double ynew = yold - prod;
-          ycol[row] = ynew;
-          key = abs_key(ynew);
-        }
-        if (con) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-          if (lane == 0 && key) atomicMax(&s_key[col], key);
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      epi_barrier();
+      if (ok && et < nc && s_on[buf][et]) {
+        const long long idx = (long long)k * P.m + c0 + et;
+        P.nrm[idx] = __longlong_as_double((long long)s_key[buf][et]);
+        P.ex[idx] = s_e[buf][et];
+      }
+      buf ^= 1;
+      if (buf == 0) aph ^= 1u;
     }
-  } else if (tid == 0) {
-    atomicOr(P.status, kStTimeout);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, kCols);
-  if (good && tid < nc && s_on[tid]) {
-    const long long idx = (long long)k * P.m + c0 + tid;
-    P.nrm[idx] = __longlong_as_double((long long)s_key[tid]);
-    P.ex[idx] = s_e[tid];
+  if (*fail && tid == 0) atomicOr(P.status, kStTimeout);
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, kCols);
   }
 }
 
+// ------------------------------------------------------------------ host
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
 int update_tc_setup() {
-  cudaError_t a = cudaFuncSetAttribute(k_update_tc<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc_smem_bytes<3>());
-  cudaError_t b = cudaFuncSetAttribute(k_update_tc<5, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc_smem_bytes<5>());
-  return (a == cudaSuccess && b == cudaSuccess) ? 0 : PEVC_ERR_CUDA;
+  cudaError_t a = cudaFuncSetAttribute(k_update_tma<5, 5, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TmGeom<5, 48>::smem);
+  cudaError_t b = cudaFuncSetAttribute(k_update_tma<3, 3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TmGeom<3, 64>::smem);
+  return (a == cudaSuccess && b == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
+}
+
+// Tensor maps over the core-matrix-major slice buffers:
+//   A: [tile * ns + slice][K group][row][8]  -> dims {8, tb, 2tb/8, tiles*ns}, box {8, 128, 4, 1}
+//   B: [slice][K group][column][8]           -> dims {8, n_max, 2tb/8, ns},    box {8, NCOL, 4, 1}
+int make_tensor_maps(SplitWorkspace& w) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return PEVC_ERR_CUDA;
+  const cuuint64_t tb = (cuuint64_t)w.tb, kg = (cuuint64_t)(2 * w.tb / 8);
+  {
+    cuuint64_t dims[4] = {8, tb, kg, (cuuint64_t)(w.tiles * w.ns)};
+    cuuint64_t strides[3] = {16, tb * 16, kg * tb * 16};
+    cuuint32_t box[4] = {8, (cuuint32_t)kTmRows, (cuuint32_t)kTmGroups, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(reinterpret_cast<CUtensorMap*>(w.tmA), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.As, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PEVC_ERR_CUDA;
+  }
+  for (int v = 0; v < 2; ++v) {
+    const cuuint32_t ncol = v == 0 ? 48 : 64;
+    cuuint64_t dims[4] = {8, (cuuint64_t)w.n_max, kg, (cuuint64_t)w.ns};
+    cuuint64_t strides[3] = {16, (cuuint64_t)w.n_max * 16, kg * (cuuint64_t)w.n_max * 16};
+    cuuint32_t box[4] = {8, ncol, (cuuint32_t)kTmGroups, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmB48 : w.tmB64), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.Xs,
+            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PEVC_ERR_CUDA;
+  }
+  return 0;
 }
 
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                              const double* nrmX, int ns, int levels, cudaStream_t s) {
   if (k_hi <= k_lo) return cudaSuccess;
-  const int nsub = (P.tb + kTcCols - 1) / kTcCols;
-  dim3 grid((P.M - i) * nsub, k_hi - k_lo);
-  if (ns == 5 && levels == 5)
-    k_update_tc<5, 5><<<grid, 128, tc_smem_bytes<5>(), s>>>(P, i, k_lo, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
-                                                             w.n_max);
-  else
-    k_update_tc<3, 3><<<grid, 128, tc_smem_bytes<3>(), s>>>(P, i, k_lo, exX, nrmX, w.As, w.eA, w.Xs, w.F, w.ns,
-                                                             w.n_max);
+  const bool five = (ns == 5 && levels == 5);
+  const int* first = five ? w.h_chunk_first48 : w.h_chunk_first64;
+  TmTiles tt;
+  tt.chunk_c0 = five ? w.chunk_c0_48 : w.chunk_c0_64;
+  tt.chunk_j = five ? w.chunk_j_48 : w.chunk_j_64;
+  tt.chunk_first = first[i];
+  tt.nchunks = first[P.M] - first[i];
+  tt.k_lo = k_lo;
+  tt.nk = k_hi - k_lo;
+  const int total = tt.nk * tt.nchunks;
+  if (total <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(total < w.nsm ? total : w.nsm);
+  const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA);
+  if (five) {
+    const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB48);
+    k_update_tma<5, 5, 48><<<grid, 192, TmGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+  } else {
+    const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB64);
+    k_update_tma<3, 3, 64><<<grid, 192, TmGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+  }
   return cudaGetLastError();
 }
 
