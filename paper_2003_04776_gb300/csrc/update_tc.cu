@@ -209,11 +209,21 @@ __global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles
       }
       const int erow = (row < tb) ? eA[tri_index(k, i) * tb + row] : 0;
       epi_barrier();
+      // this thread's row of Y for every column of the tile, loaded (all
+      // loads in flight at once) while the tile's MMAs run
+      double yv[NCOL];
+#pragma unroll
+      for (int col = 0; col < NCOL; ++col) {
+        yv[col] = 0.0;
+        if (col < nc && row < hk && s_on[buf][col] && !s_yz[buf][col])
+          yv[col] = Yt[(size_t)(c0 + col - cs) * tb + row];
+      }
       const bool ok = mbar_wait_bounded(&tfull[buf], aph, kTmWait);
       if (!ok) *fail = 1;
       tc_fence_after();
       if (ok) {
         const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * L * NCOL);
+#pragma unroll
         for (int cb = 0; cb < NCOL; cb += 16) {
           uint32_t lv[L][16];
 #pragma unroll
@@ -228,11 +238,10 @@ __global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles
               long long tv = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
-              double* ycol = Yt + (size_t)(c0 + col - cs) * tb;
               const double prod = pow2_scale((double)tv, erow + s_sc[buf][col]);
-              const double yold = s_yz[buf][col] ? 0.0 : pow2_scale(ycol[row], s_sY[buf][col]);
+              const double yold = pow2_scale(yv[col], s_sY[buf][col]);
               const double ynew = yold - prod;
-              ycol[row] = ynew;
+              Yt[(size_t)(c0 + col - cs) * tb + row] = ynew;
               key = abs_key(ynew);
             }
             if (con) {
