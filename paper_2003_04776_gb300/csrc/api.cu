@@ -47,6 +47,10 @@ struct pevc_plan_s {
   signed char* kind = nullptr;
   unsigned* status = nullptr;
   double* subd = nullptr;
+  int* dperm = nullptr;      // diagonal-kernel chunks (see Problem)
+  int* dcpos = nullptr;
+  int* dccnt = nullptr;
+  int* dcfirst = nullptr;
   // pinned host staging
   double* h_subd = nullptr;
   int32_t* h_sel = nullptr;
@@ -56,6 +60,11 @@ struct pevc_plan_s {
   int* h_ccol = nullptr;
   signed char* h_kind = nullptr;
   unsigned* h_status = nullptr;
+  int* h_dperm = nullptr;
+  int* h_dcpos = nullptr;
+  int* h_dccnt = nullptr;
+  int* h_dcfirst = nullptr;
+  int dchunk_max = 0;
   cudaEvent_t ev[6] = {};
   double stats[8] = {};
   SplitWorkspace split;
@@ -114,10 +123,12 @@ int halloc(Tp** p, size_t count) {
 void free_plan(pevc_plan_t p) {
   if (!p) return;
   void* dev[] = {p->Y, p->ex, p->nrm, p->EA, p->tcS, p->tcT, p->gmax, p->ca, p->cb, p->cbeta,
-                 p->blk, p->toff, p->cstart, p->ccol, p->kind, p->status, p->subd};
+                 p->blk, p->toff, p->cstart, p->ccol, p->kind, p->status, p->subd,
+                 p->dperm, p->dcpos, p->dccnt, p->dcfirst};
   for (void* d : dev)
     if (d) cudaFree(d);
-  void* host[] = {p->h_subd, p->h_sel, p->h_blk, p->h_toff, p->h_cstart, p->h_ccol, p->h_kind, p->h_status};
+  void* host[] = {p->h_subd, p->h_sel, p->h_blk, p->h_toff, p->h_cstart, p->h_ccol, p->h_kind, p->h_status,
+                  p->h_dperm, p->h_dcpos, p->h_dccnt, p->h_dcfirst};
   for (void* h : host)
     if (h) cudaFreeHost(h);
   for (auto& e : p->ev)
@@ -139,7 +150,7 @@ void free_plan(pevc_plan_t p) {
 }
 
 struct Structure {
-  int M = 0, m = 0;
+  int M = 0, m = 0, nchunks = 0;
 };
 
 // Host-side structure analysis: block pattern from the subdiagonal, tile
@@ -190,6 +201,34 @@ int analyse(pevc_plan_t p, int n, bool has_sel, Structure& st) {
   }
   st.M = M;
   st.m = m;
+  // diagonal-kernel chunks: per column tile, real columns first, then the
+  // complex pairs; chunks of at most 16 columns, never mixing the two kinds
+  const int kCB = 16;
+  int nch = 0, maxc = 0;
+  for (int j = 0; j < M; ++j) {
+    p->h_dcfirst[j] = nch;
+    const int cs = p->h_cstart[j], ce = p->h_cstart[j + 1];
+    int pos = cs;
+    for (int q = cs; q < ce; ++q)
+      if (p->h_kind[q] == 0) p->h_dperm[pos++] = q - cs;
+    const int nreal = pos - cs;
+    for (int q = cs; q < ce; ++q)
+      if (p->h_kind[q] != 0) p->h_dperm[pos++] = q - cs;
+    for (int s0 = 0; s0 < nreal; s0 += kCB) {
+      p->h_dcpos[nch] = cs + s0;
+      p->h_dccnt[nch] = std::min(kCB, nreal - s0);
+      ++nch;
+    }
+    for (int s0 = nreal; s0 < ce - cs; s0 += kCB) {   // kCB is even: pairs stay whole
+      p->h_dcpos[nch] = cs + s0;
+      p->h_dccnt[nch] = std::min(kCB, ce - cs - s0);
+      ++nch;
+    }
+    maxc = std::max(maxc, nch - p->h_dcfirst[j]);
+  }
+  p->h_dcfirst[M] = nch;
+  p->dchunk_max = maxc;
+  st.nchunks = nch;
   return 0;
 }
 
@@ -220,6 +259,11 @@ Problem make_problem(pevc_plan_t p, const double* S, int lds, const double* T, i
   P.ex = p->ex;
   P.nrm = p->nrm;
   P.status = p->status;
+  P.dperm = p->dperm;
+  P.dchunk_pos = p->dcpos;
+  P.dchunk_cnt = p->dccnt;
+  P.dchunk_first = p->dcfirst;
+  P.dchunk_max = p->dchunk_max;
   return P;
 }
 
@@ -256,7 +300,11 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   if (st.m > 0) {
     CK(cudaMemcpyAsync(p->ccol, p->h_ccol, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(p->kind, p->h_kind, (size_t)st.m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->dperm, p->h_dperm, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->dcpos, p->h_dcpos, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->dccnt, p->h_dccnt, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, s));
   }
+  CK(cudaMemcpyAsync(p->dcfirst, p->h_dcfirst, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), s));
   CK(cudaMemsetAsync(p->gmax, 0, sizeof(double), s));
   Problem P = make_problem(p, S, lds, T, ldt, n, st);
@@ -396,6 +444,14 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
   rc = rc ? rc : dalloc(&p->kind, nm);
   rc = rc ? rc : dalloc(&p->status, 1);
   rc = rc ? rc : dalloc(&p->subd, nm);
+  rc = rc ? rc : dalloc(&p->dperm, nm);
+  rc = rc ? rc : dalloc(&p->dcpos, nm + M);
+  rc = rc ? rc : dalloc(&p->dccnt, nm + M);
+  rc = rc ? rc : dalloc(&p->dcfirst, M + 1);
+  rc = rc ? rc : halloc(&p->h_dperm, nm);
+  rc = rc ? rc : halloc(&p->h_dcpos, nm + M);
+  rc = rc ? rc : halloc(&p->h_dccnt, nm + M);
+  rc = rc ? rc : halloc(&p->h_dcfirst, M + 1);
   rc = rc ? rc : halloc(&p->h_subd, nm);
   rc = rc ? rc : halloc(&p->h_sel, nm);
   rc = rc ? rc : halloc(&p->h_blk, nm);

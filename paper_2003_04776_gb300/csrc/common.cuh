@@ -139,6 +139,13 @@ struct Problem {
   int* ex;                  // [M*m] exponent of column q in row tile k
   double* nrm;              // [M*m] max |stored| of column q in row tile k
   unsigned* status;         // device status bits
+  // diagonal-kernel column chunks: real columns and complex pairs grouped
+  // apart, so one CTA's pivot work is never divergent
+  const int* dperm;         // [m] local column (within its column tile) at every position
+  const int* dchunk_pos;    // first position of each chunk
+  const int* dchunk_cnt;    // columns in each chunk
+  const int* dchunk_first;  // [M+1] first chunk of each column tile
+  int dchunk_max;           // most chunks in one column tile
 };
 
 __device__ __forceinline__ double* tile_ptr(const Problem& P, int k, int j) {
