@@ -52,22 +52,37 @@ def as_complex(V, kinds):
 
 
 def residuals(S, T, V, kinds, pos, a, b, beta):
-    """Relative residual of every eigenvector (one value per output column)."""
+    """Relative residual of every eigenvector (one value per output column).
+
+    S V and T V are formed with two real matrix products (library calls);
+    a pair's complex vector z = x + i y gives S z = S x + i S y."""
     S = np.asarray(S)
     T = np.asarray(T)
+    V = np.asarray(V)
+    kinds = np.asarray(kinds)
+    pos = np.asarray(pos)
     nS = np.abs(S).sum(axis=1).max()
     nT = np.abs(T).sum(axis=1).max()
-    vecs, cols = as_complex(V, kinds)
+    SV = S @ V
+    TV = T @ V
     res = np.zeros(len(kinds))
-    for z, c in zip(vecs, cols):
+    for c, k in enumerate(kinds):
+        if k == 2:
+            continue
         p = pos[c]
         al = complex(a[p], b[p])
         bt = beta[p]
-        r = bt * (S @ z) - al * (T @ z)
+        if k == 0:
+            z, sz, tz = V[:, c].astype(complex), SV[:, c].astype(complex), TV[:, c].astype(complex)
+        else:
+            z = V[:, c] + 1j * V[:, c + 1]
+            sz = SV[:, c] + 1j * SV[:, c + 1]
+            tz = TV[:, c] + 1j * TV[:, c + 1]
+        r = bt * sz - al * tz
         den = (abs(bt) * nS + abs(al) * nT) * np.abs(z).max()
         val = np.abs(r).max() / den if den > 0 else np.inf
         res[c] = val
-        if kinds[c] == 1:
+        if k == 1:
             res[c + 1] = val
     return res
 

@@ -463,6 +463,12 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
   for (auto& e : p->ev)
     if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = PEVC_ERR_CUDA;
   if (!rc && cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess) rc = PEVC_ERR_CUDA;
+  {
+    // PEVC_LOOKAHEAD=0 walks the stages strictly in order on one stream
+    // (kernel times without overlap, for measurement)
+    const char* la = getenv("PEVC_LOOKAHEAD");
+    p->lookahead = !(la && la[0] == '0');
+  }
   if (!rc) {
     p->sev = new (std::nothrow) cudaEvent_t[2 * p->Mmax]();
     if (!p->sev) rc = PEVC_ERR_NOMEM;
