@@ -73,6 +73,10 @@ typedef struct pevc_plan_s *pevc_plan_t;
 #define PEVC_ERR_CUDA 5         /* a CUDA runtime call failed                            */
 #define PEVC_ERR_NOMEM 6        /* device or pinned host allocation failed               */
 #define PEVC_ERR_UNSUPPORTED 7  /* a requested feature is not available in this build    */
+#define PEVC_ERR_TOO_LARGE 8    /* n above PEVC_STATIC_N_MAX in pevc_solve_static         */
+
+/* Largest order accepted by pevc_solve_static. */
+#define PEVC_STATIC_N_MAX 512
 
 /*
  * pevc_plan -- create a plan that owns all device workspace for pencils of
@@ -162,6 +166,43 @@ int pevc_set_profile(pevc_plan_t plan, int on);
  *        (flops count every slice product: 2 * rows * cols * K * products).
  */
 int pevc_kernel_profile(pevc_plan_t plan, double *out);
+
+/*
+ * pevc_solve_static -- pevc_solve in FP64 for pencils of order n <=
+ * PEVC_STATIC_N_MAX without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code that runs where a device allocation could block or fail
+ * at a bad moment (inside a real-time or latency-bounded loop, under a
+ * caller's own memory pool or allocation budget, or in a plugin whose host
+ * forbids allocating) -- and that cannot keep a plan alive.
+ *   S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out
+ *              as in pevc_solve (device pointers owned by the caller; m_out
+ *              is host memory)
+ *   flags      0 or PEVC_NO_NORMALISE
+ *   stream     cudaStream_t (as void*) on which the work is ordered
+ * Workspace: one file-scope device array of just under 2 MiB (the
+ * workspace of an order-512 FP64 solve), which every GPU that loads the
+ * library holds until the process exits; host-side structure arrays (about
+ * 16 KB) live on the calling thread's stack.  The call allocates nothing:
+ * no cudaMalloc, cudaFree, cudaMallocHost or allocating library routine; its
+ * host copies go through pageable memory.
+ * Set-up: the first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) once; make that first call
+ * before any stream capture on the device (a call with n = 0 does only the
+ * set-up).
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents (the call clears what must start at zero itself).  Calls
+ * whose GPU work overlaps -- on different streams, or from different host
+ * threads -- race on the array and give wrong results; order them on one
+ * stream or serialise them.  The call synchronises on return, like
+ * pevc_solve, and its kernels and tile order are those of an FP64 plan with
+ * n_max = n, so its output equals that plan's.
+ * Returns 0, -i (argument i invalid, counting S as argument 1),
+ * PEVC_ERR_TOO_LARGE when n > PEVC_STATIC_N_MAX, or a status of pevc_solve.
+ */
+int pevc_solve_static(const double *S, int lds, const double *T, int ldt, int n,
+                      const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out,
+                      unsigned flags, void *stream);
 
 #ifdef __cplusplus
 }

@@ -3,8 +3,9 @@
 Argument marshalling only: every step of the computation runs in the CUDA
 kernels of ``libpevc.so``; PyTorch provides device memory and streams.  The
 functions ``pevc_plan``, ``pevc_solve``, ``pevc_solve_batched``,
-``pevc_destroy``, ``pevc_strerror``, ``pevc_plan_info`` and
-``pevc_last_stats`` mirror the C ABI of ``include/pevc.h`` one to one (raw
+``pevc_destroy``, ``pevc_strerror``, ``pevc_plan_info``,
+``pevc_last_stats``, ``pevc_set_profile``, ``pevc_kernel_profile`` and
+``pevc_solve_static`` mirror the C ABI of ``include/pevc.h`` one to one (raw
 pointers and sizes); ``Plan`` wraps them for torch tensors.
 
 There is no CPU fallback: importing this module fails loudly when the
@@ -37,6 +38,9 @@ ERR_TIMEOUT = 4
 ERR_CUDA = 5
 ERR_NOMEM = 6
 ERR_UNSUPPORTED = 7
+ERR_TOO_LARGE = 8
+
+STATIC_N_MAX = 512   # largest order of pevc_solve_static
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libpevc.so is not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -62,9 +66,12 @@ _lib.pevc_set_profile.argtypes = [_vp, _i]
 _lib.pevc_set_profile.restype = _i
 _lib.pevc_kernel_profile.argtypes = [_vp, _vp]
 _lib.pevc_kernel_profile.restype = _i
+_lib.pevc_solve_static.argtypes = [_vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i), _u, _vp]
+_lib.pevc_solve_static.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
-           "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile")
+           "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
+           "pevc_solve_static")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -128,6 +135,17 @@ def pevc_kernel_profile(plan):
     out = (ctypes.c_double * 12)()
     st = _lib.pevc_kernel_profile(plan, out)
     return st, list(out)
+
+
+def pevc_solve_static(S: int, lds: int, T: int, ldt: int, n: int, select: int, V: int, ldv: int,
+                      scale: int, flags: int = 0, stream: int = 0):
+    """FP64 solve without device allocation (order <= STATIC_N_MAX; the
+    workspace is a device array inside the library).  Raw pointers as in
+    pevc_solve.  Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve_static(_vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(V), ldv,
+                                _vp(scale), ctypes.byref(m), int(flags), _vp(stream) if stream else None)
+    return st, m.value
 
 
 # ------------------------------------------------------------ torch wrapper

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -532,6 +533,7 @@ const char* pevc_strerror(int code) {
     case PEVC_ERR_CUDA: return "CUDA runtime error";
     case PEVC_ERR_NOMEM: return "out of memory";
     case PEVC_ERR_UNSUPPORTED: return "unsupported feature";
+    case PEVC_ERR_TOO_LARGE: return "order above PEVC_STATIC_N_MAX for pevc_solve_static";
     default: return code < 0 ? "invalid argument" : "unknown status";
   }
 }
@@ -582,3 +584,230 @@ int pevc_last_stats(pevc_plan_t plan, double* stats) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// pevc_solve_static: the FP64 solve of small pencils for callers that cannot
+// allocate device memory.  Every piece of device workspace lives in one
+// file-scope array; the host-side structure arrays live on the caller's
+// stack.  The kernels and their order are those of an FP64 plan whose n_max
+// equals the call's n (same tile order, stages walked strictly in order).
+
+namespace {
+
+constexpr int kStaticNMax = PEVC_STATIC_N_MAX;
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t static_round(size_t x) { return (x + 255) / 256 * 256; }
+constexpr int static_mmax(int n, int tb) { return ((n < 1 ? 1 : n) + tb - 2) / (tb - 1) + 1; }
+
+// Byte offsets of the workspace pieces inside the scratch array, each on a
+// 256-byte boundary; bytes = the total.
+struct StaticLayout {
+  size_t Y = 0, ex = 0, nrm = 0, EA = 0, tcS = 0, tcT = 0, gmax = 0, ca = 0, cb = 0, cbeta = 0, blk = 0,
+         toff = 0, cstart = 0, ccol = 0, kind = 0, status = 0, subd = 0, dperm = 0, dcpos = 0, dccnt = 0,
+         dcfirst = 0, bytes = 0;
+};
+
+constexpr StaticLayout static_layout(int n, int tb) {
+  StaticLayout L;
+  const size_t nm = n < 1 ? 1 : (size_t)n;
+  const size_t M = (size_t)static_mmax(n, tb);
+  size_t o = 0;
+  L.Y = o;       o = static_round(o + M * (M + 1) / 2 * (size_t)tb * tb * sizeof(double));
+  L.ex = o;      o = static_round(o + M * nm * sizeof(int));
+  L.nrm = o;     o = static_round(o + M * nm * sizeof(double));
+  L.EA = o;      o = static_round(o + M * M * sizeof(int));
+  L.tcS = o;     o = static_round(o + nm * sizeof(double));
+  L.tcT = o;     o = static_round(o + nm * sizeof(double));
+  L.gmax = o;    o = static_round(o + sizeof(double));
+  L.ca = o;      o = static_round(o + nm * sizeof(double));
+  L.cb = o;      o = static_round(o + nm * sizeof(double));
+  L.cbeta = o;   o = static_round(o + nm * sizeof(double));
+  L.blk = o;     o = static_round(o + nm);
+  L.toff = o;    o = static_round(o + (M + 1) * sizeof(int));
+  L.cstart = o;  o = static_round(o + (M + 1) * sizeof(int));
+  L.ccol = o;    o = static_round(o + nm * sizeof(int));
+  L.kind = o;    o = static_round(o + nm);
+  L.status = o;  o = static_round(o + sizeof(unsigned));
+  L.subd = o;    o = static_round(o + nm * sizeof(double));
+  L.dperm = o;   o = static_round(o + nm * sizeof(int));
+  L.dcpos = o;   o = static_round(o + (nm + M) * sizeof(int));
+  L.dccnt = o;   o = static_round(o + (nm + M) * sizeof(int));
+  L.dcfirst = o; o = static_round(o + (M + 1) * sizeof(int));
+  L.bytes = o;
+  return L;
+}
+
+// The FP64 tile choice is 32 up to order 256 and 64 up to order 1024, so the
+// largest layout below the maximum order is one of these two.
+constexpr size_t static_max(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kStaticBytes = static_max(static_layout(256, 32).bytes, static_layout(kStaticNMax, 64).bytes);
+constexpr int kStaticMMax = static_mmax(256, 32) > static_mmax(kStaticNMax, 64) ? static_mmax(256, 32)
+                                                                                 : static_mmax(kStaticNMax, 64);
+static_assert(kStaticNMax <= 1024, "the static entry point assumes the FP64 tile choice of orders <= 1024");
+
+}  // namespace
+
+// The scratch array: in host code this name only stands for the device
+// symbol; its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mutex;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device does this set-up).
+int static_scratch(unsigned char** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return PEVC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_static_scratch));
+    if (!ptr) return PEVC_ERR_CUDA;
+    g_static_addr[dev] = ptr;
+  }
+  *out = (unsigned char*)g_static_addr[dev];
+  return 0;
+}
+
+// Host copies of the structure for one call (on the caller's stack).
+struct StaticHost {
+  double subd[kStaticNMax];
+  int32_t sel[kStaticNMax];
+  signed char blk[kStaticNMax];
+  signed char kind[kStaticNMax];
+  int ccol[kStaticNMax];
+  int dperm[kStaticNMax];
+  int dcpos[kStaticNMax + kStaticMMax];
+  int dccnt[kStaticNMax + kStaticMMax];
+  int toff[kStaticMMax + 1];
+  int cstart[kStaticMMax + 1];
+  int dcfirst[kStaticMMax + 1];
+  unsigned status;
+};
+
+struct StaticF64Ops : StageOps {
+  const Problem& P;
+  explicit StaticF64Ops(const Problem& P_) : P(P_) {}
+  cudaError_t tips(cudaStream_t st) override { return launch_diag(P, 0, kDiagTip, st); }
+  cudaError_t diag(int i, cudaStream_t st) override { return launch_diag(P, i, kDiagSolve, st); }
+  cudaError_t prep(int, cudaStream_t) override { return cudaSuccess; }
+  cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t st) override {
+    return launch_update_f64(P, i, k_lo, k_hi, st);
+  }
+};
+
+int solve_static(const double* S, int lds, const double* T, int ldt, int n, const int32_t* sel, double* V,
+                 int ldv, int32_t* scale, int* m_out, unsigned flags, cudaStream_t s) {
+  *m_out = 0;
+  unsigned char* base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc) return rc;
+  if (n == 0) return 0;
+  const int tb = choose_tile(n, PEVC_FP64);
+  const StaticLayout L = static_layout(n, tb);
+  if (L.bytes > kStaticBytes) return PEVC_ERR_TOO_LARGE;
+  StaticHost h;
+  pevc_plan_s p;   // a view: every pointer below is borrowed, nothing is freed
+  p.n_max = n;
+  p.prec = PEVC_FP64;
+  p.tb = tb;
+  p.flags = flags;
+  p.stream = s;
+  p.Mmax = static_mmax(n, tb);
+  p.lookahead = false;
+  p.Y = (double*)(base + L.Y);
+  p.ex = (int*)(base + L.ex);
+  p.nrm = (double*)(base + L.nrm);
+  p.EA = (int*)(base + L.EA);
+  p.tcS = (double*)(base + L.tcS);
+  p.tcT = (double*)(base + L.tcT);
+  p.gmax = (double*)(base + L.gmax);
+  p.ca = (double*)(base + L.ca);
+  p.cb = (double*)(base + L.cb);
+  p.cbeta = (double*)(base + L.cbeta);
+  p.blk = (signed char*)(base + L.blk);
+  p.toff = (int*)(base + L.toff);
+  p.cstart = (int*)(base + L.cstart);
+  p.ccol = (int*)(base + L.ccol);
+  p.kind = (signed char*)(base + L.kind);
+  p.status = (unsigned*)(base + L.status);
+  p.subd = (double*)(base + L.subd);
+  p.dperm = (int*)(base + L.dperm);
+  p.dcpos = (int*)(base + L.dcpos);
+  p.dccnt = (int*)(base + L.dccnt);
+  p.dcfirst = (int*)(base + L.dcfirst);
+  p.h_subd = h.subd;
+  p.h_sel = h.sel;
+  p.h_blk = h.blk;
+  p.h_toff = h.toff;
+  p.h_cstart = h.cstart;
+  p.h_ccol = h.ccol;
+  p.h_kind = h.kind;
+  p.h_status = &h.status;
+  p.h_dperm = h.dperm;
+  p.h_dcpos = h.dcpos;
+  p.h_dccnt = h.dccnt;
+  p.h_dcfirst = h.dcfirst;
+
+  // 1. block structure and selection to the host (pageable copies on s)
+  CK(launch_gather_subdiag(S, lds, n, p.subd, s));
+  if (n > 1) CK(cudaMemcpyAsync(p.h_subd, p.subd, (size_t)(n - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (sel) CK(cudaMemcpyAsync(p.h_sel, sel, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  Structure st;
+  if ((rc = analyse(&p, n, sel != nullptr, st))) return rc;
+  *m_out = st.m;
+  // 2. structure to the device; the status word and the running maximum
+  //    must start at zero (the array keeps the previous call's contents)
+  CK(cudaMemcpyAsync(p.blk, p.h_blk, (size_t)n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p.toff, p.h_toff, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p.cstart, p.h_cstart, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (st.m > 0) {
+    CK(cudaMemcpyAsync(p.ccol, p.h_ccol, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p.kind, p.h_kind, (size_t)st.m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p.dperm, p.h_dperm, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p.dcpos, p.h_dcpos, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p.dccnt, p.h_dccnt, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(p.dcfirst, p.h_dcfirst, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(p.status, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(p.gmax, 0, sizeof(double), s));
+  Problem P = make_problem(&p, S, lds, T, ldt, n, st);
+  CK(launch_prepass(P, s));
+  unsigned bits = 0;
+  if ((rc = read_status(&p, &bits))) return rc;
+  if (bits) return status_from_bits(bits);
+  if (st.m > 0) {
+    // 3. the task graph, bottom-up by block row; 4. post-processing
+    CK(launch_init_state(P, s));
+    StaticF64Ops ops(P);
+    CK(walk_dag(st.M, ops, s, nullptr, nullptr, false));
+    CK(launch_post(P, V, ldv, scale, (flags & PEVC_NO_NORMALISE) == 0, s));
+  }
+  if ((rc = read_status(&p, &bits))) return rc;
+  return status_from_bits(bits);
+}
+
+}  // namespace
+
+extern "C" int pevc_solve_static(const double* S, int lds, const double* T, int ldt, int n,
+                                 const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out,
+                                 unsigned flags, void* stream) {
+  if (n < 0) return -5;
+  if (n > kStaticNMax) return PEVC_ERR_TOO_LARGE;
+  if (n > 0 && !S) return -1;
+  if (lds < std::max(n, 1)) return -2;
+  if (n > 0 && !T) return -3;
+  if (ldt < std::max(n, 1)) return -4;
+  if (n > 0 && !V_out) return -7;
+  if (ldv < std::max(n, 1)) return -8;
+  if (n > 0 && !scale_out) return -9;
+  if (!m_out) return -10;
+  if (flags & ~PEVC_NO_NORMALISE) return -11;
+  return solve_static(S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out, flags, (cudaStream_t)stream);
+}
