@@ -161,7 +161,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pevc", choices=["pevc", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16x5", "fp8x4", "fp64"])
+    ap.add_argument("--prec", default="bf16x5", choices=["bf16x3", "bf16x5", "fp8x4", "fp64"])
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

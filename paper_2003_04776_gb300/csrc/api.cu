@@ -203,8 +203,9 @@ int analyse(pevc_plan_t p, int n, bool has_sel, Structure& st) {
   st.M = M;
   st.m = m;
   // diagonal-kernel chunks: per column tile, real columns first, then the
-  // complex pairs; chunks of at most 16 columns, never mixing the two kinds
-  const int kCB = 16;
+  // complex pairs; chunks of at most kDiagChunk columns, never mixing the
+  // two kinds
+  const int kCB = kDiagChunk;
   int nch = 0, maxc = 0;
   for (int j = 0; j < M; ++j) {
     p->h_dcfirst[j] = nch;
@@ -465,10 +466,12 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
     if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = PEVC_ERR_CUDA;
   if (!rc && cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess) rc = PEVC_ERR_CUDA;
   {
-    // PEVC_LOOKAHEAD=0 walks the stages strictly in order on one stream
-    // (kernel times without overlap, for measurement)
+    // The stages run strictly in order on the plan's stream; PEVC_LOOKAHEAD=1
+    // moves the solves of the next block row to a second stream (they overlap
+    // the rest of the update; measured slower on GB300 once the update fills
+    // every SM, so it is off by default).
     const char* la = getenv("PEVC_LOOKAHEAD");
-    p->lookahead = !(la && la[0] == '0');
+    p->lookahead = la && la[0] == '1';
   }
   if (!rc) {
     p->sev = new (std::nothrow) cudaEvent_t[2 * p->Mmax]();

@@ -18,6 +18,7 @@ constexpr int kOmegaExp = 1022;        // Omega = 2^1022
 constexpr int kPrescaleExp = 1000;     // |beta| max|S|, (|a|+|b|) max|T| <= 2^1000
 constexpr int kExpZero = -(1 << 29);   // exponent of a tile column that is still zero
 constexpr int kMaxTile = 128;          // largest tile order
+constexpr int kDiagChunk = 8;          // columns per diagonal-solve CTA (even: pairs stay whole)
 
 // Device status bits (reduced to a PEVC_ERR_* value on the host).
 constexpr unsigned kStNotSchur = 1u;
@@ -25,16 +26,40 @@ constexpr unsigned kStNonfinite = 2u;
 constexpr unsigned kStIndefinite = 4u;
 constexpr unsigned kStTimeout = 8u;
 
-// Smallest E with v < 2^E for finite v > 0 (ilogb is exact, also for
-// subnormals).
-__device__ __forceinline__ int exp_above(double v) { return ilogb(v) + 1; }
+// FP64 instructions are scarce on this GPU (a warp instruction occupies a
+// sub-partition's FP64 unit for tens of cycles), so exponent extraction,
+// comparisons and maxima of non-negative values work on the IEEE-754 bit
+// patterns with integer instructions.
+
+// |x| as an ordered integer key (non-negative doubles order like their bits).
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// floor(log2 v) for the key a = abs_key(v) of a finite v != 0: the biased
+// exponent field for normal numbers, the position of the leading mantissa
+// bit for subnormals.
+__device__ __forceinline__ int ilogb_key(unsigned long long a) {
+  const int E = (int)(a >> 52);
+  return E ? E - 1023 : (63 - __clzll((long long)a)) - 1074;
+}
+
+// Smallest E with |v| < 2^E for finite v != 0.
+__device__ __forceinline__ int exp_above(double v) { return ilogb_key(abs_key(v)) + 1; }
+
+// Larger of two non-negative doubles (bitwise; no FP64 instruction).
+__device__ __forceinline__ double max_nonneg(double x, double y) {
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  return __longlong_as_double(a > b ? a : b);
+}
 
 // ProtectUpdate (Section 4, property 2) on exponent bounds: y, t, x >= 0 and
 // finite.  k >= 0 with 2^-k (y + t x) <= Omega.
 __device__ __forceinline__ int protect_update(double y, double t, double x) {
+  const unsigned long long yb = abs_key(y), tb = abs_key(t), xb = abs_key(x);
   int top = INT32_MIN / 4;
-  if (y > 0.0) top = exp_above(y);
-  if (t > 0.0 && x > 0.0) top = max(top, exp_above(t) + exp_above(x));
+  if (yb) top = ilogb_key(yb) + 1;
+  if (tb && xb) top = max(top, ilogb_key(tb) + ilogb_key(xb) + 2);
   int k = top + 1 - kOmegaExp;
   return k > 0 ? k : 0;
 }
@@ -49,8 +74,9 @@ __device__ __forceinline__ int protect_update_e(int ey_or_min, int etx_or_min) {
 // ProtectDivision (Section 4, property 1) for the numerator bound 2^sh * b
 // and denominator magnitude t > 0: k >= 0 with 2^-k 2^sh b <= t Omega.
 __device__ __forceinline__ int protect_division(double b, int sh, double t) {
-  if (!(b > 0.0)) return 0;
-  int k = exp_above(b) + sh - ilogb(t) - kOmegaExp;   // t >= 2^ilogb(t)
+  const unsigned long long bb = abs_key(b);
+  if (!bb) return 0;
+  int k = ilogb_key(bb) + 1 + sh - ilogb_key(abs_key(t)) - kOmegaExp;   // t >= 2^ilogb(t)
   return k > 0 ? k : 0;
 }
 
@@ -95,11 +121,6 @@ __device__ __forceinline__ double pow2_scale(double x, int e) {
   if (E != 0 && E != 0x7ff && En > 0 && En < 0x7ff) return __longlong_as_double(b + ((long long)e << 52));
   if (e == 0 || x == 0.0) return x;
   return ldexp(x, e);
-}
-
-// |x| as an ordered integer key (non-negative doubles order like their bits).
-__device__ __forceinline__ unsigned long long abs_key(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
 // Largest of non-negative doubles via their bit patterns (monotone for x >= 0).
@@ -163,12 +184,12 @@ __device__ __forceinline__ bool update_scales(const Problem& P, const int* exX, 
   const int kd = P.kind[q];
   const int partner = (kd == 1) ? q + 1 : (kd == 2 ? q - 1 : q);
   const long long bk = (long long)k * m, bi = (long long)i * m;
-  const double nY = fmax(P.nrm[bk + q], P.nrm[bk + partner]);
-  const double nX = fmax(nrmX[bi + q], nrmX[bi + partner]);
+  const double nY = max_nonneg(P.nrm[bk + q], P.nrm[bk + partner]);
+  const double nX = max_nonneg(nrmX[bi + q], nrmX[bi + partner]);
   const int c0 = (kd == 2) ? P.ccol[q] - 1 : P.ccol[q];
-  const double cB = fmax(fabs(P.cbeta[c0]), fabs(P.ca[c0]) + fabs(P.cb[c0]));
-  yzero = !(nY > 0.0);
-  if (!(nX > 0.0) || !(cB > 0.0)) return false;
+  const double cB = max_nonneg(fabs(P.cbeta[c0]), fabs(P.ca[c0]) + fabs(P.cb[c0]));
+  yzero = abs_key(nY) == 0;
+  if (abs_key(nX) == 0 || abs_key(cB) == 0) return false;
   const int eY = P.ex[bk + q], eX = exX[bi + q];
   const int e0 = yzero ? eX : max(eY, eX);
   const int xb = exp_above(cB) + exp_above(nX) + eX - e0;          // ||X''|| < 2^xb at e0

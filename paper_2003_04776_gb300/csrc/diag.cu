@@ -50,10 +50,18 @@ __device__ __forceinline__ double upd_norm(const DiagBlocks& D, int li0, int sz,
   return t;
 }
 
-// Robust 2x2 solve for a real eigenvalue: (beta S_bb - a T_bb) x = r, r in
-// the column's current scale; y bounds the rows above.
-__device__ __forceinline__ void real_block2(const DiagBlocks& D, int li0, bool has_above, double a, double beta,
-                                            double r0, double r1, double& y, ColStep& out) {
+// Twice the largest of |x|, |y| (an upper bound of |x| + |y|), by integer
+// arithmetic on the exponent field; requires max(|x|, |y|) < 2^1023.
+__device__ __forceinline__ double twice_max_abs(unsigned long long key) {
+  return __longlong_as_double((long long)(key + (1ull << 52)));
+}
+
+// The right-hand-side-independent part of the robust 2x2 solve of a real
+// eigenvalue, (beta S_bb - a T_bb) x = r: Gaussian elimination with complete
+// pivoting, pivots below smin raised to smin (the DLALN2 principle of Section
+// 5.2).  f = {1/piv, l, m[pi][oj]/piv, 1/u22}; ep = ilogb |u22|; pf = pi | pj << 1.
+__device__ __forceinline__ void real2_factor(const DiagBlocks& D, int li0, double a, double beta, double* f,
+                                             short& ep, unsigned char& pf) {
   double m[2][2];
   double sm = 0.0, tm = 0.0;
 #pragma unroll
@@ -80,28 +88,18 @@ __device__ __forceinline__ void real_block2(const DiagBlocks& D, int li0, bool h
   const double l = m[oi][pj] / piv;
   double u22 = m[oi][oj] - l * m[pi][oj];
   if (fabs(u22) < smin) u22 = copysign(smin, u22);
-  const int kd = protect_division(fmax(fabs(r0), fabs(r1)), 5, fabs(u22));
-  if (kd) { r0 = pow2_scale(r0, -kd); r1 = pow2_scale(r1, -kd); y = pow2_scale(y, -kd); }
-  const double rp = pi ? r1 : r0, ro = pi ? r0 : r1;
-  const double xo = (ro - l * rp) / u22;
-  const double xp = rp / piv - (m[pi][oj] / piv) * xo;
-  double w0 = oj ? xp : xo, w1 = oj ? xo : xp;
-  int ku = 0;
-  const double tn = upd_norm(D, li0, 2, beta, fabs(a));
-  const double x = fmax(fabs(w0), fabs(w1));
-  if (has_above) ku = protect_update(y, tn, x);
-  if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); }
-  if (has_above) y = pow2_scale(y, -ku) + tn * pow2_scale(x, -ku);
-  out.shift = kd + ku;
-  out.W[0][0] = w0; out.W[1][0] = w1;
-  out.P[0][0] = beta * w0; out.P[1][0] = beta * w1;
-  out.Q[0][0] = a * w0; out.Q[1][0] = a * w1;
+  f[0] = 1.0 / piv;
+  f[1] = l;
+  f[2] = m[pi][oj] / piv;
+  f[3] = 1.0 / u22;
+  ep = (short)ilogb_key(abs_key(u22));
+  pf = (unsigned char)(pi | (pj << 1));
 }
 
-// Complex 2x2 counterpart (alpha = a + i b).
-__device__ __forceinline__ void cplx_block2(const DiagBlocks& D, int li0, bool has_above, double a, double b,
-                                            double beta, double r0r, double r0i, double r1r, double r1i, double& y,
-                                            ColStep& out) {
+// Complex counterpart (alpha = a + i b): f = {l, 1/u22, 1/piv, m[pi][oj]/piv}
+// as (re, im) pairs; ep = ilogb(|Re u22| + |Im u22|).
+__device__ __forceinline__ void cplx2_factor(const DiagBlocks& D, int li0, double a, double b, double beta, double* f,
+                                             short& ep, unsigned char& pf) {
   const double amag = fabs(a) + fabs(b);
   double mr[2][2], mi[2][2];
   double sm = 0.0, tm = 0.0;
@@ -134,39 +132,13 @@ __device__ __forceinline__ void cplx_block2(const DiagBlocks& D, int li0, bool h
   double ur = mr[oi][oj] - (lr * mr[pi][oj] - li * mi[pi][oj]);
   double ui = mi[oi][oj] - (lr * mi[pi][oj] + li * mr[pi][oj]);
   if (cmag(ur, ui) < smin) { ur = smin; ui = 0.0; }
-  const int kd = protect_division(fmax(cmag(r0r, r0i), cmag(r1r, r1i)), 5, cmag(ur, ui));
-  if (kd) {
-    r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
-    r1r = pow2_scale(r1r, -kd); r1i = pow2_scale(r1i, -kd);
-    y = pow2_scale(y, -kd);
-  }
-  const double rpr = pi ? r1r : r0r, rpi = pi ? r1i : r0i;
-  const double ror = pi ? r0r : r1r, roi = pi ? r0i : r1i;
-  const double er = ror - (lr * rpr - li * rpi), ei = roi - (lr * rpi + li * rpr);
-  double xor_, xoi, q1r, q1i, q2r, q2i;
-  cdiv(er, ei, ur, ui, xor_, xoi);
-  cdiv(rpr, rpi, mr[pi][pj], mi[pi][pj], q1r, q1i);
-  cdiv(mr[pi][oj], mi[pi][oj], mr[pi][pj], mi[pi][pj], q2r, q2i);
-  const double xpr = q1r - (q2r * xor_ - q2i * xoi);
-  const double xpi = q1i - (q2r * xoi + q2i * xor_);
-  double w0r, w0i, w1r, w1i;
-  if (oj) { w0r = xpr; w0i = xpi; w1r = xor_; w1i = xoi; }
-  else    { w0r = xor_; w0i = xoi; w1r = xpr; w1i = xpi; }
-  int ku = 0;
-  const double tn = upd_norm(D, li0, 2, beta, amag);
-  const double x = fmax(cmag(w0r, w0i), cmag(w1r, w1i));
-  if (has_above) ku = protect_update(y, tn, x);
-  if (ku) {
-    w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
-    w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
-  }
-  if (has_above) y = pow2_scale(y, -ku) + tn * pow2_scale(x, -ku);
-  out.shift = kd + ku;
-  out.W[0][0] = w0r; out.W[0][1] = w0i; out.W[1][0] = w1r; out.W[1][1] = w1i;
-  out.P[0][0] = beta * w0r; out.P[0][1] = beta * w0i;
-  out.P[1][0] = beta * w1r; out.P[1][1] = beta * w1i;
-  out.Q[0][0] = a * w0r - b * w0i; out.Q[0][1] = a * w0i + b * w0r;
-  out.Q[1][0] = a * w1r - b * w1i; out.Q[1][1] = a * w1i + b * w1r;
+  f[0] = lr;
+  f[1] = li;
+  cdiv(1.0, 0.0, ur, ui, f[2], f[3]);
+  cdiv(1.0, 0.0, mr[pi][pj], mi[pi][pj], f[4], f[5]);
+  cdiv(mr[pi][oj], mi[pi][oj], mr[pi][pj], mi[pi][pj], f[6], f[7]);
+  ep = (short)ilogb_key(abs_key(cmag(ur, ui)));
+  pf = (unsigned char)(pi | (pj << 1));
 }
 
 // Tip of a complex pair: a null vector of M = beta S_jj - alpha T_jj,
@@ -222,11 +194,16 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
   __shared__ double s_W[2][CB], s_piv[2][CB];
   __shared__ short s_bs[kMaxTile];
   __shared__ unsigned char s_bz[kMaxTile];
+  __shared__ int s_boff[kMaxTile];                          // offset of a block's factors in s_pre
   __shared__ int s_nb;
   __shared__ double s_Sd[kMaxTile][2], s_Td[kMaxTile][2], s_tcS[kMaxTile], s_tcT[kMaxTile];
-  __shared__ double s_inv[kMaxTile][CB];                    // 1x1 pivots inverted: real [b][u], complex [b][2u..2u+1]
+  // right-hand-side-independent factors per (block, unit): 1x1 blocks the
+  // inverted pivot (1 double real, 2 complex), 2x2 blocks the LU factors
+  // (4 doubles real, 8 complex) -- at most 2 doubles per row and column
+  __shared__ double s_pre[2 * kMaxTile * CB];
   __shared__ double s_tn[kMaxTile][CB];                     // ProtectUpdate's t per (block, unit)
-  __shared__ short s_ep[kMaxTile][CB];                      // ilogb of |pivot| per (block, unit)
+  __shared__ short s_ep[kMaxTile][CB];                      // ilogb of the pivot (or u22) magnitude
+  __shared__ unsigned char s_pf[kMaxTile][CB];              // 2x2 pivot position pi | pj << 1
   __shared__ unsigned long long s_key[CB];
 
   // ---- stage column constants, the diagonal blocks and the block list
@@ -251,8 +228,8 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
     } else {
       const long long base = (long long)i * m;
       double nv = P.nrm[base + q];
-      if (pairs) nv = fmax(nv, P.nrm[base + q + 1]);
-      s_act[lr] = nv > 0.0;
+      if (pairs) nv = max_nonneg(nv, P.nrm[base + q + 1]);
+      s_act[lr] = abs_key(nv) != 0;
       s_e[lr] = P.ex[base + q];
       s_y[lr] = nv;
     }
@@ -269,11 +246,14 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
     s_tcT[lr] = P.tcT[gr];
   }
   if (lr == 0) {
-    int nb = 0;
+    int nb = 0, off = 0;
     for (int rr = h - 1; rr >= 0;) {
       const int st = (P.blk[r0 + rr] == 2) ? rr - 1 : rr;
+      const int sz = rr - st + 1;
       s_bs[nb] = (short)st;
-      s_bz[nb] = (unsigned char)(rr - st + 1);
+      s_bz[nb] = (unsigned char)sz;
+      s_boff[nb] = off;
+      off += (sz == 1 ? 1 : 4) * (pairs ? 2 : 1) * nu;
       ++nb;
       rr = st - 1;
     }
@@ -283,31 +263,35 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
   const DiagBlocks D{s_Sd, s_Td, s_tcS, s_tcT};
   const int nb = s_nb;
 
-  // ---- invert the pivots of every 1x1 block for every unit, in parallel
+  // ---- everything that does not depend on the right-hand side, for every
+  //      (block, unit) in parallel: pivots, factors, ProtectUpdate's t
   for (int item = lr; item < nb * nu; item += blockDim.x) {
     const int bidx = item / nu, u = item % nu;
-    if (s_bz[bidx] != 1) continue;
-    const int li = s_bs[bidx];
-    const double s = s_Sd[li][0], t = s_Td[li][0];
+    const int li = s_bs[bidx], sz = s_bz[bidx];
     const double a = s_a[u], b = s_b[u], beta = s_beta[u];
-    if (!pairs) {
-      double p = beta * s - a * t;
-      const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + fabs(a) * fabs(t)), 0x1p-1022);
-      if (fabs(p) < smin) p = copysign(smin, p);
-      s_inv[bidx][u] = 1.0 / p;
-      s_ep[bidx][u] = (short)ilogb(p);
-      s_tn[bidx][u] = fabs(beta) * s_tcS[li] + fabs(a) * s_tcT[li];
+    const double amag = fabs(a) + fabs(b);
+    double* f = s_pre + s_boff[bidx];
+    s_tn[bidx][u] = upd_norm(D, li, sz, beta, amag);
+    if (sz == 1) {
+      const double s = s_Sd[li][0], t = s_Td[li][0];
+      if (!pairs) {
+        double p = beta * s - a * t;
+        const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + fabs(a) * fabs(t)), 0x1p-1022);
+        if (fabs(p) < smin) p = copysign(smin, p);
+        f[u] = 1.0 / p;
+        s_ep[bidx][u] = (short)ilogb_key(abs_key(p));
+      } else {
+        double pr = beta * s - a * t, pim = -b * t;
+        const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + amag * fabs(t)), 0x1p-1022);
+        if (cmag(pr, pim) < smin) { pr = smin; pim = 0.0; }
+        cdiv(1.0, 0.0, pr, pim, f[2 * u], f[2 * u + 1]);
+        s_ep[bidx][u] = (short)ilogb_key(abs_key(cmag(pr, pim)));
+      }
+      s_pf[bidx][u] = 0;
+    } else if (!pairs) {
+      real2_factor(D, li, a, beta, f + 4 * u, s_ep[bidx][u], s_pf[bidx][u]);
     } else {
-      double pr = beta * s - a * t, pim = -b * t;
-      const double amag = fabs(a) + fabs(b);
-      const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + amag * fabs(t)), 0x1p-1022);
-      if (cmag(pr, pim) < smin) { pr = smin; pim = 0.0; }
-      double ir, ii;
-      cdiv(1.0, 0.0, pr, pim, ir, ii);
-      s_inv[bidx][2 * u] = ir;
-      s_inv[bidx][2 * u + 1] = ii;
-      s_ep[bidx][u] = (short)ilogb(cmag(pr, pim));
-      s_tn[bidx][u] = fabs(beta) * s_tcS[li] + amag * s_tcT[li];
+      cplx2_factor(D, li, a, b, beta, f + 8 * u, s_ep[bidx][u], s_pf[bidx][u]);
     }
   }
 
@@ -343,7 +327,8 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
         if (t < nq) s_piv[lr - li0][t] = vals[t];
     }
     __syncthreads();
-    // ---- phase A: one lane of warp 0 per unit solves the block
+    // ---- phase A: one lane of warp 0 per unit solves the block; only the
+    //      right-hand-side-dependent arithmetic is left here
     if (lr < 32) {
       int myshift = 0;
       if (lr < nu) {
@@ -352,6 +337,7 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
         const int tip = s_tip[u];
         const bool has_above = li0 > 0;
         const double a = s_a[u], b = s_b[u], beta = s_beta[u];
+        const double tn = s_tn[bidx][u];
         ColStep st;
         st.shift = 0;
 #pragma unroll
@@ -364,10 +350,8 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
           // kernel 1: the tip, then the protect for the update of the rows above
           active = true;
           double w[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-          const double amag = fabs(a) + fabs(b);
           if (!pairs) w[0][0] = 1.0;
           else cplx_tip(D, li0, a, b, beta, w[0][0], w[0][1], w[1][0], w[1][1]);
-          const double tn = upd_norm(D, li0, sz, beta, amag);
           const double x = fmax(cmag(w[0][0], w[0][1]), cmag(w[1][0], w[1][1]));
           const int ku = has_above ? protect_update(0.0, tn, x) : 0;
 #pragma unroll
@@ -387,44 +371,101 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
           // below a tip, and (correction) at the tip block itself, the column
           // is zero: W, P, Q stay 0 and nothing is scaled
         } else if (active) {
-          if (sz == 1) {
-            // precomputed inverse pivot: w = r / p as r * (1/p)
-            const double tn = s_tn[bidx][u];
-            const int ep = s_ep[bidx][u];
-            if (!pairs) {
-              double r = s_piv[0][t0c];
-              int kd = 0;
-              if (r != 0.0) { kd = exp_above(fabs(r)) - ep - kOmegaExp; kd = kd > 0 ? kd : 0; }
-              if (kd) { r = pow2_scale(r, -kd); y = pow2_scale(y, -kd); }
-              double w = r * s_inv[bidx][u];
-              const int ku = has_above ? protect_update(y, tn, fabs(w)) : 0;
-              if (ku) w = pow2_scale(w, -ku);
-              if (has_above) y = pow2_scale(y, -ku) + tn * fabs(w);
-              st.shift = kd + ku;
-              st.W[0][0] = w;
-              st.P[0][0] = beta * w;
-              st.Q[0][0] = a * w;
-            } else {
-              double rr = s_piv[0][t0c], ri = s_piv[0][t0c + 1];
-              const double mg = cmag(rr, ri);
-              int kd = 0;
-              if (mg > 0.0) { kd = exp_above(mg) + 1 - ep - kOmegaExp; kd = kd > 0 ? kd : 0; }
-              if (kd) { rr = pow2_scale(rr, -kd); ri = pow2_scale(ri, -kd); y = pow2_scale(y, -kd); }
-              const double ir = s_inv[bidx][2 * u], ii = s_inv[bidx][2 * u + 1];
-              double wr = rr * ir - ri * ii, wi = rr * ii + ri * ir;
-              const int ku = has_above ? protect_update(y, tn, cmag(wr, wi)) : 0;
-              if (ku) { wr = pow2_scale(wr, -ku); wi = pow2_scale(wi, -ku); }
-              if (has_above) y = pow2_scale(y, -ku) + tn * cmag(wr, wi);
-              st.shift = kd + ku;
-              st.W[0][0] = wr; st.W[0][1] = wi;
-              st.P[0][0] = beta * wr; st.P[0][1] = beta * wi;
-              st.Q[0][0] = a * wr - b * wi; st.Q[0][1] = a * wi + b * wr;
-            }
+          const int ep = s_ep[bidx][u];
+          const double* f = s_pre + s_boff[bidx];
+          if (sz == 1 && !pairs) {
+            // w = r / p as r * (1/p); ProtectDivision against |p| >= 2^ep
+            double r = s_piv[0][t0c];
+            const unsigned long long rb = abs_key(r);
+            int kd = rb ? ilogb_key(rb) + 1 - ep - kOmegaExp : 0;
+            kd = kd > 0 ? kd : 0;
+            if (kd) { r = pow2_scale(r, -kd); y = pow2_scale(y, -kd); }
+            double w = r * f[u];
+            const int ku = has_above ? protect_update(y, tn, fabs(w)) : 0;
+            if (ku) w = pow2_scale(w, -ku);
+            if (has_above) y = fma(tn, fabs(w), pow2_scale(y, -ku));
+            st.shift = kd + ku;
+            st.W[0][0] = w;
+            st.P[0][0] = beta * w;
+            st.Q[0][0] = a * w;
+          } else if (sz == 1) {
+            // complex: |r| <= |Re r| + |Im r| < 2^(ilogb(max) + 2); the
+            // quotient by p may grow by one more factor 2 (|p| >= cmag(p)/2)
+            double rr = s_piv[0][t0c], ri = s_piv[0][t0c + 1];
+            const unsigned long long rb = max(abs_key(rr), abs_key(ri));
+            int kd = rb ? ilogb_key(rb) + 3 - ep - kOmegaExp : 0;
+            kd = kd > 0 ? kd : 0;
+            if (kd) { rr = pow2_scale(rr, -kd); ri = pow2_scale(ri, -kd); y = pow2_scale(y, -kd); }
+            const double ir = f[2 * u], ii = f[2 * u + 1];
+            double wr = fma(rr, ir, -ri * ii), wi = fma(rr, ii, ri * ir);
+            const double x2 = twice_max_abs(max(abs_key(wr), abs_key(wi)));   // >= |Re w| + |Im w|
+            const int ku = has_above ? protect_update(y, tn, x2) : 0;
+            if (ku) { wr = pow2_scale(wr, -ku); wi = pow2_scale(wi, -ku); }
+            if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+            st.shift = kd + ku;
+            st.W[0][0] = wr; st.W[0][1] = wi;
+            st.P[0][0] = beta * wr; st.P[0][1] = beta * wi;
+            st.Q[0][0] = fma(a, wr, -b * wi); st.Q[0][1] = fma(a, wi, b * wr);
           } else if (!pairs) {
-            real_block2(D, li0, has_above, a, beta, s_piv[0][t0c], s_piv[1][t0c], y, st);
+            // real 2x2 block: forward / back substitution with the factors
+            const double* g = f + 4 * u;
+            const int pf = s_pf[bidx][u], pi = pf & 1, pj = pf >> 1;
+            double r0v = s_piv[0][t0c], r1v = s_piv[1][t0c];
+            const unsigned long long rb = max(abs_key(r0v), abs_key(r1v));
+            int kd = rb ? ilogb_key(rb) + 1 + 5 - ep - kOmegaExp : 0;
+            kd = kd > 0 ? kd : 0;
+            if (kd) { r0v = pow2_scale(r0v, -kd); r1v = pow2_scale(r1v, -kd); y = pow2_scale(y, -kd); }
+            const double rp = pi ? r1v : r0v, ro = pi ? r0v : r1v;
+            const double xo = fma(-g[1], rp, ro) * g[3];
+            const double xp = fma(-g[2], xo, rp * g[0]);
+            double w0 = pj ? xo : xp, w1 = pj ? xp : xo;
+            const double x = max_nonneg(fabs(w0), fabs(w1));
+            const int ku = has_above ? protect_update(y, tn, x) : 0;
+            if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); }
+            if (has_above) y = fma(tn, pow2_scale(x, -ku), pow2_scale(y, -ku));
+            st.shift = kd + ku;
+            st.W[0][0] = w0; st.W[1][0] = w1;
+            st.P[0][0] = beta * w0; st.P[1][0] = beta * w1;
+            st.Q[0][0] = a * w0; st.Q[1][0] = a * w1;
           } else {
-            cplx_block2(D, li0, has_above, a, b, beta, s_piv[0][t0c], s_piv[0][t0c + 1], s_piv[1][t0c],
-                        s_piv[1][t0c + 1], y, st);
+            // complex 2x2 block
+            const double* g = f + 8 * u;
+            const int pf = s_pf[bidx][u], pi = pf & 1, pj = pf >> 1;
+            double r0r = s_piv[0][t0c], r0i = s_piv[0][t0c + 1], r1r = s_piv[1][t0c], r1i = s_piv[1][t0c + 1];
+            const unsigned long long rb =
+                max(max(abs_key(r0r), abs_key(r0i)), max(abs_key(r1r), abs_key(r1i)));
+            int kd = rb ? ilogb_key(rb) + 2 + 5 - ep - kOmegaExp : 0;
+            kd = kd > 0 ? kd : 0;
+            if (kd) {
+              r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
+              r1r = pow2_scale(r1r, -kd); r1i = pow2_scale(r1i, -kd);
+              y = pow2_scale(y, -kd);
+            }
+            const double rpr = pi ? r1r : r0r, rpi = pi ? r1i : r0i;
+            const double ror = pi ? r0r : r1r, roi = pi ? r0i : r1i;
+            const double lre = g[0], lim = g[1];
+            const double er = fma(-lre, rpr, fma(lim, rpi, ror));
+            const double ei = fma(-lre, rpi, fma(-lim, rpr, roi));
+            const double xor_ = fma(er, g[2], -ei * g[3]), xoi = fma(er, g[3], ei * g[2]);
+            const double q1r = fma(rpr, g[4], -rpi * g[5]), q1i = fma(rpr, g[5], rpi * g[4]);
+            const double xpr = fma(-g[6], xor_, fma(g[7], xoi, q1r));
+            const double xpi = fma(-g[6], xoi, fma(-g[7], xor_, q1i));
+            double w0r, w0i, w1r, w1i;
+            if (pj == 0) { w0r = xpr; w0i = xpi; w1r = xor_; w1i = xoi; }
+            else         { w0r = xor_; w0i = xoi; w1r = xpr; w1i = xpi; }
+            const double x2 = twice_max_abs(max(max(abs_key(w0r), abs_key(w0i)), max(abs_key(w1r), abs_key(w1i))));
+            const int ku = has_above ? protect_update(y, tn, x2) : 0;
+            if (ku) {
+              w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
+              w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
+            }
+            if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+            st.shift = kd + ku;
+            st.W[0][0] = w0r; st.W[0][1] = w0i; st.W[1][0] = w1r; st.W[1][1] = w1i;
+            st.P[0][0] = beta * w0r; st.P[0][1] = beta * w0i;
+            st.P[1][0] = beta * w1r; st.P[1][1] = beta * w1i;
+            st.Q[0][0] = fma(a, w0r, -b * w0i); st.Q[0][1] = fma(a, w0i, b * w0r);
+            st.Q[1][0] = fma(a, w1r, -b * w1i); st.Q[1][1] = fma(a, w1i, b * w1r);
           }
           s_e[u] += st.shift;
         }
@@ -432,7 +473,9 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
         s_y[u] = y;
         myshift = st.shift;
         const int ncols = pairs ? 2 : 1;
-        for (int mm = 0; mm < ncols; ++mm) {
+#pragma unroll
+        for (int mm = 0; mm < 2; ++mm) {
+          if (mm >= ncols) break;
           s_sh[t0c + mm] = st.shift;
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
@@ -513,13 +556,11 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
   }
 }
 
-constexpr int kDiagCB = 16;
-
 cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s) {
   const int ntiles = (mode != kDiagSolve) ? P.M : (P.M - 1 - i);
   if (ntiles <= 0 || P.dchunk_max <= 0) return cudaSuccess;
   dim3 grid(P.dchunk_max, ntiles);
-  k_diag<kDiagCB><<<grid, kMaxTile, 0, s>>>(P, i, mode);
+  k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, i, mode);
   return cudaGetLastError();
 }
 
