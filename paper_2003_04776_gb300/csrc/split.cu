@@ -494,9 +494,10 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
   if (e == cudaSuccess && update_tc_setup() != 0) e = cudaErrorInvalidValue;
   if (e == cudaSuccess && make_tensor_maps(w) != 0) e = cudaErrorInvalidValue;
   {
-    // update kernel: mma.sync (default) or tcgen05 (PEVC_UPDATE_KERNEL=tc)
+    // update kernel for tiles of order 128: tcgen05 (default) or mma.sync
+    // (PEVC_UPDATE_KERNEL=mma); other tile orders always take mma.sync
     const char* sel = getenv("PEVC_UPDATE_KERNEL");
-    w.use_tc = sel && sel[0] == 't';
+    w.use_tc = !(sel && sel[0] == 'm');
   }
   w.on = e == cudaSuccess;
   if (e != cudaSuccess) {
@@ -572,7 +573,7 @@ cudaError_t launch_split_X(const Problem& P, SplitWorkspace& w, int i, int q_beg
 cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                                 const double* nrmX, int ns, int levels, cudaStream_t s) {
   if (k_hi <= k_lo) return cudaSuccess;
-  if (w.use_tc) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, s);
+  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, s);
   const int nsub = P.tb / kSplitCols;
   dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   if (ns == 5 && levels == 5)
@@ -637,7 +638,7 @@ struct SplitOps : StageOps {
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
-  if (w.use_tc) {
+  if (w.use_tc && w.tc_ok) {
     // output column chunks (width 48 and 64) inside every column tile
     int* h48c = w.h_chunks;
     int* h48j = h48c + w.max_chunks;

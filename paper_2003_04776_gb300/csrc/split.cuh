@@ -30,9 +30,12 @@ struct SplitWorkspace {
   int* ex2 = nullptr;
   double* nrm2 = nullptr;
   bool use_tc = true;            // tcgen05 update kernel (else the mma.sync one)
+  bool tc_ok = false;            // tensor maps built (tiles of order 128)
   int nsm = 0;
-  // TMA tensor maps over As and Xs (CUtensorMap storage: 128 bytes, 64-aligned)
+  // TMA tensor maps over As and Xs (CUtensorMap storage: 128 bytes, 64-aligned):
+  // A boxes of 5 and 3 slices, X'' boxes of 48 columns x 5 slices and 64 x 3
   alignas(64) unsigned char tmA[128];
+  alignas(64) unsigned char tmA3[128];
   alignas(64) unsigned char tmB48[128];
   alignas(64) unsigned char tmB64[128];
   // output column chunks of width 48 / 64 inside each column tile (per solve)

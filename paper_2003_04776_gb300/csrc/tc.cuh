@@ -69,6 +69,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parit
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
 }
+// Bounded wait measured in SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_cycles(uint64_t* mbar, uint32_t parity, long long limit) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(mbar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
 
 // 32 lanes x 16 consecutive 32-bit TMEM columns into registers.
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -77,6 +85,12 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
+}
+// 32 lanes x 8 consecutive 32-bit TMEM columns into registers.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::); }
 

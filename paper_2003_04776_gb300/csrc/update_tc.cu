@@ -3,21 +3,29 @@
 //     Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij,   k in [k_lo, k_hi), j >= i,
 // with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).
 //
-// Persistent, warp-specialised CTA of 6 warps:
-//   warp 0   TMA producer: 3-D tensor-map boxes (8 elements x rows x K groups)
-//            land directly in the canonical K-major core-matrix layout;
-//   warp 1   tensor-memory owner and MMA issuer: every slice product p x q
-//            with p + q < L is a tcgen05.mma (M=128, N=NCOL, K=16, BF16 in,
-//            FP32 out) into the accumulator of its level p + q;
-//   warps 2-5 epilogue: tcgen05.ld of the level accumulators, exact integer
-//            recombination, augmented-tile scales (Algorithms 2 and 3 of
-//            Section 4), one FP64 conversion and one FP64 subtraction per
-//            element, new column maxima.
-// Shared-memory stages form an mbarrier ring (full / empty); the level
-// accumulators are double-buffered in tensor memory so that the epilogue of
-// one output tile overlaps the MMAs of the next.  Every wait is bounded: a
-// wait that runs out sets PEVC_ERR_TIMEOUT in the status word and the CTA
-// winds down (all roles run out of bounded waits, tensor memory is freed).
+// Persistent CTA (one per SM) of ten warps:
+//   warp 0     TMA producer: per K step of 16 one 4-D box with every slice of
+//              the A row tile and one with every slice of the X'' column
+//              chunk, landing directly in the canonical K-major core-matrix
+//              layout; a ring of shared-memory stages with full / empty
+//              mbarriers;
+//   warp 1     tensor-memory owner and MMA issuer: every slice product p x q
+//              with p + q < L is one tcgen05.mma (M = 128, N = NCOL, K = 16,
+//              BF16 in, FP32 out) into the accumulator of its level p + q;
+//              the level accumulators of an output tile live in one of two
+//              tensor-memory buffers;
+//   warps 2-9  two epilogue groups of four warps (one warp per tensor-memory
+//              lane quarter); group g takes every other output tile and owns
+//              buffer g, so one group's epilogue overlaps the MMAs of the next
+//              tile and the other group's epilogue.  Per element: exact
+//              integer recombination of the levels, one FP64 conversion, the
+//              augmented-tile scales by exponent arithmetic (Algorithms 2 and
+//              3 of Section 4), one FP64 subtraction; new column maxima by a
+//              butterfly reduction of integer keys.  The per-column scales of
+//              a group's next tile are computed while its MMAs run.
+// Every wait is bounded (SM clock cycles): a wait that runs out sets
+// PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
+// out of bounded waits, tensor memory is freed).
 #include <cuda.h>
 
 #include "split.cuh"
@@ -25,27 +33,19 @@
 
 namespace pevc {
 
-constexpr int kTmRows = 128;
-constexpr int kTmKc = 32;                        // K per stage
-constexpr int kTmGroups = kTmKc / 8;             // core-matrix columns per stage
-constexpr int kTmLboA = kTmRows * 16;            // bytes between K-adjacent core matrices of A
-constexpr int kTmSbo = 128;                      // bytes between M/N-adjacent core matrices
-constexpr long kTmWait = 1L << 22;
+constexpr int kTcRows = 128;                 // M of every MMA: one row tile
+constexpr int kTcK = 16;                     // K per pipeline stage (one MMA K step)
+constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
+constexpr int kTcThreads = 64 + 256;         // producer, MMA issuer, two epilogue groups
 
 template <int NS, int NCOL>
-struct TmGeom {
-  static constexpr int lbo_b = NCOL * 16;
-  static constexpr int slice_a = kTmGroups * kTmLboA;
-  static constexpr int slice_b = kTmGroups * lbo_b;
-  static constexpr int stage = NS * (slice_a + slice_b);
-  static constexpr int stages = (NS >= 5) ? 3 : 4;
-  static constexpr int smem = stages * stage + 1024;   // + barriers
+struct TcGeom {
+  static constexpr int a_slice = kTcRows * kTcK * 2;   // bytes of one A slice per stage
+  static constexpr int b_slice = NCOL * kTcK * 2;      // bytes of one X'' slice per stage
+  static constexpr int stage = NS * (a_slice + b_slice);
+  static constexpr int stages = (200 * 1024) / stage < 8 ? (200 * 1024) / stage : 8;
+  static constexpr int smem = stages * stage + 256;    // + mbarriers and the TMEM address
 };
-
-template <int L, int NCOL>
-__host__ __device__ constexpr uint32_t tm_tmem_cols() {
-  return (2 * L * NCOL <= 128) ? 128 : (2 * L * NCOL <= 256) ? 256 : 512;
-}
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* mbar) {
@@ -61,7 +61,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)));
 }
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;\n" ::); }
+// Named barrier of one epilogue group (ids 1 and 2, 128 threads each).
+__device__ __forceinline__ void group_barrier(int g) { asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g)); }
 
 struct TmTiles {
   const int* chunk_c0;   // first output column of every column chunk (global list)
@@ -71,37 +72,83 @@ struct TmTiles {
   int k_lo, nk;
 };
 
+// Per-column data of an output tile: x = shift of the stored Y, y = shift of
+// the product (without the row exponent), z = flags (1 = column updated,
+// 2 = Y still zero), w = the column's new exponent.
+template <int L, int NCOL>
+__device__ __forceinline__ void tile_scales(const Problem& P, int i, const TmTiles& tt, int t, const int* exX,
+                                            const double* nrmX, const int* F, int col, int4* out) {
+  const int k = tt.k_lo + t / tt.nchunks;
+  const int ch = tt.chunk_first + t % tt.nchunks;
+  const int j = tt.chunk_j[ch];
+  const int c0 = tt.chunk_c0[ch];
+  const int nc = min(NCOL, P.cstart[j + 1] - c0);
+  int on = 0, sY = 0, sX = 0, en = 0, sc = 0;
+  bool yz = true;
+  if (col < nc) {
+    const int q = c0 + col;
+    on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
+    if (on && F[q] == kExpZero) on = 0;
+    sc = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
+  }
+  *out = make_int4(sY, sc, on | (yz ? 2 : 0), en);
+}
+
+// Column maxima of an 8-column block over a warp's 32 rows: a butterfly that
+// halves the columns each step.  On return lanes with (lane & 3) == 0 hold the
+// maximum of column (lane >> 2) & 7 over all 32 lanes.
+__device__ __forceinline__ unsigned long long warp_colmax8(unsigned long long (&k)[8], int lane) {
+  unsigned long long a4[4], a2[2];
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const unsigned long long mine = b4 ? k[u + 4] : k[u], other = b4 ? k[u] : k[u + 4];
+    a4[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 16));
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const unsigned long long mine = b3 ? a4[u + 2] : a4[u], other = b3 ? a4[u] : a4[u + 2];
+    a2[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
+  }
+  const unsigned long long mine = b2 ? a2[1] : a2[0], other = b2 ? a2[0] : a2[1];
+  unsigned long long r = max(mine, __shfl_xor_sync(0xffffffffu, other, 4));
+  r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
+  r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
+  return r;
+}
+
 template <int NS, int L, int NCOL>
-__global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
-                                                       const double* __restrict__ nrmX, const int* __restrict__ eA,
-                                                       const int* __restrict__ F, int ns,
-                                                       const __grid_constant__ CUtensorMap tmA,
-                                                       const __grid_constant__ CUtensorMap tmB) {
-  using G = TmGeom<NS, NCOL>;
+__global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
+                                                             const double* __restrict__ nrmX,
+                                                             const int* __restrict__ eA, const int* __restrict__ F,
+                                                             int ns, const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmB) {
+  static_assert(NCOL % 16 == 0 && 2 * L * NCOL <= 512, "two level-accumulator buffers must fit tensor memory");
+  using G = TcGeom<NS, NCOL>;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::stages * G::stage);
   uint64_t* empty = full + G::stages;
-  uint64_t* tfull = empty + G::stages;
-  uint64_t* tempty = tfull + 2;
+  uint64_t* tfull = empty + G::stages;   // [2] accumulator buffer complete
+  uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (4 warps arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
-  __shared__ int s_on[2][NCOL], s_sY[2][NCOL], s_sc[2][NCOL], s_e[2][NCOL], s_yz[2][NCOL];
-  __shared__ unsigned long long s_key[2][NCOL];
-  __shared__ int s_fail, s_stop;
+  __shared__ int4 s_col[2][NCOL];                  // per group: scales of its current tile
+  __shared__ unsigned long long s_key[2][NCOL];    // per group: new column maxima
+  __shared__ int s_fail, s_stop[2];
   volatile int* fail = &s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tb = P.tb, K2 = 2 * tb;
-  const int nkc = K2 / kTmKc;
+  const int tb = P.tb;
+  const int nks = 2 * tb / kTcK;
   const int total = tt.nk * tt.nchunks;
-  constexpr uint32_t kCols = tm_tmem_cols<L, NCOL>();
+  constexpr uint32_t kCols = 512;
   constexpr uint32_t kTx = (uint32_t)G::stage;
 
   if (tid == 0) {
     for (int s = 0; s < G::stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
     s_fail = 0;
-    s_stop = 0;
+    s_stop[0] = s_stop[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
   if (warp == 1) tc_alloc(tmem_slot, kCols);
@@ -121,15 +168,12 @@ __global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles
         const int ch = tt.chunk_first + t % tt.nchunks;
         const int c0 = tt.chunk_c0[ch];
         const int a_plane = (int)(tri_index(k, i) * ns);
-        for (int kc = 0; kc < nkc; ++kc) {
-          if (!mbar_wait_bounded(&empty[s], ph ^ 1u, kTmWait)) { *fail = 1; break; }
+        for (int kk = 0; kk < nks; ++kk) {
+          if (!mbar_wait_cycles(&empty[s], ph ^ 1u, kTcWait)) { *fail = 1; break; }
           mbar_expect_tx(&full[s], kTx);
-          unsigned char* a_dst = smem + s * G::stage;
-          unsigned char* b_dst = a_dst + NS * G::slice_a;
-          for (int p = 0; p < NS; ++p) {
-            tma_load_4d(a_dst + p * G::slice_a, &tmA, 0, 0, kc * kTmGroups, a_plane + p, &full[s]);
-            tma_load_4d(b_dst + p * G::slice_b, &tmB, 0, c0, kc * kTmGroups, p, &full[s]);
-          }
+          unsigned char* dst = smem + s * G::stage;
+          tma_load_4d(dst, &tmA, 0, 0, 2 * kk, a_plane, &full[s]);
+          tma_load_4d(dst + NS * G::a_slice, &tmB, 0, c0, 2 * kk, 0, &full[s]);
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -137,132 +181,132 @@ __global__ void __launch_bounds__(192, 1) k_update_tma(Problem P, int i, TmTiles
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(kTmRows, NCOL);
-      int s = 0, buf = 0;
-      uint32_t ph = 0, aph = 0;
-      for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
-        if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, kTmWait)) { *fail = 1; break; }
+      constexpr uint32_t idesc = idesc_bf16_f32(kTcRows, NCOL);
+      int s = 0, it = 0;
+      uint32_t ph = 0;
+      for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait_cycles(&tempty[buf], ((it >> 1) & 1) ^ 1u, kTcWait)) { *fail = 1; break; }
         tc_fence_after();
-        const uint32_t acc0 = tmem + (uint32_t)(buf * L * NCOL);
-        uint32_t started = 0;
-        for (int kc = 0; kc < nkc; ++kc) {
-          if (!mbar_wait_bounded(&full[s], ph, kTmWait)) { *fail = 1; break; }
+        const uint32_t acc = tmem + (uint32_t)(buf * L * NCOL);
+        for (int kk = 0; kk < nks; ++kk) {
+          if (!mbar_wait_cycles(&full[s], ph, kTcWait)) { *fail = 1; break; }
           tc_fence_after();
-          const uint32_t a_base = smem_addr(smem + s * G::stage);
-          const uint32_t b_base = a_base + NS * G::slice_a;
+          const uint32_t base = smem_addr(smem + s * G::stage);
+          const uint64_t ad = smem_desc(base, kTcRows * 16, 128);
+          const uint64_t bd = smem_desc(base + NS * G::a_slice, NCOL * 16, 128);
 #pragma unroll
-          for (int kk = 0; kk < kTmKc / 16; ++kk)
+          for (int p = 0; p < NS; ++p)
 #pragma unroll
-            for (int p = 0; p < NS; ++p)
-#pragma unroll
-              for (int q = 0; q < NS; ++q)
-                if (p + q < L) {
-                  const uint64_t ad = smem_desc(a_base + p * G::slice_a + kk * 2 * kTmLboA, kTmLboA, kTmSbo);
-                  const uint64_t bd = smem_desc(b_base + q * G::slice_b + kk * 2 * G::lbo_b, G::lbo_b, kTmSbo);
-                  tc_mma_bf16(acc0 + (uint32_t)((p + q) * NCOL), ad, bd, idesc, (started >> (p + q)) & 1u);
-                  started |= 1u << (p + q);
-                }
+            for (int q = 0; q < NS; ++q)
+              if (p + q < L)
+                tc_mma_bf16(acc + (uint32_t)((p + q) * NCOL), ad + (uint64_t)((p * G::a_slice) >> 4),
+                            bd + (uint64_t)((q * G::b_slice) >> 4), idesc, (kk | p) ? 1u : 0u);
           tc_commit(&empty[s]);             // frees the stage once these MMAs completed
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
         if (*fail) break;
         tc_commit(&tfull[buf]);             // the tile's accumulators are complete
-        buf ^= 1;
-        if (buf == 0) aph ^= 1u;
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int et = tid - 64;                          // 0..127
+    const int g = (warp - 2) >> 2;                    // group: every other tile, buffer g
+    const int et = tid - 64 - 128 * g;                // 0..127 within the group
     const int quarter = warp & 3;                     // tensor-memory lane quarter of this warp
     const int row = 32 * quarter + lane;
-    int buf = 0;
-    uint32_t aph = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-      // a uniform stop decision for the four epilogue warps
-      if (et == 0) s_stop = *fail;
-      epi_barrier();
-      if (s_stop) break;
+    int it = g;
+    int t = blockIdx.x + it * (int)gridDim.x;
+    if (et < NCOL) {
+      s_key[g][et] = 0ull;
+      if (t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][et]);
+    }
+    group_barrier(g);
+    for (; t < total; it += 2, t = blockIdx.x + it * (int)gridDim.x) {
       const int k = tt.k_lo + t / tt.nchunks;
       const int ch = tt.chunk_first + t % tt.nchunks;
       const int j = tt.chunk_j[ch];
       const int c0 = tt.chunk_c0[ch];
       const int cs = P.cstart[j];
       const int nc = min(NCOL, P.cstart[j + 1] - c0);
-      const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
-      double* Yt = tile_ptr(P, k, j);
-      // per-column consolidation + protection while the MMAs run
-      if (et < NCOL) {
-        int on = 0, sY = 0, sX = 0, en = 0;
-        bool yz = true;
-        if (et < nc) {
-          const int q = c0 + et;
-          on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
-          if (on && F[q] == kExpZero) on = 0;
-          s_sc[buf][et] = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
-        }
-        s_on[buf][et] = on;
-        s_sY[buf][et] = sY;
-        s_e[buf][et] = en;
-        s_yz[buf][et] = yz ? 1 : 0;
-        s_key[buf][et] = 0ull;
-      }
-      const int erow = (row < tb) ? eA[tri_index(k, i) * tb + row] : 0;
-      epi_barrier();
-      // this thread's row of Y for every column of the tile, loaded (all
-      // loads in flight at once) while the tile's MMAs run
-      double yv[NCOL];
+      const int hk = P.toff[k + 1] - P.toff[k];
+      const bool rowok = row < hk;
+      double* ycol = tile_ptr(P, k, j) + (size_t)(c0 - cs) * tb + row;   // column col at ycol[col * tb]
+      const int erow = rowok ? eA[tri_index(k, i) * tb + row] : 0;
+      // this row's Y in the first 8 columns: loads in flight while the MMAs run
+      double yv[8];
 #pragma unroll
-      for (int col = 0; col < NCOL; ++col) {
-        yv[col] = 0.0;
-        if (col < nc && row < hk && s_on[buf][col] && !s_yz[buf][col])
-          yv[col] = Yt[(size_t)(c0 + col - cs) * tb + row];
+      for (int u = 0; u < 8; ++u) {
+        const int4 cd = s_col[g][u];
+        yv[u] = (rowok && u < nc && cd.z == 1) ? ycol[(size_t)u * tb] : 0.0;
       }
-      const bool ok = mbar_wait_bounded(&tfull[buf], aph, kTmWait);
+      const bool ok = mbar_wait_cycles(&tfull[g], (uint32_t)((it >> 1) & 1), kTcWait);
       if (!ok) *fail = 1;
       tc_fence_after();
       if (ok) {
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * L * NCOL);
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(g * L * NCOL);
 #pragma unroll
-        for (int cb = 0; cb < NCOL; cb += 16) {
-          uint32_t lv[L][16];
+        for (int cb = 0; cb < NCOL; cb += 8) {
+          uint32_t lv[L][8];
 #pragma unroll
-          for (int s = 0; s < L; ++s) tc_ld16(lane_base + (uint32_t)(s * NCOL + cb), lv[s]);
+          for (int s = 0; s < L; ++s) tc_ld8(lane_base + (uint32_t)(s * NCOL + cb), lv[s]);
           tc_wait_ld();
+          if (cb + 8 == NCOL) {
+            // the buffer is drained: the MMAs of this group's next tile may start
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[g]);
+          }
+          double yn[8];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < 8; ++u) {
+            yn[u] = 0.0;
+            if (cb + 8 < NCOL) {
+              const int col = cb + 8 + u;
+              const int4 cd = s_col[g][col];
+              if (rowok && col < nc && cd.z == 1) yn[u] = ycol[(size_t)col * tb];
+            }
+          }
+          unsigned long long key[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
             const int col = cb + u;
-            const bool con = col < nc && s_on[buf][col];
-            unsigned long long key = 0;
-            if (con && row < hk) {
+            const int4 cd = s_col[g][col];
+            key[u] = 0ull;
+            if ((cd.z & 1) && rowok && col < nc) {
               long long tv = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
-              const double prod = pow2_scale((double)tv, erow + s_sc[buf][col]);
-              const double yold = pow2_scale(yv[col], s_sY[buf][col]);
+              const double prod = pow2_scale((double)tv, erow + cd.y);
+              const double yold = (cd.z & 2) ? 0.0 : pow2_scale(yv[u], cd.x);
               const double ynew = yold - prod;
-              Yt[(size_t)(c0 + col - cs) * tb + row] = ynew;
-              key = abs_key(ynew);
-            }
-            if (con) {
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-              if (lane == 0 && key) atomicMax(&s_key[buf][col], key);
+              ycol[(size_t)col * tb] = ynew;
+              key[u] = abs_key(ynew);
             }
           }
+          const unsigned long long cm = warp_colmax8(key, lane);
+          if ((lane & 3) == 0 && cm) atomicMax(&s_key[g][cb + ((lane >> 2) & 7)], cm);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) yv[u] = yn[u];
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
-      epi_barrier();
-      if (ok && et < nc && s_on[buf][et]) {
-        const long long idx = (long long)k * P.m + c0 + et;
-        P.nrm[idx] = __longlong_as_double((long long)s_key[buf][et]);
-        P.ex[idx] = s_e[buf][et];
+      group_barrier(g);
+      // new norms and exponents of the tile's columns; then the scales of the
+      // group's next tile (its MMAs are running meanwhile)
+      if (et < NCOL) {
+        const int4 cd = s_col[g][et];
+        if (ok && et < nc && (cd.z & 1)) {
+          const long long idx = (long long)k * P.m + c0 + et;
+          P.nrm[idx] = __longlong_as_double((long long)s_key[g][et]);
+          P.ex[idx] = cd.w;
+        }
+        s_key[g][et] = 0ull;
+        const int tn = blockIdx.x + (it + 2) * (int)gridDim.x;
+        if (tn < total) tile_scales<L, NCOL>(P, i, tt, tn, exX, nrmX, F, et, &s_col[g][et]);
       }
-      buf ^= 1;
-      if (buf == 0) aph ^= 1u;
+      if (et == 0) s_stop[g] = *fail;
+      group_barrier(g);
+      if (s_stop[g]) break;
     }
   }
   tc_fence_before();
@@ -293,41 +337,45 @@ static EncodeTiledFn encode_fn() {
 }
 
 int update_tc_setup() {
-  cudaError_t a = cudaFuncSetAttribute(k_update_tma<5, 5, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TmGeom<5, 48>::smem);
-  cudaError_t b = cudaFuncSetAttribute(k_update_tma<3, 3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TmGeom<3, 64>::smem);
+  cudaError_t a = cudaFuncSetAttribute(k_update_tc<5, 5, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcGeom<5, 48>::smem);
+  cudaError_t b = cudaFuncSetAttribute(k_update_tc<3, 3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcGeom<3, 64>::smem);
   return (a == cudaSuccess && b == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
 }
 
-// Tensor maps over the core-matrix-major slice buffers:
-//   A: [tile * ns + slice][K group][row][8]  -> dims {8, tb, 2tb/8, tiles*ns}, box {8, 128, 4, 1}
-//   B: [slice][K group][column][8]           -> dims {8, n_max, 2tb/8, ns},    box {8, NCOL, 4, 1}
+// Tensor maps over the core-matrix-major slice buffers (one K step of 16 =
+// two core-matrix columns per box, every slice of the operand in one box):
+//   A: [tile * ns + slice][K group][row][8] -> dims {8, tb, 2tb/8, tiles*ns}, box {8, 128, 2, NS}
+//   B: [slice][K group][column][8]          -> dims {8, n_max, 2tb/8, ns},    box {8, NCOL, 2, NS}
 int make_tensor_maps(SplitWorkspace& w) {
+  w.tc_ok = false;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return PEVC_ERR_CUDA;
+  if (w.tb != kTcRows) return 0;   // the tensor-core update handles tiles of order 128 only
   const cuuint64_t tb = (cuuint64_t)w.tb, kg = (cuuint64_t)(2 * w.tb / 8);
-  {
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  for (int v = 0; v < 2; ++v) {
+    const cuuint32_t nsl = v == 0 ? 5 : 3;
     cuuint64_t dims[4] = {8, tb, kg, (cuuint64_t)(w.tiles * w.ns)};
     cuuint64_t strides[3] = {16, tb * 16, kg * tb * 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)kTmRows, (cuuint32_t)kTmGroups, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(reinterpret_cast<CUtensorMap*>(w.tmA), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.As, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    cuuint32_t box[4] = {8, (cuuint32_t)kTcRows, 2, nsl};
+    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmA : w.tmA3), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.As, dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PEVC_ERR_CUDA;
   }
   for (int v = 0; v < 2; ++v) {
-    const cuuint32_t ncol = v == 0 ? 48 : 64;
+    const cuuint32_t ncol = v == 0 ? 48 : 64, nsl = v == 0 ? 5 : 3;
     cuuint64_t dims[4] = {8, (cuuint64_t)w.n_max, kg, (cuuint64_t)w.ns};
     cuuint64_t strides[3] = {16, (cuuint64_t)w.n_max * 16, kg * (cuuint64_t)w.n_max * 16};
-    cuuint32_t box[4] = {8, ncol, (cuuint32_t)kTmGroups, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
+    cuuint32_t box[4] = {8, ncol, 2, nsl};
     if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmB48 : w.tmB64), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.Xs,
             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PEVC_ERR_CUDA;
   }
+  w.tc_ok = true;
   return 0;
 }
 
@@ -346,13 +394,14 @@ cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, i
   const int total = tt.nk * tt.nchunks;
   if (total <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)(total < w.nsm ? total : w.nsm);
-  const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA);
   if (five) {
+    const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB48);
-    k_update_tma<5, 5, 48><<<grid, 192, TmGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+    k_update_tc<5, 5, 48><<<grid, kTcThreads, TcGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
   } else {
+    const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA3);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB64);
-    k_update_tma<3, 3, 64><<<grid, 192, TmGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+    k_update_tc<3, 3, 64><<<grid, kTcThreads, TcGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
   }
   return cudaGetLastError();
 }

@@ -110,3 +110,22 @@ def test_split_config1_full(pevc_lib, prec):
     err, res = _errors(p, V)
     print(f"config1 {prec}: err {err:.3e} resid/(nu) {res:.3e} device ms {stats[0]:.1f}")
     assert res <= 100.0 and err <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("kernel", ["tc", "mma"])
+@pytest.mark.parametrize("prec", ["bf16x5", "bf16x3"])
+@pytest.mark.parametrize("n,stress", [(700, False), (700, True), (1030, False)])
+def test_split_update_kernels_tile128(pevc_lib, monkeypatch, kernel, prec, n, stress):
+    """Tiles of order 128 run the update on the tcgen05 tensor cores (TMA-fed,
+    tensor-memory accumulators) or, selected by PEVC_UPDATE_KERNEL=mma, on the
+    mma.sync path; both must meet the same bar (ragged last tiles included)."""
+    monkeypatch.setenv("PEVC_UPDATE_KERNEL", kernel)
+    p = pencilgen.make_pencil(n, 5000 + n + int(stress), stress=stress)
+    V, sc, st, _ = _run(pevc_lib, p.S, p.T, prec, tile=128)
+    assert st == 0
+    assert np.isfinite(V).all()
+    err, res = _errors(p, V)
+    print(f"{kernel} {prec} n={n} stress={stress}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert res <= 100.0
+    if not stress:
+        assert err <= TOL_SPLIT
