@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
       __align__(16) __nv_bfloat16 pk[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) pk[u] = small_int_bf16(sl[u][p]);
-      __nv_bfloat16* dst = As + (((tri * ns + p) * (K2 / 8) + g) * tb + r) * 8ll;
+      __nv_bfloat16* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
     }
   }
@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, 
     int_slices<NS>(bot[u], f, sb);
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-      const long long gt = (long long)p * (K2 / 8) + kap / 8, gb = (long long)p * (K2 / 8) + (tb + kap) / 8;
-      Xs[(gt * mstride + q) * 8 + (kap & 7)] = small_int_bf16(st[p]);
-      Xs[(gb * mstride + q) * 8 + ((tb + kap) & 7)] = small_int_bf16(sb[p]);
+      __nv_bfloat16* xrow = Xs + ((long long)p * mstride + q) * K2;
+      xrow[kap] = small_int_bf16(st[p]);
+      xrow[tb + kap] = small_int_bf16(sb[p]);
     }
   }
 }
@@ -298,23 +298,22 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
   __syncthreads();
   if (!s_any) return;
 
-  // slices are stored core-matrix-major: [slice][k group of 8][row or column][8]
+  // slices are stored K-contiguous: [slice][row or column][K]
   const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
   auto load_stage = [&](int st, int kb) {
     __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * LD;
     __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * LD;
     constexpr int chunks = KC / 8;                        // 16-byte pieces per row
     for (int idx = tid; idx < NS * kSplitRows * chunks; idx += 256) {
-      const int r = idx % kSplitRows, c16 = (idx / kSplitRows) % chunks, p = idx / (chunks * kSplitRows);
+      const int c16 = idx % chunks, r = (idx / chunks) % kSplitRows, p = idx / (chunks * kSplitRows);
       const bool valid = r < tb;
-      const __nv_bfloat16* src = Abase + (((long long)p * (K2 / 8) + kb / 8 + c16) * tb + (valid ? r : 0)) * 8;
+      const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * c16;
       cp_async16(a_dst + (p * kSplitRows + r) * LD + 8 * c16, src, valid);
     }
     for (int idx = tid; idx < NS * kSplitCols * chunks; idx += 256) {
-      const int col = idx % kSplitCols, c16 = (idx / kSplitCols) % chunks, p = idx / (chunks * kSplitCols);
+      const int c16 = idx % chunks, col = (idx / chunks) % kSplitCols, p = idx / (chunks * kSplitCols);
       const bool valid = col < nc;
-      const __nv_bfloat16* src =
-          Xs + (((long long)p * (K2 / 8) + kb / 8 + c16) * mstride + c0 + (valid ? col : 0)) * 8;
+      const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * c16;
       cp_async16(b_dst + (p * kSplitCols + col) * LD + 8 * c16, src, valid);
     }
   };

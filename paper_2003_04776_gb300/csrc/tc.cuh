@@ -21,6 +21,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzled
+// layout that a TMA box with a 128-byte inner extent and SWIZZLE_128B writes:
+// rows of 128 bytes (64 BF16 along K), 8-row atoms of 1024 bytes sbo apart;
+// the atom base must be 1024-byte aligned.  A K step inside the row is an
+// offset of the start address (32 bytes per 16 BF16).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                       // leading byte offset: unused for swizzled K-major
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;                       // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                       // swizzle mode: 128 bytes
+  return d;
+}
+
 // Instruction descriptor of kind::f16 with BF16 operands, FP32 accumulator,
 // both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {

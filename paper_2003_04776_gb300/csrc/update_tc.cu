@@ -4,11 +4,11 @@
 // with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).
 //
 // Persistent CTA (one per SM) of ten warps:
-//   warp 0     TMA producer: per K step of 16 one 4-D box with every slice of
+//   warp 0     TMA producer: per K block of 64 one 3-D box with every slice of
 //              the A row tile and one with every slice of the X'' column
-//              chunk, landing directly in the canonical K-major core-matrix
-//              layout; a ring of shared-memory stages with full / empty
-//              mbarriers;
+//              chunk (rows of 128 bytes, 128-byte swizzle), landing directly
+//              in the K-major layout the MMA reads; a ring of shared-memory
+//              stages with full / empty mbarriers;
 //   warp 1     tensor-memory owner and MMA issuer: every slice product p x q
 //              with p + q < L is one tcgen05.mma (M = 128, N = NCOL, K = 16,
 //              BF16 in, FP32 out) into the accumulator of its level p + q;
@@ -34,25 +34,25 @@
 namespace pevc {
 
 constexpr int kTcRows = 128;                 // M of every MMA: one row tile
-constexpr int kTcK = 16;                     // K per pipeline stage (one MMA K step)
+constexpr int kTcK = 64;                     // K per pipeline stage: one 128-byte swizzle row
 constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
 constexpr int kTcThreads = 64 + 256;         // producer, MMA issuer, two epilogue groups
 
 template <int NS, int NCOL>
 struct TcGeom {
-  static constexpr int a_slice = kTcRows * kTcK * 2;   // bytes of one A slice per stage
-  static constexpr int b_slice = NCOL * kTcK * 2;      // bytes of one X'' slice per stage
+  static constexpr int a_slice = kTcRows * kTcK * 2;   // bytes of one A slice per stage (1024-multiple)
+  static constexpr int b_slice = NCOL * kTcK * 2;      // bytes of one X'' slice per stage (1024-multiple)
   static constexpr int stage = NS * (a_slice + b_slice);
-  static constexpr int stages = (200 * 1024) / stage < 8 ? (200 * 1024) / stage : 8;
-  static constexpr int smem = stages * stage + 256;    // + mbarriers and the TMEM address
+  static constexpr int stages = (225 * 1024) / stage < 4 ? (225 * 1024) / stage : 4;
+  static constexpr int smem = stages * stage + 1024 + 256;   // + alignment slack, mbarriers, TMEM address
 };
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];\n" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(mbar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(mbar))
       : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
                                                              const __grid_constant__ CUtensorMap tmB) {
   static_assert(NCOL % 16 == 0 && 2 * L * NCOL <= 512, "two level-accumulator buffers must fit tensor memory");
   using G = TcGeom<NS, NCOL>;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // swizzle atoms need 1024-byte aligned stage bases
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::stages * G::stage);
   uint64_t* empty = full + G::stages;
   uint64_t* tfull = empty + G::stages;   // [2] accumulator buffer complete
@@ -172,8 +174,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
           if (!mbar_wait_cycles(&empty[s], ph ^ 1u, kTcWait)) { *fail = 1; break; }
           mbar_expect_tx(&full[s], kTx);
           unsigned char* dst = smem + s * G::stage;
-          tma_load_4d(dst, &tmA, 0, 0, 2 * kk, a_plane, &full[s]);
-          tma_load_4d(dst + NS * G::a_slice, &tmB, 0, c0, 2 * kk, 0, &full[s]);
+          tma_load_3d(dst, &tmA, kk * kTcK, 0, a_plane, &full[s]);
+          tma_load_3d(dst + NS * G::a_slice, &tmB, kk * kTcK, c0, 0, &full[s]);
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -193,15 +195,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
           if (!mbar_wait_cycles(&full[s], ph, kTcWait)) { *fail = 1; break; }
           tc_fence_after();
           const uint32_t base = smem_addr(smem + s * G::stage);
-          const uint64_t ad = smem_desc(base, kTcRows * 16, 128);
-          const uint64_t bd = smem_desc(base + NS * G::a_slice, NCOL * 16, 128);
+          const uint64_t ad = smem_desc_sw128(base, 1024);
+          const uint64_t bd = smem_desc_sw128(base + NS * G::a_slice, 1024);
 #pragma unroll
-          for (int p = 0; p < NS; ++p)
+          for (int k16 = 0; k16 < kTcK / 16; ++k16)
 #pragma unroll
-            for (int q = 0; q < NS; ++q)
-              if (p + q < L)
-                tc_mma_bf16(acc + (uint32_t)((p + q) * NCOL), ad + (uint64_t)((p * G::a_slice) >> 4),
-                            bd + (uint64_t)((q * G::b_slice) >> 4), idesc, (kk | p) ? 1u : 0u);
+            for (int p = 0; p < NS; ++p)
+#pragma unroll
+              for (int q = 0; q < NS; ++q)
+                if (p + q < L)
+                  tc_mma_bf16(acc + (uint32_t)((p + q) * NCOL), ad + (uint64_t)((p * G::a_slice + 32 * k16) >> 4),
+                              bd + (uint64_t)((q * G::b_slice + 32 * k16) >> 4), idesc,
+                              (kk | k16 | p) ? 1u : 0u);
           tc_commit(&empty[s]);             // frees the stage once these MMAs completed
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
@@ -344,34 +349,34 @@ int update_tc_setup() {
   return (a == cudaSuccess && b == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
 }
 
-// Tensor maps over the core-matrix-major slice buffers (one K step of 16 =
-// two core-matrix columns per box, every slice of the operand in one box):
-//   A: [tile * ns + slice][K group][row][8] -> dims {8, tb, 2tb/8, tiles*ns}, box {8, 128, 2, NS}
-//   B: [slice][K group][column][8]          -> dims {8, n_max, 2tb/8, ns},    box {8, NCOL, 2, NS}
+// Tensor maps over the K-contiguous slice buffers (one K block of 64 = one
+// 128-byte swizzle row per box row, every slice of the operand in one box):
+//   A: [tile * ns + slice][row][2 tb]  -> dims {2tb, tb, tiles*ns}, box {64, 128, NS}
+//   B: [slice][column][2 tb]           -> dims {2tb, n_max, ns},    box {64, NCOL, NS}
 int make_tensor_maps(SplitWorkspace& w) {
   w.tc_ok = false;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return PEVC_ERR_CUDA;
   if (w.tb != kTcRows) return 0;   // the tensor-core update handles tiles of order 128 only
-  const cuuint64_t tb = (cuuint64_t)w.tb, kg = (cuuint64_t)(2 * w.tb / 8);
-  cuuint32_t es[4] = {1, 1, 1, 1};
+  const cuuint64_t tb = (cuuint64_t)w.tb, K2 = (cuuint64_t)(2 * w.tb);
+  cuuint32_t es[3] = {1, 1, 1};
   for (int v = 0; v < 2; ++v) {
     const cuuint32_t nsl = v == 0 ? 5 : 3;
-    cuuint64_t dims[4] = {8, tb, kg, (cuuint64_t)(w.tiles * w.ns)};
-    cuuint64_t strides[3] = {16, tb * 16, kg * tb * 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)kTcRows, 2, nsl};
-    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmA : w.tmA3), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.As, dims,
-            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    cuuint64_t dims[3] = {K2, tb, (cuuint64_t)(w.tiles * w.ns)};
+    cuuint64_t strides[2] = {K2 * 2, tb * K2 * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTcK, (cuuint32_t)kTcRows, nsl};
+    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmA : w.tmA3), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.As, dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PEVC_ERR_CUDA;
   }
   for (int v = 0; v < 2; ++v) {
     const cuuint32_t ncol = v == 0 ? 48 : 64, nsl = v == 0 ? 5 : 3;
-    cuuint64_t dims[4] = {8, (cuuint64_t)w.n_max, kg, (cuuint64_t)w.ns};
-    cuuint64_t strides[3] = {16, (cuuint64_t)w.n_max * 16, kg * (cuuint64_t)w.n_max * 16};
-    cuuint32_t box[4] = {8, ncol, 2, nsl};
-    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmB48 : w.tmB64), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, w.Xs,
-            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    cuuint64_t dims[3] = {K2, (cuuint64_t)w.n_max, (cuuint64_t)w.ns};
+    cuuint64_t strides[2] = {K2 * 2, (cuuint64_t)w.n_max * K2 * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTcK, ncol, nsl};
+    if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmB48 : w.tmB64), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.Xs,
+            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PEVC_ERR_CUDA;
   }
