@@ -123,6 +123,55 @@ __device__ __forceinline__ double pow2_scale(double x, int e) {
   return ldexp(x, e);
 }
 
+// Branch-free fast paths of the two epilogue scalings (straight-line integer
+// code, so that the independent elements of a block overlap their FP64
+// latencies).  slow is set when an input is subnormal or a result leaves the
+// normal range; the caller then recomputes with the exact helpers.
+//   i64_scaled_fast: t * 2^e rounded to nearest (ties to even), |t| < 2^63
+__device__ __forceinline__ double i64_scaled_fast(long long t, int e, bool& slow) {
+  const unsigned long long sgn = (unsigned long long)t & (1ull << 63);
+  const unsigned long long mag = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)(mag | 1ull));
+  const unsigned long long mm = mag << lz;
+  unsigned long long mant = mm >> 11;
+  const unsigned long long rest = mm & 0x7ffull;
+  mant += (unsigned long long)((rest > 0x400ull) | ((rest == 0x400ull) & (unsigned)(mant & 1ull)));
+  const unsigned long long carry = mant >> 53;
+  mant >>= carry;
+  const int E = 1086 - lz + e + (int)carry;
+  slow |= (mag != 0) & ((E <= 0) | (E >= 2047));
+  const unsigned long long bits = sgn | ((unsigned long long)(E & 0x7ff) << 52) | (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)(mag ? bits : 0ull));
+}
+//   pow2_scale_fast: y * 2^s for a normal or zero y
+__device__ __forceinline__ double pow2_scale_fast(double y, int sh, bool& slow) {
+  const long long b = __double_as_longlong(y);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const bool nz = (b & 0x7fffffffffffffffll) != 0;
+  const int En = E + sh;
+  slow |= nz & ((E == 0) | (En <= 0) | (En >= 2047));
+  return nz ? __longlong_as_double(b + ((long long)sh << 52)) : y;
+}
+
+// t * 2^e rounded to nearest (ties to even), for |t| < 2^63: the IEEE-754
+// fields are assembled with integer instructions (a 64-bit integer to FP64
+// conversion is a slow instruction on this GPU).  Results outside the normal
+// range take the library path.
+__device__ __forceinline__ double i64_scaled(long long t, int e) {
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = t < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                   // leading one at bit 63
+  unsigned long long mant = m >> 11;          // 53 significant bits
+  const unsigned long long rest = m & 0x7ffull;
+  if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ++mant;
+  int E = 1023 + 63 - lz + e;
+  if (mant >> 53) { mant >>= 1; ++E; }
+  if (E <= 0 || E >= 2047) return ldexp((double)t, e);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (mant & ((1ull << 52) - 1))));
+}
+
 // Largest of non-negative doubles via their bit patterns (monotone for x >= 0).
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));

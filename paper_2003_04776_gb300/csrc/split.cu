@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
               long long t = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) t = (t << 8) + (long long)__float2int_rn(acc[s][mt][nt][2 * h + e]);
-              const double prod = pow2_scale((double)t, s_eA[row] + sc);
+              const double prod = i64_scaled(t, s_eA[row] + sc);
               const double yold = yz ? 0.0 : pow2_scale(ycol[row], sY);
               const double ynew = yold - prod;
               ycol[row] = ynew;

@@ -18,11 +18,12 @@
 //              lane quarter); group g takes every other output tile and owns
 //              buffer g, so one group's epilogue overlaps the MMAs of the next
 //              tile and the other group's epilogue.  Per element: exact
-//              integer recombination of the levels, one FP64 conversion, the
-//              augmented-tile scales by exponent arithmetic (Algorithms 2 and
-//              3 of Section 4), one FP64 subtraction; new column maxima by a
-//              butterfly reduction of integer keys.  The per-column scales of
-//              a group's next tile are computed while its MMAs run.
+//              integer recombination of the levels, one conversion to FP64,
+//              the augmented-tile scales (Algorithms 2 and 3 of Section 4) by
+//              exponent arithmetic, one FP64 subtraction; new column maxima by a butterfly reduction of
+//              integer keys.  The per-column scales of a group's next tile are
+//              computed while its MMAs run, and its Y chunk (contiguous in
+//              HBM) is prefetched into L2 one tile ahead.
 // Every wait is bounded (SM clock cycles): a wait that runs out sets
 // PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
 // out of bounded waits, tensor memory is freed).
@@ -37,6 +38,8 @@ constexpr int kTcRows = 128;                 // M of every MMA: one row tile
 constexpr int kTcK = 64;                     // K per pipeline stage: one 128-byte swizzle row
 constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
 constexpr int kTcThreads = 64 + 256;         // producer, MMA issuer, two epilogue groups
+// (ten warps: one SM sub-partition holds three of them, so its 16K registers
+// cap a thread at 168)
 
 template <int NS, int NCOL>
 struct TcGeom {
@@ -60,6 +63,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)));
+}
+// Bulk prefetch of a contiguous global range into L2 (16-byte aligned, size a
+// multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 // Named barrier of one epilogue group (ids 1 and 2, 128 threads each).
 __device__ __forceinline__ void group_barrier(int g) { asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g)); }
@@ -92,6 +100,19 @@ __device__ __forceinline__ void tile_scales(const Problem& P, int i, const TmTil
     sc = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
   }
   *out = make_int4(sY, sc, on | (yz ? 2 : 0), en);
+}
+
+// The Y columns an output tile updates: a contiguous range of its tile.
+template <int NCOL>
+__device__ __forceinline__ void tile_y_range(const Problem& P, const TmTiles& tt, int t, const double*& y,
+                                             uint32_t& bytes) {
+  const int k = tt.k_lo + t / tt.nchunks;
+  const int ch = tt.chunk_first + t % tt.nchunks;
+  const int j = tt.chunk_j[ch];
+  const int c0 = tt.chunk_c0[ch];
+  const int nc = min(NCOL, P.cstart[j + 1] - c0);
+  y = tile_ptr(P, k, j) + (size_t)(c0 - P.cstart[j]) * P.tb;
+  bytes = (uint32_t)(nc * P.tb * sizeof(double));
 }
 
 // Column maxima of an 8-column block over a warp's 32 rows: a butterfly that
@@ -135,7 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
   __shared__ int4 s_col[2][NCOL];                  // per group: scales of its current tile
-  __shared__ unsigned long long s_key[2][NCOL];    // per group: new column maxima
+  __shared__ unsigned long long s_key[2][4][NCOL]; // per group and warp: new column maxima
   __shared__ int s_fail, s_stop[2];
   volatile int* fail = &s_fail;
 
@@ -222,12 +243,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
     const int row = 32 * quarter + lane;
     int it = g;
     int t = blockIdx.x + it * (int)gridDim.x;
-    if (et < NCOL) {
-      s_key[g][et] = 0ull;
-      if (t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][et]);
+    if (et < NCOL && t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][et]);
+    if (et == 0 && t < total) {
+      const double* yp;
+      uint32_t yb;
+      tile_y_range<NCOL>(P, tt, t, yp, yb);
+      prefetch_l2(yp, yb);
     }
     group_barrier(g);
     for (; t < total; it += 2, t = blockIdx.x + it * (int)gridDim.x) {
+      {
+        // the Y chunk of this group's next tile into L2
+        const int tn = t + 2 * (int)gridDim.x;
+        if (et == 0 && tn < total) {
+          const double* yp;
+          uint32_t yb;
+          tile_y_range<NCOL>(P, tt, tn, yp, yb);
+          prefetch_l2(yp, yb);
+        }
+      }
       const int k = tt.k_lo + t / tt.nchunks;
       const int ch = tt.chunk_first + t % tt.nchunks;
       const int j = tt.chunk_j[ch];
@@ -250,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
       tc_fence_after();
       if (ok) {
         const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(g * L * NCOL);
-#pragma unroll
+#pragma unroll 1
         for (int cb = 0; cb < NCOL; cb += 8) {
           uint32_t lv[L][8];
 #pragma unroll
@@ -272,25 +306,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
               if (rowok && col < nc && cd.z == 1) yn[u] = ycol[(size_t)col * tb];
             }
           }
-          unsigned long long key[8];
+          // straight-line fast path over the block's 8 elements; the exact
+          // path only when a value leaves the normal range
+          double ynew[8];
+          bool act[8];
+          bool slow = false;
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int col = cb + u;
             const int4 cd = s_col[g][col];
-            key[u] = 0ull;
-            if ((cd.z & 1) && rowok && col < nc) {
+            act[u] = (cd.z & 1) && rowok && col < nc;
+            long long tv = 0;
+#pragma unroll
+            for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
+            bool sl = false;
+            const double prod = i64_scaled_fast(tv, erow + cd.y, sl);
+            const double yold = (cd.z & 2) ? 0.0 : pow2_scale_fast(yv[u], cd.x, sl);
+            slow |= act[u] & sl;
+            ynew[u] = yold - prod;
+          }
+          if (__any_sync(0xffffffffu, slow)) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int4 cd = s_col[g][cb + u];
               long long tv = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
               const double prod = pow2_scale((double)tv, erow + cd.y);
               const double yold = (cd.z & 2) ? 0.0 : pow2_scale(yv[u], cd.x);
-              const double ynew = yold - prod;
-              ycol[(size_t)col * tb] = ynew;
-              key[u] = abs_key(ynew);
+              if (act[u]) ynew[u] = yold - prod;
             }
           }
+          unsigned long long key[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (act[u]) ycol[(size_t)(cb + u) * tb] = ynew[u];
+            key[u] = act[u] ? abs_key(ynew[u]) : 0ull;
+          }
           const unsigned long long cm = warp_colmax8(key, lane);
-          if ((lane & 3) == 0 && cm) atomicMax(&s_key[g][cb + ((lane >> 2) & 7)], cm);
+          if ((lane & 3) == 0) s_key[g][quarter][cb + ((lane >> 2) & 7)] = cm;
 #pragma unroll
           for (int u = 0; u < 8; ++u) yv[u] = yn[u];
         }
@@ -302,10 +356,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
         const int4 cd = s_col[g][et];
         if (ok && et < nc && (cd.z & 1)) {
           const long long idx = (long long)k * P.m + c0 + et;
-          P.nrm[idx] = __longlong_as_double((long long)s_key[g][et]);
+          const unsigned long long km =
+              max(max(s_key[g][0][et], s_key[g][1][et]), max(s_key[g][2][et], s_key[g][3][et]));
+          P.nrm[idx] = __longlong_as_double((long long)km);
           P.ex[idx] = cd.w;
         }
-        s_key[g][et] = 0ull;
         const int tn = blockIdx.x + (it + 2) * (int)gridDim.x;
         if (tn < total) tile_scales<L, NCOL>(P, i, tt, tn, exX, nrmX, F, et, &s_col[g][et]);
       }
