@@ -125,6 +125,10 @@ int pevc_solve(pevc_plan_t plan, const double *S, int lds, const double *T, int 
  * status, so one bad pencil does not stop the others.  Every n[i] must be
  * <= n_max and count <= batch_max.  Returns 0 when the arguments are valid
  * and every pencil was processed (check status[]), else -i or a PEVC_ERR_*.
+ * A plan made with batch_max > 1 owns up to 8 child workspaces with their own
+ * streams (as many as about 4 GB allows) and runs that many pencils at once;
+ * the batch is ordered after the work already on the plan's stream and the
+ * call synchronises on return.
  */
 int pevc_solve_batched(pevc_plan_t plan, int count,
                        const double *const *S, const int *lds,

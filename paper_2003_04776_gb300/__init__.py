@@ -228,6 +228,44 @@ class Plan:
                            ldv or max(n, 1), scale.data_ptr())
         return st, m
 
+    def solve_batched(self, pencils, selects=None):
+        """Several pencils [(S, T), ...] in one pevc_solve_batched call (the
+        plan needs batch_max >= len(pencils)).  Returns (status, [(V, scale,
+        status_b), ...]) with V as n x m numpy arrays."""
+        import torch
+        count = len(pencils)
+        keep = []
+        S_p, T_p, V_p, sc_p, sel_p, n_l, ld_l = [], [], [], [], [], [], []
+        for b, (S, T) in enumerate(pencils):
+            n = int(S.shape[0])
+            if n > 0:
+                St, Tt = to_device_colmajor(S), to_device_colmajor(T)
+            else:
+                St = Tt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            V = torch.empty((max(n, 1), max(n, 1)), dtype=torch.float64, device="cuda")
+            sc = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+            sel = None
+            if selects is not None and selects[b] is not None:
+                sel = torch.as_tensor(np.asarray(selects[b], dtype=np.int32)).to("cuda")
+            keep += [St, Tt, V, sc, sel]
+            S_p.append(St.data_ptr())
+            T_p.append(Tt.data_ptr())
+            V_p.append(V.data_ptr())
+            sc_p.append(sc.data_ptr())
+            sel_p.append(sel.data_ptr() if sel is not None else 0)
+            n_l.append(n)
+            ld_l.append(max(n, 1))
+        with torch.cuda.stream(self.stream):
+            st, m_out, stat = pevc_solve_batched(self.h, count, S_p, ld_l, T_p, ld_l, n_l,
+                                                 sel_p if selects is not None else None, V_p, ld_l, sc_p)
+        out = []
+        for b in range(count):
+            n, m = n_l[b], m_out[b]
+            V, sc = keep[5 * b + 2], keep[5 * b + 3]
+            Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0))
+            out.append((np.asfortranarray(Vh[:n, :m]), sc[:m].cpu().numpy(), stat[b]))
+        return st, out
+
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.
 

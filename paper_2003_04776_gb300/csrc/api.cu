@@ -74,6 +74,13 @@ struct pevc_plan_s {
   cudaStream_t aux = nullptr;
   cudaEvent_t* sev = nullptr;   // 2 * Mmax scheduling events
   bool lookahead = true;
+  // batched solves: child plans (own workspace and stream each) run pencils
+  // concurrently
+  int nchild = 0;
+  pevc_plan_s* child[8] = {};
+  cudaStream_t cstream[8] = {};
+  cudaEvent_t bev = nullptr;     // the children wait for the plan's stream
+  unsigned* h_bstatus = nullptr; // pinned [batch_max] status words
 };
 
 namespace {
@@ -123,6 +130,12 @@ int halloc(Tp** p, size_t count) {
 
 void free_plan(pevc_plan_t p) {
   if (!p) return;
+  for (int c = 0; c < 8; ++c) {
+    if (p->child[c]) free_plan(p->child[c]);
+    if (p->cstream[c]) cudaStreamDestroy(p->cstream[c]);
+  }
+  if (p->bev) cudaEventDestroy(p->bev);
+  if (p->h_bstatus) cudaFreeHost(p->h_bstatus);
   void* dev[] = {p->Y, p->ex, p->nrm, p->EA, p->tcS, p->tcT, p->gmax, p->ca, p->cb, p->cbeta,
                  p->blk, p->toff, p->cstart, p->ccol, p->kind, p->status, p->subd,
                  p->dperm, p->dcpos, p->dccnt, p->dcfirst};
@@ -276,26 +289,34 @@ int read_status(pevc_plan_t p, unsigned* bits) {
   return 0;
 }
 
-int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n,
-              const int32_t* sel, double* V, int ldv, int32_t* scale, int* m_out) {
+// Phase 1 of a solve: the subdiagonal (block structure) and the selection to
+// the host, stream-ordered and asynchronous.
+int structure_begin(pevc_plan_t p, const double* S, int lds, int n, const int32_t* sel) {
   cudaStream_t s = p->stream;
-  *m_out = 0;
-  for (double& x : p->stats) x = 0.0;
-  if (n == 0) return 0;
-  p->prof.reset();
-  CK(cudaEventRecord(p->ev[0], s));
-  // 1. block structure and selection to the host
   p->prof.begin(s);
   CK(launch_gather_subdiag(S, lds, n, p->subd, s));
   p->prof.end(s, 3, 0.0);
   if (n > 1) CK(cudaMemcpyAsync(p->h_subd, p->subd, (size_t)(n - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (sel) CK(cudaMemcpyAsync(p->h_sel, sel, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  Structure st;
-  int rc = analyse(p, n, sel != nullptr, st);
-  if (rc) return rc;
-  *m_out = st.m;
-  // 2. structure to the device, pre-processing tasks
+  return 0;
+}
+
+// Phase 2: wait for phase 1 (and everything before it on the plan's stream)
+// and analyse the structure on the host.
+int structure_end(pevc_plan_t p, int n, bool has_sel, Structure& st) {
+  CK(cudaStreamSynchronize(p->stream));
+  return analyse(p, n, has_sel, st);
+}
+
+// Phase 3: everything else, stream-ordered.  With check_prepass the call reads
+// the status after the pre-pass and returns early for a bad pencil; without it
+// the whole graph is enqueued and the status is read once at the end (the
+// kernels run to completion on any input: their loops depend only on the
+// structure).
+int solve_enqueue(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n, double* V, int ldv,
+                  int32_t* scale, const Structure& st, bool check_prepass) {
+  cudaStream_t s = p->stream;
+  // structure to the device, pre-processing tasks
   CK(cudaMemcpyAsync(p->blk, p->h_blk, (size_t)n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(p->toff, p->h_toff, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(p->cstart, p->h_cstart, (size_t)(st.M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -314,62 +335,85 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   CK(launch_prepass(P, s));
   p->prof.end(s, 3, 0.0);
   ++p->prof.launches;   // the prepass is two kernels
-  unsigned bits = 0;
-  if ((rc = read_status(p, &bits))) return rc;
-  if (bits) return status_from_bits(bits);
+  if (check_prepass) {
+    unsigned bits = 0;
+    int rc = read_status(p, &bits);
+    if (rc) return rc;
+    if (bits) return status_from_bits(bits);
+  }
   CK(cudaEventRecord(p->ev[1], s));
   if (st.m == 0) {
     CK(cudaEventRecord(p->ev[2], s));
     CK(cudaEventRecord(p->ev[3], s));
     CK(cudaEventRecord(p->ev[4], s));
-  } else {
-    p->prof.begin(s);
-    CK(launch_init_state(P, s));
-    p->prof.end(s, 3, 0.0);
-    // 3. the task graph, bottom-up by block row
-    SchedContext sc{p->aux, p->sev, p->lookahead};
-    if (p->prec == PEVC_FP64) {
-      struct F64Ops : StageOps {
-        const Problem& P;
-        pevc_plan_t p;
-        F64Ops(const Problem& P_, pevc_plan_t p_) : P(P_), p(p_) {}
-        cudaError_t tips(cudaStream_t st) override {
-          p->prof.begin(st);
-          cudaError_t e = launch_diag(P, 0, kDiagTip, st);
-          p->prof.end(st, 1, 0.0);
-          return e;
-        }
-        cudaError_t diag(int i, cudaStream_t st) override {
-          p->prof.begin(st);
-          cudaError_t e = launch_diag(P, i, kDiagSolve, st);
-          p->prof.end(st, 1, 0.0);
-          return e;
-        }
-        cudaError_t prep(int, cudaStream_t) override { return cudaSuccess; }
-        cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t st) override {
-          const double rows = p->h_toff[k_hi] - p->h_toff[k_lo], cols = P.m - p->h_cstart[i];
-          const double K = 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
-          p->prof.begin(st);
-          cudaError_t e = launch_update_f64(P, i, k_lo, k_hi, st);
-          p->prof.end(st, 0, 2.0 * rows * cols * K);
-          return e;
-        }
-      } ops(P, p);
-      CK(walk_dag(st.M, ops, s, sc.aux, sc.ev, sc.lookahead));
-      CK(cudaEventRecord(p->ev[2], s));
-      CK(cudaEventRecord(p->ev[3], s));
-    } else {
-      HostStructure hs{p->h_toff, p->h_cstart};
-      SplitConfig cfg = split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0);
-      rc = split_solve(p->split, P, hs, cfg, s, sc, p->prof, p->ev[2], p->ev[3]);
-      if (rc) return rc;
-    }
-    // 4. post-processing: consistent scaling and normalisation
-    p->prof.begin(s);
-    CK(launch_post(P, V, ldv, scale, (p->flags & PEVC_NO_NORMALISE) == 0, s));
-    p->prof.end(s, 3, 0.0);
-    CK(cudaEventRecord(p->ev[4], s));
+    return 0;
   }
+  p->prof.begin(s);
+  CK(launch_init_state(P, s));
+  p->prof.end(s, 3, 0.0);
+  // the task graph, bottom-up by block row
+  SchedContext sc{p->aux, p->sev, p->lookahead};
+  if (p->prec == PEVC_FP64) {
+    struct F64Ops : StageOps {
+      const Problem& P;
+      pevc_plan_t p;
+      F64Ops(const Problem& P_, pevc_plan_t p_) : P(P_), p(p_) {}
+      cudaError_t tips(cudaStream_t st) override {
+        p->prof.begin(st);
+        cudaError_t e = launch_diag(P, 0, kDiagTip, st);
+        p->prof.end(st, 1, 0.0);
+        return e;
+      }
+      cudaError_t diag(int i, cudaStream_t st) override {
+        p->prof.begin(st);
+        cudaError_t e = launch_diag(P, i, kDiagSolve, st);
+        p->prof.end(st, 1, 0.0);
+        return e;
+      }
+      cudaError_t prep(int, cudaStream_t) override { return cudaSuccess; }
+      cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t st) override {
+        const double rows = p->h_toff[k_hi] - p->h_toff[k_lo], cols = P.m - p->h_cstart[i];
+        const double K = 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
+        p->prof.begin(st);
+        cudaError_t e = launch_update_f64(P, i, k_lo, k_hi, st);
+        p->prof.end(st, 0, 2.0 * rows * cols * K);
+        return e;
+      }
+    } ops(P, p);
+    CK(walk_dag(st.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+    CK(cudaEventRecord(p->ev[2], s));
+    CK(cudaEventRecord(p->ev[3], s));
+  } else {
+    HostStructure hs{p->h_toff, p->h_cstart};
+    SplitConfig cfg = split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0);
+    int rc = split_solve(p->split, P, hs, cfg, s, sc, p->prof, p->ev[2], p->ev[3]);
+    if (rc) return rc;
+  }
+  // post-processing: consistent scaling and normalisation
+  p->prof.begin(s);
+  CK(launch_post(P, V, ldv, scale, (p->flags & PEVC_NO_NORMALISE) == 0, s));
+  p->prof.end(s, 3, 0.0);
+  CK(cudaEventRecord(p->ev[4], s));
+  return 0;
+}
+
+int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n,
+              const int32_t* sel, double* V, int ldv, int32_t* scale, int* m_out) {
+  cudaStream_t s = p->stream;
+  *m_out = 0;
+  for (double& x : p->stats) x = 0.0;
+  if (n == 0) return 0;
+  p->prof.reset();
+  CK(cudaEventRecord(p->ev[0], s));
+  // 1. block structure and selection to the host
+  int rc = structure_begin(p, S, lds, n, sel);
+  if (rc) return rc;
+  Structure st;
+  if ((rc = structure_end(p, n, sel != nullptr, st))) return rc;
+  *m_out = st.m;
+  // 2. pre-processing, the task graph, post-processing
+  if ((rc = solve_enqueue(p, S, lds, T, ldt, n, V, ldv, scale, st, true))) return rc;
+  unsigned bits = 0;
   if ((rc = read_status(p, &bits))) return rc;
   float ms[4] = {0, 0, 0, 0};
   cudaEventElapsedTime(&ms[0], p->ev[0], p->ev[4]);
@@ -395,6 +439,70 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
     p->kprof[3 * k + 2] += p->prof.flops[q];
   }
   return status_from_bits(bits);
+}
+
+// Argument checks of one pencil (pevc_solve's codes).
+int check_args(int n_max, const double* S, int lds, const double* T, int ldt, int n, const double* V, int ldv,
+               const int32_t* scale) {
+  if (n < 0 || n > n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !V) return -8;
+  if (ldv < std::max(n, 1)) return -9;
+  if (n > 0 && !scale) return -10;
+  return 0;
+}
+
+// A batch on the child plans: pencil b runs on child b % nchild (its own
+// workspace and stream), so up to nchild pencils are in flight at once.  Per
+// wave the host reads every child's block structure, then enqueues each
+// pencil's whole graph without waiting; the status words come back with the
+// last synchronisation.
+int solve_batched(pevc_plan_t p, int count, const double* const* S, const int* lds, const double* const* T,
+                  const int* ldt, const int* n, const int32_t* const* select, double* const* V_out,
+                  const int* ldv, int32_t* const* scale_out, int* m_out, int* status) {
+  const int K = p->nchild;
+  CK(cudaEventRecord(p->bev, p->stream));   // the batch follows the work already on the plan's stream
+  for (int c = 0; c < K; ++c) CK(cudaStreamWaitEvent(p->child[c]->stream, p->bev, 0));
+  std::vector<char> pending(count > 0 ? count : 1, 0);
+  for (int w = 0; w < count; w += K) {
+    const int nb = std::min(K, count - w);
+    for (int c = 0; c < nb; ++c) {
+      const int b = w + c;
+      m_out[b] = 0;
+      status[b] = check_args(p->n_max, S[b], lds[b], T[b], ldt[b], n[b], V_out[b], ldv[b], scale_out[b]);
+      if (status[b] || n[b] == 0) continue;
+      const int32_t* sel = select ? select[b] : nullptr;
+      status[b] = structure_begin(p->child[c], S[b], lds[b], n[b], sel);
+      pending[b] = status[b] == 0;
+    }
+    for (int c = 0; c < nb; ++c) {
+      const int b = w + c;
+      if (!pending[b]) continue;
+      pevc_plan_t q = p->child[c];
+      Structure st;
+      const int32_t* sel = select ? select[b] : nullptr;
+      int rc = structure_end(q, n[b], sel != nullptr, st);
+      if (!rc) {
+        m_out[b] = st.m;
+        rc = solve_enqueue(q, S[b], lds[b], T[b], ldt[b], n[b], V_out[b], ldv[b], scale_out[b], st, false);
+      }
+      if (!rc && cudaMemcpyAsync(&p->h_bstatus[b], q->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 q->stream) != cudaSuccess)
+        rc = PEVC_ERR_CUDA;
+      if (rc) {
+        status[b] = rc;
+        pending[b] = 0;
+        if (rc == PEVC_ERR_CUDA) return PEVC_ERR_CUDA;
+      }
+    }
+  }
+  for (int c = 0; c < K; ++c) CK(cudaStreamSynchronize(p->child[c]->stream));
+  for (int b = 0; b < count; ++b)
+    if (pending[b]) status[b] = status_from_bits(p->h_bstatus[b]);
+  return 0;
 }
 
 }  // namespace
@@ -480,6 +588,24 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
       if (cudaEventCreateWithFlags(&p->sev[q], cudaEventDisableTiming) != cudaSuccess) rc = PEVC_ERR_CUDA;
   }
   if (!rc && prec != PEVC_FP64) rc = split_alloc(p->split, n_max, p->tb, p->Mmax, prec);
+  if (!rc && batch_max > 1) {
+    // child plans for concurrent pencils, as many as about 4 GB of workspace
+    // allows (at most 8)
+    const double tiles = (double)p->Mmax * (p->Mmax + 1) / 2.0 * (double)p->tb * p->tb;
+    const double bytes = tiles * (prec == PEVC_FP64 ? 8.0 : 36.0) + 64.0 * nm;
+    int k = (int)(4e9 / bytes);
+    k = std::max(1, std::min(k, std::min(batch_max, 8)));
+    rc = halloc(&p->h_bstatus, (size_t)batch_max);
+    if (!rc && cudaEventCreateWithFlags(&p->bev, cudaEventDisableTiming) != cudaSuccess) rc = PEVC_ERR_CUDA;
+    for (int c = 0; !rc && c < k; ++c) {
+      if (cudaStreamCreateWithFlags(&p->cstream[c], cudaStreamNonBlocking) != cudaSuccess) {
+        rc = PEVC_ERR_CUDA;
+        break;
+      }
+      rc = pevc_plan(&p->child[c], n_max, 1, prec, p->tb, flags, p->cstream[c]);
+      if (!rc) p->nchild = c + 1;
+    }
+  }
   if (rc) {
     free_plan(p);
     return rc;
@@ -511,6 +637,8 @@ int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, cons
   if (count < 0 || count > plan->batch_max) return -2;
   if (count > 0 && (!S || !lds || !T || !ldt || !n || !V_out || !ldv || !scale_out || !m_out || !status))
     return -3;
+  if (plan->nchild > 0)
+    return solve_batched(plan, count, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out, status);
   for (int b = 0; b < count; ++b) {
     status[b] = pevc_solve(plan, S[b], lds[b], T[b], ldt[b], n[b], select ? select[b] : nullptr,
                            V_out[b], ldv[b], scale_out[b], &m_out[b]);
