@@ -268,13 +268,13 @@ def main():
     if roof["achieved"]:
         roof["achieved"] = round(roof["achieved"], 2)
         roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
-    roof["traffic"] = measured_traffic(roof["kernel"], n, args.prec)
     if args.prec == "fp64":
         roof["kernel"] = "k_update_f64"
     elif info[0] == 128 and not os.environ.get("PEVC_UPDATE_KERNEL", "").startswith("m"):
         roof["kernel"] = "k_update_tc"
     else:
         roof["kernel"] = "k_update_split"
+    roof["traffic"] = measured_traffic(roof["kernel"], n, args.prec)
     roof["launches_per_step"] = upd_n
     roof["avg_launch_ms"] = round(upd_ms / max(upd_n, 1), 4)
     roof["share_of_step"] = round(upd_ms / ms, 3)

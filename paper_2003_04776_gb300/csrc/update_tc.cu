@@ -37,9 +37,11 @@ namespace pevc {
 constexpr int kTcRows = 128;                 // M of every MMA: one row tile
 constexpr int kTcK = 64;                     // K per pipeline stage: one 128-byte swizzle row
 constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
-constexpr int kTcThreads = 64 + 256;         // producer, MMA issuer, two epilogue groups
-// (ten warps: one SM sub-partition holds three of them, so its 16K registers
-// cap a thread at 168)
+constexpr int kTcEpiWarps = 8;               // warps per epilogue group: two per lane quarter
+constexpr int kTcColBlock = 4;               // columns per epilogue step
+constexpr int kTcThreads = 64 + 2 * 32 * kTcEpiWarps;   // producer, MMA issuer, two epilogue groups
+// (eighteen warps: one SM sub-partition holds five of them, so its 16K
+// registers cap a thread at 96)
 
 template <int NS, int NCOL>
 struct TcGeom {
@@ -69,8 +71,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
-// Named barrier of one epilogue group (ids 1 and 2, 128 threads each).
-__device__ __forceinline__ void group_barrier(int g) { asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g)); }
+// Named barrier of one epilogue group (ids 1 and 2).
+__device__ __forceinline__ void group_barrier(int g) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(32 * kTcEpiWarps));
+}
 
 struct TmTiles {
   const int* chunk_c0;   // first output column of every column chunk (global list)
@@ -115,31 +119,27 @@ __device__ __forceinline__ void tile_y_range(const Problem& P, const TmTiles& tt
   bytes = (uint32_t)(nc * P.tb * sizeof(double));
 }
 
-// Column maxima of an 8-column block over a warp's 32 rows: a butterfly that
-// halves the columns each step.  On return lanes with (lane & 3) == 0 hold the
-// maximum of column (lane >> 2) & 7 over all 32 lanes.
-__device__ __forceinline__ unsigned long long warp_colmax8(unsigned long long (&k)[8], int lane) {
-  unsigned long long a4[4], a2[2];
-  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const unsigned long long mine = b4 ? k[u + 4] : k[u], other = b4 ? k[u] : k[u + 4];
-    a4[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 16));
-  }
+// Column maxima of a 4-column block over a warp's 32 rows: a butterfly that
+// halves the columns each step.  On return lanes with (lane & 7) == 0 hold the
+// maximum of column (lane >> 3) & 3 over all 32 lanes.
+__device__ __forceinline__ unsigned long long warp_colmax4(unsigned long long (&k)[4], int lane) {
+  unsigned long long a2[2];
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const unsigned long long mine = b3 ? a4[u + 2] : a4[u], other = b3 ? a4[u] : a4[u + 2];
-    a2[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
+    const unsigned long long mine = b4 ? k[u + 2] : k[u], other = b4 ? k[u] : k[u + 2];
+    a2[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 16));
   }
-  const unsigned long long mine = b2 ? a2[1] : a2[0], other = b2 ? a2[0] : a2[1];
-  unsigned long long r = max(mine, __shfl_xor_sync(0xffffffffu, other, 4));
+  const unsigned long long mine = b3 ? a2[1] : a2[0], other = b3 ? a2[0] : a2[1];
+  unsigned long long r = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
+  r = max(r, __shfl_xor_sync(0xffffffffu, r, 4));
   r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
   r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
   return r;
 }
 
 template <int NS, int L, int NCOL>
-__global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
+__global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
                                                              const double* __restrict__ nrmX,
                                                              const int* __restrict__ eA, const int* __restrict__ F,
                                                              int ns, const __grid_constant__ CUtensorMap tmA,
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::stages * G::stage);
   uint64_t* empty = full + G::stages;
   uint64_t* tfull = empty + G::stages;   // [2] accumulator buffer complete
-  uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (4 warps arrive)
+  uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (its group's warps arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
   __shared__ int4 s_col[2][NCOL];                  // per group: scales of its current tile
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
 
   if (tid == 0) {
     for (int s = 0; s < G::stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kTcEpiWarps); }
     s_fail = 0;
     s_stop[0] = s_stop[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
@@ -237,10 +237,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int g = (warp - 2) >> 2;                    // group: every other tile, buffer g
-    const int et = tid - 64 - 128 * g;                // 0..127 within the group
+    constexpr int CW = kTcColBlock;
+    constexpr int HALF = NCOL / 2;                    // columns of one warp
+    const int ew = warp - 2;
+    const int g = ew / kTcEpiWarps;                   // group: every other tile, buffer g
+    const int et = tid - 64 - 32 * kTcEpiWarps * g;   // thread index within the group
     const int quarter = warp & 3;                     // tensor-memory lane quarter of this warp
+    const int half = (ew >> 2) & 1;                   // which half of the tile's columns
     const int row = 32 * quarter + lane;
+    const int cbeg = half * HALF;
     int it = g;
     int t = blockIdx.x + it * (int)gridDim.x;
     if (et < NCOL && t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][et]);
@@ -272,12 +277,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
       const bool rowok = row < hk;
       double* ycol = tile_ptr(P, k, j) + (size_t)(c0 - cs) * tb + row;   // column col at ycol[col * tb]
       const int erow = rowok ? eA[tri_index(k, i) * tb + row] : 0;
-      // this row's Y in the first 8 columns: loads in flight while the MMAs run
-      double yv[8];
+      // this row's Y in the warp's first block: loads in flight while the MMAs run
+      double yv[CW];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int4 cd = s_col[g][u];
-        yv[u] = (rowok && u < nc && cd.z == 1) ? ycol[(size_t)u * tb] : 0.0;
+      for (int u = 0; u < CW; ++u) {
+        const int col = cbeg + u;
+        const int4 cd = s_col[g][col];
+        yv[u] = (rowok && col < nc && cd.z == 1) ? ycol[(size_t)col * tb] : 0.0;
       }
       const bool ok = mbar_wait_cycles(&tfull[g], (uint32_t)((it >> 1) & 1), kTcWait);
       if (!ok) *fail = 1;
@@ -285,34 +291,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
       if (ok) {
         const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(g * L * NCOL);
 #pragma unroll 1
-        for (int cb = 0; cb < NCOL; cb += 8) {
-          uint32_t lv[L][8];
+        for (int cb = cbeg; cb < cbeg + HALF; cb += CW) {
+          uint32_t lv[L][CW];
 #pragma unroll
-          for (int s = 0; s < L; ++s) tc_ld8(lane_base + (uint32_t)(s * NCOL + cb), lv[s]);
+          for (int s = 0; s < L; ++s) tc_ld4(lane_base + (uint32_t)(s * NCOL + cb), lv[s]);
           tc_wait_ld();
-          if (cb + 8 == NCOL) {
-            // the buffer is drained: the MMAs of this group's next tile may start
+          if (cb + CW == cbeg + HALF) {
+            // this warp's part of the buffer is drained: once every warp of
+            // the group arrived, the MMAs of the group's next tile may start
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[g]);
           }
-          double yn[8];
+          double yn[CW];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < CW; ++u) {
             yn[u] = 0.0;
-            if (cb + 8 < NCOL) {
-              const int col = cb + 8 + u;
+            if (cb + CW < cbeg + HALF) {
+              const int col = cb + CW + u;
               const int4 cd = s_col[g][col];
               if (rowok && col < nc && cd.z == 1) yn[u] = ycol[(size_t)col * tb];
             }
           }
-          // straight-line fast path over the block's 8 elements; the exact
+          // straight-line fast path over the block's elements; the exact
           // path only when a value leaves the normal range
-          double ynew[8];
-          bool act[8];
+          double ynew[CW];
+          bool act[CW];
           bool slow = false;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < CW; ++u) {
             const int col = cb + u;
             const int4 cd = s_col[g][col];
             act[u] = (cd.z & 1) && rowok && col < nc;
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
           }
           if (__any_sync(0xffffffffu, slow)) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < CW; ++u) {
               const int4 cd = s_col[g][cb + u];
               long long tv = 0;
 #pragma unroll
@@ -337,16 +344,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(Problem P, int i, T
               if (act[u]) ynew[u] = yold - prod;
             }
           }
-          unsigned long long key[8];
+          unsigned long long key[CW];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < CW; ++u) {
             if (act[u]) ycol[(size_t)(cb + u) * tb] = ynew[u];
             key[u] = act[u] ? abs_key(ynew[u]) : 0ull;
           }
-          const unsigned long long cm = warp_colmax8(key, lane);
-          if ((lane & 3) == 0) s_key[g][quarter][cb + ((lane >> 2) & 7)] = cm;
+          const unsigned long long cm = warp_colmax4(key, lane);
+          if ((lane & 7) == 0) s_key[g][quarter][cb + ((lane >> 3) & 3)] = cm;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) yv[u] = yn[u];
+          for (int u = 0; u < CW; ++u) yv[u] = yn[u];
         }
       }
       group_barrier(g);
