@@ -14,16 +14,18 @@
 //              BF16 in, FP32 out) into the accumulator of its level p + q;
 //              the level accumulators of an output tile live in one of two
 //              tensor-memory buffers;
-//   warps 2-9  two epilogue groups of four warps (one warp per tensor-memory
-//              lane quarter); group g takes every other output tile and owns
-//              buffer g, so one group's epilogue overlaps the MMAs of the next
-//              tile and the other group's epilogue.  Per element: exact
-//              integer recombination of the levels, one conversion to FP64,
-//              the augmented-tile scales (Algorithms 2 and 3 of Section 4) by
-//              exponent arithmetic, one FP64 subtraction; new column maxima by a butterfly reduction of
-//              integer keys.  The per-column scales of a group's next tile are
-//              computed while its MMAs run, and its Y chunk (contiguous in
-//              HBM) is prefetched into L2 one tile ahead.
+//   warps 2-17 two epilogue groups of eight warps (two per tensor-memory
+//              lane quarter, each with half of the tile's columns); group g
+//              takes every other output tile and owns buffer g, so one group's
+//              epilogue overlaps the MMAs of the next tile and the other
+//              group's epilogue.  Per element: exact integer recombination of
+//              the levels, one conversion to FP64, the augmented-tile scales
+//              (Algorithms 2 and 3 of Section 4) by exponent arithmetic, one
+//              FP64 subtraction; new column maxima (rounded-up 32-bit keys) by
+//              a butterfly reduction.  The per-column scales of a group's next
+//              tile are computed into a second slot and its Y chunk
+//              (contiguous in HBM) is prefetched into L2 while the current
+//              tile's MMAs run.
 // Every wait is bounded (SM clock cycles): a wait that runs out sets
 // PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
 // out of bounded waits, tensor memory is freed).
@@ -119,19 +121,26 @@ __device__ __forceinline__ void tile_y_range(const Problem& P, const TmTiles& tt
   bytes = (uint32_t)(nc * P.tb * sizeof(double));
 }
 
+// Upper 32 bits of |x|'s bit pattern, rounded up: non-negative doubles order
+// like these keys, and the double they stand for is an upper bound of |x|
+// (within 2^-20 relative), which is all the norm bookkeeping needs.
+__device__ __forceinline__ unsigned key32(double x) {
+  return (unsigned)((abs_key(x) + 0xffffffffull) >> 32);
+}
+
 // Column maxima of a 4-column block over a warp's 32 rows: a butterfly that
 // halves the columns each step.  On return lanes with (lane & 7) == 0 hold the
 // maximum of column (lane >> 3) & 3 over all 32 lanes.
-__device__ __forceinline__ unsigned long long warp_colmax4(unsigned long long (&k)[4], int lane) {
-  unsigned long long a2[2];
+__device__ __forceinline__ unsigned warp_colmax4(unsigned (&k)[4], int lane) {
+  unsigned a2[2];
   const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const unsigned long long mine = b4 ? k[u + 2] : k[u], other = b4 ? k[u] : k[u + 2];
+    const unsigned mine = b4 ? k[u + 2] : k[u], other = b4 ? k[u] : k[u + 2];
     a2[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 16));
   }
-  const unsigned long long mine = b3 ? a2[1] : a2[0], other = b3 ? a2[0] : a2[1];
-  unsigned long long r = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
+  const unsigned mine = b3 ? a2[1] : a2[0], other = b3 ? a2[0] : a2[1];
+  unsigned r = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
   r = max(r, __shfl_xor_sync(0xffffffffu, r, 4));
   r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
   r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
@@ -155,8 +164,8 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (its group's warps arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
-  __shared__ int4 s_col[2][NCOL];                  // per group: scales of its current tile
-  __shared__ unsigned long long s_key[2][4][NCOL]; // per group and warp: new column maxima
+  __shared__ int4 s_col[2][2][NCOL];               // per group, two tiles: column scales
+  __shared__ unsigned s_key[2][4][NCOL];           // per group and lane quarter: column maxima (upper 32 bits)
   __shared__ int s_fail, s_stop[2];
   volatile int* fail = &s_fail;
 
@@ -248,7 +257,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
     const int cbeg = half * HALF;
     int it = g;
     int t = blockIdx.x + it * (int)gridDim.x;
-    if (et < NCOL && t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][et]);
+    if (et < NCOL && t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][0][et]);
     if (et == 0 && t < total) {
       const double* yp;
       uint32_t yb;
@@ -257,8 +266,10 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
     }
     group_barrier(g);
     for (; t < total; it += 2, t = blockIdx.x + it * (int)gridDim.x) {
+      const int slot = (it >> 1) & 1;
       {
-        // the Y chunk of this group's next tile into L2
+        // the group's next tile: its Y chunk into L2 and its column scales
+        // into the other slot, while this tile's MMAs finish
         const int tn = t + 2 * (int)gridDim.x;
         if (et == 0 && tn < total) {
           const double* yp;
@@ -266,6 +277,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           tile_y_range<NCOL>(P, tt, tn, yp, yb);
           prefetch_l2(yp, yb);
         }
+        if (et < NCOL && tn < total) tile_scales<L, NCOL>(P, i, tt, tn, exX, nrmX, F, et, &s_col[g][slot ^ 1][et]);
       }
       const int k = tt.k_lo + t / tt.nchunks;
       const int ch = tt.chunk_first + t % tt.nchunks;
@@ -282,7 +294,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
 #pragma unroll
       for (int u = 0; u < CW; ++u) {
         const int col = cbeg + u;
-        const int4 cd = s_col[g][col];
+        const int4 cd = s_col[g][slot][col];
         yv[u] = (rowok && col < nc && cd.z == 1) ? ycol[(size_t)col * tb] : 0.0;
       }
       const bool ok = mbar_wait_cycles(&tfull[g], (uint32_t)((it >> 1) & 1), kTcWait);
@@ -309,7 +321,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             yn[u] = 0.0;
             if (cb + CW < cbeg + HALF) {
               const int col = cb + CW + u;
-              const int4 cd = s_col[g][col];
+              const int4 cd = s_col[g][slot][col];
               if (rowok && col < nc && cd.z == 1) yn[u] = ycol[(size_t)col * tb];
             }
           }
@@ -321,13 +333,14 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
 #pragma unroll
           for (int u = 0; u < CW; ++u) {
             const int col = cb + u;
-            const int4 cd = s_col[g][col];
+            const int4 cd = s_col[g][slot][col];
             act[u] = (cd.z & 1) && rowok && col < nc;
             long long tv = 0;
 #pragma unroll
-            for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
+            for (int s = 0; s < L; ++s)
+              tv += (long long)__float2int_rn(__uint_as_float(lv[s][u])) * (1ll << (8 * (L - 1 - s)));
             bool sl = false;
-            const double prod = i64_scaled_fast(tv, erow + cd.y, sl);
+            const double prod = pow2_scale_fast((double)tv, erow + cd.y, sl);
             const double yold = (cd.z & 2) ? 0.0 : pow2_scale_fast(yv[u], cd.x, sl);
             slow |= act[u] & sl;
             ynew[u] = yold - prod;
@@ -335,7 +348,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           if (__any_sync(0xffffffffu, slow)) {
 #pragma unroll
             for (int u = 0; u < CW; ++u) {
-              const int4 cd = s_col[g][cb + u];
+              const int4 cd = s_col[g][slot][cb + u];
               long long tv = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
@@ -344,32 +357,28 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
               if (act[u]) ynew[u] = yold - prod;
             }
           }
-          unsigned long long key[CW];
+          unsigned key[CW];
 #pragma unroll
           for (int u = 0; u < CW; ++u) {
             if (act[u]) ycol[(size_t)(cb + u) * tb] = ynew[u];
-            key[u] = act[u] ? abs_key(ynew[u]) : 0ull;
+            key[u] = act[u] ? key32(ynew[u]) : 0u;
           }
-          const unsigned long long cm = warp_colmax4(key, lane);
+          const unsigned cm = warp_colmax4(key, lane);
           if ((lane & 7) == 0) s_key[g][quarter][cb + ((lane >> 3) & 3)] = cm;
 #pragma unroll
           for (int u = 0; u < CW; ++u) yv[u] = yn[u];
         }
       }
       group_barrier(g);
-      // new norms and exponents of the tile's columns; then the scales of the
-      // group's next tile (its MMAs are running meanwhile)
+      // new norms and exponents of the tile's columns
       if (et < NCOL) {
-        const int4 cd = s_col[g][et];
+        const int4 cd = s_col[g][slot][et];
         if (ok && et < nc && (cd.z & 1)) {
           const long long idx = (long long)k * P.m + c0 + et;
-          const unsigned long long km =
-              max(max(s_key[g][0][et], s_key[g][1][et]), max(s_key[g][2][et], s_key[g][3][et]));
-          P.nrm[idx] = __longlong_as_double((long long)km);
+          const unsigned km = max(max(s_key[g][0][et], s_key[g][1][et]), max(s_key[g][2][et], s_key[g][3][et]));
+          P.nrm[idx] = __longlong_as_double((long long)km << 32);
           P.ex[idx] = cd.w;
         }
-        const int tn = blockIdx.x + (it + 2) * (int)gridDim.x;
-        if (tn < total) tile_scales<L, NCOL>(P, i, tt, tn, exX, nrmX, F, et, &s_col[g][et]);
       }
       if (et == 0) s_stop[g] = *fail;
       group_barrier(g);
