@@ -170,7 +170,7 @@ __device__ __forceinline__ void cplx_tip(const DiagBlocks& D, int li0, double a,
 }
 
 template <int CB>
-__global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mode) {
+__global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int mode) {
   const bool tips = mode != kDiagSolve;          // one CTA row per diagonal tile
   const int j = tips ? (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;
   const int i = tips ? j : i_row;
@@ -206,6 +206,19 @@ __global__ void __launch_bounds__(kMaxTile) k_diag(Problem P, int i_row, int mod
   __shared__ unsigned char s_pf[kMaxTile][CB];              // 2x2 pivot position pi | pj << 1
   __shared__ unsigned long long s_key[CB];
 
+  // one CTA per launch brings the diagonal tile's S and T columns into L2:
+  // every CTA of the launch walks the same columns, in step (prefetch
+  // addresses stay inside each column segment)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && lr < h) {
+    const int lines = (8 * h + 127) / 128;
+    const double* sc = P.S + (size_t)(r0 + lr) * P.lds + r0;
+    const double* tc = P.T + (size_t)(r0 + lr) * P.ldt + r0;
+    for (int q = 0; q <= lines; ++q) {
+      const int off = min(16 * q, h - 1);                    // in doubles: 128 bytes per line
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(sc + off));
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(tc + off));
+    }
+  }
   // ---- stage column constants, the diagonal blocks and the block list
   if (lr < nq) {
     s_lc[lr] = P.dperm[pos0 + lr];
