@@ -1,0 +1,295 @@
+// diag.cuh -- device helpers of the diagonal-tile solves (kernels 1 and 3 of
+// Section 3 with ProtectDivision / ProtectUpdate of Section 4): the staged
+// diagonal blocks, the right-hand-side-independent factors of 1x1 and 2x2
+// blocks, and one block step of one eigenvector.
+#pragma once
+
+#include "common.cuh"
+
+namespace pevc {
+
+constexpr double kUlp = 0x1p-53;
+
+struct ColStep {
+  double P[2][2];   // [block col][pair member]: beta * w
+  double Q[2][2];   //                          : Re/Im of alpha * w
+  double W[2][2];   // new stored values of the block rows
+  int shift;
+};
+
+// The tile's diagonal blocks, staged in shared memory: for local row r,
+// Sd[r][c] = S[r, bs(r) + c] and Td[r][c] = T[r, bs(r) + c] for the (one or
+// two) columns c of its block; tcS / tcT are the column-segment maxima above
+// each column's block inside the tile (the t of ProtectUpdate).
+struct DiagBlocks {
+  const double (*Sd)[2];
+  const double (*Td)[2];
+  const double* tcS;
+  const double* tcT;
+};
+
+__device__ __forceinline__ double upd_norm(const DiagBlocks& D, int li0, int sz, double beta, double amag) {
+  double t = fabs(beta) * D.tcS[li0] + amag * D.tcT[li0];
+  if (sz == 2) t += fabs(beta) * D.tcS[li0 + 1] + amag * D.tcT[li0 + 1];
+  return t;
+}
+
+// Twice the largest of |x|, |y| (an upper bound of |x| + |y|), by integer
+// arithmetic on the exponent field; requires max(|x|, |y|) < 2^1023.
+__device__ __forceinline__ double twice_max_abs(unsigned long long key) {
+  return __longlong_as_double((long long)(key + (1ull << 52)));
+}
+
+// The right-hand-side-independent part of the robust 2x2 solve of a real
+// eigenvalue, (beta S_bb - a T_bb) x = r: Gaussian elimination with complete
+// pivoting, pivots below smin raised to smin (the DLALN2 principle of Section
+// 5.2).  f = {1/piv, l, m[pi][oj]/piv, 1/u22}; ep = ilogb |u22|; pf = pi | pj << 1.
+__device__ __forceinline__ void real2_factor(const DiagBlocks& D, int li0, double a, double beta, double* f,
+                                             short& ep, unsigned char& pf) {
+  double m[2][2];
+  double sm = 0.0, tm = 0.0;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double s = D.Sd[li0 + p][q], t = D.Td[li0 + p][q];
+      m[p][q] = beta * s - a * t;
+      sm = fmax(sm, fabs(s));
+      tm = fmax(tm, fabs(t));
+    }
+  const double smin = fmax(kUlp * (fabs(beta) * sm + fabs(a) * tm), 0x1p-1022);
+  int pi = 0, pj = 0;
+  double big = fabs(m[0][0]);
+  if (fabs(m[0][1]) > big) { big = fabs(m[0][1]); pi = 0; pj = 1; }
+  if (fabs(m[1][0]) > big) { big = fabs(m[1][0]); pi = 1; pj = 0; }
+  if (fabs(m[1][1]) > big) { big = fabs(m[1][1]); pi = 1; pj = 1; }
+  if (big < smin) {
+    m[0][0] = smin; m[0][1] = 0.0; m[1][0] = 0.0; m[1][1] = smin;
+    pi = 0; pj = 0;
+  }
+  const int oi = 1 - pi, oj = 1 - pj;
+  const double piv = m[pi][pj];
+  const double l = m[oi][pj] / piv;
+  double u22 = m[oi][oj] - l * m[pi][oj];
+  if (fabs(u22) < smin) u22 = copysign(smin, u22);
+  f[0] = 1.0 / piv;
+  f[1] = l;
+  f[2] = m[pi][oj] / piv;
+  f[3] = 1.0 / u22;
+  ep = (short)ilogb_key(abs_key(u22));
+  pf = (unsigned char)(pi | (pj << 1));
+}
+
+// Complex counterpart (alpha = a + i b): f = {l, 1/u22, 1/piv, m[pi][oj]/piv}
+// as (re, im) pairs; ep = ilogb(|Re u22| + |Im u22|).
+__device__ __forceinline__ void cplx2_factor(const DiagBlocks& D, int li0, double a, double b, double beta, double* f,
+                                             short& ep, unsigned char& pf) {
+  const double amag = fabs(a) + fabs(b);
+  double mr[2][2], mi[2][2];
+  double sm = 0.0, tm = 0.0;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double s = D.Sd[li0 + p][q], t = D.Td[li0 + p][q];
+      mr[p][q] = beta * s - a * t;
+      mi[p][q] = -b * t;
+      sm = fmax(sm, fabs(s));
+      tm = fmax(tm, fabs(t));
+    }
+  const double smin = fmax(kUlp * (fabs(beta) * sm + amag * tm), 0x1p-1022);
+  int pi = 0, pj = 0;
+  double big = -1.0;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (cmag(mr[p][q], mi[p][q]) > big) { big = cmag(mr[p][q], mi[p][q]); pi = p; pj = q; }
+  if (big < smin) {
+    mr[0][0] = smin; mr[0][1] = 0.0; mr[1][0] = 0.0; mr[1][1] = smin;
+    mi[0][0] = 0.0; mi[0][1] = 0.0; mi[1][0] = 0.0; mi[1][1] = 0.0;
+    pi = 0; pj = 0;
+  }
+  const int oi = 1 - pi, oj = 1 - pj;
+  double lr, li;
+  cdiv(mr[oi][pj], mi[oi][pj], mr[pi][pj], mi[pi][pj], lr, li);
+  double ur = mr[oi][oj] - (lr * mr[pi][oj] - li * mi[pi][oj]);
+  double ui = mi[oi][oj] - (lr * mi[pi][oj] + li * mr[pi][oj]);
+  if (cmag(ur, ui) < smin) { ur = smin; ui = 0.0; }
+  f[0] = lr;
+  f[1] = li;
+  cdiv(1.0, 0.0, ur, ui, f[2], f[3]);
+  cdiv(1.0, 0.0, mr[pi][pj], mi[pi][pj], f[4], f[5]);
+  cdiv(mr[pi][oj], mi[pi][oj], mr[pi][pj], mi[pi][pj], f[6], f[7]);
+  ep = (short)ilogb_key(abs_key(cmag(ur, ui)));
+  pf = (unsigned char)(pi | (pj << 1));
+}
+
+// Tip of a complex pair: a null vector of M = beta S_jj - alpha T_jj,
+// scaled so that its entry of largest modulus is exactly 1.
+__device__ __forceinline__ void cplx_tip(const DiagBlocks& D, int li0, double a, double b, double beta,
+                                         double& w0r, double& w0i, double& w1r, double& w1i) {
+  double mr[2][2], mi[2][2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double s = D.Sd[li0 + p][q], t = D.Td[li0 + p][q];
+      mr[p][q] = beta * s - a * t;
+      mi[p][q] = -b * t;
+    }
+  // (-m01, m00) is orthogonal to row 0, (m11, -m10) to row 1; both span ker M.
+  double ur[2] = {-mr[0][1], mr[0][0]}, ui[2] = {-mi[0][1], mi[0][0]};
+  double vr[2] = {mr[1][1], -mr[1][0]}, vi[2] = {mi[1][1], -mi[1][0]};
+  const double nu = fmax(cmag(ur[0], ui[0]), cmag(ur[1], ui[1]));
+  const double nv = fmax(cmag(vr[0], vi[0]), cmag(vr[1], vi[1]));
+  if (nv > nu) { ur[0] = vr[0]; ur[1] = vr[1]; ui[0] = vi[0]; ui[1] = vi[1]; }
+  const int big = (hypot(ur[1], ui[1]) > hypot(ur[0], ui[0])) ? 1 : 0;
+  double zr[2], zi[2];
+  cdiv(ur[0], ui[0], ur[big], ui[big], zr[0], zi[0]);
+  cdiv(ur[1], ui[1], ur[big], ui[big], zr[1], zi[1]);
+  zr[big] = 1.0;
+  zi[big] = 0.0;
+  w0r = zr[0]; w0i = zi[0]; w1r = zr[1]; w1i = zi[1];
+}
+
+// Phase A of one block step for one eigenvector (unit u): the right-hand-side-
+// dependent part of the robust 1x1 / 2x2 solve and its protection.  piv holds
+// the block rows' current values (the unit's columns t0c, t0c + 1); y, active
+// and e are the unit's running bound, activity and exponent (updated).
+template <int CB>
+__device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool tips, int i0, int tip, int li0,
+                                             int sz, bool has_above, bool pairs, int t0c, int u, double a,
+                                             double b, double beta, double tn, int ep, const double* f, int pf,
+                                             const double (*piv)[CB], double& y, bool& active, int& e) {
+  ColStep st;
+  st.shift = 0;
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) { st.P[x][v] = 0.0; st.Q[x][v] = 0.0; st.W[x][v] = 0.0; }
+  if (mode == kDiagTip && i0 == tip) {
+    // kernel 1: the tip, then the protect for the update of the rows above
+    active = true;
+    double w[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    if (!pairs) w[0][0] = 1.0;
+    else cplx_tip(D, li0, a, b, beta, w[0][0], w[0][1], w[1][0], w[1][1]);
+    const double x = fmax(cmag(w[0][0], w[0][1]), cmag(w[1][0], w[1][1]));
+    const int ku = has_above ? protect_update(0.0, tn, x) : 0;
+#pragma unroll
+    for (int xx = 0; xx < 2; ++xx)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) w[xx][v] = ku ? pow2_scale(w[xx][v], -ku) : w[xx][v];
+    y = has_above ? tn * pow2_scale(x, -ku) : 0.0;
+#pragma unroll
+    for (int xx = 0; xx < 2; ++xx) {
+      st.W[xx][0] = w[xx][0]; st.W[xx][1] = w[xx][1];
+      st.P[xx][0] = beta * w[xx][0]; st.P[xx][1] = beta * w[xx][1];
+      st.Q[xx][0] = a * w[xx][0] - b * w[xx][1];
+      st.Q[xx][1] = a * w[xx][1] + b * w[xx][0];
+    }
+    e = ku;
+  } else if (tips && i0 >= tip) {
+    // below a tip, and (correction) at the tip block itself, the column
+    // is zero: W, P, Q stay 0 and nothing is scaled
+  } else if (active) {
+    if (sz == 1 && !pairs) {
+      // w = r / p as r * (1/p); ProtectDivision against |p| >= 2^ep
+      double r = piv[0][t0c];
+      const unsigned long long rb = abs_key(r);
+      int kd = rb ? ilogb_key(rb) + 1 - ep - kOmegaExp : 0;
+      kd = kd > 0 ? kd : 0;
+      if (kd) { r = pow2_scale(r, -kd); y = pow2_scale(y, -kd); }
+      double w = r * f[u];
+      const int ku = has_above ? protect_update(y, tn, fabs(w)) : 0;
+      if (ku) w = pow2_scale(w, -ku);
+      if (has_above) y = fma(tn, fabs(w), pow2_scale(y, -ku));
+      st.shift = kd + ku;
+      st.W[0][0] = w;
+      st.P[0][0] = beta * w;
+      st.Q[0][0] = a * w;
+    } else if (sz == 1) {
+      // complex: |r| <= |Re r| + |Im r| < 2^(ilogb(max) + 2); the
+      // quotient by p may grow by one more factor 2 (|p| >= cmag(p)/2)
+      double rr = piv[0][t0c], ri = piv[0][t0c + 1];
+      const unsigned long long rb = max(abs_key(rr), abs_key(ri));
+      int kd = rb ? ilogb_key(rb) + 3 - ep - kOmegaExp : 0;
+      kd = kd > 0 ? kd : 0;
+      if (kd) { rr = pow2_scale(rr, -kd); ri = pow2_scale(ri, -kd); y = pow2_scale(y, -kd); }
+      const double ir = f[2 * u], ii = f[2 * u + 1];
+      double wr = fma(rr, ir, -ri * ii), wi = fma(rr, ii, ri * ir);
+      const double x2 = twice_max_abs(max(abs_key(wr), abs_key(wi)));   // >= |Re w| + |Im w|
+      const int ku = has_above ? protect_update(y, tn, x2) : 0;
+      if (ku) { wr = pow2_scale(wr, -ku); wi = pow2_scale(wi, -ku); }
+      if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+      st.shift = kd + ku;
+      st.W[0][0] = wr; st.W[0][1] = wi;
+      st.P[0][0] = beta * wr; st.P[0][1] = beta * wi;
+      st.Q[0][0] = fma(a, wr, -b * wi); st.Q[0][1] = fma(a, wi, b * wr);
+    } else if (!pairs) {
+      // real 2x2 block: forward / back substitution with the factors
+      const double* g = f + 4 * u;
+      const int pi = pf & 1, pj = pf >> 1;
+      double r0v = piv[0][t0c], r1v = piv[1][t0c];
+      const unsigned long long rb = max(abs_key(r0v), abs_key(r1v));
+      int kd = rb ? ilogb_key(rb) + 1 + 5 - ep - kOmegaExp : 0;
+      kd = kd > 0 ? kd : 0;
+      if (kd) { r0v = pow2_scale(r0v, -kd); r1v = pow2_scale(r1v, -kd); y = pow2_scale(y, -kd); }
+      const double rp = pi ? r1v : r0v, ro = pi ? r0v : r1v;
+      const double xo = fma(-g[1], rp, ro) * g[3];
+      const double xp = fma(-g[2], xo, rp * g[0]);
+      double w0 = pj ? xo : xp, w1 = pj ? xp : xo;
+      const double x = max_nonneg(fabs(w0), fabs(w1));
+      const int ku = has_above ? protect_update(y, tn, x) : 0;
+      if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); }
+      if (has_above) y = fma(tn, pow2_scale(x, -ku), pow2_scale(y, -ku));
+      st.shift = kd + ku;
+      st.W[0][0] = w0; st.W[1][0] = w1;
+      st.P[0][0] = beta * w0; st.P[1][0] = beta * w1;
+      st.Q[0][0] = a * w0; st.Q[1][0] = a * w1;
+    } else {
+      // complex 2x2 block
+      const double* g = f + 8 * u;
+      const int pi = pf & 1, pj = pf >> 1;
+      double r0r = piv[0][t0c], r0i = piv[0][t0c + 1], r1r = piv[1][t0c], r1i = piv[1][t0c + 1];
+      const unsigned long long rb =
+          max(max(abs_key(r0r), abs_key(r0i)), max(abs_key(r1r), abs_key(r1i)));
+      int kd = rb ? ilogb_key(rb) + 2 + 5 - ep - kOmegaExp : 0;
+      kd = kd > 0 ? kd : 0;
+      if (kd) {
+        r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
+        r1r = pow2_scale(r1r, -kd); r1i = pow2_scale(r1i, -kd);
+        y = pow2_scale(y, -kd);
+      }
+      const double rpr = pi ? r1r : r0r, rpi = pi ? r1i : r0i;
+      const double ror = pi ? r0r : r1r, roi = pi ? r0i : r1i;
+      const double lre = g[0], lim = g[1];
+      const double er = fma(-lre, rpr, fma(lim, rpi, ror));
+      const double ei = fma(-lre, rpi, fma(-lim, rpr, roi));
+      const double xor_ = fma(er, g[2], -ei * g[3]), xoi = fma(er, g[3], ei * g[2]);
+      const double q1r = fma(rpr, g[4], -rpi * g[5]), q1i = fma(rpr, g[5], rpi * g[4]);
+      const double xpr = fma(-g[6], xor_, fma(g[7], xoi, q1r));
+      const double xpi = fma(-g[6], xoi, fma(-g[7], xor_, q1i));
+      double w0r, w0i, w1r, w1i;
+      if (pj == 0) { w0r = xpr; w0i = xpi; w1r = xor_; w1i = xoi; }
+      else         { w0r = xor_; w0i = xoi; w1r = xpr; w1i = xpi; }
+      const double x2 = twice_max_abs(max(max(abs_key(w0r), abs_key(w0i)), max(abs_key(w1r), abs_key(w1i))));
+      const int ku = has_above ? protect_update(y, tn, x2) : 0;
+      if (ku) {
+        w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
+        w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
+      }
+      if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+      st.shift = kd + ku;
+      st.W[0][0] = w0r; st.W[0][1] = w0i; st.W[1][0] = w1r; st.W[1][1] = w1i;
+      st.P[0][0] = beta * w0r; st.P[0][1] = beta * w0i;
+      st.P[1][0] = beta * w1r; st.P[1][1] = beta * w1i;
+      st.Q[0][0] = fma(a, w0r, -b * w0i); st.Q[0][1] = fma(a, w0i, b * w0r);
+      st.Q[1][0] = fma(a, w1r, -b * w1i); st.Q[1][1] = fma(a, w1i, b * w1r);
+    }
+    e += st.shift;
+  }
+  return st;
+}
+
+}  // namespace pevc
