@@ -5,12 +5,18 @@
 // underflow of entries that are negligible against the largest), then
 // normalised so its entry of largest modulus is exactly 1, and written to
 // V_out with zeros below the eigenvector's block.
+//
+// After consolidation the largest entry has modulus in [1, 2) (the reference
+// exponent is that of the largest represented magnitude), so the argmax works
+// on squared moduli as integer keys and the normalisation multiplies by the
+// reciprocal of the pivot computed once per column: one or two FP64
+// operations per element instead of a division.
 #include "common.cuh"
 
 namespace pevc {
 
 struct BestIdx {
-  double v;
+  unsigned long long v;   // key of the squared modulus (non-negative doubles order like their bits)
   int i;
 };
 
@@ -49,8 +55,8 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   int eref = INT32_MIN;
   for (int k = tid; k <= j; k += blockDim.x) {
     const long long idx = (long long)k * m + q;
-    const double nv = pair ? fmax(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
-    if (nv > 0.0) eref = max(eref, P.ex[idx] + ilogb(nv));
+    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+    if (abs_key(nv)) eref = max(eref, P.ex[idx] + ilogb_key(abs_key(nv)));
   }
   for (int o = 16; o > 0; o >>= 1) eref = max(eref, __shfl_xor_sync(0xffffffffu, eref, o));
   if ((tid & 31) == 0) s_ered[tid >> 5] = eref;
@@ -64,28 +70,29 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   eref = s_eref;
 
   // 2. the entry of largest modulus (first index on ties)
-  BestIdx best{-1.0, 0x7fffffff};
+  BestIdx best{0ull, 0x7fffffff};
   for (int k = 0; k <= j; ++k) {
     const long long idx = (long long)k * m + q;
-    const double nv = pair ? fmax(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
-    if (!(nv > 0.0)) continue;
+    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+    if (!abs_key(nv)) continue;
     const int sh = P.ex[idx] - eref;
     const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
     const double* Yt = tile_ptr(P, k, j);
     for (int r = tid; r < h; r += blockDim.x) {
       const double vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
-      double mg;
+      double mg2;
       if (pair) {
         const double vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
-        mg = hypot(vr, vi);
+        mg2 = fma(vr, vr, vi * vi);
       } else {
-        mg = fabs(vr);
+        mg2 = vr * vr;
       }
-      best = better(best, BestIdx{mg, r0 + r});
+      best = better(best, BestIdx{abs_key(mg2), r0 + r});
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    BestIdx other{__shfl_xor_sync(0xffffffffu, best.v, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+    BestIdx other{(unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)best.v, o),
+                  __shfl_xor_sync(0xffffffffu, best.i, o)};
     best = better(best, other);
   }
   if ((tid & 31) == 0) s_red[tid >> 5] = best;
@@ -99,9 +106,10 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   best = s_red[0];
   const int istar = best.i;
 
-  // value at istar (consolidated)
+  // value at istar (consolidated), and the normalising factors: 1 / d for
+  // a real column, conj(d) / |d|^2 for a pair (|d| in [1, 2))
   double dr = 1.0, di = 0.0;
-  if (best.v > 0.0) {
+  if (best.v) {
     int k = 0;
     while (k < j && P.toff[k + 1] <= istar) ++k;
     const long long idx = (long long)k * m + q;
@@ -111,30 +119,32 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
     dr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
     if (pair) di = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
   }
+  const double s2 = 1.0 / fma(dr, dr, di * di);
+  const double nr = pair ? dr * s2 : 1.0 / dr, ni = di * s2;
 
   // 3. write the column(s)
   double* v0 = V + (size_t)q * ldv;
   double* v1 = pair ? V + (size_t)(q + 1) * ldv : nullptr;
   for (int k = 0; k <= j; ++k) {
     const long long idx = (long long)k * m + q;
-    const double nv = pair ? fmax(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+    const bool nz = abs_key(nv) != 0;
     const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
-    const int sh = (nv > 0.0) ? P.ex[idx] - eref : 0;
+    const int sh = nz ? P.ex[idx] - eref : 0;
     const double* Yt = tile_ptr(P, k, j);
     for (int r = tid; r < h; r += blockDim.x) {
       double vr = 0.0, vi = 0.0;
-      if (nv > 0.0) {
+      if (nz) {
         vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
         if (pair) vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
       }
-      if (normalise) {
+      if (normalise && best.v) {
         if (pair) {
-          double zr, zi;
-          cdiv(vr, vi, dr, di, zr, zi);
+          const double zr = fma(vr, nr, vi * ni), zi = fma(vi, nr, -(vr * ni));
           vr = zr;
           vi = zi;
         } else {
-          vr = vr / dr;
+          vr = vr * nr;
         }
         if (r0 + r == istar) { vr = 1.0; vi = 0.0; }
       }
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   }
   if (tid == 0) {
     int32_t sc = eref;
-    if (normalise && best.v > 0.0) sc = eref + ilogb(best.v);
+    if (normalise && best.v) sc = eref + ilogb_key(abs_key(pair ? hypot(dr, di) : dr));
     scale[q] = sc;
     if (pair) scale[q + 1] = sc;
   }

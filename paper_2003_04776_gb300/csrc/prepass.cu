@@ -31,6 +31,14 @@ __device__ __forceinline__ void block_reduce_max2(double& a, double& b, double* 
   }
 }
 
+// An upper bound of 2^-32 |x| from the key of |x| (finite): exact for
+// |x| >= 2^-990, the smallest normal number below that.
+__device__ __forceinline__ double scaled_down32(unsigned long long key) {
+  const unsigned long long e = key >> 52;
+  const unsigned long long b = e > 32 ? key - (32ull << 52) : (key ? 0x0010000000000000ull : 0ull);
+  return __longlong_as_double((long long)b);
+}
+
 // One CTA per tile pair (k, l), k <= l.  Off-diagonal tiles: exponent bound
 // of ||[S_kl T_kl]||_inf.  Diagonal tiles: tcS/tcT column-segment maxima.
 __global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
@@ -47,15 +55,25 @@ __global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
   bool finite = true;
   double amax = 0.0, rs = 0.0;
   if (k < l) {
+    // integer keys for the maximum and the finiteness test; the row sums of
+    // 2^-32 |x| (kept from overflowing) accumulate upper bounds formed on the
+    // exponent field, so only the two additions use the FP64 pipe
     const int r = threadIdx.x;
     if (r < hk) {
+      unsigned long long key = 0, bad = 0;
+      double rs0 = 0.0, rs1 = 0.0;
+#pragma unroll 8
       for (int c = 0; c < hl; ++c) {
-        const double s = fabs(S[(size_t)(cl0 + c) * P.lds + rk0 + r]);
-        const double t = fabs(T[(size_t)(cl0 + c) * P.ldt + rk0 + r]);
-        finite = finite && isfinite(s) && isfinite(t);
-        amax = fmax(amax, fmax(s, t));
-        rs += ldexp(s, -32) + ldexp(t, -32);
+        const unsigned long long ks = abs_key(S[(size_t)(cl0 + c) * P.lds + rk0 + r]);
+        const unsigned long long kt = abs_key(T[(size_t)(cl0 + c) * P.ldt + rk0 + r]);
+        bad |= (ks >= 0x7ff0000000000000ull) | (kt >= 0x7ff0000000000000ull);
+        key = max(key, max(ks, kt));
+        rs0 += scaled_down32(ks);
+        rs1 += scaled_down32(kt);
       }
+      finite = !bad;
+      amax = __longlong_as_double((long long)key);
+      rs = rs0 + rs1;
     }
   } else {
     const int c = threadIdx.x;
@@ -81,8 +99,8 @@ __global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
       const int gr = cl0 + r;
       const int c_first = (P.blk[gr] == 2) ? gr - 1 : gr;
       for (int gc = c_first; gc < cl0 + hl; ++gc) {
-        rs += ldexp(fabs(S[(size_t)gc * P.lds + gr]), -32);
-        if (gc >= gr) rs += ldexp(fabs(T[(size_t)gc * P.ldt + gr]), -32);
+        rs += scaled_down32(abs_key(S[(size_t)gc * P.lds + gr]));
+        if (gc >= gr) rs += scaled_down32(abs_key(T[(size_t)gc * P.ldt + gr]));
       }
     }
   }
