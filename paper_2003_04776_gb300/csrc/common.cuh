@@ -108,6 +108,29 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
   }
 }
 
+// Complex reciprocal (pr + i pi) = 1 / (br + i bi): Smith's quotient above
+// with the numerator 1, so that it takes two divisions instead of three (the
+// second quotient is a product with the reciprocal of the denominator).
+__device__ __forceinline__ void crecip(double br, double bi, double& pr, double& pi) {
+  if (fabs(br) >= fabs(bi)) {
+    const double rho = bi / br;
+    const double inv = 1.0 / (br + bi * rho);
+    pr = inv;
+    pi = (rho != 0.0) ? -rho * inv : -(bi * inv) * inv;
+  } else {
+    const double rho = br / bi;
+    const double inv = 1.0 / (bi + br * rho);
+    pr = (rho != 0.0) ? rho * inv : (br * inv) * inv;
+    pi = -inv;
+  }
+}
+
+// (pr + i pi) = (ar + i ai) (br + i bi)
+__device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double& pr, double& pi) {
+  pr = fma(ar, br, -(ai * bi));
+  pi = fma(ar, bi, ai * br);
+}
+
 __device__ __forceinline__ double cmag(double re, double im) { return fabs(re) + fabs(im); }
 
 // x * 2^e, exact up to underflow/overflow like ldexp.  Normal results are

@@ -4,7 +4,8 @@
 //
 // One CTA owns one tile (i, j) and a chunk of at most CB columns that are all
 // real or all complex pairs (so the per-block pivot work is never divergent).
-// Thread r holds row r of the chunk in registers.  The 1x1 / 2x2 blocks of
+// Thread lr holds column lr % CB of the chunk at the rows congruent to lr / CB
+// modulo 128 / CB, in registers.  The 1x1 / 2x2 blocks of
 // S_ii are processed bottom-up; for every block the column threads solve the
 // block (real or complex; Gaussian elimination with complete pivoting for
 // 2x2, pivots below smin raised to smin -- the DLALN2 principle of Section
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
   __shared__ short s_bs[kMaxTile];
   __shared__ unsigned char s_bz[kMaxTile];
   __shared__ int s_boff[kMaxTile];                          // offset of a block's factors in s_pre
-  __shared__ int s_nb;
+  __shared__ int s_nb, s_n1;
+  __shared__ unsigned char s_bord[kMaxTile];               // block indices, the 1x1 blocks first
   __shared__ double s_Sd[kMaxTile][2], s_Td[kMaxTile][2], s_tcS[kMaxTile], s_tcT[kMaxTile];
   // right-hand-side-independent factors per (block, unit): 1x1 blocks the
   // inverted pivot (1 double real, 2 complex), 2x2 blocks the LU factors
@@ -126,34 +128,46 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
       rr = st - 1;
     }
     s_nb = nb;
+    int n1 = 0;
+    for (int q = 0; q < nb; ++q)
+      if (s_bz[q] == 1) s_bord[n1++] = (unsigned char)q;
+    s_n1 = n1;
+    int q2 = n1;
+    for (int q = 0; q < nb; ++q)
+      if (s_bz[q] == 2) s_bord[q2++] = (unsigned char)q;
   }
   __syncthreads();
   const DiagBlocks D{s_Sd, s_Td, s_tcS, s_tcT};
   const int nb = s_nb;
 
   // ---- everything that does not depend on the right-hand side, for every
-  //      (block, unit) in parallel: pivots, factors, ProtectUpdate's t
+  //      (block, unit) in parallel: pivots, factors, ProtectUpdate's t.  The
+  //      1x1 blocks come first and the 2x2 blocks after them, so that a warp
+  //      takes one kind of block at a time
+  const int n1 = s_n1;
   for (int item = lr; item < nb * nu; item += blockDim.x) {
-    const int bidx = item / nu, u = item % nu;
-    const int li = s_bs[bidx], sz = s_bz[bidx];
+    const int bidx = s_bord[item / nu], u = item % nu;
+    const bool one = item < n1 * nu;
+    const int li = s_bs[bidx];
     const double a = s_a[u], b = s_b[u], beta = s_beta[u];
     const double amag = fabs(a) + fabs(b);
     double* f = s_pre + s_boff[bidx];
-    s_tn[bidx][u] = upd_norm(D, li, sz, beta, amag);
-    if (sz == 1) {
+    s_tn[bidx][u] = upd_norm(D, li, one ? 1 : 2, beta, amag);
+    if (one) {
       const double s = s_Sd[li][0], t = s_Td[li][0];
       if (!pairs) {
         double p = beta * s - a * t;
-        const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + fabs(a) * fabs(t)), 0x1p-1022);
-        if (fabs(p) < smin) p = copysign(smin, p);
+        const double smin = max_nonneg(kUlp * (fabs(beta) * fabs(s) + fabs(a) * fabs(t)), 0x1p-1022);
+        if (abs_key(p) < abs_key(smin)) p = copysign(smin, p);
         f[u] = 1.0 / p;
         s_ep[bidx][u] = (short)ilogb_key(abs_key(p));
       } else {
         double pr = beta * s - a * t, pim = -b * t;
-        const double smin = fmax(kUlp * (fabs(beta) * fabs(s) + amag * fabs(t)), 0x1p-1022);
-        if (cmag(pr, pim) < smin) { pr = smin; pim = 0.0; }
-        cdiv(1.0, 0.0, pr, pim, f[2 * u], f[2 * u + 1]);
-        s_ep[bidx][u] = (short)ilogb_key(abs_key(cmag(pr, pim)));
+        const double smin = max_nonneg(kUlp * (fabs(beta) * fabs(s) + amag * fabs(t)), 0x1p-1022);
+        const double pm = cmag(pr, pim);
+        if (abs_key(pm) < abs_key(smin)) { pr = smin; pim = 0.0; }
+        crecip(pr, pim, f[2 * u], f[2 * u + 1]);
+        s_ep[bidx][u] = (short)ilogb_key(abs_key(abs_key(pm) < abs_key(smin) ? smin : pm));
       }
       s_pf[bidx][u] = 0;
     } else if (!pairs) {
@@ -163,44 +177,67 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
     }
   }
 
+  // ---- element ownership: thread lr holds column t = lr % CB of the chunk at
+  //      rows g + NG k (g = lr / CB, k < CB).  A warp then covers CB columns of
+  //      32 / CB interleaved row groups, so the rows above a block -- the only
+  //      rows with rank-update work -- are spread evenly over the four warps
+  //      at every step (a warp issues its FP64 instructions one at a time, so
+  //      a step lasts as long as its busiest warp)
+  constexpr int NG = kMaxTile / CB;
+  const int t = lr % CB, g = lr / CB;
+  const bool tcol = t < nq;
   double vals[CB];
 #pragma unroll
-  for (int t = 0; t < CB; ++t) {
-    vals[t] = 0.0;
-    if (mode != kDiagTip && t < nq && lr < h && s_act[pairs ? t / 2 : t])
-      vals[t] = Yt[(size_t)s_lc[t] * P.tb + lr];
+  for (int k = 0; k < CB; ++k) {
+    const int r = g + NG * k;
+    vals[k] = 0.0;
+    if (mode != kDiagTip && tcol && r < h && s_act[pairs ? t / 2 : t]) vals[k] = Yt[(size_t)s_lc[t] * P.tb + r];
   }
-  __syncthreads();
-
-  // S/T entries of the next block's columns for this thread's row (prefetched)
-  double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
+  // the next block's S and T columns are staged in shared memory (double
+  // buffered): loaded into registers at the top of a step, stored after its
+  // rank update
+  __shared__ double s_nc[2][4][kMaxTile];
   {
     const int li0 = s_bs[0], sz = s_bz[0];
     if (lr < li0) {
-      nS0 = P.S[(size_t)(r0 + li0) * P.lds + r0 + lr];
-      nT0 = P.T[(size_t)(r0 + li0) * P.ldt + r0 + lr];
+      s_nc[0][0][lr] = P.S[(size_t)(r0 + li0) * P.lds + r0 + lr];
+      s_nc[0][1][lr] = P.T[(size_t)(r0 + li0) * P.ldt + r0 + lr];
       if (sz == 2) {
-        nS1 = P.S[(size_t)(r0 + li0 + 1) * P.lds + r0 + lr];
-        nT1 = P.T[(size_t)(r0 + li0 + 1) * P.ldt + r0 + lr];
+        s_nc[0][2][lr] = P.S[(size_t)(r0 + li0 + 1) * P.lds + r0 + lr];
+        s_nc[0][3][lr] = P.T[(size_t)(r0 + li0 + 1) * P.ldt + r0 + lr];
       }
     }
   }
+  __syncthreads();
 
+  const int pa_warp = (int)(blockIdx.x + blockIdx.y) & 3;   // spreads phase A over the sub-partitions
   for (int bidx = 0; bidx < nb; ++bidx) {
     const int li0 = s_bs[bidx], sz = s_bz[bidx];
     const int i0 = r0 + li0;
-    if (lr >= li0 && lr < li0 + sz) {
+    if (tcol) {
 #pragma unroll
-      for (int t = 0; t < CB; ++t)
-        if (t < nq) s_piv[lr - li0][t] = vals[t];
+      for (int k = 0; k < CB; ++k) {
+        const int r = g + NG * k;
+        if (r >= li0 && r < li0 + sz) s_piv[r - li0][t] = vals[k];
+      }
+    }
+    double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
+    const int ln = (bidx + 1 < nb) ? s_bs[bidx + 1] : 0, szn = (bidx + 1 < nb) ? s_bz[bidx + 1] : 1;
+    if (lr < ln) {
+      nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
+      nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
+      if (szn == 2) {
+        nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
+        nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
+      }
     }
     __syncthreads();
-    // ---- phase A: one lane of warp 0 per unit solves the block; only the
+    // ---- phase A: one lane per unit solves the block; only the
     //      right-hand-side-dependent arithmetic is left here
-    if (lr < 32) {
+    if ((lr >> 5) == pa_warp) {
+      const int u = lr & 31;
       int myshift = 0;
-      if (lr < nu) {
-        const int u = lr;
+      if (u < nu) {
         const int t0c = pairs ? 2 * u : u;
         const int tip = s_tip[u];
         const bool has_above = li0 > 0;
@@ -228,66 +265,75 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
         }
       }
       const bool anysh = __any_sync(0xffffffffu, myshift != 0);
-      if (lr == 0) s_anysh = anysh ? 1 : 0;
+      if (u == 0) s_anysh = anysh ? 1 : 0;
     }
     __syncthreads();
-    // ---- phase B: every row applies the scale and the rank update
-    const double cS0 = nS0, cT0 = nT0, cS1 = nS1, cT1 = nT1;
-    if (bidx + 1 < nb) {   // prefetch the next block's columns
-      const int ln = s_bs[bidx + 1], szn = s_bz[bidx + 1];
-      nS0 = nT0 = nS1 = nT1 = 0.0;
-      if (lr < ln) {
-        nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
-        nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
-        if (szn == 2) {
-          nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
-          nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
+    // ---- phase B: the scale and the rank update of the rows above, the
+    //      solved values into the block rows
+    if (tcol) {
+      if (s_anysh) {
+        const int sh = s_sh[t];
+        if (sh) {
+#pragma unroll
+          for (int k = 0; k < CB; ++k) vals[k] = pow2_scale(vals[k], -sh);
         }
+      }
+      // row steps k run while the warp's first row group is above the block
+      // (a warp-uniform exit, so no FP64 instruction is issued for a step
+      // without work); lanes past the block's first row keep their values
+      const double (*cn)[kMaxTile] = s_nc[bidx & 1];
+      const double2 pq0 = s_PQ[0][t];
+      const int wg = (lr >> 5) * (32 / CB);
+      if (sz == 1) {
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          if (wg + NG * k >= li0) break;
+          const int r = g + NG * k;
+          const double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
+          vals[k] = r < li0 ? v : vals[k];
+        }
+      } else {
+        const double2 pq1 = s_PQ[1][t];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          if (wg + NG * k >= li0) break;
+          const int r = g + NG * k;
+          const double v = fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]))));
+          vals[k] = r < li0 ? v : vals[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < CB; ++k) {
+        const int r = g + NG * k;
+        if (r >= li0 && r < li0 + sz) vals[k] = s_W[r - li0][t];
       }
     }
-    if (lr < h) {
-      if (s_anysh) {
-#pragma unroll
-        for (int t = 0; t < CB; ++t)
-          if (t < nq && s_sh[t]) vals[t] = pow2_scale(vals[t], -s_sh[t]);
-      }
-      if (lr >= li0 && lr < li0 + sz) {
-#pragma unroll
-        for (int t = 0; t < CB; ++t)
-          if (t < nq) vals[t] = s_W[lr - li0][t];
-      } else if (lr < li0) {
-        if (sz == 1) {
-#pragma unroll
-          for (int t = 0; t < CB; ++t) {
-            if (t < nq) {
-              const double2 pq = s_PQ[0][t];
-              vals[t] = fma(cT0, pq.y, fma(-cS0, pq.x, vals[t]));
-            }
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < CB; ++t) {
-            if (t < nq) {
-              const double2 pq0 = s_PQ[0][t], pq1 = s_PQ[1][t];
-              vals[t] = fma(cT1, pq1.y, fma(-cS1, pq1.x, fma(cT0, pq0.y, fma(-cS0, pq0.x, vals[t]))));
-            }
-          }
-        }
-      }
+    if (lr < ln) {
+      double (*cw)[kMaxTile] = s_nc[(bidx + 1) & 1];
+      cw[0][lr] = nS0;
+      cw[1][lr] = nT0;
+      cw[2][lr] = nS1;
+      cw[3][lr] = nT1;
     }
   }
 
   // write back the solved tile columns and their augmented exponents / norms
+  unsigned long long key = 0ull;
+  if (tcol) {
+    const bool wr = tips || s_act[pairs ? t / 2 : t];
 #pragma unroll
-  for (int t = 0; t < CB; ++t) {
-    if (t < nq) {
-      const bool wr = tips || s_act[pairs ? t / 2 : t];
-      if (lr < h && wr) Yt[(size_t)s_lc[t] * P.tb + lr] = vals[t];
-      unsigned long long key = (lr < h) ? abs_key(vals[t]) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-      if ((lr & 31) == 0 && key) atomicMax(&s_key[t], key);
+    for (int k = 0; k < CB; ++k) {
+      const int r = g + NG * k;
+      if (r < h) {
+        if (wr) Yt[(size_t)s_lc[t] * P.tb + r] = vals[k];
+        key = max(key, abs_key(vals[k]));
+      }
     }
   }
+  // lanes lr, lr ^ CB, lr ^ 2CB, ... of a warp share the column
+#pragma unroll
+  for (int o = CB; o < 32; o <<= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+  if ((lr & 31) < CB && tcol && key) atomicMax(&s_key[t], key);
   __syncthreads();
   if (lr < nq) {
     const int u = pairs ? lr / 2 : lr;

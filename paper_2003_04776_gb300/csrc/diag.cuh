@@ -40,10 +40,18 @@ __device__ __forceinline__ double twice_max_abs(unsigned long long key) {
   return __longlong_as_double((long long)(key + (1ull << 52)));
 }
 
+// Entry (p, q) of a 2x2 array held in four registers (no local-memory array
+// for a runtime index).
+__device__ __forceinline__ double pick2(double m00, double m01, double m10, double m11, int p, int q) {
+  return p ? (q ? m11 : m10) : (q ? m01 : m00);
+}
+
 // The right-hand-side-independent part of the robust 2x2 solve of a real
 // eigenvalue, (beta S_bb - a T_bb) x = r: Gaussian elimination with complete
 // pivoting, pivots below smin raised to smin (the DLALN2 principle of Section
 // 5.2).  f = {1/piv, l, m[pi][oj]/piv, 1/u22}; ep = ilogb |u22|; pf = pi | pj << 1.
+// The two quotients by the pivot are products with its reciprocal; with
+// complete pivoting both are at most 1 in magnitude.
 __device__ __forceinline__ void real2_factor(const DiagBlocks& D, int li0, double a, double beta, double* f,
                                              short& ep, unsigned char& pf) {
   double m[2][2];
@@ -54,34 +62,40 @@ __device__ __forceinline__ void real2_factor(const DiagBlocks& D, int li0, doubl
     for (int q = 0; q < 2; ++q) {
       const double s = D.Sd[li0 + p][q], t = D.Td[li0 + p][q];
       m[p][q] = beta * s - a * t;
-      sm = fmax(sm, fabs(s));
-      tm = fmax(tm, fabs(t));
+      sm = max_nonneg(sm, fabs(s));
+      tm = max_nonneg(tm, fabs(t));
     }
-  const double smin = fmax(kUlp * (fabs(beta) * sm + fabs(a) * tm), 0x1p-1022);
+  const double smin = max_nonneg(kUlp * (fabs(beta) * sm + fabs(a) * tm), 0x1p-1022);
   int pi = 0, pj = 0;
-  double big = fabs(m[0][0]);
-  if (fabs(m[0][1]) > big) { big = fabs(m[0][1]); pi = 0; pj = 1; }
-  if (fabs(m[1][0]) > big) { big = fabs(m[1][0]); pi = 1; pj = 0; }
-  if (fabs(m[1][1]) > big) { big = fabs(m[1][1]); pi = 1; pj = 1; }
-  if (big < smin) {
+  unsigned long long big = abs_key(m[0][0]);
+  if (abs_key(m[0][1]) > big) { big = abs_key(m[0][1]); pi = 0; pj = 1; }
+  if (abs_key(m[1][0]) > big) { big = abs_key(m[1][0]); pi = 1; pj = 0; }
+  if (abs_key(m[1][1]) > big) { big = abs_key(m[1][1]); pi = 1; pj = 1; }
+  if (big < abs_key(smin)) {
     m[0][0] = smin; m[0][1] = 0.0; m[1][0] = 0.0; m[1][1] = smin;
     pi = 0; pj = 0;
   }
   const int oi = 1 - pi, oj = 1 - pj;
-  const double piv = m[pi][pj];
-  const double l = m[oi][pj] / piv;
-  double u22 = m[oi][oj] - l * m[pi][oj];
-  if (fabs(u22) < smin) u22 = copysign(smin, u22);
-  f[0] = 1.0 / piv;
+  const double piv = pick2(m[0][0], m[0][1], m[1][0], m[1][1], pi, pj);
+  const double m_oi_pj = pick2(m[0][0], m[0][1], m[1][0], m[1][1], oi, pj);
+  const double m_pi_oj = pick2(m[0][0], m[0][1], m[1][0], m[1][1], pi, oj);
+  const double m_oi_oj = pick2(m[0][0], m[0][1], m[1][0], m[1][1], oi, oj);
+  const double ipiv = 1.0 / piv;
+  const double l = m_oi_pj * ipiv;
+  const double g = m_pi_oj * ipiv;
+  double u22 = m_oi_oj - l * m_pi_oj;
+  if (abs_key(u22) < abs_key(smin)) u22 = copysign(smin, u22);
+  f[0] = ipiv;
   f[1] = l;
-  f[2] = m[pi][oj] / piv;
+  f[2] = g;
   f[3] = 1.0 / u22;
   ep = (short)ilogb_key(abs_key(u22));
   pf = (unsigned char)(pi | (pj << 1));
 }
 
 // Complex counterpart (alpha = a + i b): f = {l, 1/u22, 1/piv, m[pi][oj]/piv}
-// as (re, im) pairs; ep = ilogb(|Re u22| + |Im u22|).
+// as (re, im) pairs; ep = ilogb(|Re u22| + |Im u22|).  Two complex
+// reciprocals; the quotients by the pivot are products with its reciprocal.
 __device__ __forceinline__ void cplx2_factor(const DiagBlocks& D, int li0, double a, double b, double beta, double* f,
                                              short& ep, unsigned char& pf) {
   const double amag = fabs(a) + fabs(b);
@@ -94,10 +108,10 @@ __device__ __forceinline__ void cplx2_factor(const DiagBlocks& D, int li0, doubl
       const double s = D.Sd[li0 + p][q], t = D.Td[li0 + p][q];
       mr[p][q] = beta * s - a * t;
       mi[p][q] = -b * t;
-      sm = fmax(sm, fabs(s));
-      tm = fmax(tm, fabs(t));
+      sm = max_nonneg(sm, fabs(s));
+      tm = max_nonneg(tm, fabs(t));
     }
-  const double smin = fmax(kUlp * (fabs(beta) * sm + amag * tm), 0x1p-1022);
+  const double smin = max_nonneg(kUlp * (fabs(beta) * sm + amag * tm), 0x1p-1022);
   int pi = 0, pj = 0;
   double big = -1.0;
 #pragma unroll
@@ -111,16 +125,27 @@ __device__ __forceinline__ void cplx2_factor(const DiagBlocks& D, int li0, doubl
     pi = 0; pj = 0;
   }
   const int oi = 1 - pi, oj = 1 - pj;
-  double lr, li;
-  cdiv(mr[oi][pj], mi[oi][pj], mr[pi][pj], mi[pi][pj], lr, li);
-  double ur = mr[oi][oj] - (lr * mr[pi][oj] - li * mi[pi][oj]);
-  double ui = mi[oi][oj] - (lr * mi[pi][oj] + li * mr[pi][oj]);
+#define PEVC_PICK(A, p, q) pick2(A[0][0], A[0][1], A[1][0], A[1][1], p, q)
+  const double pvr = PEVC_PICK(mr, pi, pj), pvi = PEVC_PICK(mi, pi, pj);
+  const double a1r = PEVC_PICK(mr, oi, pj), a1i = PEVC_PICK(mi, oi, pj);
+  const double a2r = PEVC_PICK(mr, pi, oj), a2i = PEVC_PICK(mi, pi, oj);
+  const double a3r = PEVC_PICK(mr, oi, oj), a3i = PEVC_PICK(mi, oi, oj);
+#undef PEVC_PICK
+  double ipr, ipi;
+  crecip(pvr, pvi, ipr, ipi);
+  double lr, li, gr, gi;
+  cmul(a1r, a1i, ipr, ipi, lr, li);
+  cmul(a2r, a2i, ipr, ipi, gr, gi);
+  double ur = a3r - (lr * a2r - li * a2i);
+  double ui = a3i - (lr * a2i + li * a2r);
   if (cmag(ur, ui) < smin) { ur = smin; ui = 0.0; }
   f[0] = lr;
   f[1] = li;
-  cdiv(1.0, 0.0, ur, ui, f[2], f[3]);
-  cdiv(1.0, 0.0, mr[pi][pj], mi[pi][pj], f[4], f[5]);
-  cdiv(mr[pi][oj], mi[pi][oj], mr[pi][pj], mi[pi][pj], f[6], f[7]);
+  crecip(ur, ui, f[2], f[3]);
+  f[4] = ipr;
+  f[5] = ipi;
+  f[6] = gr;
+  f[7] = gi;
   ep = (short)ilogb_key(abs_key(cmag(ur, ui)));
   pf = (unsigned char)(pi | (pj << 1));
 }
