@@ -64,6 +64,20 @@ __device__ __forceinline__ int protect_update(double y, double t, double x) {
   return k > 0 ? k : 0;
 }
 
+// Exponent upper bound |x| < 2^exp_ub(x) of a finite x, read from the high
+// word's exponent field with 32-bit integer instructions (zero and
+// subnormal x give -1022).  For a normal x it is ilogb(x) + 1.
+__device__ __forceinline__ int exp_ub(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1022; }
+
+// ProtectUpdate on the exp_ub bounds (the block-step form): zero arguments
+// count as 2^-1022, which can only raise k, and never does unless the other
+// term is below 2^-1022 times Omega.
+__device__ __forceinline__ int protect_update_ub(double y, double t, double x) {
+  const int top = max(exp_ub(y), exp_ub(t) + exp_ub(x));
+  const int k = top + 1 - kOmegaExp;
+  return k > 0 ? k : 0;
+}
+
 // Same bound when t is already given as an exponent bound (t < 2^et).
 __device__ __forceinline__ int protect_update_e(int ey_or_min, int etx_or_min) {
   int top = max(ey_or_min, etx_or_min);

@@ -221,14 +221,13 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
     if (sz == 1 && !pairs) {
       // w = r / p as r * (1/p); ProtectDivision against |p| >= 2^ep
       double r = piv[0][t0c];
-      const unsigned long long rb = abs_key(r);
-      int kd = rb ? ilogb_key(rb) + 1 - ep - kOmegaExp : 0;
+      int kd = exp_ub(r) - ep - kOmegaExp;
       kd = kd > 0 ? kd : 0;
       if (kd) { r = pow2_scale(r, -kd); y = pow2_scale(y, -kd); }
       double w = r * f[u];
-      const int ku = has_above ? protect_update(y, tn, fabs(w)) : 0;
-      if (ku) w = pow2_scale(w, -ku);
-      if (has_above) y = fma(tn, fabs(w), pow2_scale(y, -ku));
+      const int ku = has_above ? protect_update_ub(y, tn, w) : 0;
+      if (ku) { w = pow2_scale(w, -ku); y = pow2_scale(y, -ku); }
+      if (has_above) y = fma(tn, fabs(w), y);
       st.shift = kd + ku;
       st.W[0][0] = w;
       st.P[0][0] = beta * w;
@@ -237,16 +236,16 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
       // complex: |r| <= |Re r| + |Im r| < 2^(ilogb(max) + 2); the
       // quotient by p may grow by one more factor 2 (|p| >= cmag(p)/2)
       double rr = piv[0][t0c], ri = piv[0][t0c + 1];
-      const unsigned long long rb = max(abs_key(rr), abs_key(ri));
-      int kd = rb ? ilogb_key(rb) + 3 - ep - kOmegaExp : 0;
+      int kd = max(exp_ub(rr), exp_ub(ri)) + 2 - ep - kOmegaExp;
       kd = kd > 0 ? kd : 0;
       if (kd) { rr = pow2_scale(rr, -kd); ri = pow2_scale(ri, -kd); y = pow2_scale(y, -kd); }
       const double ir = f[2 * u], ii = f[2 * u + 1];
       double wr = fma(rr, ir, -ri * ii), wi = fma(rr, ii, ri * ir);
       const double x2 = twice_max_abs(max(abs_key(wr), abs_key(wi)));   // >= |Re w| + |Im w|
-      const int ku = has_above ? protect_update(y, tn, x2) : 0;
-      if (ku) { wr = pow2_scale(wr, -ku); wi = pow2_scale(wi, -ku); }
-      if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+      const int ku = has_above ? protect_update_ub(y, tn, x2) : 0;
+      double x2s = x2;
+      if (ku) { wr = pow2_scale(wr, -ku); wi = pow2_scale(wi, -ku); x2s = pow2_scale(x2, -ku); y = pow2_scale(y, -ku); }
+      if (has_above) y = fma(tn, x2s, y);
       st.shift = kd + ku;
       st.W[0][0] = wr; st.W[0][1] = wi;
       st.P[0][0] = beta * wr; st.P[0][1] = beta * wi;
@@ -256,8 +255,7 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
       const double* g = f + 4 * u;
       const int pi = pf & 1, pj = pf >> 1;
       double r0v = piv[0][t0c], r1v = piv[1][t0c];
-      const unsigned long long rb = max(abs_key(r0v), abs_key(r1v));
-      int kd = rb ? ilogb_key(rb) + 1 + 5 - ep - kOmegaExp : 0;
+      int kd = max(exp_ub(r0v), exp_ub(r1v)) + 5 - ep - kOmegaExp;
       kd = kd > 0 ? kd : 0;
       if (kd) { r0v = pow2_scale(r0v, -kd); r1v = pow2_scale(r1v, -kd); y = pow2_scale(y, -kd); }
       const double rp = pi ? r1v : r0v, ro = pi ? r0v : r1v;
@@ -265,9 +263,10 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
       const double xp = fma(-g[2], xo, rp * g[0]);
       double w0 = pj ? xo : xp, w1 = pj ? xp : xo;
       const double x = max_nonneg(fabs(w0), fabs(w1));
-      const int ku = has_above ? protect_update(y, tn, x) : 0;
-      if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); }
-      if (has_above) y = fma(tn, pow2_scale(x, -ku), pow2_scale(y, -ku));
+      const int ku = has_above ? protect_update_ub(y, tn, x) : 0;
+      double xs = x;
+      if (ku) { w0 = pow2_scale(w0, -ku); w1 = pow2_scale(w1, -ku); xs = pow2_scale(x, -ku); y = pow2_scale(y, -ku); }
+      if (has_above) y = fma(tn, xs, y);
       st.shift = kd + ku;
       st.W[0][0] = w0; st.W[1][0] = w1;
       st.P[0][0] = beta * w0; st.P[1][0] = beta * w1;
@@ -277,9 +276,7 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
       const double* g = f + 8 * u;
       const int pi = pf & 1, pj = pf >> 1;
       double r0r = piv[0][t0c], r0i = piv[0][t0c + 1], r1r = piv[1][t0c], r1i = piv[1][t0c + 1];
-      const unsigned long long rb =
-          max(max(abs_key(r0r), abs_key(r0i)), max(abs_key(r1r), abs_key(r1i)));
-      int kd = rb ? ilogb_key(rb) + 2 + 5 - ep - kOmegaExp : 0;
+      int kd = max(max(exp_ub(r0r), exp_ub(r0i)), max(exp_ub(r1r), exp_ub(r1i))) + 6 - ep - kOmegaExp;
       kd = kd > 0 ? kd : 0;
       if (kd) {
         r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
@@ -299,12 +296,14 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
       if (pj == 0) { w0r = xpr; w0i = xpi; w1r = xor_; w1i = xoi; }
       else         { w0r = xor_; w0i = xoi; w1r = xpr; w1i = xpi; }
       const double x2 = twice_max_abs(max(max(abs_key(w0r), abs_key(w0i)), max(abs_key(w1r), abs_key(w1i))));
-      const int ku = has_above ? protect_update(y, tn, x2) : 0;
+      const int ku = has_above ? protect_update_ub(y, tn, x2) : 0;
+      double x2s = x2;
       if (ku) {
         w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
         w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
+        x2s = pow2_scale(x2, -ku); y = pow2_scale(y, -ku);
       }
-      if (has_above) y = fma(tn, pow2_scale(x2, -ku), pow2_scale(y, -ku));
+      if (has_above) y = fma(tn, x2s, y);
       st.shift = kd + ku;
       st.W[0][0] = w0r; st.W[0][1] = w0i; st.W[1][0] = w1r; st.W[1][1] = w1i;
       st.P[0][0] = beta * w0r; st.P[0][1] = beta * w0i;
