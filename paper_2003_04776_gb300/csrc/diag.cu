@@ -232,9 +232,16 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
       }
     }
     __syncthreads();
-    // ---- phase A: one lane per unit solves the block; only the
-    //      right-hand-side-dependent arithmetic is left here
-    if ((lr >> 5) == pa_warp) {
+    // ---- phase A: the block's solve for every unit; only the
+    //      right-hand-side-dependent arithmetic is left here (the 2x2
+    //      blocks of complex pairs in a right-hand-side solve take eight
+    //      lanes per unit, everything else one)
+    if ((lr >> 5) == pa_warp && mode == kDiagSolve && pairs && sz == 2) {
+      const bool anysh = pair2_step_warp<CB>(lr & 31, nu, li0, s_piv, s_pre + s_boff[bidx], s_ep[bidx],
+                                            s_pf[bidx], s_tn[bidx], s_a, s_b, s_beta, s_y, s_e, s_act, s_sh,
+                                            s_PQ, s_W);
+      if ((lr & 31) == 0) s_anysh = anysh ? 1 : 0;
+    } else if ((lr >> 5) == pa_warp) {
       const int u = lr & 31;
       int myshift = 0;
       if (u < nu) {

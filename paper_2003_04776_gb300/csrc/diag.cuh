@@ -316,4 +316,101 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
   return st;
 }
 
+
+// Phase A of one 2x2 block step of complex pairs in a right-hand-side solve
+// (kernel 3), taken by a whole warp: each unit (at most 4) gets 8 lanes, and
+// the independent products of its 2x2 solve and of P = beta w, Q = alpha w
+// are spread over them, so that the step issues 9 FP64 warp instructions
+// instead of 29 on one lane (a warp issues its FP64 instructions one at a
+// time).  Each value is computed with the same operations as in unit_step.
+// Writes the unit's P, Q, W, shift, running bound y and exponent e; returns
+// whether any unit shifted.  All 32 lanes call it.
+template <int CB>
+__device__ __forceinline__ bool pair2_step_warp(int lane, int nu, int li0, const double (*piv)[CB],
+                                                const double* f, const short* ep_row, const unsigned char* pf_row,
+                                                const double* tn_row, const double* s_a, const double* s_b,
+                                                const double* s_beta, double* s_y, int* s_e, const int* s_act,
+                                                int* s_sh, double2 (*s_PQ)[CB], double (*s_W)[CB]) {
+  const int u = lane >> 3, j = lane & 7, base = lane & ~7;
+  const bool mine = u < nu;
+  const int uu = mine ? u : 0;
+  const int t0c = 2 * uu;
+  const bool has_above = li0 > 0;
+  const double a = s_a[uu], b = s_b[uu], beta = s_beta[uu];
+  const double tn = tn_row[uu];
+  double y = s_y[uu];
+  const int ep = ep_row[uu];
+  const bool active = mine && s_act[uu];
+  const unsigned full = 0xffffffffu;
+  int shift = 0;
+  double* pq0 = reinterpret_cast<double*>(&s_PQ[0][t0c]);   // P(t0c), Q(t0c), P(t0c + 1), Q(t0c + 1)
+  double* pq1 = reinterpret_cast<double*>(&s_PQ[1][t0c]);
+  const int j4 = j & 3;
+  const double* g = f + 8 * uu;
+  const int pf = pf_row[uu];
+  const int pi = pf & 1, pj = pf >> 1;
+  double r0r = piv[0][t0c], r0i = piv[0][t0c + 1], r1r = piv[1][t0c], r1i = piv[1][t0c + 1];
+  int kd = max(max(exp_ub(r0r), exp_ub(r0i)), max(exp_ub(r1r), exp_ub(r1i))) + 6 - ep - kOmegaExp;
+  kd = kd > 0 ? kd : 0;
+  if (kd) {
+    r0r = pow2_scale(r0r, -kd); r0i = pow2_scale(r0i, -kd);
+    r1r = pow2_scale(r1r, -kd); r1i = pow2_scale(r1i, -kd);
+    y = pow2_scale(y, -kd);
+  }
+  const double rpr = pi ? r1r : r0r, rpi = pi ? r1i : r0i;
+  const double ror = pi ? r0r : r1r, roi = pi ? r0i : r1i;
+  const double lre = g[0], lim = g[1];
+  // lanes j4 = 0..3: Re e, Im e (e = ro - l rp), Re q, Im q (q = rp / piv)
+  const double A1 = j4 < 2 ? -lre : rpr;
+  const double B1 = j4 == 0 ? rpr : (j4 == 1 ? rpi : (j4 == 2 ? g[4] : g[5]));
+  const double C1 = j4 == 0 ? lim : (j4 == 1 ? -lim : (j4 == 2 ? -rpi : rpi));
+  const double D1 = j4 == 0 ? rpi : (j4 == 1 ? rpr : (j4 == 2 ? g[5] : g[4]));
+  const double E1 = j4 == 0 ? ror : (j4 == 1 ? roi : -0.0);
+  const double v1 = fma(A1, B1, fma(C1, D1, E1));
+  const double er = __shfl_sync(full, v1, base), ei = __shfl_sync(full, v1, base + 1);
+  const double q1r = __shfl_sync(full, v1, base + 2), q1i = __shfl_sync(full, v1, base + 3);
+  // even lanes Re xo, odd lanes Im xo (xo = e / u22)
+  const bool ev = (j & 1) == 0;
+  const double v2 = fma(er, ev ? g[2] : g[3], (ev ? -ei : ei) * (ev ? g[3] : g[2]));
+  const double xor_ = __shfl_sync(full, v2, base), xoi = __shfl_sync(full, v2, base + 1);
+  // even lanes Re xp, odd lanes Im xp (xp = q - (m / piv) xo)
+  const double v3 = fma(-g[6], ev ? xor_ : xoi, fma(ev ? g[7] : -g[7], ev ? xoi : xor_, ev ? q1r : q1i));
+  const double xpr = __shfl_sync(full, v3, base), xpi = __shfl_sync(full, v3, base + 1);
+  double w0r, w0i, w1r, w1i;
+  if (pj == 0) { w0r = xpr; w0i = xpi; w1r = xor_; w1i = xoi; }
+  else         { w0r = xor_; w0i = xoi; w1r = xpr; w1i = xpi; }
+  const double x2 = twice_max_abs(max(max(abs_key(w0r), abs_key(w0i)), max(abs_key(w1r), abs_key(w1i))));
+  const int ku = has_above ? protect_update_ub(y, tn, x2) : 0;
+  double x2s = x2;
+  if (ku) {
+    w0r = pow2_scale(w0r, -ku); w0i = pow2_scale(w0i, -ku);
+    w1r = pow2_scale(w1r, -ku); w1i = pow2_scale(w1i, -ku);
+    x2s = pow2_scale(x2, -ku); y = pow2_scale(y, -ku);
+  }
+  // lanes 0..7: block column xc = j / 4; P re, P im, Q re, Q im
+  const int xc = j >> 2;
+  const double wr = xc ? w1r : w0r, wi = xc ? w1i : w0i;
+  const double A4 = j4 < 2 ? beta : a;
+  const double B4 = (j4 == 0 || j4 == 2) ? wr : wi;
+  const double C4 = j4 < 2 ? -0.0 : (j4 == 2 ? -b : b);
+  const double D4 = j4 < 2 ? 1.0 : (j4 == 2 ? wi : wr);
+  const double v = fma(A4, B4, C4 * D4);
+  if (active) {
+    shift = kd + ku;
+    double* pq = xc ? pq1 : pq0;
+    pq[(j4 & 1) * 2 + (j4 >> 1)] = v;
+    if (j == 0) {
+      s_W[0][t0c] = w0r; s_W[0][t0c + 1] = w0i; s_W[1][t0c] = w1r; s_W[1][t0c + 1] = w1i;
+      s_sh[t0c] = shift; s_sh[t0c + 1] = shift; s_e[uu] += shift;
+      s_y[uu] = has_above ? fma(tn, x2s, y) : y;
+    }
+  } else if (mine && j == 0) {
+    pq0[0] = pq0[1] = pq0[2] = pq0[3] = 0.0;
+    pq1[0] = pq1[1] = pq1[2] = pq1[3] = 0.0;
+    s_W[0][t0c] = s_W[0][t0c + 1] = s_W[1][t0c] = s_W[1][t0c + 1] = 0.0;
+    s_sh[t0c] = 0; s_sh[t0c + 1] = 0;
+  }
+  return __any_sync(full, shift != 0);
+}
+
 }  // namespace pevc
