@@ -180,14 +180,16 @@ __device__ __forceinline__ double i64_scaled_fast(long long t, int e, bool& slow
   const unsigned long long bits = sgn | ((unsigned long long)(E & 0x7ff) << 52) | (mant & ((1ull << 52) - 1));
   return __longlong_as_double((long long)(mag ? bits : 0ull));
 }
-//   pow2_scale_fast: y * 2^s for a normal or zero y
+//   pow2_scale_fast: y * 2^s for a normal or zero y, on the two 32-bit
+//   halves (a zero test of the whole magnitude would be compiled into an
+//   FP64 comparison, an instruction on the scarce FP64 pipe)
 __device__ __forceinline__ double pow2_scale_fast(double y, int sh, bool& slow) {
-  const long long b = __double_as_longlong(y);
-  const int E = (int)((b >> 52) & 0x7ff);
-  const bool nz = (b & 0x7fffffffffffffffll) != 0;
+  const int hi = __double2hiint(y), lo = __double2loint(y);
+  const int E = (hi >> 20) & 0x7ff;
   const int En = E + sh;
-  slow |= nz & ((E == 0) | (En <= 0) | (En >= 2047));
-  return nz ? __longlong_as_double(b + ((long long)sh << 52)) : y;
+  const bool zs = E == 0;   // zero or subnormal
+  slow |= (zs & (((hi & 0xfffff) | lo) != 0)) | (!zs & ((En <= 0) | (En >= 2047)));
+  return zs ? y : __hiloint2double(hi + (sh << 20), lo);
 }
 
 // t * 2^e rounded to nearest (ties to even), for |t| < 2^63: the IEEE-754
