@@ -47,10 +47,13 @@ __device__ __forceinline__ int ilogb_key(unsigned long long a) {
 // Smallest E with |v| < 2^E for finite v != 0.
 __device__ __forceinline__ int exp_above(double v) { return ilogb_key(abs_key(v)) + 1; }
 
-// Larger of two non-negative doubles (bitwise; no FP64 instruction).
+// Larger of two non-negative doubles, by an unsigned maximum of their
+// magnitude bit patterns (a signed comparison of the raw patterns would be
+// compiled into an FP64 maximum, an instruction on the scarce FP64 pipe).
 __device__ __forceinline__ double max_nonneg(double x, double y) {
-  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
-  return __longlong_as_double(a > b ? a : b);
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y) & 0x7fffffffffffffffull;
+  return __longlong_as_double((long long)(a > b ? a : b));
 }
 
 // ProtectUpdate (Section 4, property 2) on exponent bounds: y, t, x >= 0 and

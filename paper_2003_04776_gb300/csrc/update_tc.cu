@@ -9,9 +9,11 @@
 //              chunk (rows of 128 bytes, 128-byte swizzle), landing directly
 //              in the K-major layout the MMA reads; a ring of shared-memory
 //              stages with full / empty mbarriers;
-//   warp 1     tensor-memory owner and MMA issuer: every slice product p x q
-//              with p + q < L is one tcgen05.mma (M = 128, N = NCOL, K = 16,
-//              BF16 in, FP32 out) into the accumulator of its level p + q;
+//   warp 1     tensor-memory owner and MMA issuer: the slice products p x q
+//              with p + q < L of one A slice p are one tcgen05.mma (M = 128,
+//              N = (L - p) NCOL over the stacked X'' slices, K = 16, BF16 in,
+//              FP32 out) whose consecutive NCOL-column blocks are the level
+//              accumulators p .. L - 1;
 //              the level accumulators of an output tile live in one of two
 //              tensor-memory buffers;
 //   warps 2-17 two epilogue groups of eight warps (two per tensor-memory
@@ -154,6 +156,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
                                                              int ns, const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB) {
   static_assert(NCOL % 16 == 0 && 2 * L * NCOL <= 512, "two level-accumulator buffers must fit tensor memory");
+  static_assert(NS >= L && L <= 5 && L * NCOL <= 256, "one MMA per A slice covers at most N = 256 columns");
   using G = TcGeom<NS, NCOL>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // swizzle atoms need 1024-byte aligned stage bases
@@ -213,7 +216,6 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(kTcRows, NCOL);
       int s = 0, it = 0;
       uint32_t ph = 0;
       for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x, ++it) {
@@ -227,16 +229,20 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           const uint32_t base = smem_addr(smem + s * G::stage);
           const uint64_t ad = smem_desc_sw128(base, 1024);
           const uint64_t bd = smem_desc_sw128(base + NS * G::a_slice, 1024);
+          // one MMA per A slice p: the X'' slices q < L - p are consecutive
+          // NCOL-row blocks of the stage and the level accumulators
+          // consecutive NCOL-column blocks of the buffer, so A_p times the
+          // stacked slices lands every product p x q in level p + q
 #pragma unroll
           for (int k16 = 0; k16 < kTcK / 16; ++k16)
 #pragma unroll
-            for (int p = 0; p < NS; ++p)
-#pragma unroll
-              for (int q = 0; q < NS; ++q)
-                if (p + q < L)
-                  tc_mma_bf16(acc + (uint32_t)((p + q) * NCOL), ad + (uint64_t)((p * G::a_slice + 32 * k16) >> 4),
-                              bd + (uint64_t)((q * G::b_slice + 32 * k16) >> 4), idesc,
-                              (kk | k16 | p) ? 1u : 0u);
+            for (int p = 0; p < NS && p < L; ++p) {
+              constexpr int kNq[5] = {NS < L ? NS : L, NS < L - 1 ? NS : L - 1, NS < L - 2 ? NS : L - 2,
+                                      NS < L - 3 ? NS : L - 3, NS < L - 4 ? NS : L - 4};
+              tc_mma_bf16(acc + (uint32_t)(p * NCOL), ad + (uint64_t)((p * G::a_slice + 32 * k16) >> 4),
+                          bd + (uint64_t)((32 * k16) >> 4), idesc_bf16_f32(kTcRows, kNq[p] * NCOL),
+                          (kk | k16 | p) ? 1u : 0u);
+            }
           tc_commit(&empty[s]);             // frees the stage once these MMAs completed
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
