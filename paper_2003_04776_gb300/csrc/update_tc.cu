@@ -3,7 +3,7 @@
 //     Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij,   k in [k_lo, k_hi), j >= i,
 // with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).
 //
-// Persistent CTA (one per SM) of ten warps:
+// Persistent CTA (one per SM) of nineteen warps:
 //   warp 0     TMA producer: per K block of 64 one 3-D box with every slice of
 //              the A row tile and one with every slice of the X'' column
 //              chunk (rows of 128 bytes, 128-byte swizzle), landing directly
@@ -20,14 +20,15 @@
 //              lane quarter, each with half of the tile's columns); group g
 //              takes every other output tile and owns buffer g, so one group's
 //              epilogue overlaps the MMAs of the next tile and the other
-//              group's epilogue.  Per element: exact integer recombination of
-//              the levels, one conversion to FP64, the augmented-tile scales
-//              (Algorithms 2 and 3 of Section 4) by exponent arithmetic, one
-//              FP64 subtraction; new column maxima (rounded-up 32-bit keys) by
-//              a butterfly reduction.  The per-column scales of a group's next
-//              tile are computed into a second slot and its Y chunk
-//              (contiguous in HBM) is prefetched into L2 while the current
-//              tile's MMAs run.
+//              group's epilogue;
+//   warp 18    column-scale producer: the per-column scales of the CTA's
+//              output tiles, up to four tiles ahead, into a ring of shared-
+//              memory slots (full / empty mbarriers), and each tile's Y chunk
+//              (contiguous in HBM) prefetched into L2.
+// Epilogue, per element: exact integer recombination of the levels, one
+// conversion to FP64, the augmented-tile scales (Algorithms 2 and 3 of
+// Section 4) by exponent arithmetic, one FP64 subtraction; new column maxima
+// (rounded-up 32-bit keys) by one warp reduction per column.
 // Every wait is bounded (SM clock cycles): a wait that runs out sets
 // PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
 // out of bounded waits, tensor memory is freed).
@@ -43,8 +44,10 @@ constexpr int kTcK = 64;                     // K per pipeline stage: one 128-by
 constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
 constexpr int kTcEpiWarps = 8;               // warps per epilogue group: two per lane quarter
 constexpr int kTcColBlock = 4;               // columns per epilogue step
-constexpr int kTcThreads = 64 + 2 * 32 * kTcEpiWarps;   // producer, MMA issuer, two epilogue groups
-// (eighteen warps: one SM sub-partition holds five of them, so its 16K
+constexpr int kTcScalesWarp = 2 + 2 * kTcEpiWarps;       // the column-scales producer
+constexpr int kTcThreads = 32 * (kTcScalesWarp + 1);   // producer, MMA issuer, two epilogue groups, scales
+constexpr int kTcRing = 4;                              // column-scale slots (output tiles ahead)
+// (nineteen warps: one SM sub-partition holds five of them, so its 16K
 // registers cap a thread at 96)
 
 template <int NS, int NCOL>
@@ -130,25 +133,6 @@ __device__ __forceinline__ unsigned key32(double x) {
   return (unsigned)((abs_key(x) + 0xffffffffull) >> 32);
 }
 
-// Column maxima of a 4-column block over a warp's 32 rows: a butterfly that
-// halves the columns each step.  On return lanes with (lane & 7) == 0 hold the
-// maximum of column (lane >> 3) & 3 over all 32 lanes.
-__device__ __forceinline__ unsigned warp_colmax4(unsigned (&k)[4], int lane) {
-  unsigned a2[2];
-  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const unsigned mine = b4 ? k[u + 2] : k[u], other = b4 ? k[u] : k[u + 2];
-    a2[u] = max(mine, __shfl_xor_sync(0xffffffffu, other, 16));
-  }
-  const unsigned mine = b3 ? a2[1] : a2[0], other = b3 ? a2[0] : a2[1];
-  unsigned r = max(mine, __shfl_xor_sync(0xffffffffu, other, 8));
-  r = max(r, __shfl_xor_sync(0xffffffffu, r, 4));
-  r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
-  r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
-  return r;
-}
-
 template <int NS, int L, int NCOL>
 __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
                                                              const double* __restrict__ nrmX,
@@ -167,7 +151,8 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (its group's warps arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
-  __shared__ int4 s_col[2][2][NCOL];               // per group, two tiles: column scales
+  __shared__ int4 s_col[kTcRing][NCOL];            // column scales of the next output tiles (a ring)
+  __shared__ uint64_t s_sfull[kTcRing], s_sempty[kTcRing];
   __shared__ unsigned s_key[2][4][NCOL];           // per group and lane quarter: column maxima (upper 32 bits)
   __shared__ int s_fail, s_stop[2];
   volatile int* fail = &s_fail;
@@ -182,6 +167,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   if (tid == 0) {
     for (int s = 0; s < G::stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kTcEpiWarps); }
+    for (int r = 0; r < kTcRing; ++r) { mbar_init(&s_sfull[r], 1); mbar_init(&s_sempty[r], 1); }
     s_fail = 0;
     s_stop[0] = s_stop[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
@@ -250,6 +236,29 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
         tc_commit(&tfull[buf]);             // the tile's accumulators are complete
       }
     }
+  } else if (warp == kTcScalesWarp) {
+    // -------------------------------------------------------------- scales
+    // per output tile of this CTA, in order: the column scales into the next
+    // ring slot (a chain of dependent global loads, kept off the epilogue
+    // groups) and the tile's Y chunk into L2
+    for (int it = 0;; ++it) {
+      const int t = blockIdx.x + it * (int)gridDim.x;
+      if (t >= total || __any_sync(0xffffffffu, *fail != 0)) break;   // warp-uniform exits
+      const int rs = it % kTcRing;
+      if (!__all_sync(0xffffffffu, mbar_wait_cycles(&s_sempty[rs], (uint32_t)((it / kTcRing) & 1) ^ 1u, kTcWait))) {
+        *fail = 1;
+        break;
+      }
+      for (int c = lane; c < NCOL; c += 32) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, c, &s_col[rs][c]);
+      if (lane == 0) {
+        const double* yp;
+        uint32_t yb;
+        tile_y_range<NCOL>(P, tt, t, yp, yb);
+        prefetch_l2(yp, yb);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_sfull[rs]);
+    }
   } else {
     // ------------------------------------------------------------ epilogue
     constexpr int CW = kTcColBlock;
@@ -263,28 +272,13 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
     const int cbeg = half * HALF;
     int it = g;
     int t = blockIdx.x + it * (int)gridDim.x;
-    if (et < NCOL && t < total) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, et, &s_col[g][0][et]);
-    if (et == 0 && t < total) {
-      const double* yp;
-      uint32_t yb;
-      tile_y_range<NCOL>(P, tt, t, yp, yb);
-      prefetch_l2(yp, yb);
-    }
-    group_barrier(g);
     for (; t < total; it += 2, t = blockIdx.x + it * (int)gridDim.x) {
-      const int slot = (it >> 1) & 1;
-      {
-        // the group's next tile: its Y chunk into L2 and its column scales
-        // into the other slot, while this tile's MMAs finish
-        const int tn = t + 2 * (int)gridDim.x;
-        if (et == 0 && tn < total) {
-          const double* yp;
-          uint32_t yb;
-          tile_y_range<NCOL>(P, tt, tn, yp, yb);
-          prefetch_l2(yp, yb);
-        }
-        if (et < NCOL && tn < total) tile_scales<L, NCOL>(P, i, tt, tn, exX, nrmX, F, et, &s_col[g][slot ^ 1][et]);
-      }
+      const int rs = it % kTcRing;
+      // a wait that runs out skips the tile's work but still passes both
+      // group barriers below, where the group stops together
+      const bool sok = mbar_wait_cycles(&s_sfull[rs], (uint32_t)((it / kTcRing) & 1), kTcWait);
+      if (!sok) *fail = 1;
+      const int4* scol = s_col[rs];
       const int k = tt.k_lo + t / tt.nchunks;
       const int ch = tt.chunk_first + t % tt.nchunks;
       const int j = tt.chunk_j[ch];
@@ -300,10 +294,11 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
 #pragma unroll
       for (int u = 0; u < CW; ++u) {
         const int col = cbeg + u;
-        const int4 cd = s_col[g][slot][col];
+        const int4 cd = scol[col];
         yv[u] = (rowok && col < nc && cd.z == 1) ? ycol[(size_t)col * tb] : 0.0;
       }
-      const bool ok = mbar_wait_cycles(&tfull[g], (uint32_t)((it >> 1) & 1), kTcWait);
+      // warp-uniform, since the work below synchronises the warp
+      const bool ok = __all_sync(0xffffffffu, sok && mbar_wait_cycles(&tfull[g], (uint32_t)((it >> 1) & 1), kTcWait));
       if (!ok) *fail = 1;
       tc_fence_after();
       if (ok) {
@@ -327,7 +322,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             yn[u] = 0.0;
             if (cb + CW < cbeg + HALF) {
               const int col = cb + CW + u;
-              const int4 cd = s_col[g][slot][col];
+              const int4 cd = scol[col];
               if (rowok && col < nc && cd.z == 1) yn[u] = ycol[(size_t)col * tb];
             }
           }
@@ -339,7 +334,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
 #pragma unroll
           for (int u = 0; u < CW; ++u) {
             const int col = cb + u;
-            const int4 cd = s_col[g][slot][col];
+            const int4 cd = scol[col];
             act[u] = (cd.z & 1) && rowok && col < nc;
             long long tv = 0;
 #pragma unroll
@@ -354,7 +349,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           if (__any_sync(0xffffffffu, slow)) {
 #pragma unroll
             for (int u = 0; u < CW; ++u) {
-              const int4 cd = s_col[g][slot][cb + u];
+              const int4 cd = scol[cb + u];
               long long tv = 0;
 #pragma unroll
               for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
@@ -369,8 +364,12 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             if (act[u]) ycol[(size_t)(cb + u) * tb] = ynew[u];
             key[u] = act[u] ? key32(ynew[u]) : 0u;
           }
-          const unsigned cm = warp_colmax4(key, lane);
-          if ((lane & 7) == 0) s_key[g][quarter][cb + ((lane >> 3) & 3)] = cm;
+          // column maxima over the warp's 32 rows: one warp reduction each
+#pragma unroll
+          for (int u = 0; u < CW; ++u) {
+            const unsigned cm = __reduce_max_sync(0xffffffffu, key[u]);
+            if (lane == 0) s_key[g][quarter][cb + u] = cm;
+          }
 #pragma unroll
           for (int u = 0; u < CW; ++u) yv[u] = yn[u];
         }
@@ -378,7 +377,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
       group_barrier(g);
       // new norms and exponents of the tile's columns
       if (et < NCOL) {
-        const int4 cd = s_col[g][slot][et];
+        const int4 cd = scol[et];
         if (ok && et < nc && (cd.z & 1)) {
           const long long idx = (long long)k * P.m + c0 + et;
           const unsigned km = max(max(s_key[g][0][et], s_key[g][1][et]), max(s_key[g][2][et], s_key[g][3][et]));
@@ -388,6 +387,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
       }
       if (et == 0) s_stop[g] = *fail;
       group_barrier(g);
+      if (et == 0) mbar_arrive(&s_sempty[rs]);   // the slot may take a later tile's scales
       if (s_stop[g]) break;
     }
   }
