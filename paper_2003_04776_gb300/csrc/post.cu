@@ -8,9 +8,11 @@
 //
 // After consolidation the largest entry has modulus in [1, 2) (the reference
 // exponent is that of the largest represented magnitude), so the argmax works
-// on squared moduli as integer keys and the normalisation multiplies by the
-// reciprocal of the pivot computed once per column: one or two FP64
-// operations per element instead of a division.
+// on integer keys (the magnitude bits of a real entry, of the squared modulus
+// of a complex one) and the normalisation multiplies by the reciprocal of the
+// pivot computed once per column: one FP64 operation per real element, three
+// per complex one, instead of a division; the power-of-two consolidation is
+// integer arithmetic.
 #include "common.cuh"
 
 namespace pevc {
@@ -25,6 +27,18 @@ __device__ __forceinline__ BestIdx better(BestIdx a, BestIdx b) {
   return a;
 }
 
+// x * 2^e on the two 32-bit halves for a normal x with a normal result (and
+// for zero x or e == 0); the library path otherwise.  Every test is on
+// integers, so nothing here issues to the FP64 pipe.
+__device__ __forceinline__ double scale2(double x, int e) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int E = (hi >> 20) & 0x7ff;
+  const int En = E + e;
+  if (E != 0 && E != 0x7ff && En > 0 && En < 0x7ff) return __hiloint2double(hi + (e << 20), lo);
+  if (e == 0 || (((hi & 0x7fffffff) | lo) == 0)) return x;
+  return ldexp(x, e);
+}
+
 // Column tile of output column q (cstart is non-decreasing).
 __device__ __forceinline__ int col_tile(const Problem& P, int q) {
   int lo = 0, hi = P.M - 1;
@@ -33,6 +47,25 @@ __device__ __forceinline__ int col_tile(const Problem& P, int q) {
     if (P.cstart[mid] <= q) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+constexpr int kPostTiles = 256;        // tiles of a column staged at once
+constexpr int kNoTile = INT32_MIN;     // a tile whose column segment is all zero
+
+// Per tile k in [kb, ke) of output column q: x = exponent
+// shift to the reference exponent (kNoTile for an all-zero segment), y = first
+// row, z = rows of the eigenvector's support in the tile.  Synchronises the
+// CTA before and after.
+__device__ __forceinline__ void stage_tiles(const Problem& P, int q, bool pair, int last, int eref, int kb, int ke,
+                                            int4* s_tile) {
+  __syncthreads();
+  for (int k = kb + (int)threadIdx.x; k < ke; k += blockDim.x) {
+    const long long idx = (long long)k * P.m + q;
+    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+    const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
+    s_tile[k - kb] = make_int4(abs_key(nv) ? P.ex[idx] - eref : kNoTile, r0, max(h, 0), 0);
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V, int ldv,
@@ -50,6 +83,7 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   __shared__ int s_eref;
   __shared__ BestIdx s_red[8];
   __shared__ int s_ered[8];
+  __shared__ int4 s_tile[kPostTiles];
 
   // 1. reference exponent: the largest represented magnitude over the tiles
   int eref = INT32_MIN;
@@ -69,25 +103,44 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   __syncthreads();
   eref = s_eref;
 
-  // 2. the entry of largest modulus (first index on ties)
+  // 2. the entry of largest modulus (first index on ties), and 3. the
+  //    written column(s).  Both passes run over the flattened (tile, row)
+  //    index space of the column in chunks of kPostTiles tiles, with the
+  //    per-tile shift and row range staged in shared memory, and four rows
+  //    per thread in flight.
   BestIdx best{0ull, 0x7fffffff};
-  for (int k = 0; k <= j; ++k) {
-    const long long idx = (long long)k * m + q;
-    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
-    if (!abs_key(nv)) continue;
-    const int sh = P.ex[idx] - eref;
-    const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
-    const double* Yt = tile_ptr(P, k, j);
-    for (int r = tid; r < h; r += blockDim.x) {
-      const double vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
-      double mg2;
-      if (pair) {
-        const double vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
-        mg2 = fma(vr, vr, vi * vi);
-      } else {
-        mg2 = vr * vr;
+  for (int kb = 0; kb <= j; kb += kPostTiles) {
+    const int ke = min(j + 1, kb + kPostTiles);
+    stage_tiles(P, q, pair, last, eref, kb, ke, s_tile);
+    const int nflat = (ke - kb) * tb;
+    for (int f0 = tid; f0 < nflat; f0 += 4 * (int)blockDim.x) {
+      double vr[4], vi[4];
+      int row[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * (int)blockDim.x;
+        row[u] = -1;
+        vr[u] = vi[u] = 0.0;
+        if (f < nflat) {
+          const int kk = f / tb, r = f - kk * tb;
+          const int4 ti = s_tile[kk];
+          if (r < ti.z && ti.x != kNoTile) {
+            const double* Yt = tile_ptr(P, kb + kk, j);
+            vr[u] = Yt[(size_t)lq * tb + r];
+            if (pair) vi[u] = Yt[(size_t)(lq + 1) * tb + r];
+            row[u] = ti.y + r;
+            vr[u] = scale2(vr[u], ti.x);
+            if (pair) vi[u] = scale2(vi[u], ti.x);
+          }
+        }
       }
-      best = better(best, BestIdx{abs_key(mg2), r0 + r});
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (row[u] < 0) continue;
+        // real columns compare |v| by its magnitude bits; pairs the squared modulus
+        const unsigned long long key = pair ? abs_key(fma(vr[u], vr[u], vi[u] * vi[u])) : abs_key(vr[u]);
+        best = better(best, BestIdx{key, row[u]});
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -121,35 +174,52 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   }
   const double s2 = 1.0 / fma(dr, dr, di * di);
   const double nr = pair ? dr * s2 : 1.0 / dr, ni = di * s2;
+  const bool norm = normalise && best.v;
 
-  // 3. write the column(s)
   double* v0 = V + (size_t)q * ldv;
   double* v1 = pair ? V + (size_t)(q + 1) * ldv : nullptr;
-  for (int k = 0; k <= j; ++k) {
-    const long long idx = (long long)k * m + q;
-    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
-    const bool nz = abs_key(nv) != 0;
-    const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
-    const int sh = nz ? P.ex[idx] - eref : 0;
-    const double* Yt = tile_ptr(P, k, j);
-    for (int r = tid; r < h; r += blockDim.x) {
-      double vr = 0.0, vi = 0.0;
-      if (nz) {
-        vr = pow2_scale(Yt[(size_t)lq * tb + r], sh);
-        if (pair) vi = pow2_scale(Yt[(size_t)(lq + 1) * tb + r], sh);
-      }
-      if (normalise && best.v) {
-        if (pair) {
-          const double zr = fma(vr, nr, vi * ni), zi = fma(vi, nr, -(vr * ni));
-          vr = zr;
-          vi = zi;
-        } else {
-          vr = vr * nr;
+  for (int kb = 0; kb <= j; kb += kPostTiles) {
+    const int ke = min(j + 1, kb + kPostTiles);
+    stage_tiles(P, q, pair, last, eref, kb, ke, s_tile);
+    const int nflat = (ke - kb) * tb;
+    for (int f0 = tid; f0 < nflat; f0 += 4 * (int)blockDim.x) {
+      double vr[4], vi[4];
+      int row[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * (int)blockDim.x;
+        row[u] = -1;
+        vr[u] = vi[u] = 0.0;
+        if (f < nflat) {
+          const int kk = f / tb, r = f - kk * tb;
+          const int4 ti = s_tile[kk];
+          if (r < ti.z) {
+            row[u] = ti.y + r;
+            if (ti.x != kNoTile) {
+              const double* Yt = tile_ptr(P, kb + kk, j);
+              vr[u] = scale2(Yt[(size_t)lq * tb + r], ti.x);
+              if (pair) vi[u] = scale2(Yt[(size_t)(lq + 1) * tb + r], ti.x);
+            }
+          }
         }
-        if (r0 + r == istar) { vr = 1.0; vi = 0.0; }
       }
-      v0[r0 + r] = vr;
-      if (pair) v1[r0 + r] = vi;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (row[u] < 0) continue;
+        double xr = vr[u], xi = vi[u];
+        if (norm) {
+          if (pair) {
+            const double zr = fma(xr, nr, xi * ni), zi = fma(xi, nr, -(xr * ni));
+            xr = zr;
+            xi = zi;
+          } else {
+            xr = xr * nr;
+          }
+          if (row[u] == istar) { xr = 1.0; xi = 0.0; }
+        }
+        v0[row[u]] = xr;
+        if (pair) v1[row[u]] = xi;
+      }
     }
   }
   for (int r = last + 1 + tid; r < P.n; r += blockDim.x) {

@@ -81,39 +81,57 @@ __device__ __forceinline__ __nv_bfloat16 small_int_bf16(int x) { return __float2
 
 // ---------------------------------------------------------------- A slices
 
+// One CTA per half tile (64 rows of tile (k, l)), so that the tiles the
+// resident CTAs hold between the row maxima and the slicing stay in L2.
+constexpr int kSplitARows = 64;
+
 template <int NS>
 __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __restrict__ As,
                                                  int* __restrict__ eA, int ns) {
   int k, l;
-  tile_pair(blockIdx.x, k, l);
+  tile_pair(blockIdx.x >> 1, k, l);
   const int tb = P.tb, K2 = 2 * tb;
+  const int rbase = (int)(blockIdx.x & 1) * kSplitARows;   // first local row of this half
   const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
   const int cl0 = P.toff[l], hl = P.toff[l + 1] - cl0;
   const long long tri = tri_index(k, l);
-  __shared__ int s_e[kMaxTile];
+  __shared__ int s_e[kSplitARows];
+  __shared__ unsigned long long s_part[4][kSplitARows];
   const double* S = P.S;
   const double* T = P.T;
   const int tid = threadIdx.x;
-  if (tid < tb) {
-    const int r = tid;
-    double mx = 0.0;
+  if (rbase >= tb) return;
+  // row maxima: four threads per row, each over a quarter of [S_kl T_kl]
+  {
+    const int rr = tid % kSplitARows, part = tid / kSplitARows;
+    const int r = rbase + rr;
+    unsigned long long key = 0;
     if (r < hk) {
       const int gr = rk0 + r;
-      const int cs_first = (k == l) ? max(0, gr - cl0 - (P.blk[gr] == 2 ? 1 : 0)) : 0;
-      const int ct_first = (k == l) ? gr - cl0 : 0;
-      unsigned long long key = 0;
-      for (int c = cs_first; c < hl; ++c) key = max(key, abs_key(S[(size_t)(cl0 + c) * P.lds + gr]));
-      for (int c = ct_first; c < hl; ++c) key = max(key, abs_key(T[(size_t)(cl0 + c) * P.ldt + gr]));
-      mx = __longlong_as_double((long long)key);
+      const bool isT = part >= 2;
+      const int cb = (part & 1) * (tb / 2), ce = min(hl, cb + tb / 2);
+      const int first = (k == l) ? (isT ? gr - cl0 : max(0, gr - cl0 - (P.blk[gr] == 2 ? 1 : 0))) : 0;
+      const double* src = isT ? T : S;
+      const int ld = isT ? P.ldt : P.lds;
+#pragma unroll 4
+      for (int c = max(cb, first); c < ce; ++c) key = max(key, abs_key(src[(size_t)(cl0 + c) * ld + gr]));
     }
-    const int e = (mx > 0.0) ? exp_above(mx) : 0;
-    s_e[r] = e;
-    eA[tri * tb + r] = e;
+    s_part[part][rr] = key;
+  }
+  __syncthreads();
+  if (tid < kSplitARows) {
+    const int r = rbase + tid;
+    const unsigned long long key = max(max(s_part[0][tid], s_part[1][tid]), max(s_part[2][tid], s_part[3][tid]));
+    const int e = key ? exp_above(__longlong_as_double((long long)key)) : 0;
+    s_e[tid] = e;
+    if (r < tb) eA[tri * tb + r] = e;
   }
   __syncthreads();
   const int groups = K2 / 8;
-  for (int item = tid; item < tb * groups; item += blockDim.x) {
-    const int r = item % tb, g = item / tb;
+  const int rows = min(kSplitARows, tb - rbase);
+  for (int item = tid; item < rows * groups; item += blockDim.x) {
+    const int rr = item % rows, g = item / rows;
+    const int r = rbase + rr;
     const int gr = rk0 + r;
     int sl[8][NS];
 #pragma unroll
@@ -128,7 +146,7 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
         if (k == l) ok = isT ? (gc >= gr) : (gc >= gr || (gc == gr - 1 && P.blk[gr] == 2));
         if (ok) v = isT ? T[(size_t)gc * P.ldt + gr] : S[(size_t)gc * P.lds + gr];
       }
-      int_slices<NS>(v, s_e[r], sl[u]);
+      int_slices<NS>(v, s_e[rr], sl[u]);
     }
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
@@ -554,8 +572,8 @@ int products(int ns, int levels) {
 cudaError_t launch_split_A(const Problem& P, SplitWorkspace& w, int ns, cudaStream_t s) {
   const long long tiles = (long long)P.M * (P.M + 1) / 2;
   if (tiles <= 0) return cudaSuccess;
-  if (ns == 5) k_split_A<5><<<(unsigned)tiles, 256, 0, s>>>(P, w.As, w.eA, w.ns);
-  else k_split_A<3><<<(unsigned)tiles, 256, 0, s>>>(P, w.As, w.eA, w.ns);
+  if (ns == 5) k_split_A<5><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns);
+  else k_split_A<3><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns);
   return cudaGetLastError();
 }
 
