@@ -341,7 +341,11 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             for (int s = 0; s < L; ++s)
               tv += (long long)__float2int_rn(__uint_as_float(lv[s][u])) * (1ll << (8 * (L - 1 - s)));
             bool sl = false;
-            const double prod = pow2_scale_fast((double)tv, erow + cd.y, sl);
+            // half the elements convert on the FP64 pipe, half by integer
+            // assembly of the binary64 fields (the same rounded value), so
+            // that neither pipe alone bounds the block
+            const double prod = (u & 2) ? i64_scaled_fast(tv, erow + cd.y, sl)
+                                        : pow2_scale_fast((double)tv, erow + cd.y, sl);
             const double yold = (cd.z & 2) ? 0.0 : pow2_scale_fast(yv[u], cd.x, sl);
             slow |= act[u] & sl;
             ynew[u] = yold - prod;
