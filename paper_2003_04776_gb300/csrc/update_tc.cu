@@ -331,6 +331,11 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           double ynew[CW];
           bool act[CW];
           bool slow = false;
+          // the shifts of the stored Y are per column, so this test is the
+          // same on every lane: most blocks keep Y's exponents and skip them
+          bool shy = false;
+#pragma unroll
+          for (int u = 0; u < CW; ++u) shy |= scol[cb + u].x != 0;
 #pragma unroll
           for (int u = 0; u < CW; ++u) {
             const int col = cb + u;
@@ -346,7 +351,9 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             // that neither pipe alone bounds the block
             const double prod = (u & 2) ? i64_scaled_fast(tv, erow + cd.y, sl)
                                         : pow2_scale_fast((double)tv, erow + cd.y, sl);
-            const double yold = (cd.z & 2) ? 0.0 : pow2_scale_fast(yv[u], cd.x, sl);
+            double yold = yv[u];
+            if (shy) yold = pow2_scale_fast(yv[u], cd.x, sl);
+            if (cd.z & 2) yold = 0.0;
             slow |= act[u] & sl;
             ynew[u] = yold - prod;
           }
