@@ -62,6 +62,7 @@ typedef struct pevc_plan_s *pevc_plan_t;
 /* Plan / solve flags. */
 #define PEVC_NO_NORMALISE 1u   /* return consolidated columns and exponents      */
 #define PEVC_NO_CORRECTION 2u  /* split precisions: skip the correction sweep    */
+#define PEVC_BT_EMULATED 4u    /* pevc_backtransform: FP64 GEMM by fixed-point emulation */
 
 /* Status codes. */
 #define PEVC_SUCCESS 0
@@ -207,6 +208,39 @@ int pevc_kernel_profile(pevc_plan_t plan, double *out);
 int pevc_solve_static(const double *S, int lds, const double *T, int ldt, int n,
                       const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out,
                       unsigned flags, void *stream);
+
+/*
+ * pevc_backtransform -- eigenvectors of the original pencil (Section 1).
+ * With (A, B) = (Q S Z^T, Q T Z^T) the pencil before its reduction to the
+ * real Schur pencil (S, T), a right eigenvector v of (S, T) gives the right
+ * eigenvector x = Z v of (A, B) for the same eigenvalue.  Computes X = Z V for
+ * the m columns of V as pevc_solve writes them (one FP64 GEMM on the plan's
+ * stream, cuBLAS), then, unless PEVC_NO_NORMALISE, scales every eigenvector
+ * (a real column, or the real and imaginary columns of a complex pair taken
+ * as one complex vector) so that its entry of largest modulus is exactly 1
+ * (the first such entry on ties; an all-zero vector stays zero).
+ *   plan       a plan with n <= n_max
+ *   Z, ldz     device, column-major n x n, ldz >= n; read-only
+ *   n          order of the pencil
+ *   V, ldv     device, column-major n x m, ldv >= n; read-only
+ *   m          number of columns of V (0 <= m <= n)
+ *   kinds      host int[m]: 0 a real eigenvector's column, 1 and 2 the real
+ *              and imaginary columns of a complex pair (a 1 is always
+ *              followed by a 2); or NULL for the columns of the plan's last
+ *              pevc_solve (m must then equal that solve's column count)
+ *   X, ldx     device, column-major n x m, ldx >= n, caller-allocated; must
+ *              not overlap Z or V
+ *   flags      PEVC_NO_NORMALISE | PEVC_BT_EMULATED (cuBLAS's fixed-point
+ *              emulation of the FP64 GEMM on the tensor cores)
+ * The first call allocates the plan's cuBLAS handle and, with kinds given,
+ * a device copy of them (n_max bytes); the call synchronises the plan's
+ * stream before returning.
+ * Returns 0, -i (argument i invalid, counting the plan as argument 1),
+ * PEVC_ERR_UNSUPPORTED (emulation not available), PEVC_ERR_NOMEM or
+ * PEVC_ERR_CUDA (a CUDA or cuBLAS call failed).
+ */
+int pevc_backtransform(pevc_plan_t plan, const double *Z, int ldz, int n, const double *V, int ldv, int m,
+                       const int *kinds, double *X, int ldx, unsigned flags);
 
 #ifdef __cplusplus
 }

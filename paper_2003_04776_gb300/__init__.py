@@ -29,6 +29,7 @@ PRECISIONS = {"fp64": FP64, "bf16x3": SPLIT_BF16X3, "fp8x4": SPLIT_FP8X4, "bf16x
 
 NO_NORMALISE = 1
 NO_CORRECTION = 2
+BT_EMULATED = 4      # pevc_backtransform: FP64 GEMM by fixed-point emulation
 
 SUCCESS = 0
 ERR_NOT_SCHUR = 1
@@ -68,10 +69,12 @@ _lib.pevc_kernel_profile.argtypes = [_vp, _vp]
 _lib.pevc_kernel_profile.restype = _i
 _lib.pevc_solve_static.argtypes = [_vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i), _u, _vp]
 _lib.pevc_solve_static.restype = _i
+_lib.pevc_backtransform.argtypes = [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _u]
+_lib.pevc_backtransform.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
-           "pevc_solve_static")
+           "pevc_solve_static", "pevc_backtransform")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -146,6 +149,17 @@ def pevc_solve_static(S: int, lds: int, T: int, ldt: int, n: int, select: int, V
     st = _lib.pevc_solve_static(_vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(V), ldv,
                                 _vp(scale), ctypes.byref(m), int(flags), _vp(stream) if stream else None)
     return st, m.value
+
+
+def pevc_backtransform(plan, Z: int, ldz: int, n: int, V: int, ldv: int, m: int, kinds, X: int, ldx: int,
+                       flags: int = 0):
+    """X = Z V with every eigenvector normalised (raw device pointers; kinds
+    a host sequence of m ints, or None for the plan's last solve).  Returns
+    the status."""
+    k = None
+    if kinds is not None:
+        k = (_i * max(len(kinds), 1))(*[int(x) for x in kinds])
+    return _lib.pevc_backtransform(plan, _vp(Z), ldz, n, _vp(V), ldv, m, k, _vp(X), ldx, int(flags))
 
 
 # ------------------------------------------------------------ torch wrapper
@@ -265,6 +279,26 @@ class Plan:
             Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0))
             out.append((np.asfortranarray(Vh[:n, :m]), sc[:m].cpu().numpy(), stat[b]))
         return st, out
+
+    def backtransform(self, Z, V, kinds=None, normalise: bool = True, emulated: bool = False,
+                      check: bool = True):
+        """X = Z V for the eigenvectors V of the plan's pencil (numpy n x m),
+        each eigenvector normalised to largest-modulus entry 1 unless
+        normalise is False.  kinds as in pevc_backtransform (None: the
+        columns of the plan's last solve).  Returns (X as numpy, status)."""
+        import torch
+        n, m = int(Z.shape[0]), int(V.shape[1])
+        Zt = to_device_colmajor(Z)
+        Vt = to_device_colmajor(V) if m else torch.zeros(1, dtype=torch.float64, device="cuda")
+        X = torch.empty((max(m, 1), max(n, 1)), dtype=torch.float64, device="cuda")   # column-major storage
+        flags = (0 if normalise else NO_NORMALISE) | (BT_EMULATED if emulated else 0)
+        with torch.cuda.stream(self.stream):
+            st = pevc_backtransform(self.h, Zt.data_ptr(), max(n, 1), n, Vt.data_ptr(), max(n, 1), m,
+                                    kinds, X.data_ptr(), max(n, 1), flags)
+        if check and st:
+            raise PevcError(st, "pevc_backtransform")
+        Xh = X[:m].cpu().numpy().T if m else np.zeros((n, 0))
+        return np.asfortranarray(Xh[:n, :m]), st
 
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.

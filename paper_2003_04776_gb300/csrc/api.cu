@@ -81,6 +81,12 @@ struct pevc_plan_s {
   cudaStream_t cstream[8] = {};
   cudaEvent_t bev = nullptr;     // the children wait for the plan's stream
   unsigned* h_bstatus = nullptr; // pinned [batch_max] status words
+  // back-transformation: cuBLAS handle, the column count of the last solve
+  // (whose column kinds are in kind), caller-given kinds
+  void* blas = nullptr;
+  int last_m = -1;
+  signed char* bt_kind = nullptr;
+  signed char* h_bt_kind = nullptr;
 };
 
 namespace {
@@ -160,6 +166,9 @@ void free_plan(pevc_plan_t p) {
     delete[] p->sev;
   }
   if (p->aux) cudaStreamDestroy(p->aux);
+  bt_handle_destroy(p->blas);
+  if (p->bt_kind) cudaFree(p->bt_kind);
+  if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
   delete p;
 }
 
@@ -411,6 +420,7 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   Structure st;
   if ((rc = structure_end(p, n, sel != nullptr, st))) return rc;
   *m_out = st.m;
+  p->last_m = st.m;
   // 2. pre-processing, the task graph, post-processing
   if ((rc = solve_enqueue(p, S, lds, T, ldt, n, V, ldv, scale, st, true))) return rc;
   unsigned bits = 0;
@@ -637,6 +647,7 @@ int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, cons
   if (count < 0 || count > plan->batch_max) return -2;
   if (count > 0 && (!S || !lds || !T || !ldt || !n || !V_out || !ldv || !scale_out || !m_out || !status))
     return -3;
+  plan->last_m = -1;   // the plan's column kinds no longer describe one solve
   if (plan->nchild > 0)
     return solve_batched(plan, count, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out, status);
   for (int b = 0; b < count; ++b) {
@@ -644,6 +655,48 @@ int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, cons
                            V_out[b], ldv[b], scale_out[b], &m_out[b]);
     if (status[b] == PEVC_ERR_CUDA) return PEVC_ERR_CUDA;
   }
+  return 0;
+}
+
+int pevc_backtransform(pevc_plan_t plan, const double* Z, int ldz, int n, const double* V, int ldv, int m,
+                       const int* kinds, double* X, int ldx, unsigned flags) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -4;
+  const int ld_min = n > 1 ? n : 1;
+  if (!Z && n > 0) return -2;
+  if (ldz < ld_min) return -3;
+  if (!V && m > 0) return -5;
+  if (ldv < ld_min) return -6;
+  if (m < 0 || m > n) return -7;
+  if (!X && m > 0) return -9;
+  if (ldx < ld_min) return -10;
+  if (flags & ~(PEVC_NO_NORMALISE | PEVC_BT_EMULATED)) return -11;
+  const signed char* dkind = plan->kind;
+  if (kinds) {
+    for (int q = 0; q < m; ++q) {
+      const int k = kinds[q];
+      if (k < 0 || k > 2 || (k == 1 && (q + 1 >= m || kinds[q + 1] != 2)) || (k == 2 && (q == 0 || kinds[q - 1] != 1)))
+        return -8;
+    }
+  } else if (m > 0 && plan->last_m != m) {
+    return -8;
+  }
+  if (n == 0 || m == 0) return 0;
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  if (kinds && !(flags & PEVC_NO_NORMALISE)) {
+    if (!plan->bt_kind && cudaMalloc(&plan->bt_kind, (size_t)plan->n_max) != cudaSuccess) return PEVC_ERR_NOMEM;
+    if (!plan->h_bt_kind && cudaMallocHost(&plan->h_bt_kind, (size_t)plan->n_max) != cudaSuccess)
+      return PEVC_ERR_NOMEM;
+    CK(cudaStreamSynchronize(plan->stream));   // the staging buffer may still feed an earlier copy
+    for (int q = 0; q < m; ++q) plan->h_bt_kind[q] = (signed char)kinds[q];
+    CK(cudaMemcpyAsync(plan->bt_kind, plan->h_bt_kind, (size_t)m, cudaMemcpyHostToDevice, plan->stream));
+    dkind = plan->bt_kind;
+  }
+  int rc = bt_handle(&plan->blas, plan->stream);
+  if (rc) return rc;
+  if ((rc = bt_gemm(plan->blas, (flags & PEVC_BT_EMULATED) != 0, n, m, Z, ldz, V, ldv, X, ldx))) return rc;
+  if (!(flags & PEVC_NO_NORMALISE)) CK(launch_bt_normalise(X, ldx, n, m, dkind, plan->stream));
+  CK(cudaStreamSynchronize(plan->stream));
   return 0;
 }
 

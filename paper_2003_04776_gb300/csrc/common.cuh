@@ -334,5 +334,11 @@ cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const
 cudaError_t launch_post(const Problem& P, double* V, int ldv, int32_t* scale, bool normalise,
                         cudaStream_t s);
 cudaError_t launch_gather_subdiag(const double* S, int lds, int n, double* out, cudaStream_t s);
+// back-transformation X = Z V (backtransform.cu)
+int bt_handle(void** h, cudaStream_t s);
+void bt_handle_destroy(void* h);
+int bt_gemm(void* h, bool emulated, int n, int m, const double* Z, int ldz, const double* V, int ldv, double* X,
+            int ldx);
+cudaError_t launch_bt_normalise(double* X, int ldx, int n, int m, const signed char* kind, cudaStream_t s);
 
 }  // namespace pevc

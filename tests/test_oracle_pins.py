@@ -342,3 +342,59 @@ def test_infinite_eigenvalue_vector():
     assert err < 1e-13
     # the vector of the infinite eigenvalue lies in the kernel of T
     assert np.abs(T @ V[:, r]).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Back-transformation (Section 1): x = Z v is an eigenvector of (A, B) =
+# (Q S Z^T, Q T Z^T).  The pins use the residual of the original pencil, which
+# does not go through oracle.backtransform.
+# ---------------------------------------------------------------------------
+
+def _original_pencil(p, seed):
+    from oracle.backtransform import random_orthogonal
+    Q = random_orthogonal(p.n, seed)
+    Z = random_orthogonal(p.n, seed + 1)
+    return Q, Z, Q @ p.S @ Z.T, Q @ p.T @ Z.T
+
+
+def test_backtransform_gives_eigenvectors_of_original_pencil():
+    from oracle.backtransform import backtransform
+    p = pencilgen.config_pencil(0, n=60)
+    st, Vo, sc, m = oracle.evc(p.S, p.T)
+    assert st == 0
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    Q, Z, A, B = _original_pencil(p, 777)
+    X = backtransform(Z, Vo, kinds)
+    res = check.residuals(A, B, X, kinds, pos, a, b, beta)
+    assert res.max() <= 100 * p.n * check.U, res.max() / (p.n * check.U)
+    # normalisation: the entry of largest modulus of every eigenvector is exactly 1
+    for c, k in enumerate(kinds):
+        if k == 0:
+            assert np.max(np.abs(X[:, c])) == 1.0
+        elif k == 1:
+            z = X[:, c] + 1j * X[:, c + 1]
+            i = int(np.argmax(np.abs(z)))
+            assert z[i] == 1.0
+
+
+def test_backtransform_planted_transpose_fails_the_residual():
+    from oracle.backtransform import backtransform
+    p = pencilgen.config_pencil(0, n=60)
+    st, Vo, sc, m = oracle.evc(p.S, p.T)
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    Q, Z, A, B = _original_pencil(p, 779)
+    X = backtransform(Z.T, Vo, kinds)            # the mistake: Z^T instead of Z
+    res = check.residuals(A, B, X, kinds, pos, a, b, beta)
+    assert res.max() > 1e-6
+
+
+def test_backtransform_with_identity_returns_the_vectors():
+    from oracle.backtransform import backtransform
+    p = pencilgen.config_pencil(0, n=50)
+    st, Vo, sc, m = oracle.evc(p.S, p.T)
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, _ = check.column_kinds(blk)
+    X = backtransform(np.eye(p.n), Vo, kinds)
+    assert np.array_equal(X, Vo)
