@@ -25,10 +25,12 @@
 //              output tiles, up to four tiles ahead, into a ring of shared-
 //              memory slots (full / empty mbarriers), and each tile's Y chunk
 //              (contiguous in HBM) prefetched into L2.
-// Epilogue, per element: exact integer recombination of the levels, one
-// conversion to FP64, the augmented-tile scales (Algorithms 2 and 3 of
-// Section 4) by exponent arithmetic, one FP64 subtraction; new column maxima
-// (rounded-up 32-bit keys) by one warp reduction per column.
+// Epilogue, per element: exact integer recombination of the levels, its
+// rounding to FP64 with the augmented-tile scale applied (Algorithms 2 and 3
+// of Section 4; half the elements of a block by the int64 -> FP64 conversion
+// and exponent arithmetic, half by integer assembly of the binary64 fields,
+// so that the FP64 and integer pipes share the work), one FP64 subtraction;
+// new column maxima (rounded-up 32-bit keys) by one warp reduction per column.
 // Every wait is bounded (SM clock cycles): a wait that runs out sets
 // PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
 // out of bounded waits, tensor memory is freed).
