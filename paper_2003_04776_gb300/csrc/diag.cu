@@ -5,22 +5,25 @@
 // One CTA owns one tile (i, j) and a chunk of at most CB columns that are all
 // real or all complex pairs (so the per-block pivot work is never divergent).
 // Thread lr holds column lr % CB of the chunk at the rows congruent to lr / CB
-// modulo 128 / CB, in registers.  The 1x1 / 2x2 blocks of
-// S_ii are processed bottom-up; for every block the column threads solve the
-// block (real or complex; Gaussian elimination with complete pivoting for
-// 2x2, pivots below smin raised to smin -- the DLALN2 principle of Section
-// 5.2) and pick the power-of-two scale that keeps the division and the
-// following column update below Omega; then all row threads apply the scale
-// and the rank-1/rank-2 column update
-//   y_r <- 2^-k y_r - (S_{r,blk} (beta w) - T_{r,blk} (alpha w)).
-// Every tile column carries its own exponent (an augmented tile column).
+// modulo 128 / CB, in registers.  The 1x1 / 2x2 blocks of S_ii are processed
+// bottom-up; for every block the solve of each eigenvector (real or complex;
+// Gaussian elimination with complete pivoting for 2x2, pivots below smin
+// raised to smin -- the DLALN2 principle of Section 5.2) picks the power-of-
+// two scale that keeps the division and the following column update below
+// Omega; then all threads apply the scale and the rank-1/rank-2 update
+//   y_r <- 2^-k y_r - (S_{r,blk} (beta w) - T_{r,blk} (alpha w))
+// of the rows above the block.  Every tile column carries its own exponent
+// (an augmented tile column).
 //
-// FP64 instructions are scarce on this GPU, so everything that does not depend
-// on the right-hand side is taken off the sequential block chain: the
-// diagonal blocks' entries and column norms are staged in shared memory, and
-// the pivots of all 1x1 blocks are inverted up front by all threads in
-// parallel; the step itself is then a multiplication, integer exponent logic
-// for the protection, and the rank update.
+// FP64 instructions are scarce on this GPU (the SM's FP64 unit takes 16
+// cycles per warp instruction, and a warp issues them one at a time), so
+// everything that does not depend on the right-hand side is taken off the
+// sequential block chain and computed up front by all threads (inverted
+// pivots, 2x2 LU factors with one reciprocal per pivot, ProtectUpdate's t; the
+// 1x1 and the 2x2 blocks in separate warp-uniform passes).  A step is then a
+// few multiplications, the protection's integer exponent logic on the high
+// words, and the rank update; the 2x2 blocks of complex pairs spread their
+// step over eight lanes per eigenvector.
 #include "diag.cuh"
 
 namespace pevc {
