@@ -18,7 +18,7 @@
 namespace pevc {
 
 struct BestIdx {
-  unsigned long long v;   // key of the squared modulus (non-negative doubles order like their bits)
+  unsigned long long v;   // magnitude key: bits of |v| (real) or of |v|^2 (complex); non-negative doubles order like their bits
   int i;
 };
 
@@ -52,10 +52,10 @@ __device__ __forceinline__ int col_tile(const Problem& P, int q) {
 constexpr int kPostTiles = 256;        // tiles of a column staged at once
 constexpr int kNoTile = INT32_MIN;     // a tile whose column segment is all zero
 
-// Per tile k in [kb, ke) of output column q: x = exponent
-// shift to the reference exponent (kNoTile for an all-zero segment), y = first
-// row, z = rows of the eigenvector's support in the tile.  Synchronises the
-// CTA before and after.
+// Per tile k in [kb, ke) of output column q: x = exponent shift to the
+// reference exponent (kNoTile for an all-zero segment), y = first row, z =
+// rows of the eigenvector's support in the tile.  Synchronises the CTA before
+// and after.
 __device__ __forceinline__ void stage_tiles(const Problem& P, int q, bool pair, int last, int eref, int kb, int ke,
                                             int4* s_tile) {
   __syncthreads();
