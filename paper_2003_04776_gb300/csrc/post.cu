@@ -28,15 +28,22 @@ __device__ __forceinline__ BestIdx better(BestIdx a, BestIdx b) {
 }
 
 // x * 2^e on the two 32-bit halves for a normal x with a normal result (and
-// for zero x or e == 0); the library path otherwise.  Every test is on
-// integers, so nothing here issues to the FP64 pipe.
+// for e == 0); the library path otherwise (zero, subnormal, out of range).
+// Only the exponent field is tested: a test of the whole magnitude against
+// zero would be compiled into an FP64 comparison for every element.
 __device__ __forceinline__ double scale2(double x, int e) {
   const int hi = __double2hiint(x), lo = __double2loint(x);
   const int E = (hi >> 20) & 0x7ff;
   const int En = E + e;
   if (E != 0 && E != 0x7ff && En > 0 && En < 0x7ff) return __hiloint2double(hi + (e << 20), lo);
-  if (e == 0 || (((hi & 0x7fffffff) | lo) == 0)) return x;
+  if (e == 0) return x;
   return ldexp(x, e);
+}
+
+// Magnitude key of a double (its bit pattern without the sign), assembled
+// from the two 32-bit halves.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  return ((unsigned long long)((unsigned)__double2hiint(x) & 0x7fffffffu) << 32) | (unsigned)__double2loint(x);
 }
 
 // Column tile of output column q (cstart is non-decreasing).
@@ -138,7 +145,7 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
       for (int u = 0; u < 4; ++u) {
         if (row[u] < 0) continue;
         // real columns compare |v| by its magnitude bits; pairs the squared modulus
-        const unsigned long long key = pair ? abs_key(fma(vr[u], vr[u], vi[u] * vi[u])) : abs_key(vr[u]);
+        const unsigned long long key = pair ? mag_key(fma(vr[u], vr[u], vi[u] * vi[u])) : mag_key(vr[u]);
         best = better(best, BestIdx{key, row[u]});
       }
     }
