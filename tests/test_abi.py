@@ -56,3 +56,11 @@ def test_null_plan_and_bad_arguments_are_rejected_without_gpu():
     assert pevc.pevc_destroy(None) == 0
     st, info = pevc.pevc_plan_info(None)
     assert st == -1
+
+
+def test_backtransform_argument_checks_without_gpu():
+    import paper_2003_04776_gb300 as pevc
+    # a missing plan is rejected before any CUDA call
+    assert pevc.pevc_backtransform(None, 0, 1, 1, 0, 1, 1, None, 0, 1) == -1
+    assert pevc.BT_EMULATED == 4 and pevc.NO_NORMALISE == 1
+
