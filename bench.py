@@ -188,7 +188,6 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--check", action="store_true", help="residual of sampled columns after the run")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -327,8 +326,6 @@ def main():
                                 "sample": f"{inf['columns']} eigenvectors of the same pencil (stratified over the "
                                           f"diagonal), {inf['seconds']} s on {threads} threads (OpenMP over "
                                           "eigenvectors), extrapolated to all n by sum c^2"}
-    if args.check and rank == 0:
-        line["check"] = sampled_check(seed_pencil, V, n)
     plan.close()
     if rank == 0:
         kp = prof[-1]
@@ -339,30 +336,6 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
-
-
-def sampled_check(p, V, n, count=8):
-    """Relative residual of a few sampled eigenvectors (host FP64)."""
-    import oracle
-    from oracle import check
-    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
-    kinds, pos = check.column_kinds(blk)
-    cols = np.linspace(0, n - 1, count).astype(int)
-    cols = [c - 1 if kinds[c] == 2 else c for c in cols]
-    Vh = V[cols].cpu().numpy().T
-    nS = np.abs(p.S).sum(1).max()
-    nT = np.abs(p.T).sum(1).max()
-    worst = 0.0
-    for q, c in enumerate(cols):
-        if kinds[c] == 0:
-            z = Vh[:, q].astype(complex)
-        else:
-            z = Vh[:, q] + 1j * V[c + 1].cpu().numpy()
-        al = complex(a[pos[c]], b[pos[c]])
-        r = beta[pos[c]] * (p.S @ z) - al * (p.T @ z)
-        res = np.abs(r).max() / ((abs(beta[pos[c]]) * nS + abs(al) * nT) * np.abs(z).max())
-        worst = max(worst, res)
-    return {"sampled_columns": len(cols), "max_resid_over_nu": worst / (n * 2.0 ** -53)}
 
 
 if __name__ == "__main__":
