@@ -242,6 +242,32 @@ int pevc_solve_static(const double *S, int lds, const double *T, int ldt, int n,
 int pevc_backtransform(pevc_plan_t plan, const double *Z, int ldz, int n, const double *V, int ldv, int m,
                        const int *kinds, double *X, int ldx, unsigned flags);
 
+/*
+ * pevc_solve_left -- left eigenvectors of the real Schur pencil (S, T): for
+ * every selected eigenvalue alpha / beta, u != 0 with u^H (beta S - alpha T) = 0
+ * (the paper names left eigenvectors as future work, Section 7).  u is the
+ * right eigenvector, for conj(alpha), of (S^T, T^T); with J the reversal
+ * permutation, (J S^T J, J T^T J) is again a standardised real Schur pencil, so
+ * the call forms it, runs pevc_solve's robust solve on it, and reverses the
+ * rows back.
+ *   S, lds, T, ldt, n, select, scale_out, m_out
+ *              as in pevc_solve (select marks diagonal positions of S)
+ *   U_out, ldu device, column-major n x m, caller-allocated: the columns in
+ *              the order of S's diagonal, a complex pair as (Re u, Im u) for
+ *              the eigenvalue with positive imaginary part; u is zero above
+ *              its diagonal block, and normalised like pevc_solve's columns
+ *              (entry of largest modulus exactly 1) unless the plan was made
+ *              with PEVC_NO_NORMALISE, in which case scale_out[c] = e means
+ *              the represented vector is 2^e U_out[:, c]
+ * Workspace: the first call allocates three n_max x n_max FP64 arrays and two
+ * int32[n_max] arrays on the plan (the flipped pencil and its solve); later
+ * calls allocate nothing.  The call synchronises on return.
+ * Returns 0, -i (argument i invalid, counting the plan as argument 1), or a
+ * status of pevc_solve (which then refers to the same blocks of S and T).
+ */
+int pevc_solve_left(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
+                    const int32_t *select, double *U_out, int ldu, int32_t *scale_out, int *m_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,40 @@ def residuals(S, T, V, kinds, pos, a, b, beta):
     return res
 
 
+def left_residuals(S, T, U, kinds, pos, a, b, beta):
+    """Relative residual of every left eigenvector u (u^H (beta S - alpha T)
+    = 0, alpha = a + i b with b > 0 for a pair's columns (Re u, Im u)):
+        ||u^H (beta S - alpha T)||_inf / ((|beta| ||S||_1 + |alpha| ||T||_1) ||u||_inf)
+    (the 1-norms are maximum column sums, the norms of S^T and T^T)."""
+    S = np.asarray(S)
+    T = np.asarray(T)
+    U = np.asarray(U)
+    nS = np.abs(S).sum(axis=0).max()
+    nT = np.abs(T).sum(axis=0).max()
+    US = U.T @ S      # row c: U[:, c]^T S
+    UT = U.T @ T
+    res = np.zeros(len(kinds))
+    for c, k in enumerate(kinds):
+        if k == 2:
+            continue
+        p = pos[c]
+        al = complex(a[p], b[p])
+        bt = beta[p]
+        if k == 0:
+            u, us, ut = U[:, c].astype(complex), US[c].astype(complex), UT[c].astype(complex)
+        else:
+            u = U[:, c] + 1j * U[:, c + 1]
+            us = US[c] - 1j * US[c + 1]      # u^H S = conj(u)^T S
+            ut = UT[c] - 1j * UT[c + 1]
+        r = bt * us - al * ut
+        den = (abs(bt) * nS + abs(al) * nT) * np.abs(u).max()
+        val = np.abs(r).max() / den if den > 0 else np.inf
+        res[c] = val
+        if k == 1:
+            res[c + 1] = val
+    return res
+
+
 def compare_normalised(Vref, Vgot, kinds):
     """Largest componentwise |difference| after normalising ``Vgot`` at the
     index where ``Vref`` has its largest modulus (near-ties in the maximum may

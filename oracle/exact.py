@@ -118,3 +118,37 @@ def exact_eigenvectors(ep):
             V[:, c + 1] = np.conj(col)
         c += sz
     return V, dims
+
+
+def exact_left_eigenvectors(ep):
+    """Normalised exact left eigenvectors of an ``ExactPencil``: u with
+    u^H (beta S - alpha T) = 0, i.e. the kernel of (beta S - alpha T)^H =
+    beta S^T - conj(alpha) T^T.  Layout as in exact_eigenvectors (column c of
+    a 2x2 block holds u for mu + i nu, nu > 0; column c+1 its conjugate)."""
+    n = len(ep.S)
+    U = np.zeros((n, n), dtype=complex)
+    dims = []
+    c = 0
+    while c < n:
+        sz = 2 if ep.block[c] == 1 else 1
+        if sz == 1:
+            alpha, beta = GQ(ep.S[c][c]), GQ(ep.T[c][c])
+        else:
+            lr, li = ep.lam[c]
+            alpha, beta = GQ(lr, li), GQ(1)
+        calpha = GQ(alpha.re, -alpha.im)
+        MH = [[beta * GQ(ep.S[j][i]) - calpha * GQ(ep.T[j][i]) for j in range(n)] for i in range(n)]
+        basis = nullspace(MH)
+        dims.append(len(basis))
+        v = basis[0]
+        best = max(x.abs2() for x in v)
+        istar = next(i for i, x in enumerate(v) if x.abs2() == best)
+        d = v[istar]
+        z = [x / d for x in v]
+        col = np.array([x.to_complex() for x in z])
+        U[:, c] = col
+        if sz == 2:
+            U[:, c + 1] = np.conj(col)
+        c += sz
+    return U, dims
+

@@ -71,10 +71,12 @@ _lib.pevc_solve_static.argtypes = [_vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctyp
 _lib.pevc_solve_static.restype = _i
 _lib.pevc_backtransform.argtypes = [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _u]
 _lib.pevc_backtransform.restype = _i
+_lib.pevc_solve_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
+_lib.pevc_solve_left.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
-           "pevc_solve_static", "pevc_backtransform")
+           "pevc_solve_static", "pevc_backtransform", "pevc_solve_left")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -160,6 +162,15 @@ def pevc_backtransform(plan, Z: int, ldz: int, n: int, V: int, ldv: int, m: int,
     if kinds is not None:
         k = (_i * max(len(kinds), 1))(*[int(x) for x in kinds])
     return _lib.pevc_backtransform(plan, _vp(Z), ldz, n, _vp(V), ldv, m, k, _vp(X), ldx, int(flags))
+
+
+def pevc_solve_left(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, U: int, ldu: int,
+                    scale: int):
+    """Left eigenvectors (raw device pointers as in pevc_solve).  Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve_left(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(U), ldu,
+                              _vp(scale), ctypes.byref(m))
+    return st, m.value
 
 
 # ------------------------------------------------------------ torch wrapper
@@ -299,6 +310,27 @@ class Plan:
             raise PevcError(st, "pevc_backtransform")
         Xh = X[:m].cpu().numpy().T if m else np.zeros((n, 0))
         return np.asfortranarray(Xh[:n, :m]), st
+
+    def solve_left(self, S, T, select=None, check: bool = True):
+        """Left eigenvectors u^H (beta S - alpha T) = 0 of (S, T) (numpy or
+        torch).  Returns (U as an n x m numpy array, scale int32[m], status)."""
+        import torch
+        n = int(S.shape[0])
+        St = to_device_colmajor(S)
+        Tt = to_device_colmajor(T)
+        U = torch.empty((max(n, 1), max(n, 1)), dtype=torch.float64, device="cuda")   # column-major storage
+        scale = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        sel = None
+        if select is not None:
+            sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
+        with torch.cuda.stream(self.stream):
+            st, m = pevc_solve_left(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
+                                    sel.data_ptr() if sel is not None else 0, U.data_ptr(), max(n, 1),
+                                    scale.data_ptr())
+        if check and st:
+            raise PevcError(st, "pevc_solve_left")
+        Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0))
+        return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
 
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.

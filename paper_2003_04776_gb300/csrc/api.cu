@@ -87,6 +87,13 @@ struct pevc_plan_s {
   int last_m = -1;
   signed char* bt_kind = nullptr;
   signed char* h_bt_kind = nullptr;
+  // left eigenvectors: the flipped transposed pencil, its selection, its
+  // solve's output (allocated by the first pevc_solve_left)
+  double* lS = nullptr;
+  double* lT = nullptr;
+  double* lV = nullptr;
+  int32_t* lsel = nullptr;
+  int32_t* lsc = nullptr;
 };
 
 namespace {
@@ -167,6 +174,9 @@ void free_plan(pevc_plan_t p) {
   }
   if (p->aux) cudaStreamDestroy(p->aux);
   bt_handle_destroy(p->blas);
+  void* ldev[] = {p->lS, p->lT, p->lV, p->lsel, p->lsc};
+  for (void* d : ldev)
+    if (d) cudaFree(d);
   if (p->bt_kind) cudaFree(p->bt_kind);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
   delete p;
@@ -697,6 +707,43 @@ int pevc_backtransform(pevc_plan_t plan, const double* Z, int ldz, int n, const 
   if ((rc = bt_gemm(plan->blas, (flags & PEVC_BT_EMULATED) != 0, n, m, Z, ldz, V, ldv, X, ldx))) return rc;
   if (!(flags & PEVC_NO_NORMALISE)) CK(launch_bt_normalise(X, ldx, n, m, dkind, plan->stream));
   CK(cudaStreamSynchronize(plan->stream));
+  return 0;
+}
+
+int pevc_solve_left(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+                    const int32_t* select, double* U_out, int ldu, int32_t* scale_out, int* m_out) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !U_out) return -8;
+  if (ldu < std::max(n, 1)) return -9;
+  if (n > 0 && !scale_out) return -10;
+  if (!m_out) return -11;
+  *m_out = 0;
+  if (n == 0) return 0;
+  pevc_plan_t p = plan;
+  if (cudaSetDevice(p->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  if (!p->lS) {
+    const size_t nn = (size_t)p->n_max * p->n_max;
+    int rc = dalloc(&p->lS, nn);
+    rc = rc ? rc : dalloc(&p->lT, nn);
+    rc = rc ? rc : dalloc(&p->lV, nn);
+    rc = rc ? rc : dalloc(&p->lsel, (size_t)p->n_max);
+    rc = rc ? rc : dalloc(&p->lsc, (size_t)p->n_max);
+    if (rc) return rc;
+  }
+  cudaStream_t s = p->stream;
+  CK(launch_flip_transpose(S, lds, n, p->lS, s));
+  CK(launch_flip_transpose(T, ldt, n, p->lT, s));
+  if (select) CK(launch_flip_select(select, n, p->lsel, s));
+  int rc = solve_one(p, p->lS, n, p->lT, n, n, select ? p->lsel : nullptr, p->lV, n, p->lsc, m_out);
+  p->last_m = -1;   // the plan's column kinds describe the flipped pencil
+  if (rc) return rc;
+  CK(launch_left_out(p->lV, n, *m_out, p->kind, p->lsc, U_out, ldu, scale_out, s));
+  CK(cudaStreamSynchronize(s));
   return 0;
 }
 

@@ -340,5 +340,10 @@ void bt_handle_destroy(void* h);
 int bt_gemm(void* h, bool emulated, int n, int m, const double* Z, int ldz, const double* V, int ldv, double* X,
             int ldx);
 cudaError_t launch_bt_normalise(double* X, int ldx, int n, int m, const signed char* kind, cudaStream_t s);
+// left eigenvectors through the flipped transposed pencil (left.cu)
+cudaError_t launch_flip_transpose(const double* A, int lda, int n, double* B, cudaStream_t s);
+cudaError_t launch_flip_select(const int32_t* sel, int n, int32_t* out, cudaStream_t s);
+cudaError_t launch_left_out(const double* Vp, int n, int m, const signed char* kind, const int32_t* scp, double* U,
+                            int ldu, int32_t* scale, cudaStream_t s);
 
 }  // namespace pevc

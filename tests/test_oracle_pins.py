@@ -398,3 +398,55 @@ def test_backtransform_with_identity_returns_the_vectors():
     kinds, _ = check.column_kinds(blk)
     X = backtransform(np.eye(p.n), Vo, kinds)
     assert np.array_equal(X, Vo)
+
+
+# ---------------------------------------------------------------------------
+# Left eigenvectors: u^H (beta S - alpha T) = 0.  Pinned by the left residual
+# (from the definition), exact Gaussian-rational null vectors of
+# (beta S - alpha T)^H, the support below the block, and a planted mistake.
+# ---------------------------------------------------------------------------
+
+def test_left_oracle_residual_and_support():
+    from oracle.left import evc_left
+    for n, stress in ((80, False), (60, True)):
+        p = pencilgen.make_pencil(n, 880 + n, stress=stress)
+        st, U, sc, m = evc_left(p.S, p.T)
+        assert st == 0 and m == n
+        st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+        kinds, pos = check.column_kinds(blk)
+        res = check.left_residuals(p.S, p.T, U, kinds, pos, a, b, beta)
+        assert np.isfinite(U).all()
+        assert res.max() <= 100 * n * check.U, res.max() / (n * check.U)
+        for c, k in enumerate(kinds):
+            if k != 2:
+                assert np.all(U[:pos[c], c] == 0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_left_oracle_matches_fresh_exact(n):
+    from oracle.left import evc_left
+    worst = 0.0
+    for seed in range(8):
+        ep = pencilgen.exact_pencil(n, 300 + seed)
+        S, T = ep.as_float()
+        Ux, dims = exact.exact_left_eigenvectors(ep)
+        assert all(d == 1 for d in dims)
+        st, U, sc, m = evc_left(S, T)
+        assert st == 0
+        kinds, _ = check.column_kinds(ep.block)
+        err, _ = check.compare_normalised(_real_columns(Ux, kinds), U, kinds)
+        worst = max(worst, err)
+    assert worst <= 1e-13
+
+
+def test_left_oracle_planted_conjugation_fails_the_residual():
+    from oracle.left import evc_left
+    p = pencilgen.make_pencil(70, 891)
+    st, U, sc, m = evc_left(p.S, p.T)
+    st, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    assert (kinds == 1).any()
+    Ubad = U.copy()
+    Ubad[:, kinds == 2] *= -1.0          # the mistake: the imaginary part not negated
+    res = check.left_residuals(p.S, p.T, Ubad, kinds, pos, a, b, beta)
+    assert res[kinds == 1].max() > 1e-6
