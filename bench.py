@@ -41,14 +41,65 @@ def flops_all(n: int) -> float:
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the launches of one n = 20000 solve) from the ncu capture summarised in
-# profiles/k_update_tc_bf16x5.md, valid only for the kernel sources it was
-# taken on (their hash); any later change to them reports null.
+# over the launches of one n = 20000 solve) from the ncu captures summarised in
+# profiles/k_update_tc_bf16x5.md and profiles/k_diag_n8000.md, valid only for
+# the kernel sources they were taken on (their hash); any later change to them
+# reports null.
 TRAFFIC = {
+    "k_diag": {"bytes_per_launch": 1.1207e7, "n": 20000, "prec": "bf16x5",
+               "sources": ("diag.cu", "diag.cuh", "common.cuh"),
+               "sha256_16": "c873c533c59ed5e8"},
     "k_update_tc": {"bytes_per_launch": 1.2159e9, "n": 20000, "prec": "bf16x5",
                     "sources": ("update_tc.cu", "tc.cuh", "common.cuh", "split.cuh"),
                     "sha256_16": "5acffce1442da583"},
 }
+
+
+def diag_alg_flops(n: int, tb: int, M: int) -> float:
+    """Algorithmic FP64 flops of the diagonal solves of one solve: per column
+    and diagonal tile of order tb below it, the rank updates of the rows above
+    every block column, 2 FMAs (4 flops) per (row, block column): 2 tb (tb - 1)
+    flops; stage i solves the columns of the tiles right of tile i (n - (i+1) tb
+    of them with uniform tiles).  The tips (each tile's own triangle, under
+    0.5 %) are not counted."""
+    return float(sum(max(n - (i + 1) * tb, 0) * 2.0 * tb * (tb - 1) for i in range(max(M - 1, 0))))
+
+
+def rooflines(prof, ms, n, prec, tile, peaks, peak_src, nsm, tc_kernel=True):
+    """Rooflines of the two large kernels from the per-launch CUDA-event
+    profile of the timed steps: the update (tensor-bound; FP64 pipe on the FP64
+    path) and the diagonal solves (bound by the FP64 FMA units: nsm SMs x 2
+    lanes/clk x 2 flops at the maximum SM clock).  Returns (the kernel with
+    the larger share of the step, the other)."""
+    mean = lambda k: float(np.mean([p[k] for p in prof]))
+    upd_ms, upd_n, upd_flops = mean("update_ms"), int(round(mean("update_launches"))), mean("update_tensor_flops")
+    dg_ms, dg_n = mean("diag_ms"), int(round(mean("diag_launches")))
+    if prec == "fp64":
+        upd = {"bound": "alu", "unit": "TFLOP/s",
+               "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
+               "peak": 1.02, "peak_source": "own DFMA/DMMA probe (FP64 tensor and ALU rates are equal on GB300)",
+               "kernel": "k_update_f64"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        upd = {"bound": "tensor", "unit": "TFLOP/s",
+               "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
+               "peak": pk, "peak_source": f"{peak_src} bf16 sustained",
+               "kernel": "k_update_tc" if tc_kernel else "k_update_split"}
+    clock = float(peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    dg = {"bound": "alu", "unit": "TFLOP/s",
+          "achieved": diag_alg_flops(n, tile, dg_n) / (dg_ms * 1e-3) / 1e12 if dg_ms else None,
+          "peak": round(nsm * 2 * 2 * clock / 1e12, 4),
+          "peak_source": f"FP64 FMA units: {nsm} SMs x 2 lanes/clk x 2 flops x {clock / 1e6:.0f} MHz",
+          "kernel": "k_diag"}
+    for r, t, c in ((upd, upd_ms, upd_n), (dg, dg_ms, dg_n)):
+        if r["achieved"]:
+            r["achieved"] = round(r["achieved"], 2)
+            r["frac"] = round(r["achieved"] / r["peak"], 4)
+        r["traffic"] = measured_traffic(r["kernel"], n, prec)
+        r["launches_per_step"] = c
+        r["avg_launch_ms"] = round(t / max(c, 1), 4)
+        r["share_of_step"] = round(t / ms, 3) if ms else None
+    return (dg, upd) if dg_ms >= upd_ms else (upd, dg)
 
 
 def measured_traffic(kernel: str, n: int = 20000, prec: str = "bf16x5"):
@@ -250,33 +301,12 @@ def main():
     info = plan.info
     launches = int(np.mean([p["launches"] for p in prof]))
 
-    # dominant kernel roofline (CUDA events around each launch of the update kernel)
+    # rooflines of the dominant kernel and the other large one (CUDA events
+    # around each launch, on the solve's stream)
     peaks, peak_src = load_peaks()
-    upd_ms = float(np.mean([p["update_ms"] for p in prof]))
-    upd_n = int(np.mean([p["update_launches"] for p in prof]))
-    upd_flops = float(np.mean([p["update_tensor_flops"] for p in prof]))
-    if args.prec == "fp64":
-        roof = {"bound": "alu", "unit": "TFLOP/s",
-                "achieved": upd_flops / max(upd_n, 1) / (upd_ms / max(upd_n, 1) * 1e-3) / 1e12 if upd_ms else None,
-                "peak": 1.02, "peak_source": "own DFMA/DMMA probe (FP64 tensor and ALU rates are equal on GB300)"}
-    else:
-        pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
-        roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
-                "peak": pk, "peak_source": f"{peak_src} bf16 sustained"}
-    if roof["achieved"]:
-        roof["achieved"] = round(roof["achieved"], 2)
-        roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
-    if args.prec == "fp64":
-        roof["kernel"] = "k_update_f64"
-    elif info[0] == 128 and not os.environ.get("PEVC_UPDATE_KERNEL", "").startswith("m"):
-        roof["kernel"] = "k_update_tc"
-    else:
-        roof["kernel"] = "k_update_split"
-    roof["traffic"] = measured_traffic(roof["kernel"], n, args.prec)
-    roof["launches_per_step"] = upd_n
-    roof["avg_launch_ms"] = round(upd_ms / max(upd_n, 1), 4)
-    roof["share_of_step"] = round(upd_ms / ms, 3)
+    tc = info[0] == 128 and not os.environ.get("PEVC_UPDATE_KERNEL", "").startswith("m")
+    roof, roof_other = rooflines(prof, ms, n, args.prec, info[0], peaks, peak_src,
+                                 torch.cuda.get_device_properties(0).multi_processor_count, tc)
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -287,7 +317,7 @@ def main():
                        "correction_sweeps": info[7], "parallelism": f"replicas{world}",
                        "l2": "inputs 2 x %.1f GB >> 129 MB L2, no flush" % (n * n * 8 / 1e9)},
             "eigvec_per_s": round(n * world / (ms * 1e-3), 1),
-            "gpu_launches": launches, "roofline": roof, "clocks": clk.summary()}
+            "gpu_launches": launches, "roofline": roof, "roofline_other": roof_other, "clocks": clk.summary()}
 
     if not args.no_e2e:
         # end to end through the public API: host S, T in pinned memory, result back to host
