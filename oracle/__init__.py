@@ -64,6 +64,10 @@ def lib():
             L.orc_eigpairs.restype = i
             L.orc_evc.argtypes = [i, p, i, p, i, p, i, p, i, p, ctypes.POINTER(i), i]
             L.orc_evc.restype = i
+            L.orc_eigpairs_cplx.argtypes = [i, p, i, p, i, p, p, p]
+            L.orc_eigpairs_cplx.restype = i
+            L.orc_evc_cplx.argtypes = [i, p, i, p, i, p, i, p, i, p, ctypes.POINTER(i), i]
+            L.orc_evc_cplx.restype = i
             _lib = L
     return _lib
 
@@ -133,5 +137,48 @@ def evc(S, T, select=None, normalise: bool = True, plain: bool = False, nthreads
     st = lib().orc_evc(n, S.ctypes.data, max(n, 1), T.ctypes.data, max(n, 1),
                        None if sel is None else sel.ctypes.data, flags,
                        V.ctypes.data, max(n, 1), scale.ctypes.data, ctypes.byref(m), int(nthreads))
+    mm = m.value
+    return st, V[:, :mm].copy(order="F"), scale[:mm].copy(), mm
+
+
+def _fortran_c(A):
+    A = np.asarray(A, dtype=np.complex128)
+    return A if A.flags.f_contiguous else np.asfortranarray(A)
+
+
+def eigpairs_cplx(S, T):
+    """(status, alpha, beta, sigma) of a complex triangular pencil: the
+    eigenvalue alpha/beta of every diagonal entry, pre-scaled by 2^-sigma."""
+    S, T = _fortran_c(S), _fortran_c(T)
+    n = S.shape[0]
+    alpha = np.zeros(n, dtype=np.complex128)
+    beta = np.zeros(n, dtype=np.complex128)
+    sigma = np.zeros(n, dtype=np.int32)
+    st = lib().orc_eigpairs_cplx(n, S.ctypes.data, max(n, 1), T.ctypes.data, max(n, 1),
+                                 alpha.ctypes.data, beta.ctypes.data, sigma.ctypes.data)
+    return st, alpha, beta, sigma
+
+
+def evc_cplx(S, T, select=None, normalise: bool = True, plain: bool = False, nthreads: int = 1):
+    """Eigenvectors of a complex pencil in generalized Schur form (S, T upper
+    triangular, complex128): returns (status, V, scale, m) with V complex n x m.
+
+    One column per selected diagonal entry, in the order of the diagonal;
+    with ``normalise`` each vector has largest-modulus entry exactly 1 and
+    scale is the exponent of its growth relative to a unit tip, otherwise the
+    represented vector is 2^scale * V[:, c].
+    """
+    S, T = _fortran_c(S), _fortran_c(T)
+    n = S.shape[0]
+    V = np.zeros((n, max(n, 1)), dtype=np.complex128, order="F")
+    scale = np.zeros(max(n, 1), dtype=np.int32)
+    m = ctypes.c_int(0)
+    sel = None
+    if select is not None:
+        sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32))
+    flags = (0 if normalise else FLAG_NO_NORMALISE) | (FLAG_PLAIN if plain else 0)
+    st = lib().orc_evc_cplx(n, S.ctypes.data, max(n, 1), T.ctypes.data, max(n, 1),
+                            None if sel is None else sel.ctypes.data, flags,
+                            V.ctypes.data, max(n, 1), scale.ctypes.data, ctypes.byref(m), int(nthreads))
     mm = m.value
     return st, V[:, :mm].copy(order="F"), scale[:mm].copy(), mm

@@ -140,3 +140,40 @@ def compare_normalised(Vref, Vgot, kinds):
         zr2 = zr / zr[istar]
         errs[q] = np.abs(zg2 - zr2).max()
     return (errs.max() if errs.size else 0.0), errs
+
+
+def cplx_residuals(S, T, V, alpha, beta):
+    """Relative residual of every eigenvector of a complex triangular pencil:
+    column c of V for (alpha_c, beta_c) = the pair of its diagonal entry
+    (the columns of V follow the diagonal, ``pos`` gives the entries when a
+    selection was made).  Same measure as ``residuals``."""
+    S = np.asarray(S)
+    T = np.asarray(T)
+    V = np.asarray(V)
+    nS = np.abs(S).sum(axis=1).max()
+    nT = np.abs(T).sum(axis=1).max()
+    SV = S @ V
+    TV = T @ V
+    res = np.zeros(V.shape[1])
+    for c in range(V.shape[1]):
+        al, bt = alpha[c], beta[c]
+        r = bt * SV[:, c] - al * TV[:, c]
+        den = (abs(bt) * nS + abs(al) * nT) * np.abs(V[:, c]).max()
+        res[c] = np.abs(r).max() / den if den > 0 else np.inf
+    return res
+
+
+def compare_normalised_cplx(Vref, Vgot):
+    """``compare_normalised`` for complex columns (one eigenvector each)."""
+    Vref = np.asarray(Vref)
+    Vgot = np.asarray(Vgot)
+    errs = np.zeros(Vref.shape[1])
+    for c in range(Vref.shape[1]):
+        zr, zg = Vref[:, c], Vgot[:, c]
+        istar = int(np.argmax(np.abs(zr)))
+        d = zg[istar]
+        if d == 0 or not np.isfinite(d):
+            errs[c] = np.inf
+            continue
+        errs[c] = np.abs(zg / d - zr / zr[istar]).max()
+    return (errs.max() if errs.size else 0.0), errs

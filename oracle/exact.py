@@ -152,3 +152,27 @@ def exact_left_eigenvectors(ep):
         c += sz
     return U, dims
 
+
+def exact_complex_eigenvectors(ep):
+    """Normalised exact eigenvectors of a complex triangular pencil
+    (``pencilgen.exact_complex_pencil``): for each diagonal entry c, the kernel
+    of beta S - alpha T with (alpha, beta) = (S_cc, T_cc), by the general
+    null-space computation above, divided by its first entry of largest
+    modulus.  Returns the n x n complex array and the kernel dimensions."""
+    n = len(ep.S)
+    Sg = [[GQ(*ep.S[i][j]) for j in range(n)] for i in range(n)]
+    Tg = [[GQ(*ep.T[i][j]) for j in range(n)] for i in range(n)]
+    V = np.zeros((n, n), dtype=complex)
+    dims = []
+    for c in range(n):
+        alpha, beta = Sg[c][c], Tg[c][c]
+        M = [[beta * Sg[i][j] - alpha * Tg[i][j] for j in range(n)] for i in range(n)]
+        basis = nullspace(M)
+        dims.append(len(basis))
+        v = basis[0]
+        best = max(x.abs2() for x in v)
+        istar = next(i for i, x in enumerate(v) if x.abs2() == best)
+        d = v[istar]
+        V[:, c] = np.array([(x / d).to_complex() for x in v])
+    return V, dims
+

@@ -714,4 +714,255 @@ done:
     return status;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Complex pencils (Section 8, the extension to complex data types).          */
+/* ------------------------------------------------------------------------ */
+
+/* A complex pencil (S, T) in generalized complex Schur form: both upper
+ * triangular, entries stored interleaved (re, im) in column-major order with
+ * leading dimensions counted in complex elements.  There are no 2x2 blocks:
+ * every diagonal entry gives one eigenvalue (alpha, beta) = (S_cc, T_cc),
+ * both complex, and one eigenvector x with x_c = 1, x_i = 0 below c and
+ * (beta S - alpha T) x = 0.  The substitution is the scalar method above with
+ * complex arithmetic throughout; magnitudes are bounded by |re| + |im|, which
+ * is submultiplicative for complex products, so ProtectUpdate's bound
+ * ||Y|| + ||T|| ||X|| covers the complex update. */
+
+#define CSR(i, j) S[2 * ((size_t)(j) * (size_t)lds + (size_t)(i))]
+#define CSI(i, j) S[2 * ((size_t)(j) * (size_t)lds + (size_t)(i)) + 1]
+#define CTR(i, j) T[2 * ((size_t)(j) * (size_t)ldt + (size_t)(i))]
+#define CTI(i, j) T[2 * ((size_t)(j) * (size_t)ldt + (size_t)(i)) + 1]
+
+/* (alpha, beta) of every diagonal entry, scaled by 2^-sigma so that
+ * max(|beta|, |alpha|) * max|S, T entries| <= 2^PRESCALE_EXP (magnitudes
+ * |re| + |im|).  Returns ORC_ERR_NONFINITE if an entry of the upper
+ * triangles is Inf or NaN. */
+int orc_eigpairs_cplx(int n, const double *S, int lds, const double *T, int ldt,
+                      double *alpha, double *beta, int *sigma)
+{
+    double mx = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i <= j; ++i) {
+            double ms = mag(CSR(i, j), CSI(i, j)), mt = mag(CTR(i, j), CTI(i, j));
+            if (!isfinite(ms) || !isfinite(mt))
+                return ORC_ERR_NONFINITE;
+            mx = fmax(mx, fmax(ms, mt));
+        }
+    for (int c = 0; c < n; ++c) {
+        double ar = CSR(c, c), ai = CSI(c, c), br = CTR(c, c), bi = CTI(c, c);
+        int sg = 0;
+        double coef = fmax(mag(br, bi), mag(ar, ai));
+        if (coef > 0.0 && mx > 0.0) {
+            int k = exp_above(coef) + exp_above(mx) - PRESCALE_EXP;
+            if (k > 0)
+                sg = k;
+        }
+        alpha[2 * c] = ldexp(ar, -sg);
+        alpha[2 * c + 1] = ldexp(ai, -sg);
+        beta[2 * c] = ldexp(br, -sg);
+        beta[2 * c + 1] = ldexp(bi, -sg);
+        if (sigma)
+            sigma[c] = sg;
+    }
+    return 0;
+}
+
+/* m = beta * s - alpha * t for complex scalars. */
+static void cpencil(double br, double bi, double ar, double ai, double sr, double si, double tr, double ti,
+                    double *mr, double *mi)
+{
+    *mr = (br * sr - bi * si) - (ar * tr - ai * ti);
+    *mi = (br * si + bi * sr) - (ar * ti + ai * tr);
+}
+
+/* The eigenvector of diagonal entry c: on return w[0 .. c] (re, im
+ * interleaved) and e represent 2^e w relative to the unit tip w_c = 1. */
+static int evc_cplx_one(int n, const double *S, int lds, const double *T, int ldt, const double *alpha,
+                        const double *beta, const double *cS, const double *cT, int c, double *w, double *r,
+                        int *e_out, int robust)
+{
+    (void)n;
+    const double ar = alpha[2 * c], ai = alpha[2 * c + 1], br = beta[2 * c], bi = beta[2 * c + 1];
+    const double amag = mag(ar, ai), bmag = mag(br, bi);
+    if (amag == 0.0 && bmag == 0.0)
+        return ORC_ERR_INDEFINITE;
+    int e = 0;
+    for (int i = 0; i <= c; ++i) {
+        w[2 * i] = 0.0;
+        w[2 * i + 1] = 0.0;
+    }
+    w[2 * c] = 1.0;
+    for (int i = 0; i < c; ++i) {
+        r[2 * i] = 0.0;
+        r[2 * i + 1] = 0.0;
+    }
+    /* r = -(beta S - alpha T)[0:c, c] * w_c (the tip is 1) */
+    if (c > 0) {
+        if (robust) {
+            int k = orc_protect_upd(0.0, bmag * cS[c] + amag * cT[c], 1.0);
+            if (k) {
+                scale_all(w, NULL, 2 * (c + 1), r, NULL, 0, k);
+                e += k;
+            }
+        }
+        const double xr = w[2 * c], xi = w[2 * c + 1];
+        for (int i = 0; i < c; ++i) {
+            double mr, mi;
+            cpencil(br, bi, ar, ai, CSR(i, c), CSI(i, c), CTR(i, c), CTI(i, c), &mr, &mi);
+            r[2 * i] -= mr * xr - mi * xi;
+            r[2 * i + 1] -= mr * xi + mi * xr;
+        }
+    }
+    for (int i = c - 1; i >= 0; --i) {
+        double pr, pim;
+        cpencil(br, bi, ar, ai, CSR(i, i), CSI(i, i), CTR(i, i), CTI(i, i), &pr, &pim);
+        if (robust) {
+            double smin = fmax(ULP * (bmag * mag(CSR(i, i), CSI(i, i)) + amag * mag(CTR(i, i), CTI(i, i))),
+                               DBL_MIN);
+            if (mag(pr, pim) < smin) {
+                pr = smin;
+                pim = 0.0;
+            }
+            /* |q|_1 <= 2 |a|_1 / |b|_1 for q = a / b, hence the factor 2^1 */
+            int k = protect_div_sh(mag(r[2 * i], r[2 * i + 1]), 1, mag(pr, pim));
+            if (k) {
+                scale_all(w, NULL, 2 * (c + 1), r, NULL, 2 * c, k);
+                e += k;
+            }
+        }
+        orc_cdiv(r[2 * i], r[2 * i + 1], pr, pim, &w[2 * i], &w[2 * i + 1]);
+        if (i > 0) {
+            const double xr = w[2 * i], xi = w[2 * i + 1];
+            if (robust) {
+                double y = 0.0;
+                for (int q = 0; q < i; ++q)
+                    y = fmax(y, mag(r[2 * q], r[2 * q + 1]));
+                int k = orc_protect_upd(y, bmag * cS[i] + amag * cT[i], mag(xr, xi));
+                if (k) {
+                    scale_all(w, NULL, 2 * (c + 1), r, NULL, 2 * c, k);
+                    e += k;
+                }
+            }
+            const double yr = w[2 * i], yi = w[2 * i + 1];
+            for (int q = 0; q < i; ++q) {
+                double mr, mi;
+                cpencil(br, bi, ar, ai, CSR(q, i), CSI(q, i), CTR(q, i), CTI(q, i), &mr, &mi);
+                r[2 * q] -= mr * yr - mi * yi;
+                r[2 * q + 1] -= mr * yi + mi * yr;
+            }
+        }
+    }
+    *e_out = e;
+    return 0;
+}
+
+int orc_evc_cplx(int n, const double *S, int lds, const double *T, int ldt, const int *select, int flags,
+                 double *V, int ldv, int32_t *scale, int *m_out, int nthreads)
+{
+    if (n < 0) return -1;
+    if (n > 0 && !S) return -2;
+    if (lds < (n > 1 ? n : 1)) return -3;
+    if (n > 0 && !T) return -4;
+    if (ldt < (n > 1 ? n : 1)) return -5;
+    if (n > 0 && !V) return -8;
+    if (ldv < (n > 1 ? n : 1)) return -9;
+    if (!m_out) return -11;
+    *m_out = 0;
+    if (n == 0)
+        return 0;
+    double *alpha = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double *beta = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double *cS = (double *)malloc((size_t)n * sizeof(double));
+    double *cT = (double *)malloc((size_t)n * sizeof(double));
+    int *outcol = (int *)malloc((size_t)n * sizeof(int));
+    int status = 0;
+    if (!alpha || !beta || !cS || !cT || !outcol) {
+        status = ORC_ERR_NOMEM;
+        goto done;
+    }
+    status = orc_eigpairs_cplx(n, S, lds, T, ldt, alpha, beta, NULL);
+    if (status) goto done;
+    /* cS[k] = max_{r < k} |S_rk|, cT likewise */
+    for (int k = 0; k < n; ++k) {
+        double ms = 0.0, mt = 0.0;
+        for (int q = 0; q < k; ++q) {
+            ms = fmax(ms, mag(CSR(q, k), CSI(q, k)));
+            mt = fmax(mt, mag(CTR(q, k), CTI(q, k)));
+        }
+        cS[k] = ms;
+        cT[k] = mt;
+    }
+    int m = 0;
+    for (int c = 0; c < n; ++c) {
+        outcol[c] = (!select || select[c]) ? m : -1;
+        if (outcol[c] >= 0) ++m;
+    }
+    *m_out = m;
+    const int robust = !(flags & ORC_FLAG_PLAIN);
+    const int normalise = !(flags & ORC_FLAG_NO_NORMALISE);
+    int nt = nthreads > 0 ? nthreads : 1;
+    (void)nt;
+
+#pragma omp parallel num_threads(nt)
+    {
+        double *w = (double *)malloc((size_t)n * 2 * sizeof(double));
+        double *r = (double *)malloc((size_t)n * 2 * sizeof(double));
+        int local = (!w || !r) ? ORC_ERR_NOMEM : 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int c = n - 1; c >= 0; --c) {
+            if (outcol[c] < 0 || local) continue;
+            int e = 0;
+            int st = evc_cplx_one(n, S, lds, T, ldt, alpha, beta, cS, cT, c, w, r, &e, robust);
+            if (st) {
+                local = st;
+                continue;
+            }
+            double *v = V + 2 * (size_t)outcol[c] * (size_t)ldv;
+            int32_t sc = e;
+            if (normalise) {
+                int istar = 0;
+                double best = -1.0;
+                for (int i = 0; i <= c; ++i) {
+                    double mi = hypot(w[2 * i], w[2 * i + 1]);
+                    if (mi > best) {
+                        best = mi;
+                        istar = i;
+                    }
+                }
+                if (best > 0.0)
+                    sc = e + ilogb(best);
+                const double dr = w[2 * istar], di = w[2 * istar + 1];
+                for (int i = 0; i <= c; ++i)
+                    orc_cdiv(w[2 * i], w[2 * i + 1], dr, di, &v[2 * i], &v[2 * i + 1]);
+                v[2 * istar] = 1.0;
+                v[2 * istar + 1] = 0.0;
+            } else {
+                for (int i = 0; i <= c; ++i) {
+                    v[2 * i] = w[2 * i];
+                    v[2 * i + 1] = w[2 * i + 1];
+                }
+            }
+            for (int i = c + 1; i < n; ++i) {
+                v[2 * i] = 0.0;
+                v[2 * i + 1] = 0.0;
+            }
+            if (scale)
+                scale[outcol[c]] = sc;
+        }
+#pragma omp critical
+        {
+            if (local && !status) status = local;
+        }
+        free(w);
+        free(r);
+    }
+done:
+    free(alpha);
+    free(beta);
+    free(cS);
+    free(cT);
+    free(outcol);
+    return status;
+}
+
 int orc_version(void) { return 1; }

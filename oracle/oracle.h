@@ -30,6 +30,12 @@ int orc_eigpairs(int n, const double *S, int lds, const double *T, int ldt,
                  const signed char *blk, double *a, double *b, double *beta, int *sigma);
 int orc_evc(int n, const double *S, int lds, const double *T, int ldt, const int *select,
             int flags, double *V, int ldv, int32_t *scale, int *m_out, int nthreads);
+/* Complex pencils: S, T, V interleaved (re, im) complex128, leading
+ * dimensions in complex elements; alpha, beta interleaved complex[n]. */
+int orc_eigpairs_cplx(int n, const double *S, int lds, const double *T, int ldt,
+                      double *alpha, double *beta, int *sigma);
+int orc_evc_cplx(int n, const double *S, int lds, const double *T, int ldt, const int *select,
+                 int flags, double *V, int ldv, int32_t *scale, int *m_out, int nthreads);
 int orc_version(void);
 
 #ifdef __cplusplus

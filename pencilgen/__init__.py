@@ -281,3 +281,142 @@ def exact_pencil(n: int, seed: int, two_by_two: bool = True) -> ExactPencil:
             lam[r] = (mu, nu)
             lam[r + 1] = (mu, -nu)
     return ExactPencil(S=S, T=T, block=block, lam=lam)
+
+
+# ---------------------------------------------------------------------------
+# Complex pencils in generalized (complex) Schur form.
+# ---------------------------------------------------------------------------
+
+@dataclass
+class ComplexPencil:
+    S: np.ndarray                # complex128, upper triangular, column-major
+    T: np.ndarray
+    lam: np.ndarray              # generated eigenvalue of every diagonal entry
+    stress: bool = False
+    seed: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.S.shape[0]
+
+
+def _draw_complex_eigs(rng, count, stress):
+    """Complex eigenvalues N(0,1) + i N(0,1), at least 1e-6 apart (or, in the
+    stress variant, in clusters of eight with gaps of about 1e-8)."""
+    if stress:
+        out = np.empty(count, dtype=np.complex128)
+        k = 0
+        while k < count:
+            centre = complex(rng.standard_normal(), rng.standard_normal())
+            for _ in range(8):
+                if k >= count:
+                    break
+                out[k] = centre
+                centre += 1e-8 * (1.0 + 0.1 * rng.random())
+                k += 1
+        return out
+    out = rng.standard_normal(count) + 1j * rng.standard_normal(count)
+    while True:
+        order = np.argsort(out.real, kind="stable")
+        re, im = out.real[order], out.imag[order]
+        bad = set()
+        for k in range(count):
+            j = k + 1
+            while j < count and re[j] - re[k] < 1e-6:
+                if abs(im[j] - im[k]) < 1e-6:
+                    bad.add(int(order[j]))
+                j += 1
+        if not bad:
+            return out
+        for q in sorted(bad):
+            out[q] = complex(rng.standard_normal(), rng.standard_normal())
+
+
+def make_complex_pencil(n: int, seed: int, stress: bool = False, grid: int = 64,
+                        big_frac: float = 0.05, big: float = 1e100,
+                        t_scale: float = 2.0 ** -40) -> ComplexPencil:
+    """A seeded complex pencil of order ``n`` in generalized Schur form.
+
+    T's diagonal is real, T_cc ~ U[0.5, 2] (the form complex QZ returns), and
+    S_cc = lam_c T_cc with lam_c ~ N(0,1) + i N(0,1).  Every strictly upper
+    entry of S and T is (N(0,1) + i N(0,1)) / sqrt(2).  The stress variant
+    scales T's diagonal (and with it S's) by 2^-40, clusters the eigenvalues
+    and multiplies a random 5 % of the strictly upper tiles of a fixed
+    64 x 64 grid by 1e100, as for real pencils.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam = _draw_complex_eigs(rng, n, stress)
+    tdiag = rng.uniform(0.5, 2.0, n)
+    if stress:
+        tdiag = tdiag * t_scale
+    r = 1.0 / np.sqrt(2.0)
+    S = np.asfortranarray((rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * r)
+    T = np.asfortranarray((rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * r)
+    if stress and n > grid:
+        g = (n + grid - 1) // grid
+        pick = rng.random((g, g)) < big_frac
+        for p in range(g):
+            for q in range(p + 1, g):
+                if pick[p, q]:
+                    S[p * grid:(p + 1) * grid, q * grid:(q + 1) * grid] *= big
+                    T[p * grid:(p + 1) * grid, q * grid:(q + 1) * grid] *= big
+    for M in (S, T):
+        for j in range(n - 1):
+            M[j + 1:, j] = 0.0
+    idx = np.arange(n)
+    T[idx, idx] = tdiag
+    S[idx, idx] = lam * tdiag
+    return ComplexPencil(S=S, T=T, lam=lam, stress=stress, seed=seed)
+
+
+@dataclass
+class ExactComplexPencil:
+    S: list                      # n x n lists of (Fraction re, Fraction im), row-major
+    T: list
+
+    def as_complex(self):
+        n = len(self.S)
+        Sc = np.zeros((n, n), dtype=np.complex128, order="F")
+        Tc = np.zeros((n, n), dtype=np.complex128, order="F")
+        for i in range(n):
+            for j in range(n):
+                Sc[i, j] = complex(float(self.S[i][j][0]), float(self.S[i][j][1]))
+                Tc[i, j] = complex(float(self.T[i][j][0]), float(self.T[i][j][1]))
+        return Sc, Tc
+
+
+def exact_complex_pencil(n: int, seed: int, infinite: bool = False) -> ExactComplexPencil:
+    """A complex triangular pencil with dyadic-rational parts (exact in binary64).
+
+    Diagonal: T_cc = (k1 + i k2)/8 with k1 in [4, 16], k2 in [-8, 8]; S_cc =
+    lam_c T_cc with distinct lam_c = (k3 + i k4)/16.  Off-diagonal parts are
+    k/8 with |k| <= 16.  With ``infinite`` the last diagonal entry of T is
+    zero (an infinite eigenvalue).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    F = Fraction
+    z = (F(0), F(0))
+    S = [[z] * n for _ in range(n)]
+    T = [[z] * n for _ in range(n)]
+    for r in range(n):
+        for col in range(r + 1, n):
+            S[r][col] = (F(int(rng.integers(-16, 17)), 8), F(int(rng.integers(-16, 17)), 8))
+            T[r][col] = (F(int(rng.integers(-16, 17)), 8), F(int(rng.integers(-16, 17)), 8))
+    used = set()
+    for r in range(n):
+        while True:
+            lr, li = int(rng.integers(-40, 41)), int(rng.integers(-40, 41))
+            if (lr, li) not in used:
+                used.add((lr, li))
+                break
+        lr, li = F(lr, 16), F(li, 16)
+        tr, ti = F(int(rng.integers(4, 17)), 8), F(int(rng.integers(-8, 9)), 8)
+        if infinite and r == n - 1:
+            tr, ti = F(0), F(0)
+            lr, li = F(int(rng.integers(4, 17)), 8), F(0)   # S_cc itself, nonzero
+            S[r][r] = (lr, li)
+        else:
+            S[r][r] = (lr * tr - li * ti, lr * ti + li * tr)
+        T[r][r] = (tr, ti)
+    return ExactComplexPencil(S=S, T=T)
+

@@ -50,6 +50,59 @@ def make(name, n, seed, infinite):
         f.write("\n".join(lines) + "\n")
 
 
+# Complex triangular pencils (the extension to complex data, Section 8):
+# (name, order, seed, last eigenvalue infinite)
+CPLX_CASES = [
+    ("cexact_n5_s7", 5, 7, False),
+    ("cexact_n8_s13", 8, 13, False),
+    ("cexact_n6_s29_inf", 6, 29, True),
+]
+
+
+def make_cplx(name, n, seed, infinite):
+    ep = pencilgen.exact_complex_pencil(n, seed, infinite=infinite)
+    V, dims = exact.exact_complex_eigenvectors(ep)
+    assert all(d == 1 for d in dims), dims
+    lines = [f"# {name}: complex triangular pencil of order {n}, generator seed {seed};",
+             "# exact eigenvectors (kernel of beta*S - alpha*T, (alpha, beta) = (S_cc, T_cc),",
+             "# over Q(i), normalised at the first entry of largest modulus; paper Section 2,",
+             "# tall equation and Lemma, for complex data as in Section 8)",
+             f"n {n}"]
+    for nm, M in (("S", ep.S), ("T", ep.T)):
+        for i in range(n):
+            lines.append(f"{nm} {i} " + " ".join(f"{re},{im}" for re, im in M[i]))
+    for c in range(n):
+        col = V[:, c]
+        lines.append(f"V {c} " + " ".join(f"{float(z.real)!r},{float(z.imag)!r}" for z in col))
+    with open(os.path.join(HERE, name + ".txt"), "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def load_cplx(path):
+    """Parse a complex fixture: returns (S, T, V), all complex n x n."""
+    import numpy as np
+    S = T = V = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            tok = line.split()
+            if tok[0] == "n":
+                n = int(tok[1])
+                S = np.zeros((n, n), dtype=complex, order="F")
+                T = np.zeros((n, n), dtype=complex, order="F")
+                V = np.zeros((n, n), dtype=complex)
+            elif tok[0] in ("S", "T"):
+                i = int(tok[1])
+                M = S if tok[0] == "S" else T
+                M[i, :] = [complex(float(Fraction(p.split(",")[0])), float(Fraction(p.split(",")[1])))
+                           for p in tok[2:]]
+            elif tok[0] == "V":
+                c = int(tok[1])
+                V[:, c] = [complex(float(p.split(",")[0]), float(p.split(",")[1])) for p in tok[2:]]
+    return S, T, V
+
+
 def load(path):
     """Parse a fixture: returns (S, T, block, V) with V complex n x n."""
     import numpy as np
@@ -80,4 +133,6 @@ def load(path):
 if __name__ == "__main__":
     for case in CASES:
         make(*case)
-    print("wrote", len(CASES), "fixtures")
+    for case in CPLX_CASES:
+        make_cplx(*case)
+    print("wrote", len(CASES) + len(CPLX_CASES), "fixtures")
