@@ -268,6 +268,42 @@ int pevc_backtransform(pevc_plan_t plan, const double *Z, int ldz, int n, const 
 int pevc_solve_left(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
                     const int32_t *select, double *U_out, int ldu, int32_t *scale_out, int *m_out);
 
+/*
+ * pevc_solve_cplx -- eigenvectors of a complex pencil in generalized
+ * (complex) Schur form, the extension to complex data types that the paper
+ * names in Section 8.  S and T are upper triangular with complex entries;
+ * diagonal entry c gives the eigenvalue (alpha_c, beta_c) = (S_cc, T_cc) and
+ * the eigenvector x with x_c = 1 before normalisation, x_i = 0 for i > c and
+ * (beta_c S - alpha_c T) x = 0.  The robust blocked substitution of
+ * pevc_solve runs with complex arithmetic and no 2x2 blocks (tiles of order
+ * 64, FP64 throughout, whatever the plan's precision).
+ *   S, lds     device, n x n complex128 (interleaved re, im; cuDoubleComplex
+ *              layout), column-major, lds >= n counted in complex elements,
+ *              16-byte aligned; entries below the diagonal are never read
+ *   T, ldt     the same for T
+ *   n          order, 0 <= n <= the plan's n_max
+ *   select     device int32[n] or NULL; nonzero selects diagonal entry c
+ *   V_out, ldv device, n x m complex128, column-major, caller-allocated and
+ *              16-byte aligned: one column per selected entry, in diagonal
+ *              order; zero below the tip; normalised like pevc_solve's
+ *              columns (entry of largest modulus exactly 1 + 0i) unless the
+ *              plan was made with PEVC_NO_NORMALISE (then the eigenvector is
+ *              2^scale_out[c] V_out[:, c])
+ *   scale_out  device int32[m], written
+ *   m_out      host: number of columns written
+ * Workspace: the first call allocates about 12 n_max (n_max / 64 + 3) bytes
+ * of device memory on the plan (a power-of-two exponent and a magnitude per
+ * tile segment of every column); V_out itself is the working array.  The call reads the
+ * selection back to the host, synchronises once after the input scan and
+ * again on return.
+ * Returns 0, -i (argument i invalid, counting the plan as argument 1; a
+ * misaligned S, T or V_out counts as invalid), PEVC_ERR_NONFINITE,
+ * PEVC_ERR_INDEFINITE (S_cc = T_cc = 0 for a selected c), PEVC_ERR_NOMEM or
+ * PEVC_ERR_CUDA.
+ */
+int pevc_solve_cplx(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
+                    const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
+
 #ifdef __cplusplus
 }
 #endif

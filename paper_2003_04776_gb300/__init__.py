@@ -73,10 +73,12 @@ _lib.pevc_backtransform.argtypes = [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _vp, _i,
 _lib.pevc_backtransform.restype = _i
 _lib.pevc_solve_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
 _lib.pevc_solve_left.restype = _i
+_lib.pevc_solve_cplx.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
+_lib.pevc_solve_cplx.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
-           "pevc_solve_static", "pevc_backtransform", "pevc_solve_left")
+           "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -173,6 +175,17 @@ def pevc_solve_left(plan, S: int, lds: int, T: int, ldt: int, n: int, select: in
     return st, m.value
 
 
+def pevc_solve_cplx(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, V: int, ldv: int,
+                    scale: int):
+    """Eigenvectors of a complex triangular pencil (raw device pointers to
+    complex128 column-major arrays, leading dimensions in complex elements).
+    Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve_cplx(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(V), ldv,
+                              _vp(scale), ctypes.byref(m))
+    return st, m.value
+
+
 # ------------------------------------------------------------ torch wrapper
 
 class PevcError(RuntimeError):
@@ -190,6 +203,16 @@ def to_device_colmajor(A, device="cuda"):
         return t.to(device)
     if A.dtype != torch.float64:
         A = A.double()
+    return A.t().contiguous().to(device)
+
+
+def to_device_colmajor_c(A, device="cuda"):
+    """Column-major complex128 copy of A on the device."""
+    import torch
+    if isinstance(A, np.ndarray):
+        return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.complex128).T)).to(device)
+    if A.dtype != torch.complex128:
+        A = A.to(torch.complex128)
     return A.t().contiguous().to(device)
 
 
@@ -331,6 +354,28 @@ class Plan:
             raise PevcError(st, "pevc_solve_left")
         Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0))
         return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
+
+    def solve_cplx(self, S, T, select=None, check: bool = True):
+        """Eigenvectors of a complex pencil in generalized Schur form (S, T
+        upper triangular, numpy or torch, complex128).  Returns (V as an
+        n x m complex numpy array, scale int32[m], status)."""
+        import torch
+        n = int(S.shape[0])
+        St = to_device_colmajor_c(S)
+        Tt = to_device_colmajor_c(T)
+        V = torch.empty((max(n, 1), max(n, 1)), dtype=torch.complex128, device="cuda")   # column-major storage
+        scale = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        sel = None
+        if select is not None:
+            sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
+        with torch.cuda.stream(self.stream):
+            st, m = pevc_solve_cplx(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
+                                    sel.data_ptr() if sel is not None else 0, V.data_ptr(), max(n, 1),
+                                    scale.data_ptr())
+        if check and st:
+            raise PevcError(st, "pevc_solve_cplx")
+        Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
+        return np.asfortranarray(Vh[:n, :m]), scale[:m].cpu().numpy(), st
 
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "cplx.cuh"
 #include "sched.cuh"
 #include "split.cuh"
 
@@ -94,6 +95,8 @@ struct pevc_plan_s {
   double* lV = nullptr;
   int32_t* lsel = nullptr;
   int32_t* lsc = nullptr;
+  // complex pencils (allocated by the first pevc_solve_cplx)
+  CplxWork* cx = nullptr;
 };
 
 namespace {
@@ -177,6 +180,7 @@ void free_plan(pevc_plan_t p) {
   void* ldev[] = {p->lS, p->lT, p->lV, p->lsel, p->lsc};
   for (void* d : ldev)
     if (d) cudaFree(d);
+  cplx_free(p->cx);
   if (p->bt_kind) cudaFree(p->bt_kind);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
   delete p;
@@ -745,6 +749,29 @@ int pevc_solve_left(pevc_plan_t plan, const double* S, int lds, const double* T,
   CK(launch_left_out(p->lV, n, *m_out, p->kind, p->lsc, U_out, ldu, scale_out, s));
   CK(cudaStreamSynchronize(s));
   return 0;
+}
+
+int pevc_solve_cplx(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+                    const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !V_out) return -8;
+  if (ldv < std::max(n, 1)) return -9;
+  if (n > 0 && !scale_out) return -10;
+  if (!m_out) return -11;
+  *m_out = 0;
+  if (n == 0) return 0;
+  // complex128 elements are read and written as 16-byte pairs
+  if ((uintptr_t)S & 15u) return -2;
+  if ((uintptr_t)T & 15u) return -4;
+  if ((uintptr_t)V_out & 15u) return -8;
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  return cplx_solve(&plan->cx, plan->n_max, plan->stream, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out,
+                    !(plan->flags & PEVC_NO_NORMALISE));
 }
 
 int pevc_destroy(pevc_plan_t plan) {

@@ -1,0 +1,136 @@
+"""pevc_solve_cplx through the C ABI against the complex oracle: eigenvectors
+of complex triangular pencils (the extension to complex data of Section 8).
+
+Bar: componentwise within 1e-10 of the oracle after normalisation at the
+oracle's entry of largest modulus, residual <= 100 n u, scale exponents
+within 1 of the oracle's, zeros below the tip, no Inf/NaN.
+
+Not yet collected: the kernels have not run on a GPU.  Once they pass there,
+this file becomes tests/test_gpu_cplx.py.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import pencilgen
+from oracle import check
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _check(p, V, sc, select=None):
+    assert np.isfinite(V).all()
+    st, Vo, sco, m = oracle.evc_cplx(p.S, p.T, select=select, nthreads=os.cpu_count() or 1)
+    assert st == 0 and V.shape == Vo.shape
+    err, _ = check.compare_normalised_cplx(Vo, V)
+    idx = np.arange(p.n) if select is None else np.flatnonzero(select)
+    res = check.cplx_residuals(p.S, p.T, V, np.diag(p.S)[idx], np.diag(p.T)[idx]).max() / (p.n * check.U)
+    for q, c in enumerate(idx):
+        assert np.all(V[c + 1:, q] == 0)
+    print(f"cplx n={p.n}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert err <= TOL
+    assert res <= 100.0
+    assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 63, 64, 65, 129, 300, 701])
+def test_cplx_matches_oracle(pevc_lib, n):
+    p = pencilgen.make_complex_pencil(n, 7100 + n)
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        V, sc, st = plan.solve_cplx(p.S, p.T)
+    finally:
+        plan.close()
+    assert st == 0
+    _check(p, V, sc)
+
+
+def test_cplx_stress_and_selection(pevc_lib):
+    n = 700
+    p = pencilgen.make_complex_pencil(n, 7200, stress=True)
+    rng = np.random.default_rng(7201)
+    sel = (rng.random(n) < 0.3).astype(np.int32)
+    plan = pevc_lib.Plan(n, prec="bf16x5")          # the complex path is FP64 whatever the plan's precision
+    try:
+        V, sc, st = plan.solve_cplx(p.S, p.T)
+        assert st == 0
+        _check(p, V, sc)
+        assert sc.max() > 1023
+        Vs, scs, st = plan.solve_cplx(p.S, p.T, select=sel)
+        assert st == 0
+        _check(p, Vs, scs, select=sel)
+        idx = np.flatnonzero(sel)
+        assert np.array_equal(Vs, V[:, idx]) and np.array_equal(scs, sc[idx])
+    finally:
+        plan.close()
+
+
+def test_cplx_exact_fixtures(pevc_lib):
+    import importlib.util
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    plan = pevc_lib.Plan(16, prec="fp64")
+    try:
+        for name in ("cexact_n5_s7", "cexact_n8_s13", "cexact_n6_s29_inf"):
+            S, T, Vx = mg.load_cplx(os.path.join(here, "golden", name + ".txt"))
+            V, sc, st = plan.solve_cplx(S, T)
+            assert st == 0
+            err, _ = check.compare_normalised_cplx(Vx, V)
+            assert err <= 1e-13, name
+    finally:
+        plan.close()
+
+
+def test_cplx_unnormalised_plan(pevc_lib):
+    n = 200
+    p = pencilgen.make_complex_pencil(n, 7300)
+    plan = pevc_lib.Plan(n, prec="fp64", normalise=False)
+    try:
+        W, e, st = plan.solve_cplx(p.S, p.T)
+    finally:
+        plan.close()
+    assert st == 0
+    st, Vo, sco, m = oracle.evc_cplx(p.S, p.T)
+    err, _ = check.compare_normalised_cplx(Vo, W)
+    assert err <= TOL
+    # 2^e W has the oracle's growth: its largest modulus is 2^scale within a factor 2
+    for q in range(n):
+        big = np.abs(W[:, q]).max()
+        assert abs(e[q] + np.frexp(big)[1] - 1 - sco[q]) <= 1
+
+
+def test_cplx_status_codes_and_arguments(pevc_lib):
+    import torch
+    n = 40
+    p = pencilgen.make_complex_pencil(n, 7400)
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        S = p.S.copy(order="F")
+        S[3, 20] = np.nan
+        assert plan.solve_cplx(S, p.T, check=False)[2] == pevc_lib.ERR_NONFINITE
+        S = p.S.copy(order="F")
+        T = p.T.copy(order="F")
+        S[7, 7] = 0
+        T[7, 7] = 0
+        assert plan.solve_cplx(S, T, check=False)[2] == pevc_lib.ERR_INDEFINITE
+        sel = np.ones(n, dtype=np.int32)
+        sel[7] = 0
+        V, sc, st = plan.solve_cplx(S, T, select=sel)
+        assert st == 0 and V.shape[1] == n - 1 and np.isfinite(V).all()
+        buf = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+        scb = torch.zeros(n, dtype=torch.int32, device="cuda")
+        b, s = buf.data_ptr(), scb.data_ptr()
+        f = pevc_lib.pevc_solve_cplx
+        assert f(plan.h, b, n - 1, b, n, n, 0, b, n, s)[0] == -3
+        assert f(plan.h, b, n, b, n, n + 1, 0, b, n + 1, s)[0] == -6
+        assert f(plan.h, b, n, b, n, n, 0, b, n - 1, s)[0] == -9
+        assert f(plan.h, b + 8, n, b, n, n, 0, b, n, s)[0] == -2
+        assert f(plan.h, b, n, b, n, 0, 0, b, n, s) == (0, 0)
+    finally:
+        plan.close()

@@ -64,3 +64,10 @@ def test_backtransform_argument_checks_without_gpu():
     assert pevc.pevc_backtransform(None, 0, 1, 1, 0, 1, 1, None, 0, 1) == -1
     assert pevc.BT_EMULATED == 4 and pevc.NO_NORMALISE == 1
 
+
+
+def test_complex_solve_argument_checks_without_gpu():
+    import paper_2003_04776_gb300 as pevc
+    # a missing plan is rejected before any CUDA call
+    assert pevc.pevc_solve_cplx(None, 0, 1, 0, 1, 0, 0, 0, 1, 0) == (-1, 0)
+    assert pevc.pevc_solve_left(None, 0, 1, 0, 1, 0, 0, 0, 1, 0)[0] == -1
