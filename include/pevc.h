@@ -271,7 +271,7 @@ int pevc_solve_left(pevc_plan_t plan, const double *S, int lds, const double *T,
 /*
  * pevc_solve_cplx -- eigenvectors of a complex pencil in generalized
  * (complex) Schur form, the extension to complex data types that the paper
- * names in Section 8.  S and T are upper triangular with complex entries;
+ * names in Section 7.  S and T are upper triangular with complex entries;
  * diagonal entry c gives the eigenvalue (alpha_c, beta_c) = (S_cc, T_cc) and
  * the eigenvector x with x_c = 1 before normalisation, x_i = 0 for i > c and
  * (beta_c S - alpha_c T) x = 0.  The robust blocked substitution of

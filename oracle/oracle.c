@@ -715,7 +715,7 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
-/* Complex pencils (Section 8, the extension to complex data types).          */
+/* Complex pencils (Section 7, the extension to complex data types).          */
 /* ------------------------------------------------------------------------ */
 
 /* A complex pencil (S, T) in generalized complex Schur form: both upper

@@ -1,5 +1,5 @@
 // cplx.cu -- eigenvectors of a complex pencil in generalized Schur form, the
-// extension to complex data types of Section 8.  S and T are upper triangular
+// extension to complex data types of Section 7.  S and T are upper triangular
 // with complex entries; every diagonal entry c gives the eigenvalue (alpha_c,
 // beta_c) = (S_cc, T_cc) and the eigenvector x with x_c = 1, x_i = 0 below c and
 // (beta S - alpha T) x = 0.  There are no 2x2 blocks, so the robust blocked

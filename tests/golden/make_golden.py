@@ -50,7 +50,7 @@ def make(name, n, seed, infinite):
         f.write("\n".join(lines) + "\n")
 
 
-# Complex triangular pencils (the extension to complex data, Section 8):
+# Complex triangular pencils (the extension to complex data, Section 7):
 # (name, order, seed, last eigenvalue infinite)
 CPLX_CASES = [
     ("cexact_n5_s7", 5, 7, False),
@@ -66,7 +66,7 @@ def make_cplx(name, n, seed, infinite):
     lines = [f"# {name}: complex triangular pencil of order {n}, generator seed {seed};",
              "# exact eigenvectors (kernel of beta*S - alpha*T, (alpha, beta) = (S_cc, T_cc),",
              "# over Q(i), normalised at the first entry of largest modulus; paper Section 2,",
-             "# tall equation and Lemma, for complex data as in Section 8)",
+             "# tall equation and Lemma, for complex data as in Section 7)",
              f"n {n}"]
     for nm, M in (("S", ep.S), ("T", ep.T)):
         for i in range(n):

@@ -1,5 +1,5 @@
 """pevc_solve_cplx through the C ABI against the complex oracle: eigenvectors
-of complex triangular pencils (the extension to complex data of Section 8).
+of complex triangular pencils (the extension to complex data of Section 7).
 
 Bar: componentwise within 1e-10 of the oracle after normalisation at the
 oracle's entry of largest modulus, residual <= 100 n u, scale exponents

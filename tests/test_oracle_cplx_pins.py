@@ -1,5 +1,5 @@
 """Pins of the complex-pencil oracle (the extension to complex data types that
-the paper names in Section 8) against facts fixed outside the oracle:
+the paper names in Section 7) against facts fixed outside the oracle:
 
 * exact kernels of beta*S - alpha*T over the Gaussian rationals (stored
   fixtures and fresh tiny pencils, including an infinite eigenvalue);
