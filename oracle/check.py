@@ -177,3 +177,23 @@ def compare_normalised_cplx(Vref, Vgot):
             continue
         errs[c] = np.abs(zg / d - zr / zr[istar]).max()
     return (errs.max() if errs.size else 0.0), errs
+
+
+def cplx_left_residuals(S, T, U, alpha, beta):
+    """Relative residual of every left eigenvector u of a complex triangular
+    pencil, u^H (beta S - alpha T) = 0:
+        ||u^H (beta S - alpha T)||_inf / ((|beta| ||S||_1 + |alpha| ||T||_1) ||u||_inf)."""
+    S = np.asarray(S)
+    T = np.asarray(T)
+    U = np.asarray(U)
+    nS = np.abs(S).sum(axis=0).max()
+    nT = np.abs(T).sum(axis=0).max()
+    US = np.conj(U).T @ S
+    UT = np.conj(U).T @ T
+    res = np.zeros(U.shape[1])
+    for c in range(U.shape[1]):
+        r = beta[c] * US[c] - alpha[c] * UT[c]
+        den = (abs(beta[c]) * nS + abs(alpha[c]) * nT) * np.abs(U[:, c]).max()
+        res[c] = np.abs(r).max() / den if den > 0 else np.inf
+    return res
+

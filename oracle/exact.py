@@ -176,3 +176,26 @@ def exact_complex_eigenvectors(ep):
         V[:, c] = np.array([(x / d).to_complex() for x in v])
     return V, dims
 
+
+def exact_complex_left_eigenvectors(ep):
+    """Normalised exact left eigenvectors of a complex triangular pencil: the
+    kernel of (beta S - alpha T)^H = conj(beta) S^H - conj(alpha) T^H for each
+    diagonal entry, by the general null-space computation."""
+    n = len(ep.S)
+    Sg = [[GQ(*ep.S[i][j]) for j in range(n)] for i in range(n)]
+    Tg = [[GQ(*ep.T[i][j]) for j in range(n)] for i in range(n)]
+    conj = lambda z: GQ(z.re, -z.im)   # noqa: E731
+    U = np.zeros((n, n), dtype=complex)
+    dims = []
+    for c in range(n):
+        ca, cb = conj(Sg[c][c]), conj(Tg[c][c])
+        MH = [[cb * conj(Sg[j][i]) - ca * conj(Tg[j][i]) for j in range(n)] for i in range(n)]
+        basis = nullspace(MH)
+        dims.append(len(basis))
+        v = basis[0]
+        best = max(x.abs2() for x in v)
+        istar = next(i for i, x in enumerate(v) if x.abs2() == best)
+        d = v[istar]
+        U[:, c] = np.array([(x / d).to_complex() for x in v])
+    return U, dims
+

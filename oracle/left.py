@@ -41,3 +41,25 @@ def evc_left(S, T, select=None, normalise: bool = True, nthreads: int = 1):
         U[:, oc] = (-1.0 if kd == 2 else 1.0) * Vp[::-1, q]
         sc[oc] = scp[q]
     return 0, U, sc, m
+
+
+def evc_left_cplx(S, T, select=None, normalise: bool = True, nthreads: int = 1):
+    """Left eigenvectors of a complex triangular pencil: for every selected
+    diagonal entry c, u with u^H (beta_c S - alpha_c T) = 0, (alpha_c, beta_c) =
+    (S_cc, T_cc).  u^H M = 0 is M^H u = 0, and J M^H J = conj(beta) S' -
+    conj(alpha) T' with (S', T') = (J S^H J, J T^H J), again upper triangular,
+    whose diagonal entry n-1-c is (conj(alpha_c), conj(beta_c)).  So J u is the
+    right eigenvector of (S', T') at entry n-1-c (oracle.evc_cplx); u is zero
+    above c.  Returns (status, U n x m complex, scale int32[m], m) with the
+    columns in the order of S's diagonal."""
+    from . import evc_cplx
+    S = np.asarray(S, dtype=np.complex128)
+    T = np.asarray(T, dtype=np.complex128)
+    n = S.shape[0]
+    Sp = np.asfortranarray(np.conj(S.T)[::-1, ::-1])
+    Tp = np.asfortranarray(np.conj(T.T)[::-1, ::-1])
+    selp = None if select is None else np.ascontiguousarray(np.asarray(select, dtype=np.int32)[::-1])
+    st, Vp, scp, m = evc_cplx(Sp, Tp, select=selp, normalise=normalise, nthreads=nthreads)
+    if st:
+        return st, np.zeros((n, 0), dtype=np.complex128), np.zeros(0, dtype=np.int32), 0
+    return 0, np.asfortranarray(Vp[::-1, ::-1]), scp[::-1].copy(), m

@@ -231,3 +231,59 @@ def test_cplx_status_codes():
     st, V, sc, m = oracle.evc_cplx(S, T, select=sel)
     assert st == 0 and m == 19
     assert oracle.evc_cplx(np.zeros((0, 0), complex), np.zeros((0, 0), complex))[0] == 0
+
+
+# ---------------------------------------------------------------------------
+# Left eigenvectors of complex pencils: pinned by the left residual from the
+# definition (no flip), exact null vectors of (beta S - alpha T)^H over the
+# Gaussian rationals, the support above the tip, and a planted conjugation.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_cplx_left_oracle_matches_fresh_exact(n):
+    from oracle.left import evc_left_cplx
+    worst = 0.0
+    for seed in range(8):
+        ep = pencilgen.exact_complex_pencil(n, 500 + seed, infinite=(seed % 4 == 3))
+        S, T = ep.as_complex()
+        Ux, dims = exact.exact_complex_left_eigenvectors(ep)
+        assert all(d == 1 for d in dims)
+        st, U, sc, m = evc_left_cplx(S, T)
+        assert st == 0 and m == n
+        err, _ = check.compare_normalised_cplx(Ux, U)
+        worst = max(worst, err)
+    assert worst <= 1e-13
+
+
+def test_cplx_left_oracle_residual_support_selection():
+    from oracle.left import evc_left_cplx
+    for n, stress in ((150, False), (300, True)):
+        p = pencilgen.make_complex_pencil(n, 510 + n, stress=stress)
+        st, U, sc, m = evc_left_cplx(p.S, p.T, nthreads=4)
+        assert st == 0 and m == n and np.isfinite(U).all()
+        a, b = _diag(p.S, p.T)
+        res = check.cplx_left_residuals(p.S, p.T, U, a, b)
+        assert res.max() <= BAR * n
+        for c in range(n):
+            assert np.all(U[:c, c] == 0)
+            # the tip itself survives normalisation unless the growth exceeds the binary64 range
+            assert U[c, c] != 0 or (stress and sc[c] > 1074)
+    sel = (np.arange(n) % 4 == 2).astype(np.int32)
+    st, Us, scs, ms = evc_left_cplx(p.S, p.T, select=sel, nthreads=4)
+    idx = np.flatnonzero(sel)
+    assert st == 0 and ms == idx.size
+    assert np.array_equal(Us, U[:, idx]) and np.array_equal(scs, sc[idx])
+
+
+def test_cplx_left_planted_conjugation_fails_the_residual():
+    from oracle.left import evc_left_cplx
+    p = pencilgen.make_complex_pencil(90, 520)
+    st, U, sc, m = evc_left_cplx(p.S, p.T)
+    a, b = _diag(p.S, p.T)
+    assert check.cplx_left_residuals(p.S, p.T, U, a, b).max() <= BAR * p.n
+    # the mistake: the flipped pencil transposed without conjugation
+    Sp = np.asfortranarray(p.S.T[::-1, ::-1])
+    Tp = np.asfortranarray(p.T.T[::-1, ::-1])
+    st, Vp, _, _ = oracle.evc_cplx(Sp, Tp)
+    Ubad = Vp[::-1, ::-1]
+    assert check.cplx_left_residuals(p.S, p.T, Ubad, a, b)[:-10].min() > 1e-6
