@@ -304,6 +304,26 @@ int pevc_solve_left(pevc_plan_t plan, const double *S, int lds, const double *T,
 int pevc_solve_cplx(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
                     const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
 
+/*
+ * pevc_solve_cplx_left -- left eigenvectors of a complex triangular pencil:
+ * for every selected diagonal entry c, u != 0 with u^H (beta_c S - alpha_c T)
+ * = 0 (left eigenvectors and complex data are both future work in Section 7).
+ * With J the reversal permutation, J (beta S - alpha T)^H J = conj(beta) S' -
+ * conj(alpha) T' for (S', T') = (J S^H J, J T^H J), again upper triangular, so
+ * J u is pevc_solve_cplx's eigenvector of (S', T') at entry n-1-c: the call
+ * forms (S', T') in plan workspace, solves, and reverses rows and columns.
+ *   arguments  as in pevc_solve_cplx; U_out holds one column per selected
+ *              entry in the order of S's diagonal, zero above the entry,
+ *              normalised so the entry of largest modulus is exactly 1 + 0i
+ *              (the last such entry on ties) unless the plan was made with
+ *              PEVC_NO_NORMALISE
+ * Workspace: the first call allocates two n_max x n_max complex128 arrays and
+ * an int32[n_max] array on the plan, besides pevc_solve_cplx's workspace.
+ * Returns as pevc_solve_cplx.
+ */
+int pevc_solve_cplx_left(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
+                         const int32_t *select, double *U_out, int ldu, int32_t *scale_out, int *m_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,10 +75,13 @@ _lib.pevc_solve_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, c
 _lib.pevc_solve_left.restype = _i
 _lib.pevc_solve_cplx.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
 _lib.pevc_solve_cplx.restype = _i
+_lib.pevc_solve_cplx_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
+_lib.pevc_solve_cplx_left.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
-           "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx")
+           "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
+           "pevc_solve_cplx_left")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -183,6 +186,16 @@ def pevc_solve_cplx(plan, S: int, lds: int, T: int, ldt: int, n: int, select: in
     m = _i(0)
     st = _lib.pevc_solve_cplx(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(V), ldv,
                               _vp(scale), ctypes.byref(m))
+    return st, m.value
+
+
+def pevc_solve_cplx_left(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, U: int, ldu: int,
+                         scale: int):
+    """Left eigenvectors of a complex triangular pencil (raw device pointers
+    as in pevc_solve_cplx).  Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve_cplx_left(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(U),
+                                   ldu, _vp(scale), ctypes.byref(m))
     return st, m.value
 
 
@@ -376,6 +389,27 @@ class Plan:
             raise PevcError(st, "pevc_solve_cplx")
         Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
         return np.asfortranarray(Vh[:n, :m]), scale[:m].cpu().numpy(), st
+
+    def solve_cplx_left(self, S, T, select=None, check: bool = True):
+        """Left eigenvectors u^H (beta S - alpha T) = 0 of a complex triangular
+        pencil.  Returns (U as an n x m complex numpy array, scale, status)."""
+        import torch
+        n = int(S.shape[0])
+        St = to_device_colmajor_c(S)
+        Tt = to_device_colmajor_c(T)
+        U = torch.empty((max(n, 1), max(n, 1)), dtype=torch.complex128, device="cuda")   # column-major storage
+        scale = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        sel = None
+        if select is not None:
+            sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
+        with torch.cuda.stream(self.stream):
+            st, m = pevc_solve_cplx_left(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
+                                         sel.data_ptr() if sel is not None else 0, U.data_ptr(), max(n, 1),
+                                         scale.data_ptr())
+        if check and st:
+            raise PevcError(st, "pevc_solve_cplx_left")
+        Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
+        return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
 
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.

@@ -774,6 +774,28 @@ int pevc_solve_cplx(pevc_plan_t plan, const double* S, int lds, const double* T,
                     !(plan->flags & PEVC_NO_NORMALISE));
 }
 
+int pevc_solve_cplx_left(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+                         const int32_t* select, double* U_out, int ldu, int32_t* scale_out, int* m_out) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !U_out) return -8;
+  if (ldu < std::max(n, 1)) return -9;
+  if (n > 0 && !scale_out) return -10;
+  if (!m_out) return -11;
+  *m_out = 0;
+  if (n == 0) return 0;
+  if ((uintptr_t)S & 15u) return -2;
+  if ((uintptr_t)T & 15u) return -4;
+  if ((uintptr_t)U_out & 15u) return -8;
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  return cplx_solve_left(&plan->cx, plan->n_max, plan->stream, S, lds, T, ldt, n, select, U_out, ldu, scale_out,
+                         m_out, !(plan->flags & PEVC_NO_NORMALISE));
+}
+
 int pevc_destroy(pevc_plan_t plan) {
   if (!plan) return 0;
   cudaStreamSynchronize(plan->stream);

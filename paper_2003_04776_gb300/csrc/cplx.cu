@@ -570,6 +570,66 @@ __global__ void __launch_bounds__(256) k_cx_post(int n, const int* __restrict__ 
   for (int r = c + 1 + tid; r < n; r += 256) st2(v + 2 * r, make_double2(0.0, 0.0));
 }
 
+// ---------------------------------------------------------------------------
+// Left eigenvectors: u^H (beta S - alpha T) = 0 is (beta S - alpha T)^H u = 0,
+// and with J the reversal permutation J (beta S - alpha T)^H J = conj(beta) S'
+// - conj(alpha) T' for the upper triangular (S', T') = (J S^H J, J T^H J), whose
+// diagonal entry n-1-c is (conj(alpha_c), conj(beta_c)).  So J u is the right
+// eigenvector of (S', T') at entry n-1-c.
+// ---------------------------------------------------------------------------
+
+// B(i, j) = conj(A(n-1-j, n-1-i)), B column-major with leading dimension n:
+// 32 x 32 tiles through shared memory, coalesced on both sides.
+__global__ void __launch_bounds__(256) k_cx_flip_ct(const double* __restrict__ A, int lda, int n,
+                                                    double* __restrict__ B) {
+  __shared__ double2 tile[32][33];
+  const int bi = blockIdx.x, bj = blockIdx.y, tx = threadIdx.x, ty = threadIdx.y;
+  const int rbase = n - 32 * bj - 32;    // rows of A feeding B's columns 32 bj .. 32 bj + 31
+  const int cbase = n - 32 * bi - 32;    // columns of A feeding B's rows 32 bi .. 32 bi + 31
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = rbase + tx, c = cbase + ty + 8 * k;
+    if (r >= 0 && c >= 0) tile[ty + 8 * k][tx] = ld2(A + 2 * ((size_t)c * lda + r));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 32 * bi + tx, j = 32 * bj + ty + 8 * k;
+    if (i < n && j < n) {
+      const double2 z = tile[31 - tx][31 - ty - 8 * k];
+      st2(B + 2 * ((size_t)j * n + i), make_double2(z.x, -z.y));
+    }
+  }
+}
+
+__global__ void k_cx_flip_sel(const int32_t* __restrict__ sel, int n, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sel[n - 1 - i];
+}
+
+// Reverses the n x m array V (leading dimension ldv) in place as one
+// sequence in column-major order: element (r, q) trades places with
+// (n-1-r, m-1-q), which reverses the rows and the column order at once.
+// scale[0 .. m) is reversed as well.
+__global__ void __launch_bounds__(256) k_cx_reverse(double* __restrict__ V, int ldv, int n, int m,
+                                                    int32_t* __restrict__ scale) {
+  const long long half = ((long long)n * m) >> 1;
+  const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < half) {
+    const int q = (int)(L / n), r = (int)(L % n);
+    double* a = V + 2 * ((size_t)q * ldv + r);
+    double* b = V + 2 * ((size_t)(m - 1 - q) * ldv + (n - 1 - r));
+    const double2 za = ld2(a), zb = ld2(b);
+    st2(a, zb);
+    st2(b, za);
+  }
+  if (L < (m >> 1)) {
+    const int t = scale[L];
+    scale[L] = scale[m - 1 - L];
+    scale[m - 1 - L] = t;
+  }
+}
+
 int cx_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? PEVC_ERR_NOMEM : PEVC_ERR_CUDA; }
 
 #define CXK(call)                                  \
@@ -603,11 +663,17 @@ struct CplxWork {
   int32_t* h_sel = nullptr;
   int* h_ccol = nullptr;
   unsigned* h_status = nullptr;
+  // left eigenvectors: the flipped conjugate-transposed pencil and selection
+  // (allocated by the first left solve)
+  double* lS = nullptr;
+  double* lT = nullptr;
+  int32_t* lsel = nullptr;
 };
 
 void cplx_free(CplxWork* w) {
   if (!w) return;
-  void* dev[] = {w->alpha, w->beta, w->ccol, w->ex, w->nrm, w->tnS, w->tnT, w->gmax, w->status};
+  void* dev[] = {w->alpha, w->beta, w->ccol, w->ex, w->nrm, w->tnS, w->tnT, w->gmax, w->status,
+                 w->lS, w->lT, w->lsel};
   for (void* d : dev)
     if (d) cudaFree(d);
   void* host[] = {w->h_sel, w->h_ccol, w->h_status};
@@ -707,6 +773,44 @@ int cplx_solve(CplxWork** wp, int n_max, cudaStream_t s, const double* S, int ld
   }
   k_cx_post<<<m, 256, 0, s>>>(n, w->ccol, V, ldv, w->ex, w->nrm, lde, scale, normalise ? 1 : 0);
   CXK(cudaGetLastError());
+  CXK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int cplx_solve_left(CplxWork** wp, int n_max, cudaStream_t s, const double* S, int lds, const double* T, int ldt,
+                    int n, const int32_t* select, double* U, int ldu, int32_t* scale, int* m_out, bool normalise) {
+  *m_out = 0;
+  if (n == 0) return 0;
+  if (!*wp) {
+    const int rc = cplx_alloc(wp, n_max);
+    if (rc) return rc;
+  }
+  CplxWork* w = *wp;
+  if (!w->lS) {
+    const size_t nn = (size_t)std::max(n_max, 1) * std::max(n_max, 1);
+    int rc = cx_alloc(&w->lS, 2 * nn);
+    rc = rc ? rc : cx_alloc(&w->lT, 2 * nn);
+    rc = rc ? rc : cx_alloc(&w->lsel, (size_t)std::max(n_max, 1));
+    if (rc) return rc;
+  }
+  const dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_cx_flip_ct<<<grid, block, 0, s>>>(S, lds, n, w->lS);
+  CXK(cudaGetLastError());
+  k_cx_flip_ct<<<grid, block, 0, s>>>(T, ldt, n, w->lT);
+  CXK(cudaGetLastError());
+  if (select) {
+    k_cx_flip_sel<<<(n + 255) / 256, 256, 0, s>>>(select, n, w->lsel);
+    CXK(cudaGetLastError());
+  }
+  const int rc = cplx_solve(wp, n_max, s, w->lS, n, w->lT, n, n, select ? w->lsel : nullptr, U, ldu, scale, m_out,
+                            normalise);
+  if (rc) return rc;
+  const int m = *m_out;
+  const long long half = (long long)n * m / 2;   // >= m / 2, the scale pairs
+  if (half > 0) {
+    k_cx_reverse<<<(unsigned)((half + 255) / 256), 256, 0, s>>>(U, ldu, n, m, scale);
+    CXK(cudaGetLastError());
+  }
   CXK(cudaStreamSynchronize(s));
   return 0;
 }

@@ -134,3 +134,45 @@ def test_cplx_status_codes_and_arguments(pevc_lib):
         assert f(plan.h, b, n, b, n, 0, 0, b, n, s) == (0, 0)
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 65, 300])
+def test_cplx_left_matches_oracle(pevc_lib, n):
+    from oracle.left import evc_left_cplx
+    p = pencilgen.make_complex_pencil(n, 7500 + n)
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        U, sc, st = plan.solve_cplx_left(p.S, p.T)
+        V, _, st2 = plan.solve_cplx(p.S, p.T)        # the plan stays usable for right solves
+    finally:
+        plan.close()
+    assert st == 0 and st2 == 0
+    assert np.isfinite(U).all()
+    ost, Uo, sco, m = evc_left_cplx(p.S, p.T, nthreads=os.cpu_count() or 1)
+    assert ost == 0 and U.shape == Uo.shape
+    err, _ = check.compare_normalised_cplx(Uo, U)
+    res = check.cplx_left_residuals(p.S, p.T, U, np.diag(p.S), np.diag(p.T)).max() / (n * check.U)
+    for c in range(n):
+        assert np.all(U[:c, c] == 0)
+    print(f"cplx left n={n}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert err <= TOL and res <= 100.0
+    assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+def test_cplx_left_selection_and_stress(pevc_lib):
+    from oracle.left import evc_left_cplx
+    n = 400
+    p = pencilgen.make_complex_pencil(n, 7600, stress=True)
+    sel = (np.arange(n) % 5 == 3).astype(np.int32)
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        U, sc, st = plan.solve_cplx_left(p.S, p.T, select=sel)
+    finally:
+        plan.close()
+    assert st == 0 and np.isfinite(U).all()
+    ost, Uo, sco, m = evc_left_cplx(p.S, p.T, select=sel, nthreads=os.cpu_count() or 1)
+    assert U.shape == Uo.shape
+    err, _ = check.compare_normalised_cplx(Uo, U)
+    idx = np.flatnonzero(sel)
+    res = check.cplx_left_residuals(p.S, p.T, U, np.diag(p.S)[idx], np.diag(p.T)[idx]).max() / (n * check.U)
+    assert err <= TOL and res <= 100.0
