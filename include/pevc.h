@@ -324,6 +324,21 @@ int pevc_solve_cplx(pevc_plan_t plan, const double *S, int lds, const double *T,
 int pevc_solve_cplx_left(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
                          const int32_t *select, double *U_out, int ldu, int32_t *scale_out, int *m_out);
 
+/*
+ * pevc_watchdog_selftest -- exercises the bounded device waits.  Every wait
+ * inside the library's kernels is bounded in SM clock cycles; when a bound
+ * runs out the kernel records a timeout in the plan's status word and
+ * returns, the call reports PEVC_ERR_TIMEOUT and the CUDA context stays
+ * usable.  This call runs one such wait (an mbarrier wait, as in the
+ * tensor-core update) on the plan's stream.
+ *   withhold  0: the awaited arrival happens first, the wait completes
+ *             1: the arrival is withheld, the wait gives up after `cycles`
+ *   cycles    the bound, 0 < cycles <= 4e9 (about 2 s of SM clock)
+ * Synchronises on return.  Returns 0 (wait completed), PEVC_ERR_TIMEOUT (the
+ * bound ran out), -i for an invalid argument or PEVC_ERR_CUDA.
+ */
+int pevc_watchdog_selftest(pevc_plan_t plan, int withhold, long long cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,11 +77,13 @@ _lib.pevc_solve_cplx.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, c
 _lib.pevc_solve_cplx.restype = _i
 _lib.pevc_solve_cplx_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
 _lib.pevc_solve_cplx_left.restype = _i
+_lib.pevc_watchdog_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
+_lib.pevc_watchdog_selftest.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
            "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
-           "pevc_solve_cplx_left")
+           "pevc_solve_cplx_left", "pevc_watchdog_selftest")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -197,6 +199,12 @@ def pevc_solve_cplx_left(plan, S: int, lds: int, T: int, ldt: int, n: int, selec
     st = _lib.pevc_solve_cplx_left(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(U),
                                    ldu, _vp(scale), ctypes.byref(m))
     return st, m.value
+
+
+def pevc_watchdog_selftest(plan, withhold: int, cycles: int) -> int:
+    """One bounded device wait, its arrival withheld or not.  Returns the
+    status (0, or ERR_TIMEOUT when the bound ran out)."""
+    return _lib.pevc_watchdog_selftest(plan, int(withhold), int(cycles))
 
 
 # ------------------------------------------------------------ torch wrapper

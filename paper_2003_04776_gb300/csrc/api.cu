@@ -20,6 +20,11 @@
 
 #include "common.cuh"
 #include "cplx.cuh"
+
+namespace pevc {
+// Bounded-wait self-test (watchdog.cu).
+cudaError_t launch_watchdog_probe(unsigned* status, int withhold, long long cycles, cudaStream_t s);
+}  // namespace pevc
 #include "sched.cuh"
 #include "split.cuh"
 
@@ -794,6 +799,19 @@ int pevc_solve_cplx_left(pevc_plan_t plan, const double* S, int lds, const doubl
   if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
   return cplx_solve_left(&plan->cx, plan->n_max, plan->stream, S, lds, T, ldt, n, select, U_out, ldu, scale_out,
                          m_out, !(plan->flags & PEVC_NO_NORMALISE));
+}
+
+int pevc_watchdog_selftest(pevc_plan_t plan, int withhold, long long cycles) {
+  if (!plan) return -1;
+  if (withhold != 0 && withhold != 1) return -2;
+  if (cycles <= 0 || cycles > 4000000000LL) return -3;   // at most about 2 s of SM clock
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  CK(cudaMemsetAsync(plan->status, 0, sizeof(unsigned), plan->stream));
+  CK(launch_watchdog_probe(plan->status, withhold, cycles, plan->stream));
+  unsigned bits = 0;
+  const int rc = read_status(plan, &bits);
+  if (rc) return rc;
+  return (bits & kStTimeout) ? PEVC_ERR_TIMEOUT : 0;
 }
 
 int pevc_destroy(pevc_plan_t plan) {

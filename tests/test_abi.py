@@ -71,3 +71,9 @@ def test_complex_solve_argument_checks_without_gpu():
     # a missing plan is rejected before any CUDA call
     assert pevc.pevc_solve_cplx(None, 0, 1, 0, 1, 0, 0, 0, 1, 0) == (-1, 0)
     assert pevc.pevc_solve_left(None, 0, 1, 0, 1, 0, 0, 0, 1, 0)[0] == -1
+
+
+def test_watchdog_selftest_argument_checks_without_gpu():
+    import paper_2003_04776_gb300 as pevc
+    assert pevc.pevc_watchdog_selftest(None, 1, 1000) == -1
+    assert pevc.ERR_TIMEOUT == 4
