@@ -174,6 +174,40 @@ def test_protect_division_properties():
             assert Fraction(b) > Fraction(t) * OMEGA * Fraction(2) ** (k - 3)
 
 
+def test_protect_properties_million_samples():
+    """The same two properties on 10^6 draws each across the whole binary64
+    range (subnormals included), checked in floating point after the exact
+    power-of-two scaling: one rounding in the check, hence the 4u slack."""
+    rng = np.random.default_rng(10)
+    N = 1_000_000
+    y, t, x = (_random_magnitudes(rng, N) for _ in range(3))
+    zero = rng.random((3, N)) < 0.02                  # some exact zeros
+    y[zero[0]] = 0.0
+    t[zero[1]] = 0.0
+    x[zero[2]] = 0.0
+    L = oracle.lib()
+    ku = np.fromiter((L.orc_protect_upd(a, b, c) for a, b, c in zip(y.tolist(), t.tolist(), x.tolist())),
+                     dtype=np.int64, count=N)
+    assert ku.min() >= 0
+    # 2^-k (y + t x) <= Omega, with t x formed after scaling t (no overflow)
+    lhs = np.ldexp(y, -ku) + np.ldexp(t, -ku) * x
+    assert np.all(lhs <= 2.0 ** 1022 * (1 + 4 * 2.0 ** -53))
+    # not over-scaled: with k > 0, 2^-(k-4) (y + t x) > Omega
+    pos = ku > 0
+    with np.errstate(over="ignore"):                  # an overflowing product is above Omega all the same
+        big = np.maximum(np.ldexp(y[pos], 4 - ku[pos]), np.ldexp(t[pos], 4 - ku[pos]) * x[pos])
+        assert np.all(2 * big > 2.0 ** 1022)
+    b = np.minimum(_random_magnitudes(rng, N), 2.0 ** 1022)   # precondition |b| <= Omega
+    b[rng.random(N) < 0.02] = 0.0
+    d = _random_magnitudes(rng, N)
+    kd = np.fromiter((L.orc_protect_div(p_, q_) for p_, q_ in zip(b.tolist(), d.tolist())), dtype=np.int64, count=N)
+    assert kd.min() >= 0
+    # 2^-k b <= t Omega, compared as 2^-k b / 2^1022 <= t (both sides exact or one rounding)
+    assert np.all(np.ldexp(b, -kd - 1022) <= d * (1 + 4 * 2.0 ** -53))
+    pos = kd > 0
+    assert np.all(np.ldexp(b[pos], 3 - kd[pos] - 1022) > d[pos] * (1 - 4 * 2.0 ** -53))
+
+
 def test_complex_division_accuracy_and_range():
     rng = np.random.default_rng(9)
     for _ in range(3000):
