@@ -6,9 +6,12 @@ package never imports the library: the two are independent restatements of
 Kjelgaard Mikkelsen & Myllykoski (PPAM 2019).
 
 ``oracle.c`` holds the arithmetic (see its header for the method and the
-readings of the paper); this module compiles it and wraps it with ctypes.
-``check.py`` holds the residual and comparison helpers and ``exact.py`` the
-exact-rational brute force used to pin the oracle on tiny pencils.
+readings of the paper), for real Schur pencils and for complex triangular
+pencils; this module compiles it and wraps it with ctypes.  ``left.py`` gives
+left eigenvectors through the flipped pencil, ``backtransform.py`` the
+eigenvectors of the original pencil, ``check.py`` the residual and
+comparison helpers and ``exact.py`` the exact-rational brute force used to
+pin the oracle on tiny pencils.
 """
 from __future__ import annotations
 

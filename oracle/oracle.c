@@ -42,6 +42,9 @@
  *     index on ties), so that entry is exactly 1; scale[c] = e + ilogb(|max|),
  *     the binary exponent of the growth relative to a unit tip.
  *
+ * Complex pencils (orc_evc_cplx, at the end of this file): the same
+ * substitution for complex triangular (S, T) with 1x1 steps only.
+ *
  * All arithmetic is IEEE binary64 with round-to-nearest; the build uses
  * -ffp-contract=off so no fused multiply-add changes the rounding.
  */
