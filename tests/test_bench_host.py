@@ -1,6 +1,7 @@
 """Host-side logic of bench.py (no GPU): the roofline of the dominant kernel,
-the diagonal solves' algorithmic flops, and the traffic records' source
-hashes (a record reports only for the kernel sources it was measured on)."""
+the diagonal solves' algorithmic flops, the traffic records' source hashes (a
+record reports only for the kernel sources it was measured on), and the
+reference arm's JSON line and oracle sampling."""
 import os
 import sys
 
@@ -46,3 +47,49 @@ def test_traffic_records_apply_only_to_their_workload():
         assert bench.measured_traffic(k, n=4000) is None
         assert bench.measured_traffic(k, prec="fp64") is None
     assert bench.measured_traffic("k_post") is None
+
+
+def _ref_args(n=256, steps=2, warmup=1):
+    import argparse
+    return argparse.Namespace(n=n, steps=steps, warmup=warmup, gpus=1)
+
+
+def test_reference_line_keeps_the_contract(monkeypatch, capsys):
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    calls = []
+
+    def fake_sample(pencil, budget, threads):
+        calls.append((pencil.n, budget, threads))
+        return 12.5, {"columns": 3, "seconds": 0.1, "work_flops": 1e9}
+
+    monkeypatch.setattr(bench, "cpu_oracle_sample", fake_sample)
+    assert bench.run_reference(_ref_args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert len(calls) == 3 and all(c[0] == 256 for c in calls)          # warm-up + timed steps
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] == 12.5 and line["unit"] == "GFLOP/s" and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert abs(line["ms_per_step"] - bench.flops_all(256) / 12.5e9 * 1e3) < 0.1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == 12.5 and cb["cores"] >= 1 and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == 12.5 and e2e["unit"] == "GFLOP/s"
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"].startswith("schur-pencil n=256")
+
+
+def test_reference_other_ranks_exit_without_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda *a: (_ for _ in ()).throw(AssertionError("ran")))
+    assert bench.run_reference(_ref_args()) == 0
+    assert capsys.readouterr().out == ""
+
+
+def test_cpu_oracle_sample_times_a_stratified_subset():
+    import pencilgen
+    p = pencilgen.make_pencil(200, 31)
+    rate, info = bench.cpu_oracle_sample(p, 0.05, 2)
+    assert rate > 0 and 1 <= info["columns"] <= 200
+    # the work is the sum of 2 (c+1)^2 over the sampled columns (both columns of a pair)
+    assert 0 < info["work_flops"] <= bench.flops_all(200) * 1.01
