@@ -93,3 +93,16 @@ def test_cpu_oracle_sample_times_a_stratified_subset():
     assert rate > 0 and 1 <= info["columns"] <= 200
     # the work is the sum of 2 (c+1)^2 over the sampled columns (both columns of a pair)
     assert 0 < info["work_flops"] <= bench.flops_all(200) * 1.01
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    cs = bench.ClockSampler()
+    assert cs.summary()["reasons"] == ["unsampled"]
+    for sm, act in ((1965, "Not Active"), (1980, "Active"), (1995, "Not Active"), ("[N/A]", "Not Active")):
+        line = f"{sm}, 2070, Not Active, Not Active, Not Active, {act}"
+        cs.samples.append([p.strip() for p in line.split(",")])
+    s = cs.summary()
+    assert s["sm_mhz"] == 1980.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["sw_power_cap"]          # "Not Active" is not a reason
+    cs.samples.append(["2070", "2070", "Active", "Not Active", "Active", "Not Active"])
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
