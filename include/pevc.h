@@ -325,6 +325,27 @@ int pevc_solve_cplx_left(pevc_plan_t plan, const double *S, int lds, const doubl
                          const int32_t *select, double *U_out, int ldu, int32_t *scale_out, int *m_out);
 
 /*
+ * pevc_backtransform_cplx -- eigenvectors of the original complex pencil:
+ * with (A, B) = (Q S Z^H, Q T Z^H) the complex QZ reduction of (A, B), an
+ * eigenvector v of the triangular (S, T) gives x = Z v for (A, B) (Section 1,
+ * for complex data).  X = Z V is one complex FP64 GEMM (cuBLAS ZGEMM on the
+ * plan's stream); then, unless PEVC_NO_NORMALISE, every column is scaled so
+ * that its entry of largest modulus (the first on ties) is exactly 1 + 0i.
+ *   Z, ldz     device, n x n complex128, column-major, 16-byte aligned
+ *   n          order, <= the plan's n_max
+ *   V, ldv     device, n x m complex128 (pevc_solve_cplx's output)
+ *   m          0 <= m <= n
+ *   X, ldx     device, n x m complex128, caller-allocated, not overlapping Z
+ *              or V
+ *   flags      0 or PEVC_NO_NORMALISE
+ * The first call creates the plan's cuBLAS handle.  Synchronises on return.
+ * Returns 0, -i (argument i invalid, counting the plan as argument 1) or
+ * PEVC_ERR_CUDA.
+ */
+int pevc_backtransform_cplx(pevc_plan_t plan, const double *Z, int ldz, int n, const double *V, int ldv, int m,
+                            double *X, int ldx, unsigned flags);
+
+/*
  * pevc_watchdog_selftest -- exercises the bounded device waits.  Every wait
  * inside the library's kernels is bounded in SM clock cycles; when a bound
  * runs out the kernel records a timeout in the plan's status word and

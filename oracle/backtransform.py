@@ -48,3 +48,28 @@ def random_orthogonal(n: int, seed: int):
     rng = np.random.Generator(np.random.PCG64(seed))
     q, r = np.linalg.qr(rng.standard_normal((n, n)))
     return q * np.sign(np.diag(r))
+
+
+def backtransform_cplx(Z, V, normalise: bool = True):
+    """X = Z V for complex eigenvectors (the eigenvectors of (Q S Z^H, Q T Z^H)),
+    each column divided by its first entry of largest modulus, which is then
+    exactly 1; an all-zero column stays zero."""
+    X = np.asfortranarray(np.asarray(Z, dtype=np.complex128) @ np.asarray(V, dtype=np.complex128))
+    if not normalise:
+        return X
+    for c in range(X.shape[1]):
+        i = int(np.argmax(np.abs(X[:, c])))
+        d = X[i, c]
+        if d != 0:
+            X[:, c] = X[:, c] / d
+            X[i, c] = 1.0
+    return X
+
+
+def random_unitary(n: int, seed: int):
+    """A seeded random unitary matrix (the Q factor of a complex Gaussian matrix)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q, r = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    d = np.diag(r)
+    return q * (d / np.abs(d))
+

@@ -77,13 +77,15 @@ _lib.pevc_solve_cplx.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, c
 _lib.pevc_solve_cplx.restype = _i
 _lib.pevc_solve_cplx_left.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
 _lib.pevc_solve_cplx_left.restype = _i
+_lib.pevc_backtransform_cplx.argtypes = [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _i, _u]
+_lib.pevc_backtransform_cplx.restype = _i
 _lib.pevc_watchdog_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
 _lib.pevc_watchdog_selftest.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
            "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
-           "pevc_solve_cplx_left", "pevc_watchdog_selftest")
+           "pevc_solve_cplx_left", "pevc_backtransform_cplx", "pevc_watchdog_selftest")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -199,6 +201,13 @@ def pevc_solve_cplx_left(plan, S: int, lds: int, T: int, ldt: int, n: int, selec
     st = _lib.pevc_solve_cplx_left(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None, _vp(U),
                                    ldu, _vp(scale), ctypes.byref(m))
     return st, m.value
+
+
+def pevc_backtransform_cplx(plan, Z: int, ldz: int, n: int, V: int, ldv: int, m: int, X: int, ldx: int,
+                            flags: int = 0) -> int:
+    """X = Z V for complex eigenvectors with every column normalised (raw
+    device pointers to complex128 arrays).  Returns the status."""
+    return _lib.pevc_backtransform_cplx(plan, _vp(Z), ldz, n, _vp(V), ldv, m, _vp(X), ldx, int(flags))
 
 
 def pevc_watchdog_selftest(plan, withhold: int, cycles: int) -> int:
@@ -418,6 +427,22 @@ class Plan:
             raise PevcError(st, "pevc_solve_cplx_left")
         Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
         return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
+
+    def backtransform_cplx(self, Z, V, normalise: bool = True, check: bool = True):
+        """X = Z V for complex eigenvectors V (numpy or torch, complex128):
+        the eigenvectors of (Q S Z^H, Q T Z^H).  Returns (X, status)."""
+        import torch
+        n, m = int(Z.shape[0]), int(V.shape[1])
+        Zt = to_device_colmajor_c(Z)
+        Vt = to_device_colmajor_c(V)
+        X = torch.empty((max(m, 1), max(n, 1)), dtype=torch.complex128, device="cuda")   # column-major storage
+        with torch.cuda.stream(self.stream):
+            st = pevc_backtransform_cplx(self.h, Zt.data_ptr(), max(n, 1), n, Vt.data_ptr(), max(n, 1), m,
+                                         X.data_ptr(), max(n, 1), 0 if normalise else NO_NORMALISE)
+        if check and st:
+            raise PevcError(st, "pevc_backtransform_cplx")
+        Xh = X[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
+        return np.asfortranarray(Xh[:n, :m]), st
 
     def solve(self, S, T, select=None, check: bool = True):
         """Eigenvectors of (S, T) given as numpy arrays or torch tensors.

@@ -719,6 +719,32 @@ int pevc_backtransform(pevc_plan_t plan, const double* Z, int ldz, int n, const 
   return 0;
 }
 
+int pevc_backtransform_cplx(pevc_plan_t plan, const double* Z, int ldz, int n, const double* V, int ldv, int m,
+                            double* X, int ldx, unsigned flags) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -4;
+  const int ld_min = n > 1 ? n : 1;
+  if (!Z && n > 0) return -2;
+  if (ldz < ld_min) return -3;
+  if (!V && m > 0) return -5;
+  if (ldv < ld_min) return -6;
+  if (m < 0 || m > n) return -7;
+  if (!X && m > 0) return -8;
+  if (ldx < ld_min) return -9;
+  if (flags & ~PEVC_NO_NORMALISE) return -10;
+  if ((uintptr_t)Z & 15u) return -2;
+  if ((uintptr_t)V & 15u) return -5;
+  if ((uintptr_t)X & 15u) return -8;
+  if (n == 0 || m == 0) return 0;
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  int rc = bt_handle(&plan->blas, plan->stream);
+  if (rc) return rc;
+  if ((rc = bt_zgemm(plan->blas, n, m, Z, ldz, V, ldv, X, ldx))) return rc;
+  if (!(flags & PEVC_NO_NORMALISE)) CK(launch_bt_normalise_c(X, ldx, n, m, plan->stream));
+  CK(cudaStreamSynchronize(plan->stream));
+  return 0;
+}
+
 int pevc_solve_left(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
                     const int32_t* select, double* U_out, int ldu, int32_t* scale_out, int* m_out) {
   if (!plan) return -1;

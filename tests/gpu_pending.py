@@ -195,3 +195,26 @@ def test_watchdog_wait_runs_out_and_context_survives(pevc_lib):
         assert st == 0 and np.isfinite(V).all()
     finally:
         plan.close()
+
+
+def test_cplx_backtransform_matches_oracle(pevc_lib):
+    from oracle.backtransform import backtransform_cplx, random_unitary
+    n = 300
+    p = pencilgen.make_complex_pencil(n, 7800)
+    Q, Z = random_unitary(n, 7801), random_unitary(n, 7802)
+    A, B = Q @ p.S @ Z.conj().T, Q @ p.T @ Z.conj().T
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        V, sc, st = plan.solve_cplx(p.S, p.T)
+        X, st2 = plan.backtransform_cplx(Z, V)
+        Xr, st3 = plan.backtransform_cplx(Z, V, normalise=False)
+    finally:
+        plan.close()
+    assert st == 0 and st2 == 0 and st3 == 0
+    st, Vo, sco, m = oracle.evc_cplx(p.S, p.T, nthreads=os.cpu_count() or 1)
+    Xo = backtransform_cplx(Z, Vo)
+    err, _ = check.compare_normalised_cplx(Xo, X)
+    res = check.cplx_residuals(A, B, X, np.diag(p.S), np.diag(p.T)).max() / (n * check.U)
+    assert err <= TOL and res <= 100.0
+    ref = Z @ V
+    assert np.abs(Xr - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())

@@ -287,3 +287,30 @@ def test_cplx_left_planted_conjugation_fails_the_residual():
     st, Vp, _, _ = oracle.evc_cplx(Sp, Tp)
     Ubad = Vp[::-1, ::-1]
     assert check.cplx_left_residuals(p.S, p.T, Ubad, a, b)[:-10].min() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Back-transformation of complex eigenvectors: x = Z v is an eigenvector of
+# (A, B) = (Q S Z^H, Q T Z^H).  Pinned by the residual of the original pencil,
+# which does not go through oracle.backtransform.
+# ---------------------------------------------------------------------------
+
+def test_cplx_backtransform_gives_eigenvectors_of_original_pencil():
+    from oracle.backtransform import backtransform_cplx, random_unitary
+    n = 160
+    p = pencilgen.make_complex_pencil(n, 530)
+    Q, Z = random_unitary(n, 531), random_unitary(n, 532)
+    assert np.abs(Z.conj().T @ Z - np.eye(n)).max() < 1e-13
+    A, B = Q @ p.S @ Z.conj().T, Q @ p.T @ Z.conj().T
+    st, V, sc, m = oracle.evc_cplx(p.S, p.T)
+    X = backtransform_cplx(Z, V)
+    a, b = _diag(p.S, p.T)
+    assert check.cplx_residuals(A, B, X, a, b).max() <= BAR * n
+    for c in range(n):
+        i = int(np.argmax(np.abs(X[:, c])))
+        assert X[i, c] == 1.0
+    # the planted mistake: conj(Z) instead of Z (a conjugation dropped or doubled)
+    Xbad = backtransform_cplx(Z.conj(), V)
+    assert check.cplx_residuals(A, B, Xbad, a, b)[5:].min() > 1e-6
+    # Z = I returns the vectors themselves
+    assert np.abs(backtransform_cplx(np.eye(n), V) - V).max() == 0.0

@@ -14,9 +14,9 @@ def test_pending_gpu_tests_import_and_use_existing_api():
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)                      # imports only; no GPU work at import time
     tests = [n for n, f in inspect.getmembers(mod, inspect.isfunction) if n.startswith("test_")]
-    assert len(tests) >= 8
+    assert len(tests) >= 9
     src = inspect.getsource(mod)
-    for name in ("solve_cplx", "solve_cplx_left"):
+    for name in ("solve_cplx", "solve_cplx_left", "backtransform_cplx"):
         assert hasattr(pevc.Plan, name) and f".{name}(" in src
     for name in ("pevc_solve_cplx", "pevc_watchdog_selftest", "ERR_NONFINITE", "ERR_INDEFINITE", "ERR_TIMEOUT"):
         assert hasattr(pevc, name)
