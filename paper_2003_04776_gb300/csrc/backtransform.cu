@@ -46,7 +46,7 @@ int bt_gemm(void* h, bool emulated, int n, int m, const double* Z, int ldz, cons
 }
 
 struct BtBest {
-  unsigned long long v;   // magnitude key (|x| or the squared modulus)
+  unsigned long long v;   // magnitude key: the bits of |x|, or of the modulus hypot(re, im)
   int i;
 };
 
@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(256) k_bt_normalise(double* X, int ldx, int n,
   BtBest best{0ull, 0x7fffffff};
   for (int r = tid; r < n; r += blockDim.x) {
     const double vr = x0[r];
-    const unsigned long long key = pair ? abs_key(fma(vr, vr, x1[r] * x1[r])) : abs_key(vr);
+    // the modulus itself, not its square: a square overflows above 2^511 and
+    // would make every large entry tie (unnormalised columns reach 2^1022)
+    const unsigned long long key = pair ? abs_key(hypot(vr, x1[r])) : abs_key(vr);
     best = bt_better(best, BtBest{key, r});
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256) k_bt_normalise_c(double* X, int ldx, int 
   BtBest best{0ull, 0x7fffffff};
   for (int r = tid; r < n; r += blockDim.x) {
     const double vr = x[2 * r], vi = x[2 * r + 1];
-    best = bt_better(best, BtBest{abs_key(fma(vr, vr, vi * vi)), r});
+    best = bt_better(best, BtBest{abs_key(hypot(vr, vi)), r});   // the modulus: its square could overflow
   }
   for (int o = 16; o > 0; o >>= 1) {
     BtBest other{(unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)best.v, o),
