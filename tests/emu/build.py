@@ -1,0 +1,110 @@
+"""Builds the kernel emulation library for the tests -- TEST INFRASTRUCTURE.
+
+The FP64 real-pencil path (host driver, pre-pass, diagonal solves, FP64
+updates, post-pass, left flips) and the complex-pencil path are preprocessed
+from the library's CUDA sources into host C++ (launch syntax into
+emu::launch calls, dynamic shared memory onto the emulated block's buffer,
+the L2 prefetch hint dropped, the FP64 mma.sync onto its model) and compiled
+with g++ against the cuda_runtime.h stand-in beside this file.  The
+split-precision, tcgen05 and cuBLAS pieces are stubbed out (an FP64 plan never
+calls them); the back-transform normalisation kernels are compiled on their
+own.  The result goes to tests/emu/_build/libpevc_emu.so.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import re
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+CSRC = os.path.join(ROOT, "paper_2003_04776_gb300", "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libpevc_emu.so")
+FILES = ["api.cu", "prepass.cu", "diag.cu", "update_f64.cu", "post.cu", "left.cu", "cplx.cu"]
+
+
+def _convert(src: str, name: str) -> str:
+    src = re.sub(r'#include "([\w.]+)"', lambda m: f'#include "{CSRC}/{m.group(1)}"', src)
+    src = re.sub(r"extern __shared__ (\w+) (\w+)\[\];", r"\1* \2 = reinterpret_cast<\1*>(emu::dyn_smem);", src)
+    src = re.sub(r"\b(k_\w+(?:<[^<>()]*>)?)<<<", r"emu::launch(\1, ", src)
+    src = src.replace(">>>(", ", ")
+    src = re.sub(r'\s*asm volatile\("prefetch\.global\.L2[^;]*;', "", src)
+    src = re.sub(r'asm volatile\("mma\.sync.*?"d"\(b\)\);', "emu::dmma_m8n8k4(c0, c1, a, b);", src, flags=re.S)
+    if "asm" in src:
+        raise RuntimeError(f"{name}: inline PTX the emulation does not model")
+    return src
+
+
+STUBS = '''
+#include "{csrc}/common.cuh"
+#include "{csrc}/split.cuh"
+namespace pevc {{
+int split_alloc(SplitWorkspace&, int, int, int, int) {{ return PEVC_ERR_UNSUPPORTED; }}
+void split_free(SplitWorkspace&) {{}}
+SplitConfig split_config(int, bool) {{ return SplitConfig{{}}; }}
+int split_solve(SplitWorkspace&, const Problem&, const HostStructure&, const SplitConfig&, cudaStream_t,
+                const SchedContext&, Profiler&, cudaEvent_t, cudaEvent_t) {{ return PEVC_ERR_UNSUPPORTED; }}
+int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
+void bt_handle_destroy(void*) {{}}
+int bt_gemm(void*, bool, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
+int bt_zgemm(void*, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
+cudaError_t launch_watchdog_probe(unsigned*, int, long long, cudaStream_t) {{ return 0; }}
+}}
+'''
+
+
+def _bt_source() -> str:
+    src = open(os.path.join(CSRC, "backtransform.cu")).read()
+    body = src[src.index("struct BtBest {"):src.index("// X = Z V for complex128 column-major arrays")]
+    return (f'#include "{CSRC}/common.cuh"\nnamespace pevc {{\n{_convert(body, "backtransform.cu")}\n'
+            "cudaError_t launch_bt_normalise(double* X, int ldx, int n, int m, const signed char* kind, cudaStream_t s) {\n"
+            "  if (m > 0 && n > 0) emu::launch(k_bt_normalise, m, 256, 0, s, X, ldx, n, kind);\n  return 0;\n}\n"
+            "cudaError_t launch_bt_normalise_c(double* X, int ldx, int n, int m, cudaStream_t s) {\n"
+            "  if (m > 0 && n > 0) emu::launch(k_bt_normalise_c, m, 256, 0, s, X, ldx, n);\n  return 0;\n}\n}\n"
+            'extern "C" void emu_bt_normalise(double* X, int ldx, int n, int m, const signed char* k) '
+            "{ pevc::launch_bt_normalise(X, ldx, n, m, k, nullptr); }\n"
+            'extern "C" void emu_bt_normalise_c(double* X, int ldx, int n, int m) '
+            "{ pevc::launch_bt_normalise_c(X, ldx, n, m, nullptr); }\n")
+
+
+def build() -> str:
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
+        os.path.join(HERE, f) for f in ("build.py", "cuda_runtime.h", "cuda_bf16.h")]
+    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = []
+    for f in FILES:
+        out = os.path.join(BUILD, f.replace(".cu", ".cpp"))
+        with open(out, "w") as fh:
+            fh.write(_convert(open(os.path.join(CSRC, f)).read(), f))
+        srcs.append(out)
+    for name, text in (("stubs.cpp", STUBS.format(csrc=CSRC)), ("bt.cpp", _bt_source())):
+        out = os.path.join(BUILD, name)
+        with open(out, "w") as fh:
+            fh.write(text)
+        srcs.append(out)
+
+    def cc(src):
+        obj = src[:-4] + ".o"
+        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", "-I", HERE, "-I", os.path.join(ROOT, "include"),
+               "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode:
+            raise RuntimeError(f"g++ failed for {src}:\n{r.stderr[-4000:]}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(cc, srcs))
+    tmp = LIB + f".tmp{os.getpid()}"
+    r = subprocess.run(["g++", "-shared", "-pthread", "-o", tmp, *objs], capture_output=True, text=True)
+    if r.returncode:
+        raise RuntimeError(r.stderr[-4000:])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build())

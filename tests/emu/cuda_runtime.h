@@ -1,0 +1,233 @@
+// cuda_runtime.h stand-in for the kernel emulation tests -- TEST INFRASTRUCTURE.
+//
+// Compiles the library's CUDA C++ kernel sources as host C++ and runs them on
+// a model of the CUDA thread model: one host thread per thread of a block
+// (blocks of a grid run one after another), std::barrier for
+// __syncthreads, per-warp exchange slots for shuffles, votes and reductions,
+// CTA-wide statics for __shared__, host memory for device memory, and
+// synchronous stream operations (launches run in program order, which every
+// stream and event dependency of the library respects).  Math functions are
+// the host's.  The one tensor-core instruction of the FP64 path,
+// mma.sync.m8n8k4 f64, is modelled from its documented fragment layout.
+// Kernels written with other inline PTX (tcgen05, TMA, mbarrier waits) are
+// not covered.  Nothing in the library uses this file.
+#pragma once
+#include <math.h>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <cfloat>
+#include <atomic>
+#include <barrier>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#define __host__
+#define __device__
+#define __global__
+#define __forceinline__ inline
+#define __launch_bounds__(...)
+#define __shared__ static
+
+typedef int cudaError_t;
+enum { cudaSuccess = 0, cudaErrorMemoryAllocation = 2 };
+typedef void* cudaStream_t;
+typedef void* cudaEvent_t;
+enum cudaMemcpyKind { cudaMemcpyHostToDevice, cudaMemcpyDeviceToHost, cudaMemcpyDeviceToDevice };
+enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize };
+struct double2 { double x, y; };
+inline double2 make_double2(double x, double y) { return {x, y}; }
+struct dim3 {
+  unsigned x, y, z;
+  dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {}
+};
+struct uint3 { unsigned x, y, z; };
+struct int4 { int x, y, z, w; };
+inline int4 make_int4(int x, int y, int z, int w) { return {x, y, z, w}; }
+
+inline cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return 0; }
+inline cudaError_t cudaGetLastError() { return 0; }
+inline cudaError_t cudaStreamSynchronize(cudaStream_t) { return 0; }
+inline cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t b, cudaMemcpyKind, cudaStream_t) {
+  memcpy(d, s, b);
+  return 0;
+}
+inline cudaError_t cudaMemsetAsync(void* d, int v, size_t b, cudaStream_t) {
+  memset(d, v, b);
+  return 0;
+}
+inline cudaError_t cudaMalloc(void** p, size_t b) {
+  *p = calloc(b ? b : 1, 1);
+  return *p ? 0 : cudaErrorMemoryAllocation;
+}
+inline cudaError_t cudaMallocHost(void** p, size_t b) { return cudaMalloc(p, b); }
+template <class T>
+inline cudaError_t cudaMalloc(T** p, size_t b) { return cudaMalloc(reinterpret_cast<void**>(p), b); }
+template <class T>
+inline cudaError_t cudaMallocHost(T** p, size_t b) { return cudaMalloc(reinterpret_cast<void**>(p), b); }
+inline cudaError_t cudaFree(void* p) { free(p); return 0; }
+inline cudaError_t cudaFreeHost(void* p) { free(p); return 0; }
+template <class F>
+inline cudaError_t cudaFuncSetAttribute(F, cudaFuncAttribute, int) { return 0; }
+
+namespace emu {
+struct Warp {
+  std::barrier<> bar{32};
+  uint64_t slot[32];
+};
+struct Cta {
+  std::barrier<>* bar;
+};
+inline thread_local uint3 tIdx, bIdx;
+inline thread_local dim3 bDim, gDim;
+inline thread_local Warp* warp = nullptr;
+inline thread_local int lane = 0;
+inline thread_local Cta* cta = nullptr;
+inline thread_local unsigned char* dyn_smem = nullptr;
+
+template <class T>
+inline T shfl(T v, int src) {
+  static_assert(sizeof(T) <= 8);
+  uint64_t b = 0;
+  memcpy(&b, &v, sizeof(T));
+  warp->slot[lane] = b;
+  warp->bar.arrive_and_wait();
+  const uint64_t r = warp->slot[src & 31];
+  warp->bar.arrive_and_wait();
+  T out;
+  memcpy(&out, &r, sizeof(T));
+  return out;
+}
+
+template <class K, class... A>
+void launch(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t, A... args) {
+  // one host thread per CUDA thread of a block, reused for every block of the
+  // grid in turn (blocks run one after another; a barrier separates them)
+  const int nt = (int)(block.x * block.y * block.z);
+  const long long nb = (long long)grid.x * grid.y * grid.z;
+  if (nt <= 0 || nb <= 0) return;
+  std::vector<unsigned char> dyn(smem ? smem : 16);
+  std::barrier<> bar(nt);
+  Cta c{&bar};
+  std::vector<std::unique_ptr<Warp>> ws((nt + 31) / 32);
+  for (auto& w : ws) w.reset(new Warp);
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      tIdx = uint3{(unsigned)(t % block.x), (unsigned)((t / block.x) % block.y), (unsigned)(t / (block.x * block.y))};
+      bDim = block;
+      gDim = grid;
+      warp = ws[t / 32].get();
+      lane = t % 32;
+      cta = &c;
+      dyn_smem = dyn.data();
+      for (long long b = 0; b < nb; ++b) {
+        bIdx = uint3{(unsigned)(b % grid.x), (unsigned)((b / grid.x) % grid.y), (unsigned)(b / ((long long)grid.x * grid.y))};
+        kernel(args...);
+        bar.arrive_and_wait();   // the block's shared memory is reused by the next block
+      }
+    });
+  for (auto& x : th) x.join();
+}
+}  // namespace emu
+
+#define threadIdx emu::tIdx
+#define blockIdx emu::bIdx
+#define blockDim emu::bDim
+#define gridDim emu::gDim
+
+inline void __syncthreads() { emu::cta->bar->arrive_and_wait(); }
+template <class T>
+inline T __shfl_sync(unsigned, T v, int src) { return emu::shfl(v, src & 31); }
+template <class T>
+inline T __shfl_xor_sync(unsigned, T v, int o) { return emu::shfl(v, emu::lane ^ o); }
+inline int __reduce_max_sync(unsigned, int v) {
+  int best = v;
+  for (int l = 0; l < 32; ++l) best = std::max(best, emu::shfl(v, l));
+  return best;
+}
+inline int __any_sync(unsigned, int p) {
+  int r = 0;
+  for (int l = 0; l < 32; ++l) r |= emu::shfl(p ? 1 : 0, l);
+  return r;
+}
+inline int __all_sync(unsigned, int p) {
+  int r = 1;
+  for (int l = 0; l < 32; ++l) r &= emu::shfl(p ? 1 : 0, l);
+  return r;
+}
+
+inline long long __double_as_longlong(double d) { long long r; memcpy(&r, &d, 8); return r; }
+inline double __longlong_as_double(long long l) { double r; memcpy(&r, &l, 8); return r; }
+inline int __double2hiint(double d) { return (int)((unsigned long long)__double_as_longlong(d) >> 32); }
+inline int __double2loint(double d) { return (int)(uint32_t)__double_as_longlong(d); }
+inline double __hiloint2double(int hi, int lo) {
+  return __longlong_as_double((long long)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo));
+}
+inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
+template <class T>
+inline T max(T a, T b) { return a > b ? a : b; }
+template <class T>
+inline T min(T a, T b) { return a < b ? a : b; }
+inline unsigned atomicOr(unsigned* a, unsigned v) { return std::atomic_ref<unsigned>(*a).fetch_or(v); }
+inline int atomicOr(int* a, int v) { return std::atomic_ref<int>(*a).fetch_or(v); }
+inline int atomicAdd(int* a, int v) { return std::atomic_ref<int>(*a).fetch_add(v); }
+inline unsigned atomicAdd(unsigned* a, unsigned v) { return std::atomic_ref<unsigned>(*a).fetch_add(v); }
+inline int atomicMax(int* a, int v) {
+  std::atomic_ref<int> r(*a);
+  int cur = r.load();
+  while (cur < v && !r.compare_exchange_weak(cur, v)) {}
+  return cur;
+}
+inline unsigned long long atomicMax(unsigned long long* a, unsigned long long v) {
+  std::atomic_ref<unsigned long long> r(*a);
+  unsigned long long cur = r.load();
+  while (cur < v && !r.compare_exchange_weak(cur, v)) {}
+  return cur;
+}
+
+// ---- additions for the real-pencil path ----
+#define __align__(n) __attribute__((aligned(n)))
+enum { cudaStreamNonBlocking = 1, cudaEventDisableTiming = 2 };
+enum cudaDeviceAttr { cudaDevAttrMultiProcessorCount };
+inline cudaError_t cudaSetDevice(int) { return 0; }
+inline cudaError_t cudaGetDevice(int* d) { *d = 0; return 0; }
+inline cudaError_t cudaDeviceGetAttribute(int* v, cudaDeviceAttr, int) { *v = 152; return 0; }
+inline cudaError_t cudaStreamCreateWithFlags(cudaStream_t* s, unsigned) { *s = (void*)0x1; return 0; }
+inline cudaError_t cudaStreamDestroy(cudaStream_t) { return 0; }
+inline cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned = 0) { return 0; }
+inline cudaError_t cudaEventCreate(cudaEvent_t* e) { *e = (void*)0x1; return 0; }
+inline cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned) { *e = (void*)0x1; return 0; }
+inline cudaError_t cudaEventDestroy(cudaEvent_t) { return 0; }
+inline cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t, cudaEvent_t) { *ms = 0.f; return 0; }
+template <class T>
+inline cudaError_t cudaGetSymbolAddress(void** p, T& sym) { *p = (void*)&sym; return 0; }
+
+namespace emu {
+inline void allgather(double v, double (&out)[32]) {
+  uint64_t b;
+  memcpy(&b, &v, 8);
+  warp->slot[lane] = b;
+  warp->bar.arrive_and_wait();
+  for (int l = 0; l < 32; ++l) memcpy(&out[l], &warp->slot[l], 8);
+  warp->bar.arrive_and_wait();
+}
+// mma.sync.m8n8k4 row.col f64: A 8x4 from lane row*4 + k, B 4x8 from lane
+// col*4 + k, C/D at row = lane >> 2, cols 2 (lane & 3) + {0, 1}.
+inline void dmma_m8n8k4(double& c0, double& c1, double a, double b) {
+  double A[32], B[32];
+  allgather(a, A);
+  allgather(b, B);
+  const int row = lane >> 2, col0 = (lane & 3) * 2;
+  double acc0 = c0, acc1 = c1;
+  for (int k = 0; k < 4; ++k) {
+    acc0 = fma(A[row * 4 + k], B[col0 * 4 + k], acc0);
+    acc1 = fma(A[row * 4 + k], B[(col0 + 1) * 4 + k], acc1);
+  }
+  c0 = acc0;
+  c1 = acc1;
+}
+}  // namespace emu

@@ -1,0 +1,126 @@
+"""The library's CUDA C++ kernels, run on a CPU model of the CUDA thread model
+(tests/emu/), against the oracle.
+
+The emulation compiles the kernel sources and the host driver as host C++
+(one host thread per CUDA thread, barriers for __syncthreads, per-warp
+exchange slots for shuffles and votes) and calls the library's own C entry
+points with host arrays.  It checks the kernels' logic -- index maps, warp
+exchanges, scale bookkeeping, the stage walk -- between GPU runs, and covers
+code that has not yet run on a GPU.  It is not a parity claim: the GPU tests
+are.  The FP64 real path, the complex path and the back-transform
+normalisation are covered; the tcgen05 / TMA kernels are not (inline PTX).
+Sizes are small, since every warp exchange is a host barrier.
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import pencilgen
+from oracle import check
+from oracle.backtransform import backtransform, backtransform_cplx
+from oracle.left import evc_left_cplx
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _emu_build():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("pevc_emu_build", os.path.join(HERE, "emu", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+vp, ci = ctypes.c_void_p, ctypes.c_int
+
+
+@pytest.fixture(scope="module")
+def emu():
+    L = ctypes.CDLL(_emu_build().build())
+    L.pevc_plan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ctypes.c_uint, vp]
+    for f in ("pevc_solve", "pevc_solve_cplx", "pevc_solve_cplx_left"):
+        getattr(L, f).argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, vp, ctypes.POINTER(ci)]
+    L.pevc_destroy.argtypes = [vp]
+    L.emu_bt_normalise.argtypes = [vp, ci, ci, ci, vp]
+    L.emu_bt_normalise_c.argtypes = [vp, ci, ci, ci]
+    return L
+
+
+def _call(L, fn, S, T, dtype, tile=32, sel=None):
+    n = S.shape[0]
+    h = vp()
+    assert L.pevc_plan(ctypes.byref(h), n, 1, 0, tile, 0, None) == 0
+    S = np.asfortranarray(S, dtype=dtype)
+    T = np.asfortranarray(T, dtype=dtype)
+    V = np.zeros((n, n), dtype=dtype, order="F")
+    sc = np.zeros(n, dtype=np.int32)
+    m = ci(0)
+    s = None if sel is None else np.ascontiguousarray(sel, dtype=np.int32)
+    st = getattr(L, fn)(h, S.ctypes.data, n, T.ctypes.data, n, n, None if s is None else s.ctypes.data,
+                        V.ctypes.data, n, sc.ctypes.data, ctypes.byref(m))
+    L.pevc_destroy(h)
+    return st, V[:, :m.value].copy(), sc[:m.value].copy()
+
+
+def test_emulated_fp64_real_solve_matches_oracle(emu):
+    # three tiles of 32 (a ragged last one), real and complex-pair columns, and a selection
+    p = pencilgen.make_pencil(70, 9100)
+    sel = (np.arange(70) % 3 == 0).astype(np.int32)
+    for s in (None, sel):
+        st, V, sc = _call(emu, "pevc_solve", p.S, p.T, np.float64, tile=32, sel=s)
+        assert st == 0
+        ost, Vo, sco, m = oracle.evc(p.S, p.T, select=s)
+        _, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+        kinds, pos = check.column_kinds(blk, s)
+        err, _ = check.compare_normalised(Vo, V, kinds)
+        res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta).max() / (70 * check.U)
+        assert V.shape == Vo.shape and err <= 1e-12 and res <= 100.0
+        assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+def test_emulated_complex_solve_matches_oracle(emu):
+    # two tiles of 64 (the second ragged), then a stress pencil in one tile
+    for n, seed, stress in ((65, 9200, False), (40, 9201, True)):
+        p = pencilgen.make_complex_pencil(n, seed, stress=stress)
+        st, V, sc = _call(emu, "pevc_solve_cplx", p.S, p.T, np.complex128)
+        assert st == 0 and np.isfinite(V).all()
+        ost, Vo, sco, m = oracle.evc_cplx(p.S, p.T)
+        err, _ = check.compare_normalised_cplx(Vo, V)
+        res = check.cplx_residuals(p.S, p.T, V, np.diag(p.S), np.diag(p.T)).max() / (n * check.U)
+        assert err <= 1e-12 and res <= 100.0
+        assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+def test_emulated_complex_left_solve_matches_oracle(emu):
+    n = 70
+    p = pencilgen.make_complex_pencil(n, 9300)
+    sel = (np.arange(n) % 4 != 1).astype(np.int32)
+    st, U, sc = _call(emu, "pevc_solve_cplx_left", p.S, p.T, np.complex128, sel=sel)
+    assert st == 0
+    ost, Uo, sco, m = evc_left_cplx(p.S, p.T, select=sel)
+    assert U.shape == Uo.shape
+    err, _ = check.compare_normalised_cplx(Uo, U)
+    idx = np.flatnonzero(sel)
+    res = check.cplx_left_residuals(p.S, p.T, U, np.diag(p.S)[idx], np.diag(p.T)[idx]).max() / (n * check.U)
+    assert err <= 1e-12 and res <= 100.0
+
+
+@pytest.mark.parametrize("big", [1.0, 1e200, 2.0 ** 1020])
+def test_emulated_backtransform_normalisation(emu, big):
+    """The entry of largest modulus becomes exactly 1, also for columns whose
+    squared modulus would overflow (unnormalised inputs reach 2^1022)."""
+    rng = np.random.default_rng(9400)
+    n, m = 300, 4
+    X = np.asfortranarray(rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) * big
+    X[:, 2] = 0.0                                          # an all-zero column stays zero
+    Y = X.copy(order="F")
+    emu.emu_bt_normalise_c(Y.ctypes.data, n, n, m)
+    assert np.abs(Y - backtransform_cplx(np.eye(n), X)).max() <= 1e-15
+    R = np.asfortranarray(np.stack([X[:, 0].real, X[:, 0].imag, X[:, 1].real, X[:, 2].real], axis=1))
+    kinds = [1, 2, 0, 0]
+    k = np.asarray(kinds, dtype=np.int8)
+    Rr = R.copy(order="F")
+    emu.emu_bt_normalise(Rr.ctypes.data, n, n, m, k.ctypes.data)
+    assert np.abs(Rr - backtransform(np.eye(n), R, kinds)).max() <= 1e-15
