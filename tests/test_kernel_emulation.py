@@ -33,6 +33,7 @@ def _emu_build():
     spec.loader.exec_module(mod)
     return mod
 
+
 vp, ci = ctypes.c_void_p, ctypes.c_int
 
 
