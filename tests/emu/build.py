@@ -50,7 +50,6 @@ int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
 void bt_handle_destroy(void*) {{}}
 int bt_gemm(void*, bool, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
 int bt_zgemm(void*, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
-cudaError_t launch_watchdog_probe(unsigned*, int, long long, cudaStream_t) {{ return 0; }}
 }}
 '''
 
@@ -69,6 +68,28 @@ def _bt_source() -> str:
             "{ pevc::launch_bt_normalise_c(X, ldx, n, m, nullptr); }\n")
 
 
+def _watchdog_source() -> str:
+    """watchdog.cu with its mbarrier PTX replaced by the model in cuda_runtime.h
+    (the wait helper of tc.cuh restated on the modelled try_wait)."""
+    src = open(os.path.join(CSRC, "watchdog.cu")).read()
+    src = src.replace('#include "tc.cuh"\n', "")
+    src = src.replace('#include "common.cuh"', f'#include "{CSRC}/common.cuh"')
+    src = re.sub(r'asm volatile\("mbarrier\.arrive.*?\(&bar\)\)\);', "emu::mbar_arrive(&bar);", src, flags=re.S)
+    src = re.sub(r"\b(k_\w+)<<<", r"emu::launch(\1, ", src).replace(">>>(", ", ")
+    helpers = ("namespace pevc {\n"
+               "inline void mbar_init(uint64_t* m, uint32_t c) { emu::mbar_init(m, c); }\n"
+               "inline bool mbar_wait_cycles(uint64_t* m, uint32_t parity, long long limit) {\n"
+               "  if (emu::mbar_try_wait(m, parity)) return true;\n"
+               "  const long long t0 = clock64();\n"
+               "  while (!emu::mbar_try_wait(m, parity))\n"
+               "    if (clock64() - t0 > limit) return false;\n"
+               "  return true;\n}\n}\n")
+    src = src.replace("namespace pevc {", helpers + "namespace pevc {", 1)
+    if "asm" in src:
+        raise RuntimeError("watchdog.cu: inline PTX the emulation does not model")
+    return src
+
+
 def build() -> str:
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
         os.path.join(HERE, f) for f in ("build.py", "cuda_runtime.h", "cuda_bf16.h")]
@@ -81,7 +102,8 @@ def build() -> str:
         with open(out, "w") as fh:
             fh.write(_convert(open(os.path.join(CSRC, f)).read(), f))
         srcs.append(out)
-    for name, text in (("stubs.cpp", STUBS.format(csrc=CSRC)), ("bt.cpp", _bt_source())):
+    for name, text in (("stubs.cpp", STUBS.format(csrc=CSRC)), ("bt.cpp", _bt_source()),
+                       ("watchdog.cpp", _watchdog_source())):
         out = os.path.join(BUILD, name)
         with open(out, "w") as fh:
             fh.write(text)

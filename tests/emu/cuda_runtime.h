@@ -8,9 +8,11 @@
 // synchronous stream operations (launches run in program order, which every
 // stream and event dependency of the library respects).  Math functions are
 // the host's.  The one tensor-core instruction of the FP64 path,
-// mma.sync.m8n8k4 f64, is modelled from its documented fragment layout.
-// Kernels written with other inline PTX (tcgen05, TMA, mbarrier waits) are
-// not covered.  Nothing in the library uses this file.
+// mma.sync.m8n8k4 f64, is modelled from its documented fragment layout, and
+// the mbarrier operations of the bounded-wait self-test (init, arrive,
+// try_wait by phase parity) and clock64 from their documented semantics.
+// Kernels written with other inline PTX (tcgen05, TMA) are not covered.
+// Nothing in the library uses this file.
 #pragma once
 #include <math.h>
 #include <cmath>
@@ -231,3 +233,29 @@ inline void dmma_m8n8k4(double& c0, double& c1, double a, double b) {
   c1 = acc1;
 }
 }  // namespace emu
+
+// ---- mbarrier and clock model for the bounded-wait self-test ----
+// An mbarrier word holds {expected count, pending count, phase}; an arrival
+// that completes the phase flips its parity and rearms the count, and
+// try_wait.parity(p) succeeds once the phase with parity p has completed.
+#include <chrono>
+namespace emu {
+inline void mbar_init(uint64_t* m, uint32_t count) { *m = ((uint64_t)count << 32) | ((uint64_t)count << 1); }
+inline void mbar_arrive(uint64_t* m) {
+  std::atomic_ref<uint64_t> r(*m);
+  uint64_t cur = r.load(), nxt;
+  do {
+    const uint64_t cnt = cur >> 32, pend = (cur >> 1) & 0x7fffffffu, ph = cur & 1u;
+    nxt = pend > 1 ? (cnt << 32) | ((pend - 1) << 1) | ph : (cnt << 32) | (cnt << 1) | (ph ^ 1u);
+  } while (!r.compare_exchange_weak(cur, nxt));
+}
+inline bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  return (std::atomic_ref<uint64_t>(*m).load() & 1u) != parity;
+}
+}  // namespace emu
+inline long long clock64() {
+  // about 2 GHz, the order of this GPU's SM clock
+  return (long long)(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                         std::chrono::steady_clock::now().time_since_epoch()).count() * 2);
+}
+

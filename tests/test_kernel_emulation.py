@@ -7,8 +7,9 @@ exchange slots for shuffles and votes) and calls the library's own C entry
 points with host arrays.  It checks the kernels' logic -- index maps, warp
 exchanges, scale bookkeeping, the stage walk -- between GPU runs, and covers
 code that has not yet run on a GPU.  It is not a parity claim: the GPU tests
-are.  The FP64 real path, the complex path and the back-transform
-normalisation are covered; the tcgen05 / TMA kernels are not (inline PTX).
+are.  The FP64 real path, the complex path, the back-transform normalisation
+and the bounded-wait self-test are covered; the tcgen05 / TMA kernels are not
+(inline PTX).
 Sizes are small, since every warp exchange is a host barrier.
 """
 import ctypes
@@ -125,3 +126,22 @@ def test_emulated_backtransform_normalisation(emu, big):
     Rr = R.copy(order="F")
     emu.emu_bt_normalise(Rr.ctypes.data, n, n, m, k.ctypes.data)
     assert np.abs(Rr - backtransform(np.eye(n), R, kinds)).max() <= 1e-15
+
+
+def test_emulated_watchdog_selftest(emu):
+    """The bounded-wait self-test on the modelled mbarrier: the wait completes
+    when the arrival happens and gives up with ERR_TIMEOUT when it is withheld;
+    a solve on the same plan afterwards is unaffected."""
+    emu.pevc_watchdog_selftest.argtypes = [vp, ci, ctypes.c_longlong]
+    h = vp()
+    assert emu.pevc_plan(ctypes.byref(h), 40, 1, 0, 32, 0, None) == 0
+    try:
+        assert emu.pevc_watchdog_selftest(h, 0, 2_000_000) == 0
+        assert emu.pevc_watchdog_selftest(h, 1, 2_000_000) == 4          # PEVC_ERR_TIMEOUT
+        assert emu.pevc_watchdog_selftest(h, 2, 10) == -2
+        assert emu.pevc_watchdog_selftest(h, 1, 0) == -3
+    finally:
+        emu.pevc_destroy(h)
+    p = pencilgen.make_pencil(40, 9500)
+    st, V, sc = _call(emu, "pevc_solve", p.S, p.T, np.float64)
+    assert st == 0 and np.isfinite(V).all()
