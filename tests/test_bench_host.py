@@ -106,3 +106,13 @@ def test_clock_summary_parses_nvidia_smi_lines():
     assert s["reasons"] == ["sw_power_cap"]          # "Not Active" is not a reason
     cs.samples.append(["2070", "2070", "Active", "Not Active", "Active", "Not Active"])
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+
+
+def test_parse_args_defaults_and_complex_workload():
+    a = bench.parse_args([])
+    assert (a.gpus, a.steps, a.warmup, a.impl, a.prec, a.n, a.workload) == (1, 5, 3, "pevc", "bf16x5", 20000, "real")
+    b = bench.parse_args(["--workload", "cplx", "--n", "4000", "--steps", "2"])
+    assert b.workload == "cplx" and b.n == 4000 and b.steps == 2
+    # 8 n^3 / 3 to leading order; exact for the sum over columns of 8 c^2
+    assert bench.flops_cplx(3) == 8.0 * (0 + 1 + 4)
+    assert abs(bench.flops_cplx(20000) / (8 * 20000 ** 3 / 3) - 1) < 1e-4
