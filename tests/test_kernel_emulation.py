@@ -145,3 +145,64 @@ def test_emulated_watchdog_selftest(emu):
     p = pencilgen.make_pencil(40, 9500)
     st, V, sc = _call(emu, "pevc_solve", p.S, p.T, np.float64)
     assert st == 0 and np.isfinite(V).all()
+
+
+def _check_real(p, V, sc, sel=None):
+    ost, Vo, sco, m = oracle.evc(p.S, p.T, select=sel)
+    _, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk, sel)
+    err, _ = check.compare_normalised(Vo, V, kinds)
+    res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta).max() / (p.n * check.U)
+    assert V.shape == Vo.shape and err <= 1e-12 and res <= 100.0
+
+
+def test_emulated_real_left_static_and_batched_entry_points(emu):
+    """The host logic of three more entry points, on the emulated kernels:
+    left eigenvectors (flips and output permutation), the no-allocation solve
+    (its one file-scope workspace), and the batched solve (child workspaces,
+    per-pencil statuses, one pencil with an error among good ones)."""
+    from oracle.left import evc_left
+    p = pencilgen.make_pencil(50, 9600)
+    # left eigenvectors
+    emu.pevc_solve_left.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, vp, ctypes.POINTER(ci)]
+    st, U, sc = _call(emu, "pevc_solve_left", p.S, p.T, np.float64)
+    assert st == 0
+    ost, Uo, sco, m = evc_left(p.S, p.T)
+    _, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    err, _ = check.compare_normalised(Uo, U, kinds)
+    assert U.shape == Uo.shape and err <= 1e-12
+    assert check.left_residuals(p.S, p.T, U, kinds, pos, a, b, beta).max() <= 100 * 50 * check.U
+    # the no-allocation solve
+    emu.pevc_solve_static.argtypes = [vp, ci, vp, ci, ci, vp, vp, ci, vp, ctypes.POINTER(ci), ctypes.c_uint, vp]
+    S, T = np.asfortranarray(p.S), np.asfortranarray(p.T)
+    V = np.zeros((50, 50), order="F")
+    scs = np.zeros(50, dtype=np.int32)
+    m = ci(0)
+    assert emu.pevc_solve_static(S.ctypes.data, 50, T.ctypes.data, 50, 50, None, V.ctypes.data, 50,
+                                 scs.ctypes.data, ctypes.byref(m), 0, None) == 0
+    _check_real(p, V[:, :m.value], scs[:m.value])
+    # the batched solve: three pencils of different orders, the middle one not in Schur form
+    pens = [pencilgen.make_pencil(n, 9610 + n) for n in (20, 33, 47)]
+    Sb = [np.asfortranarray(q.S) for q in pens]
+    Tb = [np.asfortranarray(q.T) for q in pens]
+    # two adjacent 1x1 blocks become the 2x2 block S = [[0, 1], [1, 0]], T = I: real eigenvalues +-1
+    c = next(int(r) for r in range(32) if pens[1].block[r] == 0 and pens[1].block[r + 1] == 0)
+    Sb[1][c:c + 2, c:c + 2] = [[0.0, 1.0], [1.0, 0.0]]
+    Tb[1][c:c + 2, c:c + 2] = np.eye(2)
+    Vb = [np.zeros((q.n, q.n), order="F") for q in pens]
+    scb = [np.zeros(q.n, dtype=np.int32) for q in pens]
+    P, I = vp * 3, ci * 3
+    emu.pevc_solve_batched.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    h = vp()
+    assert emu.pevc_plan(ctypes.byref(h), 47, 3, 0, 32, 0, None) == 0
+    mo, so = I(), I()
+    st = emu.pevc_solve_batched(h, 3, P(*[x.ctypes.data for x in Sb]), I(20, 33, 47),
+                                P(*[x.ctypes.data for x in Tb]), I(20, 33, 47), I(20, 33, 47), None,
+                                P(*[x.ctypes.data for x in Vb]), I(20, 33, 47), P(*[x.ctypes.data for x in scb]),
+                                mo, so)
+    emu.pevc_destroy(h)
+    assert st == 0
+    assert so[0] == 0 and so[2] == 0 and so[1] == 1          # PEVC_ERR_NOT_SCHUR for the middle pencil only
+    for q, Vq, sq, mq in ((pens[0], Vb[0], scb[0], mo[0]), (pens[2], Vb[2], scb[2], mo[2])):
+        _check_real(q, Vq[:, :mq], sq[:mq])
