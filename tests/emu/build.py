@@ -1,14 +1,15 @@
 """Builds the kernel emulation library for the tests -- TEST INFRASTRUCTURE.
 
-The FP64 real-pencil path (host driver, pre-pass, diagonal solves, FP64
-updates, post-pass, left flips) and the complex-pencil path are preprocessed
-from the library's CUDA sources into host C++ (launch syntax into
-emu::launch calls, dynamic shared memory onto the emulated block's buffer,
-the L2 prefetch hint dropped, the FP64 mma.sync onto its model) and compiled
-with g++ against the cuda_runtime.h stand-in beside this file.  The
-split-precision, tcgen05 and cuBLAS pieces are stubbed out (an FP64 plan never
-calls them); the back-transform normalisation kernels are compiled on their
-own.  The result goes to tests/emu/_build/libpevc_emu.so.
+The real-pencil path (host driver, pre-pass, diagonal solves, FP64 updates,
+the split-precision path with its mma.sync update, post-pass, left flips) and
+the complex-pencil path are preprocessed from the library's CUDA sources into
+host C++ (launch syntax into emu::launch calls, dynamic shared memory onto the
+emulated block's buffer, the L2 prefetch hint dropped, the PTX of the FP64 and
+BF16 mma.sync, ldmatrix and cp.async onto their models) and compiled with g++
+against the cuda_runtime.h stand-in beside this file.  The tcgen05 update and
+the cuBLAS pieces are stubbed out (without tensor maps the split path takes
+its mma.sync update); the back-transform normalisation kernels and the
+bounded-wait self-test are compiled on their own.  The result goes to tests/emu/_build/libpevc_emu.so.
 """
 from __future__ import annotations
 
@@ -22,12 +23,46 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_2003_04776_gb300", "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpevc_emu.so")
-FILES = ["api.cu", "prepass.cu", "diag.cu", "update_f64.cu", "post.cu", "left.cu", "cplx.cu"]
+FILES = ["api.cu", "prepass.cu", "diag.cu", "update_f64.cu", "post.cu", "left.cu", "cplx.cu", "split.cu"]
+
+# split.cu's PTX helpers, replaced by their models in cuda_runtime.h
+SPLIT_HELPERS = {
+    "void cp_async16(": "__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) "
+                        "{ emu::cp_async16(smem, gmem, valid); }",
+    "void cp_async_commit(": "__device__ __forceinline__ void cp_async_commit() {}",
+    "void cp_async_wait(": "template <int N>\n__device__ __forceinline__ void cp_async_wait() {}",
+    "void ldmatrix_x4(": "__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* smem) "
+                         "{ emu::ldmatrix_x4(r, smem); }",
+    "void mma_bf16(": "__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, "
+                      "unsigned b1) { emu::mma_bf16(c, a, b0, b1); }",
+}
+
+
+def _replace_function(src: str, marker: str, new_def: str) -> str:
+    """Replaces the definition containing `marker` (from the start of its
+    declaration, a template line included, to its closing brace)."""
+    i = src.index(marker)
+    start = src.rfind("\n", 0, i) + 1
+    prev = src.rfind("\n", 0, start - 1) + 1
+    if src[prev:start].startswith("template"):
+        start = prev
+    j = src.index("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        depth += src[k] == "{"
+        depth -= src[k] == "}"
+        if depth == 0:
+            return src[:start] + new_def + src[k + 1:]
+    raise RuntimeError(marker)
 
 
 def _convert(src: str, name: str) -> str:
+    if name == "split.cu":
+        for marker, new_def in SPLIT_HELPERS.items():
+            src = _replace_function(src, marker, new_def)
     src = re.sub(r'#include "([\w.]+)"', lambda m: f'#include "{CSRC}/{m.group(1)}"', src)
-    src = re.sub(r"extern __shared__ (\w+) (\w+)\[\];", r"\1* \2 = reinterpret_cast<\1*>(emu::dyn_smem);", src)
+    src = re.sub(r"extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];",
+                 r"\1* \2 = reinterpret_cast<\1*>(emu::dyn_smem);", src)
     src = re.sub(r"\b(k_\w+(?:<[^<>()]*>)?)<<<", r"emu::launch(\1, ", src)
     src = src.replace(">>>(", ", ")
     src = re.sub(r'\s*asm volatile\("prefetch\.global\.L2[^;]*;', "", src)
@@ -41,11 +76,12 @@ STUBS = '''
 #include "{csrc}/common.cuh"
 #include "{csrc}/split.cuh"
 namespace pevc {{
-int split_alloc(SplitWorkspace&, int, int, int, int) {{ return PEVC_ERR_UNSUPPORTED; }}
-void split_free(SplitWorkspace&) {{}}
-SplitConfig split_config(int, bool) {{ return SplitConfig{{}}; }}
-int split_solve(SplitWorkspace&, const Problem&, const HostStructure&, const SplitConfig&, cudaStream_t,
-                const SchedContext&, Profiler&, cudaEvent_t, cudaEvent_t) {{ return PEVC_ERR_UNSUPPORTED; }}
+// the tcgen05 update is outside the emulation: no tensor maps, so the split
+// path takes its mma.sync update at every tile order
+int update_tc_setup() {{ return 0; }}
+int make_tensor_maps(SplitWorkspace& w) {{ w.tc_ok = false; return 0; }}
+cudaError_t launch_update_tc(const Problem&, const SplitWorkspace&, int, int, int, const int*, const double*, int, int,
+                             cudaStream_t) {{ return 1; }}
 int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
 void bt_handle_destroy(void*) {{}}
 int bt_gemm(void*, bool, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}

@@ -7,12 +7,11 @@
 // CTA-wide statics for __shared__, host memory for device memory, and
 // synchronous stream operations (launches run in program order, which every
 // stream and event dependency of the library respects).  Math functions are
-// the host's.  The one tensor-core instruction of the FP64 path,
-// mma.sync.m8n8k4 f64, is modelled from its documented fragment layout, and
-// the mbarrier operations of the bounded-wait self-test (init, arrive,
-// try_wait by phase parity) and clock64 from their documented semantics.
-// Kernels written with other inline PTX (tcgen05, TMA) are not covered.
-// Nothing in the library uses this file.
+// the host's.  The PTX the library uses outside its tcgen05 kernel is
+// modelled from its documented semantics: mma.sync m8n8k4 f64 and m16n8k16
+// bf16 (fragment layouts), ldmatrix.x4, cp.async (completed at once), and the
+// mbarrier operations and clock64 of the bounded-wait self-test.  The tcgen05
+// / TMA update is not covered.  Nothing in the library uses this file.
 #pragma once
 #include <math.h>
 #include <cmath>
@@ -34,7 +33,7 @@
 #define __shared__ static
 
 typedef int cudaError_t;
-enum { cudaSuccess = 0, cudaErrorMemoryAllocation = 2 };
+enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorMemoryAllocation = 2 };
 typedef void* cudaStream_t;
 typedef void* cudaEvent_t;
 enum cudaMemcpyKind { cudaMemcpyHostToDevice, cudaMemcpyDeviceToHost, cudaMemcpyDeviceToDevice };
@@ -258,4 +257,66 @@ inline long long clock64() {
   return (long long)(std::chrono::duration_cast<std::chrono::nanoseconds>(
                          std::chrono::steady_clock::now().time_since_epoch()).count() * 2);
 }
+
+// ---- the split path's PTX: cp.async, ldmatrix.x4 and mma.sync m16n8k16 bf16 ----
+struct uint4 { unsigned x, y, z, w; };
+inline size_t __cvta_generic_to_shared(const void* p) { return (size_t)p; }
+inline int __float2int_rn(float f) { return (int)lrintf(f); }
+namespace emu {
+// cp.async of 16 bytes with zero fill, completed at once (the waits become no-ops)
+inline void cp_async16(void* smem, const void* gmem, bool valid) {
+  if (valid) memcpy(smem, gmem, 16);
+  else memset(smem, 0, 16);
+}
+// ldmatrix.sync.aligned.m8n8.x4.b16: lanes 8i .. 8i+7 give the row addresses
+// of matrix i; lane L receives, from each matrix i, the 32-bit pair of
+// elements 2 (L % 4), 2 (L % 4) + 1 of row L / 4.
+inline void ldmatrix_x4(unsigned (&r)[4], const void* row_addr) {
+  const uint64_t mine = (uint64_t)(size_t)row_addr;
+  uint64_t addr[32];
+  warp->slot[lane] = mine;
+  warp->bar.arrive_and_wait();
+  for (int l = 0; l < 32; ++l) addr[l] = warp->slot[l];
+  warp->bar.arrive_and_wait();
+  for (int i = 0; i < 4; ++i)
+    memcpy(&r[i], reinterpret_cast<const unsigned char*>((size_t)addr[8 * i + lane / 4]) + 4 * (lane % 4), 4);
+}
+inline float bf16_lo(unsigned w) { const unsigned b = w << 16; float f; memcpy(&f, &b, 4); return f; }
+inline float bf16_hi(unsigned w) { const unsigned b = w & 0xffff0000u; float f; memcpy(&f, &b, 4); return f; }
+// mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 (g = lane / 4, t = lane % 4):
+//   A regs (row, k pair): {g, 2t}, {g+8, 2t}, {g, 2t+8}, {g+8, 2t+8};
+//   B regs (k pair, col): {2t, g}, {2t+8, g};  C: rows g, g+8, cols 2t, 2t+1.
+// The split path's products are exact integers below 2^24, so the order of
+// the FP32 additions does not matter.
+inline void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  unsigned A[32][4], B[32][2];
+  for (int q = 0; q < 4; ++q) {
+    warp->slot[lane] = a[q];
+    warp->bar.arrive_and_wait();
+    for (int l = 0; l < 32; ++l) A[l][q] = (unsigned)warp->slot[l];
+    warp->bar.arrive_and_wait();
+  }
+  for (int q = 0; q < 2; ++q) {
+    warp->slot[lane] = q ? b1 : b0;
+    warp->bar.arrive_and_wait();
+    for (int l = 0; l < 32; ++l) B[l][q] = (unsigned)warp->slot[l];
+    warp->bar.arrive_and_wait();
+  }
+  auto a_el = [&](int row, int k) {
+    const int l = (row % 8) * 4 + (k % 8) / 2, q = row / 8 + 2 * (k / 8);
+    return (k & 1) ? bf16_hi(A[l][q]) : bf16_lo(A[l][q]);
+  };
+  auto b_el = [&](int k, int col) {
+    const int l = col * 4 + (k % 8) / 2, q = k / 8;
+    return (k & 1) ? bf16_hi(B[l][q]) : bf16_lo(B[l][q]);
+  };
+  const int g = lane >> 2, t = lane & 3;
+  for (int e = 0; e < 4; ++e) {
+    const int row = g + 8 * (e >> 1), col = 2 * t + (e & 1);
+    float acc = c[e];
+    for (int k = 0; k < 16; ++k) acc += a_el(row, k) * b_el(k, col);
+    c[e] = acc;
+  }
+}
+}  // namespace emu
 

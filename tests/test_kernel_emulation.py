@@ -7,9 +7,9 @@ exchange slots for shuffles and votes) and calls the library's own C entry
 points with host arrays.  It checks the kernels' logic -- index maps, warp
 exchanges, scale bookkeeping, the stage walk -- between GPU runs, and covers
 code that has not yet run on a GPU.  It is not a parity claim: the GPU tests
-are.  The FP64 real path, the complex path, the back-transform normalisation
-and the bounded-wait self-test are covered; the tcgen05 / TMA kernels are not
-(inline PTX).
+are.  The FP64 real path, the split-precision path with its mma.sync update,
+the complex path, the back-transform normalisation and the bounded-wait
+self-test are covered; the tcgen05 / TMA update is not.
 Sizes are small, since every warp exchange is a host barrier.
 """
 import ctypes
@@ -206,3 +206,27 @@ def test_emulated_real_left_static_and_batched_entry_points(emu):
     assert so[0] == 0 and so[2] == 0 and so[1] == 1          # PEVC_ERR_NOT_SCHUR for the middle pencil only
     for q, Vq, sq, mq in ((pens[0], Vb[0], scb[0], mo[0]), (pens[2], Vb[2], scb[2], mo[2])):
         _check_real(q, Vq[:, :mq], sq[:mq])
+
+
+@pytest.mark.parametrize("prec,n", [(3, 70), (1, 36)])    # PEVC_SPLIT_BF16X5, PEVC_SPLIT_BF16X3 (+ correction)
+def test_emulated_split_solve_matches_oracle(emu, prec, n):
+    """The split-precision path with its mma.sync update (BF16 slices, FP32
+    level accumulators, FP64 recombination), the slicing kernels it shares with
+    the tcgen05 update, and the correction sweep of BF16x3."""
+    p = pencilgen.make_pencil(n, 9800 + n)
+    h = vp()
+    assert emu.pevc_plan(ctypes.byref(h), n, 1, prec, 32, 0, None) == 0
+    S, T = np.asfortranarray(p.S), np.asfortranarray(p.T)
+    V = np.zeros((n, n), order="F")
+    sc = np.zeros(n, dtype=np.int32)
+    m = ci(0)
+    st = emu.pevc_solve(h, S.ctypes.data, n, T.ctypes.data, n, n, None, V.ctypes.data, n, sc.ctypes.data,
+                        ctypes.byref(m))
+    emu.pevc_destroy(h)
+    assert st == 0 and np.isfinite(V).all()
+    ost, Vo, sco, mo = oracle.evc(p.S, p.T)
+    _, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+    kinds, pos = check.column_kinds(blk)
+    err, _ = check.compare_normalised(Vo, V[:, :m.value], kinds)
+    res = check.residuals(p.S, p.T, V[:, :m.value], kinds, pos, a, b, beta).max() / (n * check.U)
+    assert err <= 1e-8 and res <= 100.0
