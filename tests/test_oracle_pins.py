@@ -484,3 +484,63 @@ def test_left_oracle_planted_conjugation_fails_the_residual():
     Ubad[:, kinds == 2] *= -1.0          # the mistake: the imaginary part not negated
     res = check.left_residuals(p.S, p.T, Ubad, kinds, pos, a, b, beta)
     assert res[kinds == 1].max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Invariances of the eigenvector problem (pins from the mathematics, which a
+# misplaced index, a transposed operand or a mishandled scale would break).
+# ---------------------------------------------------------------------------
+
+def test_power_of_two_scaling_of_the_pencil_leaves_the_vectors():
+    """(2^a S, 2^b T) has the eigenvalues 2^(a-b) lambda and the same eigenvectors."""
+    p = pencilgen.make_pencil(150, 640)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    kinds, _ = check.column_kinds(p.block)
+    for a, b in ((7, 0), (0, -5), (300, 300), (-200, 100)):
+        st2, V2, sc2, m2 = oracle.evc(np.ldexp(p.S, a), np.ldexp(p.T, b))
+        assert st2 == 0
+        err, _ = check.compare_normalised(V, V2, kinds)
+        assert err <= 1e-13, (a, b, err)
+
+
+def test_diagonal_similarity_maps_the_vectors():
+    """(D S D^-1, D T D^-1) with D diagonal has the eigenvectors D v (row i
+    scaled by d_i).  A misplaced row index in the update (an off-by-one row,
+    say) breaks this; a transposed read, which lands on the zero lower
+    triangle, keeps it and is caught by the residual pins instead."""
+    p = pencilgen.make_pencil(120, 641)
+    rng = np.random.default_rng(642)
+    d = np.ldexp(1.0, rng.integers(-6, 7, p.n))        # powers of two: D S D^-1 is exact
+    S2 = np.asfortranarray(p.S * d[:, None] / d[None, :])
+    T2 = np.asfortranarray(p.T * d[:, None] / d[None, :])
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    st2, V2, sc2, m2 = oracle.evc(S2, T2)
+    assert st == st2 == 0
+    kinds, _ = check.column_kinds(p.block)
+    err, _ = check.compare_normalised(V2, d[:, None] * V, kinds)
+    assert err <= 1e-12
+
+
+def test_cplx_scalar_multiple_and_conjugation():
+    """(c S, c T) for a complex c has the same eigenvectors (beta' S' - alpha' T'
+    = c^2 (beta S - alpha T)); (conj S, conj T) has the conjugate ones."""
+    p = pencilgen.make_complex_pencil(130, 643)
+    st, V, sc, m = oracle.evc_cplx(p.S, p.T)
+    c = complex(0.6, -0.8) * 3.0
+    st2, V2, _, _ = oracle.evc_cplx(c * p.S, c * p.T)
+    st3, V3, _, _ = oracle.evc_cplx(np.conj(p.S), np.conj(p.T))
+    assert st == st2 == st3 == 0
+    assert check.compare_normalised_cplx(V, V2)[0] <= 1e-12
+    assert check.compare_normalised_cplx(np.conj(V), V3)[0] <= 1e-15
+
+
+def test_cplx_diagonal_similarity_maps_the_vectors():
+    p = pencilgen.make_complex_pencil(100, 644)
+    rng = np.random.default_rng(645)
+    d = np.ldexp(1.0, rng.integers(-6, 7, p.n)) * np.exp(1j * rng.uniform(0, 2 * np.pi, p.n))
+    S2 = np.asfortranarray(p.S * d[:, None] / d[None, :])
+    T2 = np.asfortranarray(p.T * d[:, None] / d[None, :])
+    st, V, sc, m = oracle.evc_cplx(p.S, p.T)
+    st2, V2, sc2, m2 = oracle.evc_cplx(S2, T2)
+    assert st == st2 == 0
+    assert check.compare_normalised_cplx(V2, d[:, None] * V)[0] <= 1e-12
