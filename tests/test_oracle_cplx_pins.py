@@ -314,3 +314,35 @@ def test_cplx_backtransform_gives_eigenvectors_of_original_pencil():
     assert check.cplx_residuals(A, B, Xbad, a, b)[5:].min() > 1e-6
     # Z = I returns the vectors themselves
     assert np.abs(backtransform_cplx(np.eye(n), V) - V).max() == 0.0
+
+
+def test_cplx_repeated_eigenvalue_needs_the_perturbed_pivot():
+    ep = pencilgen.exact_complex_pencil(10, 652)
+    S, T = ep.as_complex()
+    S[6, 6], T[6, 6] = S[1, 1], T[1, 1]                   # the same (alpha, beta): a pivot exactly 0
+    st, V, sc, m = oracle.evc_cplx(S, T)
+    assert st == 0 and np.isfinite(V).all()
+    a, b = np.diag(S), np.diag(T)
+    assert check.cplx_residuals(S, T, V, a, b).max() <= BAR * 10
+    assert 40 <= sc[6] <= 70, sc[6]                        # growth about 1/u from smin (reading 9)
+
+
+def test_cplx_huge_entries_need_the_prescaling():
+    p = pencilgen.make_complex_pencil(80, 653)
+    st, V, sc, m = oracle.evc_cplx(p.S, p.T)
+    st2, V2, sc2, m2 = oracle.evc_cplx(p.S * 2.0 ** 1010, p.T * 2.0 ** 1010)
+    assert st2 == 0 and np.isfinite(V2).all()
+    assert check.compare_normalised_cplx(V, V2)[0] <= 1e-13
+
+
+def test_cplx_column_bound_covers_the_row_above_the_diagonal():
+    """The complex twin of the real growth pencil (the row just above the
+    diagonal holds the column's largest entry)."""
+    l2 = 2.0 ** -400 * (1 + 1j)
+    l1 = l2 * (1.0 + 2.0 ** -50)
+    S = np.array([[0.5, 2.0 ** 600 * 1j, 0.0], [0.0, l1, 2.0 ** 600], [0.0, 0.0, l2]], dtype=complex, order="F")
+    T = np.asfortranarray(np.eye(3, dtype=complex))
+    st, V, sc, m = oracle.evc_cplx(S, T)
+    assert st == 0 and np.isfinite(V).all()
+    assert sc[2] > 1023
+    assert check.cplx_residuals(S, T, V, np.diag(S), np.diag(T)).max() <= BAR * 3

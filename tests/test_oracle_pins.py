@@ -544,3 +544,52 @@ def test_cplx_diagonal_similarity_maps_the_vectors():
     st2, V2, sc2, m2 = oracle.evc_cplx(S2, T2)
     assert st == st2 == 0
     assert check.compare_normalised_cplx(V2, d[:, None] * V)[0] <= 1e-12
+
+
+def test_repeated_eigenvalue_needs_the_perturbed_pivot():
+    """An eigenvalue repeated exactly makes a pivot of the substitution exactly
+    zero; the pivot raised to smin keeps every vector finite and within the
+    residual bar (the vector of a pencil perturbed by about u)."""
+    ep = pencilgen.exact_pencil(12, 650, two_by_two=False)
+    S, T = ep.as_float()
+    S[7, 7], T[7, 7] = S[2, 2], T[2, 2]                   # (alpha_7, beta_7) = (alpha_2, beta_2): pivot exactly 0
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0 and np.isfinite(V).all()
+    st, blk, a, b, beta, _ = oracle.eigpairs(S, T)
+    kinds, pos = check.column_kinds(blk)
+    assert check.residuals(S, T, V, kinds, pos, a, b, beta).max() <= 100 * 12 * check.U
+    # reading 9: the zero pivot is raised to smin = u (|beta||S_22| + |alpha||T_22|), so the vector grows
+    # by about 1/u = 2^53 (a floor of 2^-1022 alone would make it grow by about 2^1022)
+    assert 40 <= sc[7] <= 70, sc[7]
+
+
+def test_huge_entries_need_the_prescaling():
+    """Entries near 2^1010: beta S - alpha T would overflow without the
+    power-of-two pre-scaling of (alpha, beta); the vectors are those of the
+    unscaled pencil."""
+    p = pencilgen.make_pencil(90, 651)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    st2, V2, sc2, m2 = oracle.evc(np.ldexp(p.S, 1010), np.ldexp(p.T, 1010))
+    assert st2 == 0 and np.isfinite(V2).all()
+    kinds, _ = check.column_kinds(p.block)
+    assert check.compare_normalised(V, V2, kinds)[0] <= 1e-13
+
+
+def _growth_pencil():
+    """n = 3, T = I: x_1 = -S_12 / (lambda_1 - lambda_2) reaches Omega
+    (2^600 / 2^-450), and the update of row 0 multiplies it by S_01 = 2^600, the
+    largest entry of column 1 above the diagonal, in the row just above it."""
+    l2 = 2.0 ** -400
+    l1 = l2 * (1.0 + 2.0 ** -50)                          # lambda_1 - lambda_2 = 2^-450, exact
+    S = np.array([[0.5, 2.0 ** 600, 0.0], [0.0, l1, 2.0 ** 600], [0.0, 0.0, l2]], order="F")
+    return S, np.asfortranarray(np.eye(3))
+
+
+def test_column_bound_covers_the_row_above_the_diagonal():
+    S, T = _growth_pencil()
+    st, V, sc, m = oracle.evc(S, T)
+    assert st == 0 and np.isfinite(V).all()
+    assert sc[2] > 1023                                   # the growth is represented, not overflowed
+    st, blk, a, b, beta, _ = oracle.eigpairs(S, T)
+    kinds, pos = check.column_kinds(blk)
+    assert check.residuals(S, T, V, kinds, pos, a, b, beta).max() <= 100 * 3 * check.U
