@@ -20,13 +20,13 @@
 
 #include "common.cuh"
 #include "cplx.cuh"
+#include "sched.cuh"
+#include "split.cuh"
 
 namespace pevc {
 // Bounded-wait self-test (watchdog.cu).
 cudaError_t launch_watchdog_probe(unsigned* status, int withhold, long long cycles, cudaStream_t s);
 }  // namespace pevc
-#include "sched.cuh"
-#include "split.cuh"
 
 using namespace pevc;
 
@@ -782,24 +782,37 @@ int pevc_solve_left(pevc_plan_t plan, const double* S, int lds, const double* T,
   return 0;
 }
 
-int pevc_solve_cplx(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
-                    const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out) {
+namespace {
+
+// Arguments shared by the complex solves (numbered as in the ABI, the plan
+// first): 0 when they are valid, else -i.  complex128 elements are read and
+// written as 16-byte pairs, so S, T and the output must be 16-byte aligned.
+int cplx_args(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n, const double* out,
+              int ldo, const int32_t* scale_out, const int* m_out) {
   if (!plan) return -1;
   if (n < 0 || n > plan->n_max) return -6;
   if (n > 0 && !S) return -2;
   if (lds < std::max(n, 1)) return -3;
   if (n > 0 && !T) return -4;
   if (ldt < std::max(n, 1)) return -5;
-  if (n > 0 && !V_out) return -8;
-  if (ldv < std::max(n, 1)) return -9;
+  if (n > 0 && !out) return -8;
+  if (ldo < std::max(n, 1)) return -9;
   if (n > 0 && !scale_out) return -10;
   if (!m_out) return -11;
+  if (n > 0 && ((uintptr_t)S & 15u)) return -2;
+  if (n > 0 && ((uintptr_t)T & 15u)) return -4;
+  if (n > 0 && ((uintptr_t)out & 15u)) return -8;
+  return 0;
+}
+
+}  // namespace
+
+int pevc_solve_cplx(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+                    const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out) {
+  const int bad = cplx_args(plan, S, lds, T, ldt, n, V_out, ldv, scale_out, m_out);
+  if (bad) return bad;
   *m_out = 0;
   if (n == 0) return 0;
-  // complex128 elements are read and written as 16-byte pairs
-  if ((uintptr_t)S & 15u) return -2;
-  if ((uintptr_t)T & 15u) return -4;
-  if ((uintptr_t)V_out & 15u) return -8;
   if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
   return cplx_solve(&plan->cx, plan->n_max, plan->stream, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out,
                     !(plan->flags & PEVC_NO_NORMALISE));
@@ -807,21 +820,10 @@ int pevc_solve_cplx(pevc_plan_t plan, const double* S, int lds, const double* T,
 
 int pevc_solve_cplx_left(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
                          const int32_t* select, double* U_out, int ldu, int32_t* scale_out, int* m_out) {
-  if (!plan) return -1;
-  if (n < 0 || n > plan->n_max) return -6;
-  if (n > 0 && !S) return -2;
-  if (lds < std::max(n, 1)) return -3;
-  if (n > 0 && !T) return -4;
-  if (ldt < std::max(n, 1)) return -5;
-  if (n > 0 && !U_out) return -8;
-  if (ldu < std::max(n, 1)) return -9;
-  if (n > 0 && !scale_out) return -10;
-  if (!m_out) return -11;
+  const int bad = cplx_args(plan, S, lds, T, ldt, n, U_out, ldu, scale_out, m_out);
+  if (bad) return bad;
   *m_out = 0;
   if (n == 0) return 0;
-  if ((uintptr_t)S & 15u) return -2;
-  if ((uintptr_t)T & 15u) return -4;
-  if ((uintptr_t)U_out & 15u) return -8;
   if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
   return cplx_solve_left(&plan->cx, plan->n_max, plan->stream, S, lds, T, ldt, n, select, U_out, ldu, scale_out,
                          m_out, !(plan->flags & PEVC_NO_NORMALISE));
