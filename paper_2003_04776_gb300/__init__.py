@@ -385,10 +385,10 @@ class Plan:
         Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0))
         return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
 
-    def solve_cplx(self, S, T, select=None, check: bool = True):
-        """Eigenvectors of a complex pencil in generalized Schur form (S, T
-        upper triangular, numpy or torch, complex128).  Returns (V as an
-        n x m complex numpy array, scale int32[m], status)."""
+    def _solve_cplx_with(self, fn, name, S, T, select, check):
+        """Marshals a complex solve (right or left eigenvectors): complex128
+        column-major copies of S and T on the device, the output in a torch
+        tensor, the result back as an n x m complex numpy array."""
         import torch
         n = int(S.shape[0])
         St = to_device_colmajor_c(S)
@@ -399,34 +399,23 @@ class Plan:
         if select is not None:
             sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
         with torch.cuda.stream(self.stream):
-            st, m = pevc_solve_cplx(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
-                                    sel.data_ptr() if sel is not None else 0, V.data_ptr(), max(n, 1),
-                                    scale.data_ptr())
+            st, m = fn(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
+                       sel.data_ptr() if sel is not None else 0, V.data_ptr(), max(n, 1), scale.data_ptr())
         if check and st:
-            raise PevcError(st, "pevc_solve_cplx")
+            raise PevcError(st, name)
         Vh = V[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
         return np.asfortranarray(Vh[:n, :m]), scale[:m].cpu().numpy(), st
+
+    def solve_cplx(self, S, T, select=None, check: bool = True):
+        """Eigenvectors of a complex pencil in generalized Schur form (S, T
+        upper triangular, numpy or torch, complex128).  Returns (V as an
+        n x m complex numpy array, scale int32[m], status)."""
+        return self._solve_cplx_with(pevc_solve_cplx, "pevc_solve_cplx", S, T, select, check)
 
     def solve_cplx_left(self, S, T, select=None, check: bool = True):
         """Left eigenvectors u^H (beta S - alpha T) = 0 of a complex triangular
         pencil.  Returns (U as an n x m complex numpy array, scale, status)."""
-        import torch
-        n = int(S.shape[0])
-        St = to_device_colmajor_c(S)
-        Tt = to_device_colmajor_c(T)
-        U = torch.empty((max(n, 1), max(n, 1)), dtype=torch.complex128, device="cuda")   # column-major storage
-        scale = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
-        sel = None
-        if select is not None:
-            sel = torch.as_tensor(np.asarray(select, dtype=np.int32)).to("cuda")
-        with torch.cuda.stream(self.stream):
-            st, m = pevc_solve_cplx_left(self.h, St.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), n,
-                                         sel.data_ptr() if sel is not None else 0, U.data_ptr(), max(n, 1),
-                                         scale.data_ptr())
-        if check and st:
-            raise PevcError(st, "pevc_solve_cplx_left")
-        Uh = U[:m].cpu().numpy().T if m else np.zeros((n, 0), dtype=complex)
-        return np.asfortranarray(Uh[:n, :m]), scale[:m].cpu().numpy(), st
+        return self._solve_cplx_with(pevc_solve_cplx_left, "pevc_solve_cplx_left", S, T, select, check)
 
     def backtransform_cplx(self, Z, V, normalise: bool = True, check: bool = True):
         """X = Z V for complex eigenvectors V (numpy or torch, complex128):
