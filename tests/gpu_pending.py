@@ -218,3 +218,25 @@ def test_cplx_backtransform_matches_oracle(pevc_lib):
     assert err <= TOL and res <= 100.0
     ref = Z @ V
     assert np.abs(Xr - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_cplx_stress_every_tile_and_repeated_eigenvalue(pevc_lib):
+    """Every off-diagonal tile scaled by 1e100 over several tiles (segments of
+    different exponents meet in every update), and an exactly repeated
+    eigenvalue (a zero pivot raised to smin): scale exponents within 1 of the
+    oracle's."""
+    p = pencilgen.make_complex_pencil(300, 7900, stress=True, big_frac=1.0)
+    ep = pencilgen.exact_complex_pencil(10, 652)
+    S2, T2 = ep.as_complex()
+    S2[6, 6], T2[6, 6] = S2[1, 1], T2[1, 1]
+    plan = pevc_lib.Plan(300, prec="fp64")
+    try:
+        V, sc, st = plan.solve_cplx(p.S, p.T)
+        V2, sc2, st2 = plan.solve_cplx(S2, T2)
+    finally:
+        plan.close()
+    assert st == 0 and st2 == 0
+    _check(p, V, sc)
+    assert np.isfinite(V2).all() and 40 <= sc2[6] <= 70
+    ost, Vo2, sco2, m2 = oracle.evc_cplx(S2, T2)
+    assert np.all(np.abs(sc2.astype(np.int64) - sco2.astype(np.int64)) <= 1)

@@ -107,6 +107,36 @@ def test_emulated_complex_left_solve_matches_oracle(emu):
     idx = np.flatnonzero(sel)
     res = check.cplx_left_residuals(p.S, p.T, U, np.diag(p.S)[idx], np.diag(p.T)[idx]).max() / (n * check.U)
     assert err <= 1e-12 and res <= 100.0
+    assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+def test_emulated_complex_stress_over_several_tiles(emu):
+    """Three tiles with every off-diagonal tile scaled by 1e100 and T's diagonal
+    by 2^-40: the updates consolidate segments of different exponents, guard
+    the right update and protect the left one, and the post-pass brings every
+    column to one power of two -- all visible in the scale exponents."""
+    p = pencilgen.make_complex_pencil(130, 9900, stress=True, big_frac=1.0)
+    st, V, sc = _call(emu, "pevc_solve_cplx", p.S, p.T, np.complex128)
+    assert st == 0 and np.isfinite(V).all()
+    ost, Vo, sco, m = oracle.evc_cplx(p.S, p.T)
+    assert sco.max() > 1023
+    err, _ = check.compare_normalised_cplx(Vo, V)
+    res = check.cplx_residuals(p.S, p.T, V, np.diag(p.S), np.diag(p.T)).max() / (130 * check.U)
+    assert err <= 1e-12 and res <= 100.0
+    assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+def test_emulated_complex_repeated_eigenvalue(emu):
+    """An exactly repeated eigenvalue: the zero pivot is raised to smin, so the
+    vector is finite and grows by about 1/u, as in the oracle."""
+    ep = pencilgen.exact_complex_pencil(10, 652)
+    S, T = ep.as_complex()
+    S[6, 6], T[6, 6] = S[1, 1], T[1, 1]
+    st, V, sc = _call(emu, "pevc_solve_cplx", S, T, np.complex128)
+    assert st == 0 and np.isfinite(V).all()
+    ost, Vo, sco, m = oracle.evc_cplx(S, T)
+    assert 40 <= sc[6] <= 70 and abs(int(sc[6]) - int(sco[6])) <= 1
+    assert check.cplx_residuals(S, T, V, np.diag(S), np.diag(T)).max() <= 100 * 10 * check.U
 
 
 @pytest.mark.parametrize("big", [1.0, 1e200, 2.0 ** 1020])
