@@ -90,6 +90,34 @@ int bt_zgemm(void*, int, int, const double*, int, const double*, int, double*, i
 '''
 
 
+# The scalar helpers of common.cuh that the tcgen05 epilogue and the
+# protection are built from, exported one by one for unit tests.
+HELPERS = '''
+#include "{csrc}/common.cuh"
+extern "C" {{
+double emu_i64_scaled_fast(long long t, int e, int* slow) {{
+  bool s = false;
+  const double r = pevc::i64_scaled_fast(t, e, s);
+  *slow = s;
+  return r;
+}}
+double emu_i64_scaled(long long t, int e) {{ return pevc::i64_scaled(t, e); }}
+double emu_pow2_scale_fast(double y, int sh, int* slow) {{
+  bool s = false;
+  const double r = pevc::pow2_scale_fast(y, sh, s);
+  *slow = s;
+  return r;
+}}
+double emu_pow2_scale(double x, int e) {{ return pevc::pow2_scale(x, e); }}
+int emu_exp_ub(double x) {{ return pevc::exp_ub(x); }}
+int emu_protect_update(double y, double t, double x) {{ return pevc::protect_update(y, t, x); }}
+int emu_protect_update_ub(double y, double t, double x) {{ return pevc::protect_update_ub(y, t, x); }}
+int emu_protect_division(double b, int sh, double t) {{ return pevc::protect_division(b, sh, t); }}
+double emu_max_nonneg(double x, double y) {{ return pevc::max_nonneg(x, y); }}
+}}
+'''
+
+
 def _bt_source() -> str:
     src = open(os.path.join(CSRC, "backtransform.cu")).read()
     body = src[src.index("struct BtBest {"):src.index("// X = Z V for complex128 column-major arrays")]
@@ -139,7 +167,7 @@ def build() -> str:
             fh.write(_convert(open(os.path.join(CSRC, f)).read(), f))
         srcs.append(out)
     for name, text in (("stubs.cpp", STUBS.format(csrc=CSRC)), ("bt.cpp", _bt_source()),
-                       ("watchdog.cpp", _watchdog_source())):
+                       ("watchdog.cpp", _watchdog_source()), ("helpers.cpp", HELPERS.format(csrc=CSRC))):
         out = os.path.join(BUILD, name)
         with open(out, "w") as fh:
             fh.write(text)

@@ -260,3 +260,79 @@ def test_emulated_split_solve_matches_oracle(emu, prec, n):
     err, _ = check.compare_normalised(Vo, V[:, :m.value], kinds)
     res = check.residuals(p.S, p.T, V[:, :m.value], kinds, pos, a, b, beta).max() / (n * check.U)
     assert err <= 1e-8 and res <= 100.0
+
+
+def test_epilogue_and_protection_helpers(emu):
+    """The scalar helpers the tcgen05 epilogue and the protection are built
+    from (common.cuh), compiled as host code, against exact rational
+    arithmetic: the int64 -> binary64 assembly rounds to nearest, ties to even,
+    the power-of-two scalings are exact, and the exponent bounds bound."""
+    from fractions import Fraction
+    cd, cll = ctypes.c_double, ctypes.c_longlong
+    f = emu
+    f.emu_i64_scaled_fast.argtypes = [cll, ci, ctypes.POINTER(ci)]
+    f.emu_i64_scaled_fast.restype = cd
+    f.emu_i64_scaled.argtypes = [cll, ci]
+    f.emu_i64_scaled.restype = cd
+    f.emu_pow2_scale_fast.argtypes = [cd, ci, ctypes.POINTER(ci)]
+    f.emu_pow2_scale_fast.restype = cd
+    f.emu_pow2_scale.argtypes = [cd, ci]
+    f.emu_pow2_scale.restype = cd
+    f.emu_exp_ub.argtypes = [cd]
+    for name in ("emu_protect_update", "emu_protect_update_ub"):
+        getattr(f, name).argtypes = [cd, cd, cd]
+    f.emu_protect_division.argtypes = [cd, ci, cd]
+    f.emu_max_nonneg.argtypes = [cd, cd]
+    f.emu_max_nonneg.restype = cd
+    rng = np.random.default_rng(9950)
+    OMEGA = Fraction(2) ** 1022
+    slow = ci(0)
+    ties = [(2 ** 53 + 1) << s for s in (1, 3, 9)] + [(2 ** 53 + 3) << 1, -((2 ** 54 + 2) << 2) - 4]
+    ts = [int(x) for x in (rng.integers(-2 ** 62, 2 ** 62, 3000) >> rng.integers(0, 62, 3000))] + ties + [0, 1, -1]
+    for t in ts:
+        for e in (int(rng.integers(-1140, 1040)), int(rng.integers(-60, 60))):
+            exact = Fraction(t) * Fraction(2) ** e
+            r = f.emu_i64_scaled_fast(t, e, ctypes.byref(slow))
+            big = exact != 0 and (abs(exact) < Fraction(2) ** -1022 or abs(exact) >= Fraction(2) ** 1024)
+            if slow.value == 0:
+                assert r == float(exact), (t, e)        # correctly rounded, ties to even
+            else:
+                assert big or abs(exact) < Fraction(2) ** -1021
+            if Fraction(2) ** -1022 <= abs(exact) < Fraction(2) ** 1023:
+                assert f.emu_i64_scaled(t, e) == float(exact)
+    ys = np.concatenate([_ldexp_samples(rng, 2000), [0.0, -0.0, 5e-324, -2.2250738585072014e-308]])
+    for y in ys.tolist():
+        sh = int(rng.integers(-1100, 1100))
+        r = f.emu_pow2_scale_fast(y, sh, ctypes.byref(slow))
+        if slow.value == 0:
+            assert r == math_ldexp(y, sh)
+        assert f.emu_pow2_scale(y, sh) == math_ldexp(y, sh)
+        if y != 0 and np.isfinite(y):
+            eu = f.emu_exp_ub(y)
+            assert abs(y) < 2.0 ** eu if eu < 1024 else True
+            if abs(y) >= 2.2250738585072014e-308:
+                assert eu == np.frexp(abs(y))[1]
+    for _ in range(3000):
+        y, t, x = (abs(float(v)) for v in _ldexp_samples(rng, 3))
+        for fn in ("emu_protect_update", "emu_protect_update_ub"):
+            k = getattr(f, fn)(y, t, x)
+            assert k >= 0 and Fraction(y) + Fraction(t) * Fraction(x) <= OMEGA * Fraction(2) ** k
+        b, tt, sh = min(abs(y), 2.0 ** 1000), max(t, 2.0 ** -1000), int(rng.integers(0, 6))
+        kd = f.emu_protect_division(b, sh, tt)
+        assert kd >= 0 and Fraction(b) * Fraction(2) ** sh <= Fraction(tt) * OMEGA * Fraction(2) ** kd
+        assert f.emu_max_nonneg(y, t) == max(y, t)
+
+
+def _ldexp_samples(rng, count):
+    """Signed magnitudes spread over the whole binary64 range, subnormals included."""
+    v = np.ldexp(rng.uniform(0.5, 1.0, count), rng.integers(-1074, 1024, count))
+    v = np.where(np.isfinite(v), v, 1.0)
+    return v * rng.choice([-1.0, 1.0], count)
+
+
+def math_ldexp(x, e):
+    import math
+    try:
+        return math.ldexp(x, e)
+    except OverflowError:
+        return math.copysign(float("inf"), x)
