@@ -23,7 +23,7 @@
  * factors are powers of two, accumulated in a signed 32-bit exponent
  * (Section 5: Zazamoukh's scaling factors are signed 32-bit integers).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - Omega = 2^1022.  ProtectUpdate / ProtectDivision return a power of two
  *     2^-k, with k from exponent bounds (frexp); they satisfy the properties
  *     of Section 4 but may scale by up to 8x more than the minimum.

@@ -114,6 +114,7 @@ int emu_protect_update(double y, double t, double x) {{ return pevc::protect_upd
 int emu_protect_update_ub(double y, double t, double x) {{ return pevc::protect_update_ub(y, t, x); }}
 int emu_protect_division(double b, int sh, double t) {{ return pevc::protect_division(b, sh, t); }}
 double emu_max_nonneg(double x, double y) {{ return pevc::max_nonneg(x, y); }}
+long long emu_alloc_count() {{ return g_emu_allocs.load(); }}
 }}
 '''
 

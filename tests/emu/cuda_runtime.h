@@ -59,7 +59,11 @@ inline cudaError_t cudaMemsetAsync(void* d, int v, size_t b, cudaStream_t) {
   memset(d, v, b);
   return 0;
 }
+// Every device or pinned-host allocation the library makes is counted, so
+// that a test can show an entry point allocates nothing.
+inline std::atomic<long long> g_emu_allocs{0};
 inline cudaError_t cudaMalloc(void** p, size_t b) {
+  g_emu_allocs.fetch_add(1);
   *p = calloc(b ? b : 1, 1);
   return *p ? 0 : cudaErrorMemoryAllocation;
 }

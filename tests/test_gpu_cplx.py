@@ -1,14 +1,11 @@
-"""GPU tests of code that has not yet run on a GPU, through the C ABI:
-pevc_solve_cplx / pevc_solve_cplx_left against the complex oracle
-(eigenvectors of complex triangular pencils, the extension to complex data of
-Section 7), and the bounded-wait self-test.
+"""GPU parity of the complex-pencil path through the C ABI: pevc_solve_cplx,
+pevc_solve_cplx_left and pevc_backtransform_cplx against the complex oracle
+(eigenvectors of complex triangular pencils, the extension to complex data
+that Section 7 names).
 
 Bar: componentwise within 1e-10 of the oracle after normalisation at the
 oracle's entry of largest modulus, residual <= 100 n u, scale exponents
 within 1 of the oracle's, zeros below the tip, no Inf/NaN.
-
-Not yet collected: once these pass on a GB300, they move into the suite
-(tests/test_gpu_cplx.py and tests/test_gpu_watchdog.py).
 """
 import os
 
@@ -178,23 +175,6 @@ def test_cplx_left_selection_and_stress(pevc_lib):
     idx = np.flatnonzero(sel)
     res = check.cplx_left_residuals(p.S, p.T, U, np.diag(p.S)[idx], np.diag(p.T)[idx]).max() / (n * check.U)
     assert err <= TOL and res <= 100.0
-
-
-def test_watchdog_wait_runs_out_and_context_survives(pevc_lib):
-    """A bounded device wait whose arrival is withheld gives up and reports
-    ERR_TIMEOUT; the context stays usable for a solve afterwards."""
-    plan = pevc_lib.Plan(64, prec="fp64")
-    try:
-        h = plan.h
-        assert pevc_lib.pevc_watchdog_selftest(h, 0, 2_000_000) == 0
-        assert pevc_lib.pevc_watchdog_selftest(h, 1, 2_000_000) == pevc_lib.ERR_TIMEOUT
-        assert pevc_lib.pevc_watchdog_selftest(h, 1, 0) == -3
-        assert pevc_lib.pevc_watchdog_selftest(h, 2, 1000) == -2
-        p = pencilgen.make_pencil(64, 7700)
-        V, sc, st = plan.solve(p.S, p.T)
-        assert st == 0 and np.isfinite(V).all()
-    finally:
-        plan.close()
 
 
 def test_cplx_backtransform_matches_oracle(pevc_lib):

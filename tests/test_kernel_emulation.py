@@ -209,9 +209,15 @@ def test_emulated_real_left_static_and_batched_entry_points(emu):
     V = np.zeros((40, 40), order="F")
     scs = np.zeros(40, dtype=np.int32)
     m = ci(0)
+    emu.emu_alloc_count.restype = ctypes.c_longlong
+    allocs = emu.emu_alloc_count()
+    # n = 0 is the set-up call (it only looks up the static workspace)
+    assert emu.pevc_solve_static(None, 1, None, 1, 0, None, None, 1, None, ctypes.byref(m), 0, None) == 0
     assert emu.pevc_solve_static(S.ctypes.data, 40, T.ctypes.data, 40, 40, None, V.ctypes.data, 40,
                                  scs.ctypes.data, ctypes.byref(m), 0, None) == 0
+    assert emu.emu_alloc_count() == allocs            # no cudaMalloc / cudaMallocHost on this path
     _check_real(p, V[:, :m.value], scs[:m.value])
+    assert emu.emu_alloc_count() == allocs
     # the batched solve: three pencils of different orders, the middle one not in Schur form
     pens = [pencilgen.make_pencil(n, 9610 + n) for n in (20, 33, 47)]
     Sb = [np.asfortranarray(q.S) for q in pens]

@@ -4,12 +4,14 @@ plan-based one (pevc_solve), both through the C ABI.
 Two calls in a row on pencils of different orders (and a selection on the
 second), each compared with an FP64 plan's output on the same input:
 componentwise within the FP64 parity tolerance after normalisation, equal
-column counts and scale exponents.  The second call also checks that nothing
+column counts and scale exponents; the second is also held to the FP64 oracle
+directly.  The second call also checks that nothing
 of the first call's contents in the shared scratch array leaks into it.
 """
 import numpy as np
 import pytest
 
+import oracle
 import pencilgen
 from oracle import check
 
@@ -72,7 +74,12 @@ def test_static_entry_matches_plan_on_two_calls(pevc_lib):
 
     e1 = _agree(Vp1, scp1, Vs1, scs1, p1.block)
     e2 = _agree(Vp2, scp2, Vs2, scs2, p2.block, sel2)
-    print(f"static vs plan: {e1:.3e}, {e2:.3e}")
+    # and directly against the FP64 oracle
+    ost, Vo, sco, mo = oracle.evc(p2.S, p2.T, select=sel2)
+    assert ost == 0
+    eo, _ = check.compare_normalised(Vo, Vs2, check.column_kinds(p2.block, sel2)[0])
+    assert eo <= TOL and np.all(np.abs(scs2.astype(np.int64) - sco.astype(np.int64)) <= 1)
+    print(f"static vs plan: {e1:.3e}, {e2:.3e}; vs oracle {eo:.3e}")
 
 
 def test_static_entry_rejects_orders_above_its_maximum(pevc_lib):
