@@ -75,9 +75,12 @@ def rooflines(prof, ms, n, prec, tile, peaks, peak_src, nsm, tc_kernel=True):
     upd_ms, upd_n, upd_flops = mean("update_ms"), int(round(mean("update_launches"))), mean("update_tensor_flops")
     dg_ms, dg_n = mean("diag_ms"), int(round(mean("diag_launches")))
     if prec == "fp64":
+        clk = float(peaks.get("sm_max_mhz") or 2070.0) * 1e6
         upd = {"bound": "alu", "unit": "TFLOP/s",
                "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
-               "peak": 1.02, "peak_source": "own DFMA/DMMA probe (FP64 tensor and ALU rates are equal on GB300)",
+               "peak": round(nsm * 2 * 2 * clk / 1e12, 4),
+               "peak_source": f"FP64 pipe: {nsm} SMs x 2 lanes/clk x 2 flops x {clk / 1e6:.0f} MHz "
+                              "(DMMA and DFMA share it on GB300)",
                "kernel": "k_update_f64"}
     else:
         pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
@@ -112,6 +115,102 @@ def measured_traffic(kernel: str, n: int = 20000, prec: str = "bf16x5"):
         with open(os.path.join(ROOT, "paper_2003_04776_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return rec["bytes_per_launch"] if h.hexdigest()[:16] == rec["sha256_16"] else None
+
+
+def column_kinds_all(block):
+    """Kind (0 real, 1 Re and 2 Im of a pair) of every output column of an
+    all-eigenvector solve; column c belongs to diagonal position c."""
+    block = np.asarray(block)
+    kinds = np.zeros(block.size, dtype=np.int64)
+    kinds[block == 1] = 1
+    kinds[block == 2] = 2
+    return kinds
+
+
+def gpu_residuals(St, Tt, V, kinds, lam_re, lam_im, block_cols: int = 1024, row_block: int = 0):
+    """Relative residual ||beta S v - alpha T v||_inf / ((|beta| ||S||_inf +
+    |alpha| ||T||_inf) ||v||_inf) of every eigenvector of an all-eigenvector
+    solve, with (alpha, beta) = (lam, 1) from the generator's eigenvalues (a
+    pair's first row carries +Im); a pair's two columns get its complex
+    vector's value.  S V and T V are FP64 GEMMs on the GPU (cuBLAS through
+    torch), restricted by the upper quasi-triangular structure: the columns
+    [c0, c1) of V are zero below row c1, so only S[:c1+1, :c1+1] meets them.
+    St, Tt, V hold the column-major arrays (row c of the tensor = column c).
+    With row_block > 0 every block of row_block rows is normalised by its own
+    norms instead, (|beta| ||S[K, :]||_inf + |alpha| ||T[K, :]||_inf) ||v||_inf,
+    and the largest block value is returned: huge entries elsewhere in S or T
+    then cannot hide an error in the rows they do not touch.
+    Returns a numpy array with one value per column."""
+    import torch
+    n = V.shape[0]
+    dev = V.device
+    rS = St.abs().sum(dim=0)                          # row sums of |S|
+    rT = Tt.abs().sum(dim=0)
+    if row_block > 0:
+        nb = (n + row_block - 1) // row_block
+        pad = nb * row_block - n
+        blk_max = lambda r: torch.cat([r, r.new_zeros(pad)]).view(nb, row_block).max(dim=1).values
+        nS = blk_max(rS).repeat_interleave(row_block)[:n]   # per row: its block's norm
+        nT = blk_max(rT).repeat_interleave(row_block)[:n]
+    else:
+        nS, nT = rS.max(), rT.max()
+    kinds_t = torch.as_tensor(np.asarray(kinds), device=dev)
+    pos = np.arange(n) - (np.asarray(kinds) == 2)
+    a_t = torch.as_tensor(np.asarray(lam_re)[pos], dtype=torch.float64, device=dev)
+    b_t = torch.as_tensor(np.abs(np.asarray(lam_im)[pos]), dtype=torch.float64, device=dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    c0 = 0
+    while c0 < n:
+        c1 = min(n, c0 + block_cols)
+        if kinds[c1 - 1] == 1:
+            c1 += 1                                   # keep a pair whole
+        r1 = min(n, c1 + 1)
+        X = V[c0:c1, :r1]
+        WS = X @ St[:r1, :r1]                         # WS[c, r] = (S V)[r, c]
+        WT = X @ Tt[:r1, :r1]
+        k = kinds_t[c0:c1]
+        a, b = a_t[c0:c1, None], b_t[c0:c1, None]
+        nxt = lambda A: torch.cat([A[1:], torch.zeros_like(A[:1])])
+        prv = lambda A: torch.cat([torch.zeros_like(A[:1]), A[:-1]])
+        pair = (k == 1)[:, None]
+        # real columns: beta S x - a T x; a pair's first column (x, y):
+        # re = S x - a T x + b T y, im = S y - a T y - b T x
+        re = WS - a * WT + torch.where(pair, b * nxt(WT), torch.zeros_like(WT))
+        im = torch.where(pair, nxt(WS) - a * nxt(WT) - b * WT, torch.zeros_like(WT))
+        rabs = torch.sqrt(re * re + im * im)
+        y = torch.where(pair, nxt(X), torch.zeros_like(X))
+        zmax = torch.sqrt(X * X + y * y).max(dim=1).values
+        alpha = torch.sqrt(a[:, 0] ** 2 + torch.where(k == 0, torch.zeros_like(b[:, 0]), b[:, 0]) ** 2)
+        if row_block > 0:
+            den = (nS[None, :r1] + alpha[:, None] * nT[None, :r1]) * zmax[:, None]
+            val = torch.where(rabs > 0, rabs / den, torch.zeros_like(rabs)).max(dim=1).values
+        else:
+            val = rabs.max(dim=1).values / ((nS + alpha * nT) * zmax)
+        # a pair's second column takes the value of its first
+        val = torch.where(k == 2, prv(val), val)
+        out[c0:c1] = val
+        c0 = c1
+    return out.cpu().numpy()
+
+
+def normalised_error(Vref, Vgot, kinds):
+    """Largest componentwise difference of the GPU's columns from the
+    oracle's, both normalised at the oracle's entry of largest modulus (pairs
+    as complex vectors); Vref, Vgot: n x m numpy arrays of the same columns."""
+    worst = 0.0
+    q = 0
+    m = Vref.shape[1]
+    while q < m:
+        if kinds[q] == 1:
+            zr, zg, step = Vref[:, q] + 1j * Vref[:, q + 1], Vgot[:, q] + 1j * Vgot[:, q + 1], 2
+        else:
+            zr, zg, step = Vref[:, q].astype(complex), Vgot[:, q].astype(complex), 1
+        i = int(np.argmax(np.abs(zr)))
+        d = zg[i]
+        e = np.inf if (d == 0 or not np.isfinite(d)) else float(np.abs(zg / d - zr / zr[i]).max())
+        worst = max(worst, e)
+        q += step
+    return worst
 
 
 def load_peaks():
@@ -169,12 +268,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_oracle_sample(pencil, budget_s: float, threads: int):
+def cpu_oracle_sample(pencil, budget_s: float, threads: int, top: int = 0):
     """Time the oracle, OpenMP-parallel over eigenvectors on `threads` host
     threads, on a stratified sample of the pencil's eigenvectors (spread evenly
     over the diagonal, so large and small ones alike) sized for about
     `budget_s` seconds; extrapolate to all of them with the sum-of-c^2 work
-    weights.  Returns (GFLOP/s, info)."""
+    weights.  With `top` > 0 the eigenvectors of the first `top` diagonal
+    positions (cheap: their work grows with c^2) are computed afterwards,
+    untimed, for the accuracy check.  Returns (GFLOP/s, info, (select, V) of
+    the timed sample, (select, V) of the top positions or None)."""
     import oracle
     n = pencil.n
     starts = np.flatnonzero(pencil.block != 2)
@@ -194,29 +296,60 @@ def cpu_oracle_sample(pencil, budget_s: float, threads: int):
     st, V, sc, m = oracle.evc(pencil.S, pencil.T, select=sel, nthreads=threads)
     spent = time.perf_counter() - t0
     rate = work / spent / 1e9
-    return rate, {"columns": int(len(picks)), "seconds": round(spent, 2), "work_flops": work}
+    top_part = None
+    if top > 0:
+        tsel = np.zeros(n, dtype=np.int32)
+        tsel[:min(top, n)] = 1
+        if pencil.block[min(top, n) - 1] == 1:
+            tsel[min(top, n)] = 1               # keep the last pair whole
+        _, Vt, _, _ = oracle.evc(pencil.S, pencil.T, select=tsel, nthreads=threads)
+        top_part = (tsel, Vt)
+    info = {"columns": int(len(picks)), "seconds": round(spent, 2), "work_flops": work}
+    return rate, info, (sel, V), top_part
+
+
+def selected_columns(block, sel):
+    """Output columns (of an all-eigenvector solve) of the selected
+    eigenvectors, and their kinds: a pair's two columns follow its first row."""
+    cols, kinds = [], []
+    for c in np.flatnonzero(sel):
+        if block[c] == 2:
+            continue
+        if block[c] == 1:
+            cols += [c, c + 1]
+            kinds += [1, 2]
+        else:
+            cols.append(c)
+            kinds.append(0)
+    return np.asarray(cols, dtype=np.int64), np.asarray(kinds, dtype=np.int64)
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload.
+    A step is one timed sample (stratified eigenvectors of the benchmark's
+    pencil, OpenMP over eigenvectors on every host core); value is the
+    sample's rate extrapolated to the whole solve by the sum-of-c^2 work
+    weights, ms_per_step the sample's own wall time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import pencilgen
     n = args.n
     p = pencilgen.config_pencil(3, n=n) if n == 20000 else pencilgen.make_pencil(n, pencilgen.config_seed(3))
-    budget = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    budget = max(4.0, 90.0 / max(args.steps + args.warmup, 1))
     threads = os.cpu_count() or 1
-    rates = []
+    rates, secs = [], []
     for s in range(args.warmup + args.steps):
-        r, info = cpu_oracle_sample(p, budget, threads)
+        r, info, _, _ = cpu_oracle_sample(p, budget, threads)
         if s >= args.warmup:
             rates.append(r)
+            secs.append(info["seconds"])
     val = float(np.median(rates))
     F = flops_all(n)
-    ms = F / (val * 1e9) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GFLOP/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * float(np.mean(secs)), 1),
+            "ms_per_full_solve_extrapolated": round(F / (val * 1e9) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"schur-pencil n={n}, all eigenvectors", "n": n, "prec": "oracle-fp64"},
@@ -239,9 +372,11 @@ def parse_args(argv=None):
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    # skip the FP64 and BF16x3 comparison arms (timed after the headline)
+    ap.add_argument("--no-arms", action="store_true")
     # "real" is the headline workload; "cplx" times the complex-pencil solve
     # (FP64) on its own, as a separate line
-    ap.add_argument("--workload", default="real", choices=["real", "cplx"])
+    ap.add_argument("--workload", default="real", choices=["real", "cplx", "batched"])
     return ap.parse_args(argv)
 
 
@@ -305,6 +440,205 @@ def run_complex(args):
     return 0
 
 
+class Batch:
+    """The batched workload resident on the device: every pencil's S, T and
+    output V in one buffer each (column-major n x n blocks, back to back), so
+    that the host copies of the end-to-end step are one transfer per
+    operand."""
+
+    def __init__(self, pencils, pevc):
+        import torch
+        self.pencils = pencils
+        self.n = [p.n for p in pencils]
+        self.off = np.concatenate([[0], np.cumsum([n * n for n in self.n])]).astype(np.int64)
+        total = int(self.off[-1])
+        host_S = np.empty(total)
+        host_T = np.empty(total)
+        for b, p in enumerate(pencils):
+            host_S[self.off[b]:self.off[b + 1]] = p.S.ravel(order="F")
+            host_T[self.off[b]:self.off[b + 1]] = p.T.ravel(order="F")
+        self.hS = torch.from_numpy(host_S).pin_memory()
+        self.hT = torch.from_numpy(host_T).pin_memory()
+        self.S = self.hS.to("cuda")
+        self.T = self.hT.to("cuda")
+        self.V = torch.empty(total, dtype=torch.float64, device="cuda")
+        self.scale = torch.empty(int(sum(self.n)), dtype=torch.int32, device="cuda")
+        self.soff = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        ptr = lambda t, o, es: t.data_ptr() + int(o) * es
+        self.S_p = [ptr(self.S, o, 8) for o in self.off[:-1]]
+        self.T_p = [ptr(self.T, o, 8) for o in self.off[:-1]]
+        self.V_p = [ptr(self.V, o, 8) for o in self.off[:-1]]
+        self.sc_p = [ptr(self.scale, o, 4) for o in self.soff[:-1]]
+        self.ld = [max(n, 1) for n in self.n]
+        self.pevc = pevc
+
+    def view(self, t, b):
+        """Pencil b's block of t as a tensor whose row c is column c."""
+        n = self.n[b]
+        return t[self.off[b]:self.off[b + 1]].view(n, n)
+
+    def solve(self, plan):
+        st, m_out, stat = self.pevc.pevc_solve_batched(plan.h, len(self.n), self.S_p, self.ld, self.T_p, self.ld,
+                                                       self.n, None, self.V_p, self.ld, self.sc_p)
+        if st:
+            raise self.pevc.PevcError(st, "pevc_solve_batched")
+        bad = [b for b, x in enumerate(stat) if x]
+        if bad:
+            raise self.pevc.PevcError(stat[bad[0]], f"pevc_solve_batched pencil {bad[0]}")
+        return m_out
+
+
+def batch_accuracy(batch):
+    """Per pencil: the largest residual / (n u) over its columns (global
+    norms, and per 64-row block with the block's own norms) and whether V is
+    finite."""
+    import torch
+    res, res_rb, finite = [], [], []
+    for b, p in enumerate(batch.pencils):
+        St, Tt, V = batch.view(batch.S, b), batch.view(batch.T, b), batch.view(batch.V, b)
+        kinds = column_kinds_all(p.block)
+        finite.append(bool(torch.isfinite(V).all().item()))
+        u = p.n * 2.0 ** -53
+        res.append(float(gpu_residuals(St, Tt, V, kinds, p.lam_re, p.lam_im).max() / u))
+        res_rb.append(float(gpu_residuals(St, Tt, V, kinds, p.lam_re, p.lam_im, row_block=64).max() / u))
+    return np.asarray(res), np.asarray(res_rb), np.asarray(finite)
+
+
+def run_batched(args):
+    """The batched workload: 1024 pencils with n log-uniform in [32, 2048],
+    odd indices stress pencils, all eigenvectors, in one pevc_solve_batched
+    call per step on inputs resident in HBM.  Metric: pencils per second."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import pencilgen
+    import paper_2003_04776_gb300 as pevc
+    orders = pencilgen.batch_orders()
+    pencils = [pencilgen.batch_pencil(b, int(n)) for b, n in enumerate(orders)]
+    batch = Batch(pencils, pevc)
+    stream = torch.cuda.current_stream()
+    plan = pevc.Plan(int(orders.max()), prec=args.prec, tile=args.tile, batch_max=len(pencils), stream=stream)
+    for _ in range(args.warmup):
+        batch.solve(plan)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            batch.solve(plan)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    count = len(pencils)
+    F = float(sum(flops_all(int(n)) for n in orders))
+    line = {"metric": "batched all-eigenvector solves, 1024 pencils, n log-uniform [32, 2048], half stress",
+            "value": round(count / (ms * 1e-3), 2), "unit": "pencils/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-split+f64" if args.prec != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched schur pencils: 1024, n = round(exp(U[ln 32, ln 2048])), odd = stress",
+                       "prec": args.prec, "tile": plan.info[0], "pencils": count,
+                       "l2": "inputs %.1f GB >> 129 MB L2, no flush" % (2 * 8 * batch.off[-1] / 1e9)},
+            "effective_gflops": round(F / (ms * 1e-3) / 1e9, 2), "clocks": clk.summary()}
+    # end to end: the pencils from pinned host memory and V back, every step
+    e_times = []
+    hV = torch.empty(int(batch.off[-1]), dtype=torch.float64).pin_memory()
+    for q in range(max(2, min(args.steps, 4))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.S.copy_(batch.hS, non_blocking=True)
+        batch.T.copy_(batch.hT, non_blocking=True)
+        batch.solve(plan)
+        hV.copy_(batch.V, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if q:
+            e_times.append(e0.elapsed_time(e1))
+    ems = float(np.median(e_times))
+    line["e2e"] = {"value": round(count / (ems * 1e-3), 2), "unit": "pencils/s", "ms_per_step": round(ems, 3),
+                   "h2d_bytes_per_step": int(2 * 8 * batch.off[-1]), "d2h_bytes_per_step": int(8 * batch.off[-1])}
+    plan.close()
+    res, res_rb, finite = batch_accuracy(batch)
+    line["accuracy"] = {"max_resid_over_nu": float(res.max()), "max_rowblock_resid_over_nu": float(res_rb.max()),
+                        "resid_over_nu_percentiles_50_90_99": [float(np.percentile(res, q)) for q in (50, 90, 99)],
+                        "pencils_nonfinite": int((~finite).sum()),
+                        "checker": "every column of every pencil, FP64 GEMMs on the GPU (cuBLAS via torch)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        picks = list(range(0, count, 32))           # every 32nd pencil: plain ones (even indices)
+        t0 = time.perf_counter()
+        outs = [oracle.evc(pencils[b].S, pencils[b].T, nthreads=threads) for b in picks]
+        spent = time.perf_counter() - t0
+        Fs = float(sum(flops_all(int(orders[b])) for b in picks))
+        rate = Fs / spent                            # flop/s of the oracle on the sample
+        line["cpu_baseline"] = {"value": round(count / (F / rate), 4), "unit": "pencils/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{len(picks)} pencils (every 32nd), {spent:.1f} s on {threads} threads, "
+                                          "extrapolated to the batch by sum 2n^3/3"}
+        errs = []
+        for b, (st, Vo, sco, m) in zip(picks, outs):
+            Vg = batch.view(batch.V, b).cpu().numpy().T
+            errs.append(normalised_error(Vo, Vg, column_kinds_all(pencils[b].block)))
+        line["accuracy"]["max_err_vs_oracle"] = float(max(errs))
+        line["accuracy"]["err_pencils"] = f"{len(picks)} plain pencils (every 32nd)"
+    print(json.dumps(line))
+    return 0
+
+
+def accuracy_of(St, Tt, V, pencil):
+    """Accuracy of an all-eigenvector solve, outside any timed region: the
+    residual of every column (GPU FP64 GEMMs) and the count of non-finite
+    entries of V."""
+    import torch
+    kinds = column_kinds_all(pencil.block)
+    nonfinite = int((~torch.isfinite(V)).sum().item())
+    res = gpu_residuals(St, Tt, V, kinds, pencil.lam_re, pencil.lam_im)
+    return {"max_resid_over_nu": float(res.max() / (pencil.n * 2.0 ** -53)), "resid_columns": int(res.size),
+            "nonfinite": nonfinite,
+            "checker": "relative residual of every column, FP64 GEMMs on the GPU (cuBLAS via torch)"}
+
+
+def timed_solves(pevc, St, Tt, n, prec, tile, stream, warmup, steps, V, scale, dist=None, clock_index=None):
+    """warmup untimed solves, then `steps` solves bracketed by CUDA events on
+    the solve's stream (barrier + synchronize on both sides under torchrun).
+    Returns (ms per solve, per-step kernel profiles, plan info, clocks)."""
+    import torch
+    plan = pevc.Plan(n, prec=prec, tile=tile, stream=stream)
+    plan.profile(True)
+
+    def step():
+        st, m = plan.solve_colmajor(St, Tt, n, V, scale)
+        if st:
+            raise pevc.PevcError(st, "pevc_solve")
+
+    try:
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        prof = []
+        clk = ClockSampler(clock_index if clock_index is not None else 0)
+        with clk:
+            ev0.record(stream)
+            for _ in range(steps):
+                step()
+                prof.append(plan.kernel_profile())
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1) / steps
+        info = plan.info
+    finally:
+        plan.close()
+    return ms, prof, info, clk.summary(), step
+
+
 def main():
     args = parse_args()
 
@@ -312,6 +646,8 @@ def main():
         return run_reference(args)
     if args.workload == "cplx":
         return run_complex(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -334,48 +670,23 @@ def main():
     Tt = pevc.to_device_colmajor(seed_pencil.T)
     V = torch.empty((n, n), dtype=torch.float64, device="cuda")
     scale = torch.empty(n, dtype=torch.int32, device="cuda")
-    plan = pevc.Plan(n, prec=args.prec, tile=args.tile, stream=stream)
-    plan.profile(True)
 
-    def step():
-        st, m = plan.solve_colmajor(St, Tt, n, V, scale)
-        if st:
-            raise pevc.PevcError(st, "pevc_solve")
-        return m
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    prof = []
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-            prof.append(plan.kernel_profile())
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms, prof, info, clocks, _ = timed_solves(pevc, St, Tt, n, args.prec, args.tile, stream, args.warmup,
+                                             args.steps, V, scale, dist, local)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     F = flops_all(n)
     value = F * world / (ms * 1e-3) / 1e9
-    info = plan.info
     launches = int(np.mean([p["launches"] for p in prof]))
 
     # rooflines of the dominant kernel and the other large one (CUDA events
     # around each launch, on the solve's stream)
     peaks, peak_src = load_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
     tc = info[0] == 128 and not os.environ.get("PEVC_UPDATE_KERNEL", "").startswith("m")
-    roof, roof_other = rooflines(prof, ms, n, args.prec, info[0], peaks, peak_src,
-                                 torch.cuda.get_device_properties(0).multi_processor_count, tc)
+    roof, roof_other = rooflines(prof, ms, n, args.prec, info[0], peaks, peak_src, nsm, tc)
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -386,7 +697,7 @@ def main():
                        "correction_sweeps": info[7], "parallelism": f"replicas{world}",
                        "l2": "inputs 2 x %.1f GB >> 129 MB L2, no flush" % (n * n * 8 / 1e9)},
             "eigvec_per_s": round(n * world / (ms * 1e-3), 1),
-            "gpu_launches": launches, "roofline": roof, "roofline_other": roof_other, "clocks": clk.summary()}
+            "gpu_launches": launches, "roofline": roof, "roofline_other": roof_other, "clocks": clocks}
 
     if not args.no_e2e:
         # end to end through the public API: host S, T in pinned memory, result back to host
@@ -395,11 +706,14 @@ def main():
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
         sch = torch.empty(n, dtype=torch.int32).pin_memory()
         steps_e2e = max(1, min(args.steps, 5))
+        plan = pevc.Plan(n, prec=args.prec, tile=args.tile, stream=stream)
 
         def e2e_step():
             St.copy_(Sh, non_blocking=True)
             Tt.copy_(Th, non_blocking=True)
-            step()
+            st, m = plan.solve_colmajor(St, Tt, n, V, scale)
+            if st:
+                raise pevc.PevcError(st, "pevc_solve")
             Vh.copy_(V, non_blocking=True)
             sch.copy_(scale, non_blocking=True)
 
@@ -413,19 +727,57 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+        plan.close()
         ems = float(np.median(times))   # host copies vary from step to step
         line["e2e"] = {"value": round(F * world / (ems * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
                        "ms_per_step": round(ems, 3),
                        "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + n * 4}
+        del Sh, Th, Vh, sch
+
+    extra = rank == 0 and world == 1 and not args.no_arms
+    if rank == 0:
+        line["accuracy"] = accuracy_of(St, Tt, V, seed_pencil)
+
+    # the comparison the target turns on: the plain FP64-DMMA path and the
+    # 3-slice split path with its correction sweep, timed the same way
+    if extra:
+        for prec, key, steps in (("fp64", "fp64_path", 2), ("bf16x3", "bf16x3_path", 3)):
+            if prec == args.prec:
+                continue
+            Va = torch.empty((n, n), dtype=torch.float64, device="cuda")
+            ms_a, prof_a, info_a, clk_a, _ = timed_solves(pevc, St, Tt, n, prec, 0, stream, 1, steps, Va, scale)
+            r_main, r_other = rooflines(prof_a, ms_a, n, prec, info_a[0], peaks, peak_src, nsm, info_a[0] == 128)
+            upd = r_main if r_main["kernel"].startswith("k_update") else r_other
+            line[key] = {"ms_per_step": round(ms_a, 3), "value": round(F / (ms_a * 1e-3) / 1e9, 2),
+                         "unit": "GFLOP/s", "eigvec_per_s": round(n / (ms_a * 1e-3), 1), "steps": steps,
+                         "warmup": 1, "tile": info_a[0], "slices": info_a[6], "correction_sweeps": info_a[7],
+                         "roofline_update": upd, "roofline_diag": r_other if upd is r_main else r_main,
+                         "clocks": clk_a, "accuracy": accuracy_of(St, Tt, Va, seed_pencil)}
+            del Va
+        if "fp64_path" in line:
+            line["split_speedup_over_fp64"] = round(line["fp64_path"]["ms_per_step"] / ms, 2)
 
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        r, inf = cpu_oracle_sample(seed_pencil, 20.0, threads)
+        r, inf, (sel, Vo), top = cpu_oracle_sample(seed_pencil, 20.0, threads, top=1024)
         line["cpu_baseline"] = {"value": round(r, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{inf['columns']} eigenvectors of the same pencil (stratified over the "
                                           f"diagonal), {inf['seconds']} s on {threads} threads (OpenMP over "
                                           "eigenvectors), extrapolated to all n by sum c^2"}
-    plan.close()
+        # the GPU's columns against the oracle's: the timed sample and every
+        # eigenvector of the first 1024 diagonal positions
+        errs = []
+        for s_, Vo_ in ((sel, Vo), top):
+            cols, kinds = selected_columns(seed_pencil.block, s_)
+            Vg = V[torch.as_tensor(cols, device="cuda")].cpu().numpy().T
+            errs.append(normalised_error(Vo_, Vg, kinds))
+        line["accuracy"]["max_err_vs_oracle"] = float(max(errs))
+        line["accuracy"]["err_columns"] = (f"{inf['columns']} stratified eigenvectors and every eigenvector of the "
+                                           "first 1024 diagonal positions, normalised at the oracle's largest entry")
+        r1, inf1, _, _ = cpu_oracle_sample(seed_pencil, 6.0, 1)
+        line["cpu_baseline_1core"] = {"value": round(r1, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"{inf1['columns']} eigenvectors (stratified), {inf1['seconds']} s "
+                                                "on one thread (the xTGEVC analogue), extrapolated by sum c^2"}
     if rank == 0:
         kp = prof[-1]
         print("breakdown (last step): " + ", ".join(

@@ -32,8 +32,9 @@
 // so that the FP64 and integer pipes share the work), one FP64 subtraction;
 // new column maxima (rounded-up 32-bit keys) by one warp reduction per column.
 // Every wait is bounded (SM clock cycles): a wait that runs out sets
-// PEVC_ERR_TIMEOUT in the status word and the CTA winds down (every role runs
-// out of bounded waits, tensor memory is freed).
+// PEVC_ERR_TIMEOUT in the status word and the CTA winds down: every role runs
+// out of bounded waits, the producer waits (bounded) for the loads it issued,
+// the MMA issuer for the MMAs it issued, and tensor memory is freed.
 #include <cuda.h>
 
 #include "split.cuh"
@@ -151,7 +152,8 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   uint64_t* empty = full + G::stages;
   uint64_t* tfull = empty + G::stages;   // [2] accumulator buffer complete
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained (its group's warps arrive)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* drain = tempty + 2;          // MMAs in flight completed (failure path only)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
   __shared__ int4 s_col[kTcRing][NCOL];            // column scales of the next output tiles (a ring)
   __shared__ uint64_t s_sfull[kTcRing], s_sempty[kTcRing];
@@ -169,6 +171,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   if (tid == 0) {
     for (int s = 0; s < G::stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kTcEpiWarps); }
+    mbar_init(drain, 1);
     for (int r = 0; r < kTcRing; ++r) { mbar_init(&s_sfull[r], 1); mbar_init(&s_sempty[r], 1); }
     s_fail = 0;
     s_stop[0] = s_stop[1] = 0;
@@ -185,7 +188,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
     // ---------------------------------------------------------------- TMA
     if (lane == 0) {
       int s = 0;
-      uint32_t ph = 0;
+      uint32_t ph = 0, used = 0, last_ph = 0;   // per stage: loaded at least once, parity of its last load
       for (int t = blockIdx.x; t < total && !*fail; t += gridDim.x) {
         const int k = tt.k_lo + t / tt.nchunks;
         const int ch = tt.chunk_first + t % tt.nchunks;
@@ -197,9 +200,17 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           unsigned char* dst = smem + s * G::stage;
           tma_load_3d(dst, &tmA, kk * kTcK, 0, a_plane, &full[s]);
           tma_load_3d(dst + NS * G::a_slice, &tmB, kk * kTcK, c0, 0, &full[s]);
+          used |= 1u << s;
+          last_ph = (last_ph & ~(1u << s)) | (ph << s);
           if (++s == G::stages) { s = 0; ph ^= 1u; }
         }
       }
+      // after a failure, the loads already issued land before shared memory
+      // is released (a load the MMA warp consumed has completed its phase,
+      // so its wait returns at once)
+      if (*fail)
+        for (int q = 0; q < G::stages; ++q)
+          if (used & (1u << q)) mbar_wait_cycles(&full[q], (last_ph >> q) & 1u, kTcWait);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
@@ -236,6 +247,12 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
         }
         if (*fail) break;
         tc_commit(&tfull[buf]);             // the tile's accumulators are complete
+      }
+      // after a failure, every MMA already issued completes before tensor
+      // memory is freed: one more commit, to its own barrier, and a bounded wait
+      if (*fail) {
+        tc_commit(drain);
+        mbar_wait_cycles(drain, 0u, kTcWait);
       }
     }
   } else if (warp == kTcScalesWarp) {

@@ -61,7 +61,7 @@ def test_reference_line_keeps_the_contract(monkeypatch, capsys):
 
     def fake_sample(pencil, budget, threads):
         calls.append((pencil.n, budget, threads))
-        return 12.5, {"columns": 3, "seconds": 0.1, "work_flops": 1e9}
+        return 12.5, {"columns": 3, "seconds": 0.1, "work_flops": 1e9}, None, None
 
     monkeypatch.setattr(bench, "cpu_oracle_sample", fake_sample)
     assert bench.run_reference(_ref_args()) == 0
@@ -70,7 +70,8 @@ def test_reference_line_keeps_the_contract(monkeypatch, capsys):
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["value"] == 12.5 and line["unit"] == "GFLOP/s" and line["higher_is_better"] is True
     assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
-    assert abs(line["ms_per_step"] - bench.flops_all(256) / 12.5e9 * 1e3) < 0.1
+    assert line["ms_per_step"] == 100.0                                  # the sample's own time per step
+    assert abs(line["ms_per_full_solve_extrapolated"] - bench.flops_all(256) / 12.5e9 * 1e3) < 0.1
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == 12.5 and cb["cores"] >= 1 and cb["sample"]
     e2e = line["e2e"]
@@ -89,8 +90,11 @@ def test_reference_other_ranks_exit_without_work(monkeypatch, capsys):
 def test_cpu_oracle_sample_times_a_stratified_subset():
     import pencilgen
     p = pencilgen.make_pencil(200, 31)
-    rate, info = bench.cpu_oracle_sample(p, 0.05, 2)
+    rate, info, (sel, V), top = bench.cpu_oracle_sample(p, 0.05, 2, top=17)
     assert rate > 0 and 1 <= info["columns"] <= 200
+    cols, kinds = bench.selected_columns(p.block, sel)
+    assert V.shape == (200, cols.size) and top[1].shape[1] == bench.selected_columns(p.block, top[0])[0].size
+    assert top[0][:17].all() and not top[0][18:].any()
     # the work is the sum of 2 (c+1)^2 over the sampled columns (both columns of a pair)
     assert 0 < info["work_flops"] <= bench.flops_all(200) * 1.01
 
@@ -116,3 +120,73 @@ def test_parse_args_defaults_and_complex_workload():
     # 8 n^3 / 3 to leading order; exact for the sum over columns of 8 c^2
     assert bench.flops_cplx(3) == 8.0 * (0 + 1 + 4)
     assert abs(bench.flops_cplx(20000) / (8 * 20000 ** 3 / 3) - 1) < 1e-4
+
+
+def test_gpu_residual_checker_matches_the_oracle_residuals():
+    """The benchmark's all-column residual (written for the GPU, run here on
+    torch's CPU tensors) against oracle/check.py's, on the oracle's own
+    eigenvectors of a plain and a stress pencil; a planted error in one
+    column is seen by both."""
+    import torch
+    import oracle
+    import pencilgen
+    from oracle import check
+    for n, stress in ((150, False), (130, True)):
+        p = pencilgen.make_pencil(n, 4401 + n, stress=stress)
+        st, V, sc, m = oracle.evc(p.S, p.T)
+        assert st == 0 and m == n
+        _, blk, a, b, beta, _ = oracle.eigpairs(p.S, p.T)
+        kinds, pos = check.column_kinds(blk)
+        ref = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta)
+        to_t = lambda A: torch.from_numpy(np.ascontiguousarray(np.asarray(A).T))
+        got = bench.gpu_residuals(to_t(p.S), to_t(p.T), to_t(V), bench.column_kinds_all(p.block),
+                                  p.lam_re, p.lam_im, block_cols=37)
+        assert np.array_equal(bench.column_kinds_all(p.block), kinds)
+        # the generator's eigenvalue differs from the rounded block's by O(u)
+        assert np.all(np.abs(got - ref) <= 4 * n * check.U + 1e-3 * ref), (got - ref).max()
+        V2 = V.copy()
+        c = n // 2
+        V2[c // 2, c] += 1e-6 * np.abs(V2[:, c]).max()
+        bad = bench.gpu_residuals(to_t(p.S), to_t(p.T), to_t(V2), kinds, p.lam_re, p.lam_im, block_cols=64)
+        assert bad[c] > 1e3 * n * check.U and np.delete(bad, [c - 1, c, c + 1]).max() <= 100 * n * check.U
+
+
+def test_normalised_error_is_scale_free_and_sees_a_changed_entry():
+    import pencilgen
+    import oracle
+    p = pencilgen.make_pencil(60, 4501)
+    st, V, sc, m = oracle.evc(p.S, p.T)
+    kinds = bench.column_kinds_all(p.block)
+    W = V * -3.5                                   # a real multiple of every column
+    assert bench.normalised_error(V, W, kinds) <= 1e-15
+    q = int(np.flatnonzero(kinds == 1)[0])
+    Z = (V[:, q] + 1j * V[:, q + 1]) * (0.3 - 2j)  # a complex multiple of one pair
+    W[:, q], W[:, q + 1] = Z.real, Z.imag
+    assert bench.normalised_error(V, W, kinds) <= 1e-14
+    W[0, 5] += 1e-7
+    assert bench.normalised_error(V, W, kinds) >= 1e-8
+
+
+def test_row_block_residual_sees_an_error_that_huge_tiles_hide():
+    """On a stress pencil (a 1e100 tile swamps ||S||_inf) an error planted in
+    rows whose block holds no huge entry is invisible to the global residual
+    and plain in the row-block one; the oracle's own vectors pass both."""
+    import torch
+    import oracle
+    import pencilgen
+    n = 192
+    p = pencilgen.make_pencil(n, 4601, stress=True)
+    S = p.S.copy()
+    S[0:64, 128:192] *= 1e100                   # rows 0..63 hold the only huge tile
+    st, V, sc, m = oracle.evc(S, p.T)
+    assert st == 0
+    kinds = bench.column_kinds_all(p.block)
+    to_t = lambda A: torch.from_numpy(np.ascontiguousarray(np.asarray(A).T))
+    good = bench.gpu_residuals(to_t(S), to_t(p.T), to_t(V), kinds, p.lam_re, p.lam_im, row_block=64)
+    assert good.max() <= 100 * n * 2.0 ** -53
+    c = 120 if kinds[120] != 2 else 121
+    V2 = V.copy()
+    V2[c - 40, c] += 1e-6 * np.abs(V2[:, c]).max()  # row 80: block 1, no huge entry
+    glob = bench.gpu_residuals(to_t(S), to_t(p.T), to_t(V2), kinds, p.lam_re, p.lam_im)
+    rb = bench.gpu_residuals(to_t(S), to_t(p.T), to_t(V2), kinds, p.lam_re, p.lam_im, row_block=64)
+    assert glob[c] <= 100 * n * 2.0 ** -53 < 1e3 * n * 2.0 ** -53 < rb[c]

@@ -75,3 +75,60 @@ def test_batched_matches_single_solves_and_oracle(pevc_lib, prec, tol):
     finally:
         plan.close()
         single.close()
+
+
+_ORACLE_CACHE = {}
+
+
+def _config4_oracle(pencils):
+    """The oracle's eigenvectors of the plain (even-index) pencils of the
+    batched workload, computed once per session."""
+    if not _ORACLE_CACHE:
+        threads = os.cpu_count() or 1
+        for b in range(0, len(pencils), 2):
+            st, Vo, sco, m = oracle.evc(pencils[b].S, pencils[b].T, nthreads=threads)
+            assert st == 0
+            _ORACLE_CACHE[b] = (Vo, sco)
+    return _ORACLE_CACHE
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x5", 1e-8)])
+def test_batched_config4_workload(pevc_lib, prec, tol):
+    """The batched workload at its stated size: 1024 pencils, n log-uniform in
+    [32, 2048], odd indices stress pencils, all eigenvectors, one call.  Every
+    pencil: finite, residual <= 100 n u over every column (also per 64-row
+    block with the block's own norms); plain pencils within tol of the oracle
+    componentwise.  The per-pencil error distribution is printed."""
+    import sys
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    orders = pencilgen.batch_orders()
+    assert orders.size == 1024 and orders.min() >= 32 and orders.max() <= 2048
+    pencils = [pencilgen.batch_pencil(b, int(n)) for b, n in enumerate(orders)]
+    assert all(p.stress == bool(b % 2) for b, p in enumerate(pencils))
+    batch = bench.Batch(pencils, pevc_lib)
+    plan = pevc_lib.Plan(int(orders.max()), prec=prec, batch_max=len(pencils))
+    try:
+        m_out = batch.solve(plan)
+    finally:
+        plan.close()
+    torch.cuda.synchronize()
+    assert m_out == [int(n) for n in orders]
+    res, res_rb, finite = bench.batch_accuracy(batch)
+    assert finite.all()
+    ref = _config4_oracle(pencils)
+    errs, dsc = [], 0
+    for b, (Vo, sco) in ref.items():
+        Vg = batch.view(batch.V, b).cpu().numpy().T
+        kinds, _ = check.column_kinds(pencils[b].block)
+        errs.append(check.compare_normalised(Vo, Vg, kinds)[0])
+        sc = batch.scale[int(batch.soff[b]):int(batch.soff[b + 1])].cpu().numpy()
+        dsc = max(dsc, int(np.abs(sc.astype(np.int64) - sco.astype(np.int64)).max()))
+    errs = np.asarray(errs)
+    q = lambda a: ", ".join(f"{x:.2e}" for x in np.percentile(a, [50, 90, 99, 100]))
+    print(f"config4 {prec}: residual/(n u) p50/p90/p99/max {q(res)}; per-block {q(res_rb)}; "
+          f"plain pencils' error vs oracle {q(errs)}; scale exponents within {dsc}")
+    assert res.max() <= 100.0 and res_rb.max() <= 100.0
+    assert errs.max() <= tol
+    assert dsc <= 1
