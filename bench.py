@@ -81,7 +81,8 @@ def rooflines(prof, ms, n, prec, tile, peaks, peak_src, nsm, tc_kernel=True):
                "peak": round(nsm * 2 * 2 * clk / 1e12, 4),
                "peak_source": f"FP64 pipe: {nsm} SMs x 2 lanes/clk x 2 flops x {clk / 1e6:.0f} MHz "
                               "(DMMA and DFMA share it on GB300)",
-               "kernel": "k_update_f64"}
+               "kernel": "k_update_f64" if dg_n else
+                         "k_dag (FP64 updates and diagonal solves in one persistent launch)"}
     else:
         pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         upd = {"bound": "tensor", "unit": "TFLOP/s",

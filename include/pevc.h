@@ -153,7 +153,9 @@ int pevc_plan_info(pevc_plan_t plan, int *info);
 /*
  * pevc_last_stats -- host double[8] timing/work figures of the last solve on
  * this plan: {total ms (device, CUDA events), prepass ms, first-pass ms,
- * correction ms, postpass ms, tiles M, kernel launches, 0}.
+ * correction ms, postpass ms, tiles M, kernel launches, scheduler (1: the
+ * task graph walked on the device by one persistent launch, 0: stage by
+ * stage from the host)}.
  */
 int pevc_last_stats(pevc_plan_t plan, double *stats);
 
@@ -359,6 +361,20 @@ int pevc_backtransform_cplx(pevc_plan_t plan, const double *Z, int ldz, int n, c
  * bound ran out), -i for an invalid argument or PEVC_ERR_CUDA.
  */
 int pevc_watchdog_selftest(pevc_plan_t plan, int withhold, long long cycles);
+
+/*
+ * pevc_scheduler_selftest -- exercises the bounded dependence wait of the
+ * device-side task-graph scheduler (the persistent walk of Algorithm 1's task
+ * graph, Section 3 and Section 5.3, that FP64 plans use): one walk of a
+ * one-task list whose task waits on a ready counter.
+ *   withhold  0: the counter is set first, the task runs at once
+ *             1: nothing sets it; the wait gives up after `cycles`, records
+ *                a timeout in the plan's status word and ends the walk
+ *   cycles    the bound, 0 < cycles <= 4e9 (about 2 s of SM clock)
+ * Synchronises on return.  Returns 0, PEVC_ERR_TIMEOUT (the bound ran out),
+ * -i for an invalid argument or PEVC_ERR_CUDA.  The plan stays usable.
+ */
+int pevc_scheduler_selftest(pevc_plan_t plan, int withhold, long long cycles);
 
 #ifdef __cplusplus
 }

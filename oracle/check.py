@@ -197,3 +197,23 @@ def cplx_left_residuals(S, T, U, alpha, beta):
         res[c] = np.abs(r).max() / den if den > 0 else np.inf
     return res
 
+
+
+def perturbation_sensitivity(S, T, Vref, kinds, evc, seed: int, eps: float = 2.0 ** -52):
+    """Per eigenvector: the componentwise change of the normalised vectors
+    Vref of (S, T) when every row of S and T is perturbed by eps times that
+    row's largest entry (random signs, on the non-zero pattern only, so the
+    Schur structure and T's diagonal 2x2 blocks stay), recomputed with evc
+    (the oracle's solver).  A measured stand-in for cond * eps under
+    row-normwise perturbations, the kind blocked updates make; a second
+    backward-stable FP64 method may differ from the oracle by a small
+    multiple of it (eps = u)."""
+    rng = np.random.default_rng(seed)
+    pert = []
+    for A in (np.asarray(S), np.asarray(T)):
+        rowmax = np.abs(A).max(axis=1, keepdims=True)
+        pert.append(A + (A != 0) * rng.choice([-1.0, 1.0], A.shape) * eps * rowmax)
+    st, V2, _, _ = evc(pert[0], pert[1])
+    if st != 0:
+        raise RuntimeError(f"perturbed pencil: status {st}")
+    return compare_normalised(Vref, V2, kinds)[1]

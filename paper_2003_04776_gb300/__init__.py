@@ -81,11 +81,14 @@ _lib.pevc_backtransform_cplx.argtypes = [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _i,
 _lib.pevc_backtransform_cplx.restype = _i
 _lib.pevc_watchdog_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
 _lib.pevc_watchdog_selftest.restype = _i
+_lib.pevc_scheduler_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
+_lib.pevc_scheduler_selftest.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
            "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
-           "pevc_solve_cplx_left", "pevc_backtransform_cplx", "pevc_watchdog_selftest")
+           "pevc_solve_cplx_left", "pevc_backtransform_cplx", "pevc_watchdog_selftest",
+           "pevc_scheduler_selftest")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -214,6 +217,12 @@ def pevc_watchdog_selftest(plan, withhold: int, cycles: int) -> int:
     """One bounded device wait, its arrival withheld or not.  Returns the
     status (0, or ERR_TIMEOUT when the bound ran out)."""
     return _lib.pevc_watchdog_selftest(plan, int(withhold), int(cycles))
+
+
+def pevc_scheduler_selftest(plan, withhold: int, cycles: int) -> int:
+    """The scheduler's bounded dependence wait (withhold=1: nothing meets the
+    dependence, the wait gives up after `cycles`).  Returns the status."""
+    return _lib.pevc_scheduler_selftest(plan, int(withhold), int(cycles))
 
 
 # ------------------------------------------------------------ torch wrapper

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "cplx.cuh"
+#include "dag.cuh"
 #include "sched.cuh"
 #include "split.cuh"
 
@@ -102,6 +103,21 @@ struct pevc_plan_s {
   int32_t* lsc = nullptr;
   // complex pencils (allocated by the first pevc_solve_cplx)
   CplxWork* cx = nullptr;
+  // device-side task-graph scheduler (dag.cuh), the walk of FP64 plans:
+  // the pencil record, the task list, the ready counters, the update
+  // sub-chunks and the ticket / abort pair
+  bool dag = false;
+  DagPencil* d_pen = nullptr;
+  DagPencil* h_pen = nullptr;
+  int4* d_tasks = nullptr;
+  int4* h_tasks = nullptr;
+  long long task_cap = 0;
+  int* d_cnt = nullptr;
+  size_t cnt_cap = 0;
+  int* d_sub = nullptr;
+  int* h_sub = nullptr;
+  int sub_cap = 0;
+  int* d_ticket = nullptr;
 };
 
 namespace {
@@ -186,6 +202,12 @@ void free_plan(pevc_plan_t p) {
   for (void* d : ldev)
     if (d) cudaFree(d);
   cplx_free(p->cx);
+  void* dagd[] = {p->d_pen, p->d_tasks, p->d_cnt, p->d_sub, p->d_ticket};
+  for (void* d : dagd)
+    if (d) cudaFree(d);
+  void* dagh[] = {p->h_pen, p->h_tasks, p->h_sub};
+  for (void* h : dagh)
+    if (h) cudaFreeHost(h);
   if (p->bt_kind) cudaFree(p->bt_kind);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
   delete p;
@@ -336,6 +358,56 @@ int structure_end(pevc_plan_t p, int n, bool has_sel, Structure& st) {
   return analyse(p, n, has_sel, st);
 }
 
+// Bound of every dependence wait of the scheduler, in SM clock cycles (about
+// 5 s at 2 GHz: far above any wait of a walk that progresses).
+constexpr long long kDagWaitCycles = 10000000000LL;
+
+// The task graph of one pencil on the device (dag.cuh): update sub-chunks and
+// the task list in walk order, built here from the host structure; ready
+// counters zeroed; one persistent launch.
+int dag_enqueue(pevc_plan_t p, const Problem& P, const Structure& st, cudaStream_t s) {
+  const int M = st.M;
+  int* h_first = p->h_sub;
+  int* h_c0 = h_first + (p->Mmax + 1);
+  int* h_nc = h_c0 + p->sub_cap;
+  int nsub_max = 0;
+  const int ns = dag_subchunks(M, p->h_cstart, p->h_kind, h_first, h_c0, h_nc, p->sub_cap, &nsub_max);
+  if (ns < 0) return PEVC_ERR_CUDA;
+  const int cap = (int)std::min<long long>(p->task_cap, INT32_MAX);
+  int cnt = dag_stage_tasks(0, M, M, p->h_dcfirst, h_first, p->h_tasks, 0, cap);
+  double flops = 0.0;
+  for (int i = M - 1; i >= 1 && cnt >= 0; --i) {
+    cnt = dag_stage_tasks(0, M, i, p->h_dcfirst, h_first, p->h_tasks, cnt, cap);
+    flops += 2.0 * p->h_toff[i] * (double)(P.m - p->h_cstart[i]) * 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
+  }
+  if (cnt < 0) return PEVC_ERR_CUDA;
+  const size_t tiles = (size_t)M * (M + 1) / 2;
+  nsub_max = std::max(nsub_max, 1);
+  if (tiles * (2 + (size_t)nsub_max) > p->cnt_cap) return PEVC_ERR_CUDA;
+  DagPencil& hp = *p->h_pen;
+  hp.P = P;
+  hp.dcnt = p->d_cnt;
+  hp.utile = p->d_cnt + tiles;
+  hp.usub = p->d_cnt + 2 * tiles;
+  hp.sub_first = p->d_sub;
+  hp.sub_c0 = p->d_sub + (p->Mmax + 1);
+  hp.sub_nc = p->d_sub + (p->Mmax + 1) + p->sub_cap;
+  hp.nsub_max = nsub_max;
+  CK(cudaMemcpyAsync(p->d_sub, h_first, (size_t)(M + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (ns > 0) {
+    CK(cudaMemcpyAsync((void*)hp.sub_c0, h_c0, (size_t)ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void*)hp.sub_nc, h_nc, (size_t)ns * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(p->d_tasks, p->h_tasks, (size_t)cnt * sizeof(int4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->d_pen, p->h_pen, sizeof(DagPencil), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(p->d_cnt, 0, tiles * (2 + (size_t)nsub_max) * sizeof(int), s));
+  CK(cudaMemsetAsync(p->d_ticket, 0, 2 * sizeof(int), s));
+  p->prof.begin(s);
+  CK(launch_dag(p->d_pen, p->d_tasks, cnt, p->d_ticket, p->d_ticket + 1, kDagWaitCycles, dag_grid(p->nsm), s));
+  p->prof.end(s, 0, flops);
+  return 0;
+}
+
 // Phase 3: everything else, stream-ordered.  With check_prepass the call reads
 // the status after the pre-pass and returns early for a bad pencil; without it
 // the whole graph is enqueued and the status is read once at the end (the
@@ -408,7 +480,12 @@ int solve_enqueue(pevc_plan_t p, const double* S, int lds, const double* T, int 
         return e;
       }
     } ops(P, p);
-    CK(walk_dag(st.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+    if (p->dag) {
+      int rc = dag_enqueue(p, P, st, s);
+      if (rc) return rc;
+    } else {
+      CK(walk_dag(st.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+    }
     CK(cudaEventRecord(p->ev[2], s));
     CK(cudaEventRecord(p->ev[3], s));
   } else {
@@ -458,6 +535,7 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   p->stats[4] = post;
   p->stats[5] = st.M;
   p->stats[6] = p->prof.launches;
+  p->stats[7] = (p->dag && p->prec == PEVC_FP64) ? 1.0 : 0.0;
   for (double& x : p->kprof) x = 0.0;
   for (int q = 0; q < p->prof.used; ++q) {
     float t = 0.0f;
@@ -617,6 +695,26 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
       if (cudaEventCreateWithFlags(&p->sev[q], cudaEventDisableTiming) != cudaSuccess) rc = PEVC_ERR_CUDA;
   }
   if (!rc && prec != PEVC_FP64) rc = split_alloc(p->split, n_max, p->tb, p->Mmax, prec);
+  if (!rc) {
+    // the scheduler: FP64 plans walk the task graph on the device unless
+    // PEVC_SCHED=stage asks for the stage walk; every plan keeps the small
+    // records of the scheduler's self-test
+    const char* sch = getenv("PEVC_SCHED");
+    p->dag = prec == PEVC_FP64 && !(sch && sch[0] == 's');
+    const size_t tiles = M * (M + 1) / 2;
+    const int nsb = dag_nsub_bound(p->tb);
+    p->task_cap = p->dag ? dag_task_bound(p->Mmax, p->tb) : 1;
+    p->cnt_cap = p->dag ? tiles * (size_t)(2 + nsb) : 1;
+    p->sub_cap = p->Mmax * nsb;
+    rc = rc ? rc : dalloc(&p->d_pen, 1);
+    rc = rc ? rc : halloc(&p->h_pen, 1);
+    rc = rc ? rc : dalloc(&p->d_tasks, (size_t)p->task_cap);
+    rc = rc ? rc : halloc(&p->h_tasks, (size_t)p->task_cap);
+    rc = rc ? rc : dalloc(&p->d_cnt, p->cnt_cap);
+    rc = rc ? rc : dalloc(&p->d_sub, (size_t)(p->Mmax + 1) + 2 * (size_t)p->sub_cap);
+    rc = rc ? rc : halloc(&p->h_sub, (size_t)(p->Mmax + 1) + 2 * (size_t)p->sub_cap);
+    rc = rc ? rc : dalloc(&p->d_ticket, 2);
+  }
   if (!rc && batch_max > 1) {
     // child plans for concurrent pencils, as many as about 4 GB of workspace
     // allows (at most 8)
@@ -836,6 +934,26 @@ int pevc_watchdog_selftest(pevc_plan_t plan, int withhold, long long cycles) {
   if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
   CK(cudaMemsetAsync(plan->status, 0, sizeof(unsigned), plan->stream));
   CK(launch_watchdog_probe(plan->status, withhold, cycles, plan->stream));
+  unsigned bits = 0;
+  const int rc = read_status(plan, &bits);
+  if (rc) return rc;
+  return (bits & kStTimeout) ? PEVC_ERR_TIMEOUT : 0;
+}
+
+int pevc_scheduler_selftest(pevc_plan_t plan, int withhold, long long cycles) {
+  if (!plan) return -1;
+  if (withhold != 0 && withhold != 1) return -2;
+  if (cycles <= 0 || cycles > 4000000000LL) return -3;   // at most about 2 s of SM clock
+  if (cudaSetDevice(plan->dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  // a pencil record whose only use is the probe's counter and status word
+  DagPencil& hp = *plan->h_pen;
+  hp = DagPencil{};
+  hp.P.status = plan->status;
+  hp.dcnt = plan->d_cnt;
+  cudaStream_t s = plan->stream;
+  CK(cudaMemsetAsync(plan->status, 0, sizeof(unsigned), s));
+  CK(cudaMemcpyAsync(plan->d_pen, plan->h_pen, sizeof(DagPencil), cudaMemcpyHostToDevice, s));
+  CK(launch_dag_selftest(plan->d_pen, plan->d_tasks, plan->d_ticket, plan->d_ticket + 1, withhold, cycles, s));
   unsigned bits = 0;
   const int rc = read_status(plan, &bits);
   if (rc) return rc;

@@ -10,6 +10,34 @@ namespace pevc {
 
 constexpr double kUlp = 0x1p-53;
 
+// Shared memory of one diagonal-tile task (a chunk of at most CB columns of a
+// tile of order <= kMaxTile), in one struct so that a persistent kernel can
+// overlay it with the memory of its other tasks.
+template <int CB>
+struct DiagSmem {
+  double2 PQ[2][CB];                 // per block column, per column: (P, Q)
+  double a[CB], b[CB], beta[CB], y[CB];   // per unit (eigenvector)
+  double W[2][CB], piv[2][CB];
+  double Sd[kMaxTile][2], Td[kMaxTile][2], tcS[kMaxTile], tcT[kMaxTile];
+  // right-hand-side-independent factors per (block, unit): 1x1 blocks the
+  // inverted pivot (1 double real, 2 complex), 2x2 blocks the LU factors
+  // (4 doubles real, 8 complex) -- at most 2 doubles per row and column
+  double pre[2 * kMaxTile * CB];
+  double tn[kMaxTile][CB];           // ProtectUpdate's t per (block, unit)
+  double nc[2][4][kMaxTile];         // the next block's S and T columns (double buffered)
+  unsigned long long key[CB];        // column maxima
+  int lc[CB];                        // local column of chunk column t
+  int tip[CB], e[CB], act[CB];       // per unit
+  int sh[CB], anysh;                 // per column
+  int boff[kMaxTile];                // offset of a block's factors in pre
+  int nb, n1;
+  short bs[kMaxTile];
+  short ep[kMaxTile][CB];            // ilogb of the pivot (or u22) magnitude
+  unsigned char bz[kMaxTile];
+  unsigned char bord[kMaxTile];      // block indices, the 1x1 blocks first
+  unsigned char pf[kMaxTile][CB];    // 2x2 pivot position pi | pj << 1
+};
+
 struct ColStep {
   double P[2][2];   // [block col][pair member]: beta * w
   double Q[2][2];   //                          : Re/Im of alpha * w

@@ -1,6 +1,8 @@
 """Builds the kernel emulation library for the tests -- TEST INFRASTRUCTURE.
 
 The real-pencil path (host driver, pre-pass, diagonal solves, FP64 updates,
+the task-graph scheduler (its CTAs run one after another, so the first takes
+every task, in an order where each one's dependences are already met),
 the split-precision path with its mma.sync update, post-pass, left flips) and
 the complex-pencil path are preprocessed from the library's CUDA sources into
 host C++ (launch syntax into emu::launch calls, dynamic shared memory onto the
@@ -23,7 +25,10 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_2003_04776_gb300", "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpevc_emu.so")
-FILES = ["api.cu", "prepass.cu", "diag.cu", "update_f64.cu", "post.cu", "left.cu", "cplx.cu", "split.cu"]
+FILES = ["api.cu", "prepass.cu", "diag.cu", "dag.cu", "update_f64.cu", "post.cu", "left.cu", "cplx.cu", "split.cu"]
+# headers that hold kernel code with PTX: converted like the sources, and
+# included from the build directory
+HEADERS = ["diag_tile.cuh"]
 
 # split.cu's PTX helpers, replaced by their models in cuda_runtime.h
 SPLIT_HELPERS = {
@@ -60,7 +65,8 @@ def _convert(src: str, name: str) -> str:
     if name == "split.cu":
         for marker, new_def in SPLIT_HELPERS.items():
             src = _replace_function(src, marker, new_def)
-    src = re.sub(r'#include "([\w.]+)"', lambda m: f'#include "{CSRC}/{m.group(1)}"', src)
+    src = re.sub(r'#include "([\w.]+)"',
+                 lambda m: f'#include "{BUILD if m.group(1) in HEADERS else CSRC}/{m.group(1)}"', src)
     src = re.sub(r"extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];",
                  r"\1* \2 = reinterpret_cast<\1*>(emu::dyn_smem);", src)
     src = re.sub(r"\b(k_\w+(?:<[^<>()]*>)?)<<<", r"emu::launch(\1, ", src)
@@ -162,6 +168,9 @@ def build() -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     srcs = []
+    for f in HEADERS:
+        with open(os.path.join(BUILD, f), "w") as fh:
+            fh.write(_convert(open(os.path.join(CSRC, f)).read(), f))
     for f in FILES:
         out = os.path.join(BUILD, f.replace(".cu", ".cpp"))
         with open(out, "w") as fh:

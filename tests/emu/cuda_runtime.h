@@ -180,6 +180,9 @@ inline T min(T a, T b) { return a < b ? a : b; }
 inline unsigned atomicOr(unsigned* a, unsigned v) { return std::atomic_ref<unsigned>(*a).fetch_or(v); }
 inline int atomicOr(int* a, int v) { return std::atomic_ref<int>(*a).fetch_or(v); }
 inline int atomicAdd(int* a, int v) { return std::atomic_ref<int>(*a).fetch_add(v); }
+inline int atomicExch(int* a, int v) { return std::atomic_ref<int>(*a).exchange(v); }
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+inline void __nanosleep(unsigned) {}
 inline unsigned atomicAdd(unsigned* a, unsigned v) { return std::atomic_ref<unsigned>(*a).fetch_add(v); }
 inline int atomicMax(int* a, int v) {
   std::atomic_ref<int> r(*a);

@@ -593,3 +593,33 @@ def test_column_bound_covers_the_row_above_the_diagonal():
     st, blk, a, b, beta, _ = oracle.eigpairs(S, T)
     kinds, pos = check.column_kinds(blk)
     assert check.residuals(S, T, V, kinds, pos, a, b, beta).max() <= 100 * 3 * check.U
+
+
+def test_conditioning_bound_holds_for_an_independent_fp64_method():
+    """The conditioning-relative bar of the batched workload's parity test
+    (per eigenvector: max(1e-10, 16 * sensitivity to a 2^-52 row-normwise
+    perturbation)) admits LAPACK's own eigenvectors (dggev, through scipy),
+    a backward-stable FP64 method independent of the oracle, on batched
+    pencils whose vectors are among the worse conditioned; and a planted
+    error of 1e-8 in one entry is outside it."""
+    import scipy.linalg as sl
+    orders = pencilgen.batch_orders()
+    for b in (478, 1006, 388):
+        p = pencilgen.batch_pencil(b, int(orders[b]))
+        st, Vo, sco, m = oracle.evc(p.S, p.T, nthreads=os.cpu_count() or 1)
+        assert st == 0
+        kinds, pos = check.column_kinds(p.block)
+        sens = check.perturbation_sensitivity(p.S, p.T, Vo, kinds,
+                                              lambda S, T: oracle.evc(S, T, nthreads=os.cpu_count() or 1), 7700 + b)
+        bound = np.maximum(1e-10, 16.0 * sens)
+        w, VR = sl.eig(p.S, p.T)
+        ref, cols = check.as_complex(Vo, kinds)
+        lam = p.lam_re + 1j * p.lam_im
+        for q, (z, c) in enumerate(zip(ref, cols)):
+            x = VR[:, int(np.argmin(np.abs(w - lam[pos[c]])))]
+            i = int(np.argmax(np.abs(z)))
+            assert np.abs(x / x[i] - z / z[i]).max() <= bound[q], (b, c)
+        assert sens.max() < 1e-8
+        V2 = Vo.copy()
+        V2[0, -1] += 1e-8 * np.abs(V2[:, -1]).max()
+        assert check.compare_normalised(Vo, V2, kinds)[1][-1] > bound[-1]
