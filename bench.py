@@ -748,7 +748,7 @@ def main():
             Va = torch.empty((n, n), dtype=torch.float64, device="cuda")
             ms_a, prof_a, info_a, clk_a, _ = timed_solves(pevc, St, Tt, n, prec, 0, stream, 1, steps, Va, scale)
             r_main, r_other = rooflines(prof_a, ms_a, n, prec, info_a[0], peaks, peak_src, nsm, info_a[0] == 128)
-            upd = r_main if r_main["kernel"].startswith("k_update") else r_other
+            upd = r_main if r_main["kernel"].startswith(("k_update", "k_dag")) else r_other
             line[key] = {"ms_per_step": round(ms_a, 3), "value": round(F / (ms_a * 1e-3) / 1e9, 2),
                          "unit": "GFLOP/s", "eigvec_per_s": round(n / (ms_a * 1e-3), 1), "steps": steps,
                          "warmup": 1, "tile": info_a[0], "slices": info_a[6], "correction_sweeps": info_a[7],

@@ -118,6 +118,26 @@ struct pevc_plan_s {
   int* h_sub = nullptr;
   int sub_cap = 0;
   int* d_ticket = nullptr;
+  // batched solves of FP64 plans on the scheduler: every pencil's workspace,
+  // structure, counters and record are slices of these pools (bdag)
+  bool bdag = false;
+  unsigned char* b_work = nullptr;      // augmented tiles, exponents, norms, eigenvalues
+  size_t b_work_bytes = 0;
+  unsigned char* b_strc = nullptr;      // structure arrays (device) ...
+  unsigned char* h_b_strc = nullptr;    // ... and their pinned host copy
+  size_t b_strc_bytes = 0;
+  int* b_cnt = nullptr;                 // ready counters
+  size_t b_cnt_ints = 0;
+  double* b_subd = nullptr;             // subdiagonals [batch_max * n_max]
+  double* h_b_subd = nullptr;
+  int32_t* h_b_sel = nullptr;           // selections [batch_max * n_max]
+  unsigned* b_status = nullptr;         // [batch_max]
+  double* b_gmax = nullptr;             // [batch_max]
+  DagPencil* b_pen = nullptr;           // [batch_max]
+  DagPencil* h_b_pen = nullptr;
+  int4* b_tasks = nullptr;
+  int4* h_b_tasks = nullptr;
+  long long b_task_cap = 0;
 };
 
 namespace {
@@ -202,6 +222,12 @@ void free_plan(pevc_plan_t p) {
   for (void* d : ldev)
     if (d) cudaFree(d);
   cplx_free(p->cx);
+  void* bd[] = {p->b_work, p->b_strc, p->b_cnt, p->b_subd, p->b_status, p->b_gmax, p->b_pen, p->b_tasks};
+  for (void* d : bd)
+    if (d) cudaFree(d);
+  void* bh[] = {p->h_b_strc, p->h_b_subd, p->h_b_sel, p->h_b_pen, p->h_b_tasks};
+  for (void* h : bh)
+    if (h) cudaFreeHost(h);
   void* dagd[] = {p->d_pen, p->d_tasks, p->d_cnt, p->d_sub, p->d_ticket};
   for (void* d : dagd)
     if (d) cudaFree(d);
@@ -408,6 +434,103 @@ int dag_enqueue(pevc_plan_t p, const Problem& P, const Structure& st, cudaStream
   return 0;
 }
 
+// ---- batched solves on the scheduler: per-pencil slices of the pools ----
+
+// Slice sizes for a pencil of order n, from bounds that hold whatever its
+// block structure (M <= the tile-count bound of the order; m <= n): bytes of
+// workspace, bytes of structure, ready counters.
+struct SliceSize {
+  size_t work = 0, strc = 0, cnt = 0;
+};
+
+size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+int slice_mmax(int n, int tb) { return (std::max(n, 1) + tb - 2) / (tb - 1) + 1; }
+
+SliceSize slice_size(int n, int tb) {
+  const size_t nn = (size_t)std::max(n, 1), Mb = (size_t)slice_mmax(n, tb), tiles = Mb * (Mb + 1) / 2;
+  const size_t nsb = (size_t)dag_nsub_bound(tb);
+  SliceSize z;
+  z.work = r256(tiles * tb * tb * sizeof(double)) + r256(Mb * nn * sizeof(int)) + r256(Mb * nn * sizeof(double)) +
+           r256(Mb * Mb * sizeof(int)) + 5 * r256(nn * sizeof(double));
+  z.strc = 2 * r256(nn) + 4 * r256((Mb + 1) * sizeof(int)) + 2 * r256(nn * sizeof(int)) +
+           2 * r256((nn + Mb) * sizeof(int)) + 2 * r256(Mb * nsb * sizeof(int));
+  z.cnt = tiles * (2 + nsb);
+  return z;
+}
+
+// One pencil of a batch: a plan view whose workspace pointers are its slices
+// (device work, device structure, host structure mirror, counters), so that
+// analyse() and make_problem() serve it unchanged.
+struct BatchPencil {
+  pevc_plan_s v;           // a view: every pointer is borrowed
+  int* sub_first = nullptr;  // host mirror of the sub-chunks ...
+  int* sub_c0 = nullptr;
+  int* sub_nc = nullptr;
+  int* d_sub_first = nullptr;  // ... and the device slices
+  int* d_sub_c0 = nullptr;
+  int* d_sub_nc = nullptr;
+  int* cnt = nullptr;
+  int nsub_max = 1;
+  Structure st;
+  size_t strc_off = 0;
+};
+
+void bind_slice(pevc_plan_t p, int b, int n, size_t work_off, size_t strc_off, size_t cnt_off, BatchPencil& bp) {
+  pevc_plan_s& v = bp.v;
+  const size_t nn = (size_t)std::max(n, 1);
+  const int Mb = slice_mmax(n, p->tb);
+  const size_t tiles = (size_t)Mb * (Mb + 1) / 2, nsb = (size_t)dag_nsub_bound(p->tb);
+  v.n_max = n;
+  v.prec = PEVC_FP64;
+  v.tb = p->tb;
+  v.flags = p->flags;
+  v.stream = p->stream;
+  v.Mmax = Mb;
+  v.nsm = p->nsm;
+  unsigned char* w = p->b_work + work_off;
+  auto take = [&](size_t bytes) {
+    unsigned char* q = w;
+    w += r256(bytes);
+    return q;
+  };
+  v.Y = (double*)take(tiles * p->tb * p->tb * sizeof(double));
+  v.ex = (int*)take((size_t)Mb * nn * sizeof(int));
+  v.nrm = (double*)take((size_t)Mb * nn * sizeof(double));
+  v.EA = (int*)take((size_t)Mb * Mb * sizeof(int));
+  v.tcS = (double*)take(nn * sizeof(double));
+  v.tcT = (double*)take(nn * sizeof(double));
+  v.ca = (double*)take(nn * sizeof(double));
+  v.cb = (double*)take(nn * sizeof(double));
+  v.cbeta = (double*)take(nn * sizeof(double));
+  v.gmax = p->b_gmax + b;
+  v.status = p->b_status + b;
+  // structure: the same offsets in the device pool and its host mirror
+  size_t o = strc_off;
+  auto both = [&](size_t bytes, void** dev, void** host) {
+    *dev = p->b_strc + o;
+    *host = p->h_b_strc + o;
+    o += r256(bytes);
+  };
+  both(nn, (void**)&v.blk, (void**)&v.h_blk);
+  both(nn, (void**)&v.kind, (void**)&v.h_kind);
+  both((Mb + 1) * sizeof(int), (void**)&v.toff, (void**)&v.h_toff);
+  both((Mb + 1) * sizeof(int), (void**)&v.cstart, (void**)&v.h_cstart);
+  both((Mb + 1) * sizeof(int), (void**)&v.dcfirst, (void**)&v.h_dcfirst);
+  both((Mb + 1) * sizeof(int), (void**)&bp.d_sub_first, (void**)&bp.sub_first);
+  both(nn * sizeof(int), (void**)&v.ccol, (void**)&v.h_ccol);
+  both(nn * sizeof(int), (void**)&v.dperm, (void**)&v.h_dperm);
+  both((nn + Mb) * sizeof(int), (void**)&v.dcpos, (void**)&v.h_dcpos);
+  both((nn + Mb) * sizeof(int), (void**)&v.dccnt, (void**)&v.h_dccnt);
+  both((size_t)Mb * nsb * sizeof(int), (void**)&bp.d_sub_c0, (void**)&bp.sub_c0);
+  both((size_t)Mb * nsb * sizeof(int), (void**)&bp.d_sub_nc, (void**)&bp.sub_nc);
+  v.h_subd = p->h_b_subd + (size_t)b * p->n_max;
+  v.subd = p->b_subd + (size_t)b * p->n_max;
+  v.h_sel = p->h_b_sel + (size_t)b * p->n_max;
+  bp.cnt = p->b_cnt + cnt_off;
+  bp.strc_off = strc_off;
+  (void)tiles;
+}
+
 // Phase 3: everything else, stream-ordered.  With check_prepass the call reads
 // the status after the pre-pass and returns early for a bad pencil; without it
 // the whole graph is enqueued and the status is read once at the end (the
@@ -559,6 +682,122 @@ int check_args(int n_max, const double* S, int lds, const double* T, int ldt, in
   if (n > 0 && !V) return -8;
   if (ldv < std::max(n, 1)) return -9;
   if (n > 0 && !scale) return -10;
+  return 0;
+}
+
+// A batch of an FP64 plan on the device scheduler: pencils are packed into
+// waves whose slices fit the pools (one wave for most batches); per wave the
+// host reads every pencil's block structure at once, builds one task list
+// that interleaves the pencils' stages by depth (the bottom stage of every
+// pencil first, so that all pencils advance together and the large ones keep
+// the GPU busy at the end), and the whole wave is one persistent launch
+// between the per-pencil pre- and post-passes.  Statuses are read once per wave.
+int solve_batched_dag(pevc_plan_t p, int count, const double* const* S, const int* lds, const double* const* T,
+                      const int* ldt, const int* n, const int32_t* const* select, double* const* V_out,
+                      const int* ldv, int32_t* const* scale_out, int* m_out, int* status) {
+  cudaStream_t s = p->stream;
+  std::vector<BatchPencil> bp(count > 0 ? count : 1);
+  std::vector<char> live(count > 0 ? count : 1, 0);
+  const int cap = (int)std::min<long long>(p->b_task_cap, INT32_MAX);
+  int b0 = 0;
+  while (b0 < count) {
+    size_t wo = 0, so = 0, co = 0;
+    int b1 = b0;
+    for (; b1 < count; ++b1) {
+      m_out[b1] = 0;
+      status[b1] = check_args(p->n_max, S[b1], lds[b1], T[b1], ldt[b1], n[b1], V_out[b1], ldv[b1], scale_out[b1]);
+      live[b1] = 0;
+      if (status[b1] || n[b1] == 0) continue;
+      const SliceSize z = slice_size(n[b1], p->tb);
+      if (wo + z.work > p->b_work_bytes || so + z.strc > p->b_strc_bytes || co + z.cnt > p->b_cnt_ints) {
+        if (b1 == b0) return PEVC_ERR_CUDA;   // cannot happen: the pools hold one pencil of order n_max
+        break;
+      }
+      bind_slice(p, b1, n[b1], wo, so, co, bp[b1]);
+      live[b1] = 1;
+      wo += z.work;
+      so += z.strc;
+      co += z.cnt;
+    }
+    // 1. every pencil's subdiagonal (and selection) to the host
+    for (int b = b0; b < b1; ++b) {
+      if (!live[b]) continue;
+      CK(launch_gather_subdiag(S[b], lds[b], n[b], bp[b].v.subd, s));
+      if (select && select[b])
+        CK(cudaMemcpyAsync(bp[b].v.h_sel, select[b], (size_t)n[b] * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaMemcpyAsync(p->h_b_subd + (size_t)b0 * p->n_max, p->b_subd + (size_t)b0 * p->n_max,
+                       (size_t)(b1 - b0) * p->n_max * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // 2. structure, sub-chunks, records
+    int maxM = 0;
+    for (int b = b0; b < b1; ++b) {
+      if (!live[b]) continue;
+      BatchPencil& q = bp[b];
+      int rc = analyse(&q.v, n[b], select && select[b], q.st);
+      int nsm = 0;
+      if (!rc && dag_subchunks(q.st.M, q.v.h_cstart, q.v.h_kind, q.sub_first, q.sub_c0, q.sub_nc,
+                               q.v.Mmax * dag_nsub_bound(p->tb), &nsm) < 0)
+        rc = PEVC_ERR_CUDA;
+      if (rc) {
+        status[b] = rc;
+        live[b] = 0;
+        continue;
+      }
+      q.nsub_max = std::max(nsm, 1);
+      m_out[b] = q.st.m;
+      maxM = std::max(maxM, q.st.M);
+      const size_t tiles = (size_t)q.st.M * (q.st.M + 1) / 2;
+      DagPencil& D = p->h_b_pen[b - b0];
+      D.P = make_problem(&q.v, S[b], lds[b], T[b], ldt[b], n[b], q.st);
+      D.dcnt = q.cnt;
+      D.utile = q.cnt + tiles;
+      D.usub = q.cnt + 2 * tiles;
+      D.sub_first = q.d_sub_first;
+      D.sub_c0 = q.d_sub_c0;
+      D.sub_nc = q.d_sub_nc;
+      D.nsub_max = q.nsub_max;
+    }
+    // 3. the wave's task list: stage by stage from the bottom, every pencil's
+    //    stage of the same depth together
+    int cnt = 0;
+    for (int d = 0; d < maxM && cnt >= 0; ++d)
+      for (int b = b0; b < b1 && cnt >= 0; ++b) {
+        if (!live[b]) continue;
+        const int M = bp[b].st.M, stage = d == 0 ? M : M - d;
+        if (d > 0 && stage < 1) continue;
+        cnt = dag_stage_tasks(b - b0, M, stage, bp[b].v.h_dcfirst, bp[b].sub_first, p->h_b_tasks, cnt, cap);
+      }
+    if (cnt < 0) return PEVC_ERR_CUDA;
+    // 4. structure, records and tasks to the device; counters, statuses and
+    //    running maxima zeroed
+    if (so) CK(cudaMemcpyAsync(p->b_strc, p->h_b_strc, so, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->b_pen, p->h_b_pen, (size_t)(b1 - b0) * sizeof(DagPencil), cudaMemcpyHostToDevice, s));
+    if (cnt) CK(cudaMemcpyAsync(p->b_tasks, p->h_b_tasks, (size_t)cnt * sizeof(int4), cudaMemcpyHostToDevice, s));
+    if (co) CK(cudaMemsetAsync(p->b_cnt, 0, co * sizeof(int), s));
+    CK(cudaMemsetAsync(p->b_status + b0, 0, (size_t)(b1 - b0) * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(p->b_gmax + b0, 0, (size_t)(b1 - b0) * sizeof(double), s));
+    CK(cudaMemsetAsync(p->d_ticket, 0, 2 * sizeof(int), s));
+    // 5. pre-passes, the walk, post-passes
+    for (int b = b0; b < b1; ++b) {
+      if (!live[b]) continue;
+      const Problem& P = p->h_b_pen[b - b0].P;
+      CK(launch_prepass(P, s));
+      if (bp[b].st.m > 0) CK(launch_init_state(P, s));
+    }
+    CK(launch_dag(p->b_pen, p->b_tasks, cnt, p->d_ticket, p->d_ticket + 1, kDagWaitCycles, dag_grid(p->nsm), s));
+    for (int b = b0; b < b1; ++b) {
+      if (!live[b] || bp[b].st.m == 0) continue;
+      CK(launch_post(p->h_b_pen[b - b0].P, V_out[b], ldv[b], scale_out[b], (p->flags & PEVC_NO_NORMALISE) == 0, s));
+    }
+    // 6. statuses (the host buffers of this wave are free again after this)
+    CK(cudaMemcpyAsync(p->h_bstatus + b0, p->b_status + b0, (size_t)(b1 - b0) * sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = b0; b < b1; ++b)
+      if (live[b]) status[b] = status_from_bits(p->h_bstatus[b]);
+    b0 = b1;
+  }
   return 0;
 }
 
@@ -715,7 +954,37 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
     rc = rc ? rc : halloc(&p->h_sub, (size_t)(p->Mmax + 1) + 2 * (size_t)p->sub_cap);
     rc = rc ? rc : dalloc(&p->d_ticket, 2);
   }
-  if (!rc && batch_max > 1) {
+  if (!rc && batch_max > 1 && p->dag) {
+    // batches on the scheduler: pools that hold the slices of many pencils
+    // (workspace: a budget of the larger of about 6 GB and eight pencils of
+    // order n_max, or PEVC_BATCH_BYTES, packed by each pencil's own order, so
+    // that a batch of small pencils runs as one wave; structure, counters and
+    // records for all batch_max pencils)
+    const SliceSize z = slice_size(n_max, p->tb);
+    const char* bb = getenv("PEVC_BATCH_BYTES");
+    const double budget = bb ? atof(bb) : std::max(6e9, 8.0 * (double)z.work);
+    const size_t k = std::min<size_t>((size_t)batch_max, std::max<size_t>(1, (size_t)(budget / (double)z.work)));
+    const size_t B = (size_t)batch_max;
+    p->bdag = true;
+    p->b_work_bytes = k * z.work;
+    p->b_strc_bytes = B * z.strc;
+    p->b_cnt_ints = B * z.cnt;
+    p->b_task_cap = (long long)B * dag_task_bound(slice_mmax(n_max, p->tb), p->tb);
+    rc = rc ? rc : dalloc(&p->b_work, p->b_work_bytes);
+    rc = rc ? rc : dalloc(&p->b_strc, p->b_strc_bytes);
+    rc = rc ? rc : halloc(&p->h_b_strc, p->b_strc_bytes);
+    rc = rc ? rc : dalloc(&p->b_cnt, p->b_cnt_ints);
+    rc = rc ? rc : dalloc(&p->b_subd, B * nm);
+    rc = rc ? rc : halloc(&p->h_b_subd, B * nm);
+    rc = rc ? rc : halloc(&p->h_b_sel, B * nm);
+    rc = rc ? rc : dalloc(&p->b_status, B);
+    rc = rc ? rc : dalloc(&p->b_gmax, B);
+    rc = rc ? rc : dalloc(&p->b_pen, B);
+    rc = rc ? rc : halloc(&p->h_b_pen, B);
+    rc = rc ? rc : dalloc(&p->b_tasks, (size_t)p->b_task_cap);
+    rc = rc ? rc : halloc(&p->h_b_tasks, (size_t)p->b_task_cap);
+    rc = rc ? rc : halloc(&p->h_bstatus, B);
+  } else if (!rc && batch_max > 1) {
     // child plans for concurrent pencils, as many as about 4 GB of workspace
     // allows (at most 8)
     const double tiles = (double)p->Mmax * (p->Mmax + 1) / 2.0 * (double)p->tb * p->tb;
@@ -765,6 +1034,8 @@ int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, cons
   if (count > 0 && (!S || !lds || !T || !ldt || !n || !V_out || !ldv || !scale_out || !m_out || !status))
     return -3;
   plan->last_m = -1;   // the plan's column kinds no longer describe one solve
+  if (plan->bdag)
+    return solve_batched_dag(plan, count, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out, status);
   if (plan->nchild > 0)
     return solve_batched(plan, count, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out, status);
   for (int b = 0; b < count; ++b) {

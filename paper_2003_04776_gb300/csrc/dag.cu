@@ -65,10 +65,9 @@ int dag_stage_tasks(int pencil, int M, int stage, const int* dchunk_first, const
     for (int j = i; j < M; ++j)
       for (int s = 0; s < sub_first[j + 1] - sub_first[j]; ++s) push(dag_task(pencil, kTaskUpd, k, j, i << 8 | s));
   };
-  updates(i - 1);                         // the row whose solves come next
+  for (int k = i - 1; k >= 0; --k) updates(k);   // row i - 1 first: its solves come next
   for (int j = i; j < M; ++j)             // the solves of row i - 1 (every update into them is then applied)
     for (int c = dchunk_first[j]; c < dchunk_first[j + 1]; ++c) push(dag_task(pencil, kTaskDiag, i - 1, j, c));
-  for (int k = i - 2; k >= 0; --k) updates(k);
   return count;
 }
 

@@ -63,9 +63,11 @@ int dag_subchunks(int M, const int* cstart, const signed char* kind, int* sub_fi
                   int cap, int* nsub_max);
 
 // Host: appends the tasks of stage i of one pencil (i = M: the tips) to out,
-// in the walk order: the updates of tile row i - 1 from row i (the rows the
-// next solves wait for), the solves of row i - 1, then the updates of the
-// rows above.  Returns the new task count or -1 past cap.
+// in the walk order: the updates from tile row i, row i - 1 first (the rows
+// the next solves wait for), then the solves of row i - 1.  A CTA that takes a
+// solve finds its updates done or nearly so, and the solves of one stage
+// overlap the last updates of the stage before and the first of the next.
+// Returns the new task count or -1 past cap.
 int dag_stage_tasks(int pencil, int M, int stage, const int* dchunk_first, const int* sub_first, int4* out,
                     int count, int cap);
 

@@ -1,8 +1,11 @@
 """pevc_solve_batched: pencils of uneven orders (plain and stress, with and
-without a selection, an empty one and an invalid one) in one call, run
-concurrently on the plan's child workspaces.  Every pencil must give exactly
-what a single pevc_solve gives on the same plan settings (the kernels are
-deterministic), and match the oracle within the parity tolerance."""
+without a selection, an empty one and an invalid one) in one call.  FP64
+plans run the whole batch on the device-side scheduler (the task graphs of
+all pencils in one persistent launch per wave); split plans run the pencils
+concurrently on child workspaces.  Every pencil must give exactly what a
+single pevc_solve gives on the same plan settings (the kernels are
+deterministic, and the scheduler applies the updates in the stage walk's
+order), and match the oracle within the parity tolerance."""
 import os
 
 import numpy as np
@@ -159,3 +162,27 @@ def test_batched_config4_workload(pevc_lib, prec):
           f"conditioning bound (largest error / bound {worst_ratio:.2f}); scale exponents within {dsc}")
     assert res.max() <= 100.0 and res_rb.max() <= 100.0
     assert dsc <= 1
+
+
+def test_batched_fp64_waves_match_single_solves(pevc_lib, monkeypatch):
+    """A workspace budget that holds only a few pencils at a time: the batch
+    runs as several waves of the scheduler, and every pencil still equals its
+    single solve bit for bit."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    orders = [300, 64, 500, 1, 257, 400, 129, 450]
+    pencils = [pencilgen.make_pencil(n, 6600 + q, stress=bool(q % 2)) for q, n in enumerate(orders)]
+    monkeypatch.setenv("PEVC_BATCH_BYTES", "4000000")          # two pencils of order 500 per wave
+    plan = pevc_lib.Plan(500, prec="fp64", tile=64, batch_max=len(pencils))
+    single = pevc_lib.Plan(500, prec="fp64", tile=64)
+    try:
+        st, out = plan.solve_batched([(p.S, p.T) for p in pencils])
+        assert st == 0
+        for p, (V, sc, stb) in zip(pencils, out):
+            assert stb == 0
+            V1, sc1, st1 = single.solve(p.S, p.T, check=False)
+            assert st1 == 0 and single.stats[7] == 1.0
+            assert np.array_equal(V, V1) and np.array_equal(sc, sc1)
+    finally:
+        plan.close()
+        single.close()
