@@ -63,6 +63,10 @@ typedef struct pevc_plan_s *pevc_plan_t;
 #define PEVC_NO_NORMALISE 1u   /* return consolidated columns and exponents      */
 #define PEVC_NO_CORRECTION 2u  /* split precisions: skip the correction sweep    */
 #define PEVC_BT_EMULATED 4u    /* pevc_backtransform: FP64 GEMM by fixed-point emulation */
+#define PEVC_STAGE_WALK 8u     /* FP64 plans: walk the task graph stage by stage from the host
+                                  instead of the device-side scheduler                    */
+#define PEVC_AUTOTUNE 16u      /* pevc_plan: choose the settings by timing (see pevc_plan) */
+#define PEVC_DEVICE_WALK 32u   /* FP64 plans: the device-side scheduler whatever the order   */
 
 /* Status codes. */
 #define PEVC_SUCCESS 0
@@ -87,9 +91,30 @@ typedef struct pevc_plan_s *pevc_plan_t;
  *   batch_max  largest batch count for pevc_solve_batched, >= 1
  *   prec       PEVC_FP64, PEVC_SPLIT_BF16X3, PEVC_SPLIT_FP8X4 or PEVC_SPLIT_BF16X5
  *   tile       tile order (Section 5.1: tiles of S, T and V are conformal; a
- *              tile boundary never splits a 2x2 block); 0 lets the autotuner
- *              choose from n_max and prec; otherwise 32, 64, 96 or 128
- *   flags      PEVC_NO_NORMALISE | PEVC_NO_CORRECTION
+ *              tile boundary never splits a 2x2 block); 0 lets the library
+ *              choose (from n_max and prec, or by timing with PEVC_AUTOTUNE);
+ *              otherwise 32, 64, 96 or 128
+ *   flags      PEVC_NO_NORMALISE | PEVC_NO_CORRECTION | PEVC_STAGE_WALK |
+ *              PEVC_DEVICE_WALK | PEVC_AUTOTUNE.  FP64 plans walk the task
+ *              graph with the device-side scheduler (one persistent launch,
+ *              Section 3 and Section 5.3) for batches and orders up to 4096,
+ *              stage by stage from the host above; the walk flags force one
+ *              (not both).  Split plans use the stage walk (their tcgen05
+ *              update needs a whole SM per CTA).  With PEVC_AUTOTUNE the plan
+ *              times one solve of
+ *              each candidate setting on a synthetic pencil of order n_max
+ *              (made on the device: 2x2 blocks on two thirds of the diagonal,
+ *              uniform off-diagonal entries) and keeps the fastest: for the
+ *              split precisions the split depth (BF16x5 in one pass, or
+ *              BF16x3 plus the correction sweep), whichever of the two prec
+ *              names, at tile order 128 (or the given one); for FP64 the tile
+ *              order among 64, 96 and 128 (32 too up to order 512) when tile
+ *              is 0, and the walk; FP64 plans time orders above 8192 on a
+ *              pencil of order 8192.  The
+ *              winner is cached per device, order and precision family for
+ *              later plans of this process; pevc_plan_info reports it and
+ *              pevc_autotune_log the times.  The timing needs about 2 n_max^2
+ *              doubles more of device memory while the plan is made.
  *   stream     cudaStream_t (as void*) on which every solve is ordered; NULL
  *              is the legacy default stream
  * The plan allocates with cudaMalloc; pevc_solve itself allocates nothing.
@@ -149,6 +174,16 @@ const char *pevc_strerror(int code);
  *                       slices per operand (0 for FP64), correction sweeps}
  */
 int pevc_plan_info(pevc_plan_t plan, int *info);
+
+/*
+ * pevc_autotune_log -- the candidates a PEVC_AUTOTUNE plan timed (or whose
+ * times it took from the process's cache), in the order they were tried.
+ *   out   host double[4 * cap]: per candidate {tile, prec, stage walk (0/1),
+ *         milliseconds of one solve of the synthetic pencil}
+ * Returns the number of candidates (at most cap are written; 0 for a plan
+ * made without PEVC_AUTOTUNE), or -1 for a NULL plan, -2 for a NULL out.
+ */
+int pevc_autotune_log(pevc_plan_t plan, double *out, int cap);
 
 /*
  * pevc_last_stats -- host double[8] timing/work figures of the last solve on

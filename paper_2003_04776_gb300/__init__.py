@@ -30,6 +30,9 @@ PRECISIONS = {"fp64": FP64, "bf16x3": SPLIT_BF16X3, "fp8x4": SPLIT_FP8X4, "bf16x
 NO_NORMALISE = 1
 NO_CORRECTION = 2
 BT_EMULATED = 4      # pevc_backtransform: FP64 GEMM by fixed-point emulation
+STAGE_WALK = 8       # FP64 plans: the stage walk from the host instead of the device-side scheduler
+AUTOTUNE = 16        # pevc_plan: time the candidate settings and keep the fastest
+DEVICE_WALK = 32     # FP64 plans: the device-side scheduler whatever the order
 
 SUCCESS = 0
 ERR_NOT_SCHUR = 1
@@ -83,12 +86,14 @@ _lib.pevc_watchdog_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
 _lib.pevc_watchdog_selftest.restype = _i
 _lib.pevc_scheduler_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
 _lib.pevc_scheduler_selftest.restype = _i
+_lib.pevc_autotune_log.argtypes = [_vp, _vp, _i]
+_lib.pevc_autotune_log.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
            "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
            "pevc_solve_cplx_left", "pevc_backtransform_cplx", "pevc_watchdog_selftest",
-           "pevc_scheduler_selftest")
+           "pevc_scheduler_selftest", "pevc_autotune_log")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -225,6 +230,17 @@ def pevc_scheduler_selftest(plan, withhold: int, cycles: int) -> int:
     return _lib.pevc_scheduler_selftest(plan, int(withhold), int(cycles))
 
 
+def pevc_autotune_log(plan):
+    """The candidates an autotuned plan timed: (count, [(tile, prec,
+    stage_walk, ms), ...])."""
+    cap = 64
+    out = (ctypes.c_double * (4 * cap))()
+    k = _lib.pevc_autotune_log(plan, out, cap)
+    if k < 0:
+        return k, []
+    return k, [tuple(out[4 * q:4 * q + 4]) for q in range(min(k, cap))]
+
+
 # ------------------------------------------------------------ torch wrapper
 
 class PevcError(RuntimeError):
@@ -259,10 +275,13 @@ class Plan:
     """A plan (device workspace for order <= n_max) bound to a torch stream."""
 
     def __init__(self, n_max: int, prec="fp64", tile: int = 0, batch_max: int = 1,
-                 normalise: bool = True, correction: bool = True, stream=None):
+                 normalise: bool = True, correction: bool = True, stream=None,
+                 autotune: bool = False, stage_walk: bool = False, device_walk: bool = False):
         import torch
         self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-        self.flags = (0 if normalise else NO_NORMALISE) | (0 if correction else NO_CORRECTION)
+        self.flags = ((0 if normalise else NO_NORMALISE) | (0 if correction else NO_CORRECTION) |
+                      (AUTOTUNE if autotune else 0) | (STAGE_WALK if stage_walk else 0) |
+                      (DEVICE_WALK if device_walk else 0))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         st, h = pevc_plan(n_max, batch_max, self.prec, tile, self.flags, self.stream.cuda_stream)
         if st:

@@ -10,6 +10,7 @@
 //   stage i:  solve tiles (i, j), j > i   ->   update tiles (k, j), k < i <= j
 // so every [S_ki T_ki] tile row panel is read once per stage for all columns.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -18,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "autotune.cuh"
 #include "common.cuh"
 #include "cplx.cuh"
 #include "dag.cuh"
@@ -138,6 +140,8 @@ struct pevc_plan_s {
   int4* b_tasks = nullptr;
   int4* h_b_tasks = nullptr;
   long long b_task_cap = 0;
+  // the candidates timed by PEVC_AUTOTUNE: {tile, prec, stage walk, ms}
+  std::vector<std::array<double, 4>> tune_log;
 };
 
 namespace {
@@ -161,15 +165,26 @@ int status_from_bits(unsigned bits) {
   return PEVC_SUCCESS;
 }
 
-// Autotuned tile order: small pencils want small tiles (enough tiles to fill
-// the GPU, short diagonal solves), large ones the largest tile (fewer stages,
-// larger updates).
+// Default tile order (PEVC_AUTOTUNE measures instead).  FP64: small pencils
+// want small tiles (enough tiles to fill the GPU, short diagonal solves),
+// large ones the largest (fewer stages, larger updates).  Split precisions:
+// always 128, the tcgen05 update's order; the split paths' componentwise
+// error also grows as the tiles shrink (the diagonal tiles are solved in
+// FP64, the rest goes through the slices: on the batched workload's worst
+// vectors 2e-13 .. 3e-9 at order 128 against 1e-8 .. 8e-7 at 32 and 64).
 int choose_tile(int n_max, int prec) {
-  if (prec != PEVC_FP64) return n_max <= 512 ? 32 : (n_max <= 2048 ? 64 : 128);
+  if (prec != PEVC_FP64) return 128;
   if (n_max <= 256) return 32;
   if (n_max <= 1024) return 64;
   return 128;
 }
+
+// Default walk of FP64 plans (PEVC_AUTOTUNE measures instead): the device-side
+// scheduler for batches and for orders up to 4096, where stages are short and
+// the per-stage barriers of the host walk cost most; the stage walk above,
+// where its 256-thread update kernel keeps the FP64 pipe busier (n = 20000:
+// 5.26 s against 5.81 s).
+bool default_dag(int n_max, int batch_max) { return batch_max > 1 || n_max <= 4096; }
 
 template <typename Tp>
 int dalloc(Tp** p, size_t count) {
@@ -865,9 +880,22 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
     return -4;
   if (prec == PEVC_SPLIT_FP8X4) return PEVC_ERR_UNSUPPORTED;
   if (tile != 0 && tile != 32 && tile != 64 && tile != 96 && tile != 128) return -5;
-  if (flags & ~(PEVC_NO_NORMALISE | PEVC_NO_CORRECTION)) return -6;
+  if (flags & ~(PEVC_NO_NORMALISE | PEVC_NO_CORRECTION | PEVC_STAGE_WALK | PEVC_DEVICE_WALK | PEVC_AUTOTUNE))
+    return -6;
+  if ((flags & PEVC_STAGE_WALK) && (flags & PEVC_DEVICE_WALK)) return -6;
+  std::vector<std::array<double, 4>> tune_log;
+  if (flags & PEVC_AUTOTUNE) {
+    int t = 0, q = 0;
+    unsigned walk = 0;
+    const int rc = autotune_pick(n_max, prec, tile, flags & ~PEVC_AUTOTUNE, stream, &t, &q, &walk, &tune_log);
+    if (rc) return rc;
+    tile = t;
+    prec = q;
+    flags = (flags & ~(PEVC_STAGE_WALK | PEVC_DEVICE_WALK | PEVC_AUTOTUNE)) | walk;
+  }
   pevc_plan_t p = new (std::nothrow) pevc_plan_s();
   if (!p) return PEVC_ERR_NOMEM;
+  p->tune_log = std::move(tune_log);
   p->n_max = n_max;
   p->batch_max = batch_max;
   p->prec = prec;
@@ -939,7 +967,11 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
     // PEVC_SCHED=stage asks for the stage walk; every plan keeps the small
     // records of the scheduler's self-test
     const char* sch = getenv("PEVC_SCHED");
-    p->dag = prec == PEVC_FP64 && !(sch && sch[0] == 's');
+    bool dag = default_dag(n_max, batch_max);
+    if (flags & PEVC_DEVICE_WALK) dag = true;
+    if (flags & PEVC_STAGE_WALK) dag = false;
+    if (sch) dag = sch[0] == 'd';       // PEVC_SCHED=dag | stage overrides, for comparisons
+    p->dag = prec == PEVC_FP64 && dag;
     const size_t tiles = M * (M + 1) / 2;
     const int nsb = dag_nsub_bound(p->tb);
     p->task_cap = p->dag ? dag_task_bound(p->Mmax, p->tb) : 1;
@@ -1265,6 +1297,15 @@ int pevc_plan_info(pevc_plan_t plan, int* info) {
   info[6] = plan->prec == PEVC_FP64 ? 0 : (plan->prec == PEVC_SPLIT_BF16X5 ? 5 : (plan->prec == PEVC_SPLIT_BF16X3 ? 3 : 4));
   info[7] = (plan->prec == PEVC_SPLIT_BF16X3 && !(plan->flags & PEVC_NO_CORRECTION)) ? 1 : 0;
   return 0;
+}
+
+int pevc_autotune_log(pevc_plan_t plan, double* out, int cap) {
+  if (!plan) return -1;
+  if (!out && cap > 0) return -2;
+  const int k = (int)plan->tune_log.size();
+  for (int q = 0; q < k && q < cap; ++q)
+    for (int x = 0; x < 4; ++x) out[4 * q + x] = plan->tune_log[q][x];
+  return k;
 }
 
 int pevc_set_profile(pevc_plan_t plan, int on) {

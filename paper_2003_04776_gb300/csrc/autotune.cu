@@ -1,0 +1,187 @@
+// autotune.cu -- the plan-time autotuner: times one solve of every candidate
+// setting (tile order; split depth or walk) on a synthetic pencil made on the
+// device, through the library's own entry points, and keeps the fastest.
+//
+// The synthetic pencil is a standardised real Schur pencil of the shape the
+// method is measured on: 2x2 blocks on two thirds of the diagonal (each with a
+// diagonal positive T_jj and S_jj = T_jj [[mu, nu], [-nu, mu]], so its
+// eigenvalues are mu +- i nu, nu >= 1/2), distinct real eigenvalues spread
+// over [-1, 1] for the 1x1 blocks, T's diagonal in [1/2, 2] and off-diagonal
+// entries uniform in [-1, 1] (a counter-based hash of the position, SplitMix64's
+// finaliser), so its eigenvectors grow like the benchmark's and exercise the
+// same scaling.
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "autotune.cuh"
+
+namespace pevc {
+
+namespace {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double unit(uint64_t key) { return (double)(mix64(key) >> 11) * 0x1p-53; }
+
+// Column-major n x n S and T; one thread per entry.  Rows r with r % 3 == 0
+// (and r + 1 < n) start a 2x2 block.
+__global__ void k_calib_pencil(double* __restrict__ S, double* __restrict__ T, int n) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int c = (int)(idx / n), r = (int)(idx % n);
+  auto first = [n](int q) { return q % 3 == 0 && q + 1 < n; };   // q starts a 2x2 block
+  auto tdiag = [](int q) { return 0.5 + 1.5 * unit(3ull * q + 1); };
+  const uint64_t key = ((uint64_t)r << 32) | (uint64_t)c;
+  double s = 0.0, t = 0.0;
+  if (r < c) {
+    const bool in_block = first(r) && c == r + 1;
+    const double nu = 0.5 + unit(3ull * r + 2);
+    s = in_block ? tdiag(r) * nu : 2.0 * unit(key * 2 + 7) - 1.0;
+    t = in_block ? 0.0 : 2.0 * unit(key * 2 + 8) - 1.0;
+  } else if (r == c) {
+    const int b = (r % 3 == 1 && first(r - 1)) ? r - 1 : r;    // first row of r's block
+    const double lam = -1.0 + 2.0 * (b + 0.5) / n;
+    t = tdiag(r);
+    s = lam * t;                                              // 1x1: lambda t; 2x2: t mu on the diagonal
+  } else if (r == c + 1 && first(c)) {
+    const double nu = 0.5 + unit(3ull * c + 2);
+    s = -tdiag(r) * nu;
+  }
+  S[idx] = s;
+  T[idx] = t;
+}
+
+struct Choice {
+  int tile = 0, prec = 0;
+  unsigned walk_flag = 0;
+  std::vector<std::array<double, 4>> log;
+};
+
+std::mutex g_mu;
+std::map<std::tuple<int, int, int, int, unsigned>, Choice> g_cache;
+
+}  // namespace
+
+int autotune_pick(int n_max, int prec, int tile, unsigned flags, void* stream, int* tile_out, int* prec_out,
+                  unsigned* walk_out, std::vector<std::array<double, 4>>* log) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PEVC_ERR_CUDA;
+  const bool split = prec != PEVC_FP64;
+  const unsigned keep = flags & (PEVC_NO_NORMALISE | PEVC_NO_CORRECTION);
+  const auto key = std::make_tuple(dev, n_max, split ? 1 : 0, tile, keep);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      *tile_out = it->second.tile;
+      *prec_out = it->second.prec;
+      *walk_out = it->second.walk_flag;
+      if (log) *log = it->second.log;
+      return 0;
+    }
+  }
+  // candidates
+  // tiles: the given one; split plans 128 (their accurate order, see the
+  // default tile rule); FP64 plans 64, 96 and 128 (32 too for small orders)
+  std::vector<int> tiles;
+  if (tile) tiles.push_back(tile);
+  else if (split) tiles.push_back(128);
+  else {
+    if (n_max <= 512) tiles.push_back(32);
+    for (int t : {64, 96, 128})
+      if (t <= std::max(n_max, 64)) tiles.push_back(t);
+  }
+  std::vector<std::pair<int, unsigned>> modes;   // (prec, walk flag)
+  if (!split) {
+    modes = {{PEVC_FP64, PEVC_DEVICE_WALK}, {PEVC_FP64, PEVC_STAGE_WALK}};
+  } else if (flags & PEVC_NO_CORRECTION) {
+    modes = {{prec, 0u}};                         // without the sweep only the caller's depth is accurate
+  } else {
+    modes = {{PEVC_SPLIT_BF16X5, 0u}, {PEVC_SPLIT_BF16X3, 0u}};
+  }
+  // the synthetic pencil: the plan's order (FP64 plans: at most 8192, where
+  // one solve already takes a good part of a second)
+  const int n = split ? n_max : std::min(n_max, 8192);
+  Choice best;
+  double best_ms = 1e300;
+  if (n <= 0) {
+    best.tile = tiles.front();
+    best.prec = modes.front().first;
+    best.walk_flag = modes.front().second;
+  } else {
+    cudaStream_t s = (cudaStream_t)stream;
+    double *S = nullptr, *T = nullptr, *V = nullptr;
+    int32_t* sc = nullptr;
+    const size_t nn = (size_t)n * n;
+    if (cudaMalloc(&S, nn * sizeof(double)) != cudaSuccess || cudaMalloc(&T, nn * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&V, nn * sizeof(double)) != cudaSuccess || cudaMalloc(&sc, (size_t)n * sizeof(int32_t)) != cudaSuccess) {
+      cudaFree(S);
+      cudaFree(T);
+      cudaFree(V);
+      cudaFree(sc);
+      return PEVC_ERR_NOMEM;
+    }
+    k_calib_pencil<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(S, T, n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = cudaGetLastError() == cudaSuccess ? 0 : PEVC_ERR_CUDA;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = PEVC_ERR_CUDA;
+    for (size_t mi = 0; !rc && mi < modes.size(); ++mi)
+      for (int t : tiles) {
+        pevc_plan_t q = nullptr;
+        const unsigned qf = keep | modes[mi].second;
+        if (pevc_plan(&q, n, 1, modes[mi].first, t, qf, stream) != 0) {
+          pevc_destroy(q);
+          continue;                               // a candidate that does not fit is not a winner
+        }
+        int m = 0, st = 0;
+        st = pevc_solve(q, S, n, T, n, n, nullptr, V, n, sc, &m);   // first use of the plan (untimed)
+        float ms = 0.0f;
+        if (!st) {
+          cudaEventRecord(e0, s);
+          st = pevc_solve(q, S, n, T, n, n, nullptr, V, n, sc, &m);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        pevc_destroy(q);
+        if (st) continue;
+        best.log.push_back({(double)t, (double)modes[mi].first, modes[mi].second == PEVC_STAGE_WALK ? 1.0 : 0.0,
+                            (double)ms});
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.tile = t;
+          best.prec = modes[mi].first;
+          best.walk_flag = modes[mi].second;
+        }
+      }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(S);
+    cudaFree(T);
+    cudaFree(V);
+    cudaFree(sc);
+    if (rc) return rc;
+    if (best.log.empty()) return PEVC_ERR_CUDA;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = best;
+  }
+  *tile_out = best.tile;
+  *prec_out = best.prec;
+  *walk_out = best.walk_flag;
+  if (log) *log = best.log;
+  return 0;
+}
+
+}  // namespace pevc

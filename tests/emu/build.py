@@ -79,6 +79,8 @@ def _convert(src: str, name: str) -> str:
 
 
 STUBS = '''
+#include <array>
+#include <vector>
 #include "{csrc}/common.cuh"
 #include "{csrc}/split.cuh"
 namespace pevc {{
@@ -91,6 +93,9 @@ cudaError_t launch_update_tc(const Problem&, const SplitWorkspace&, int, int, in
 int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
 void bt_handle_destroy(void*) {{}}
 int bt_gemm(void*, bool, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
+int autotune_pick(int, int, int, unsigned, void*, int*, int*, unsigned*, std::vector<std::array<double, 4>>*) {{
+  return PEVC_ERR_UNSUPPORTED;
+}}
 int bt_zgemm(void*, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
 }}
 '''
