@@ -67,6 +67,8 @@ typedef struct pevc_plan_s *pevc_plan_t;
                                   instead of the device-side scheduler                    */
 #define PEVC_AUTOTUNE 16u      /* pevc_plan: choose the settings by timing (see pevc_plan) */
 #define PEVC_DEVICE_WALK 32u   /* FP64 plans: the device-side scheduler whatever the order   */
+#define PEVC_BT_CUBLAS 64u     /* pevc_backtransform: cuBLAS FP64 GEMM instead of the library's
+                                  split GEMM                                               */
 
 /* Status codes. */
 #define PEVC_SUCCESS 0
@@ -251,8 +253,17 @@ int pevc_solve_static(const double *S, int lds, const double *T, int ldt, int n,
  * With (A, B) = (Q S Z^T, Q T Z^T) the pencil before its reduction to the
  * real Schur pencil (S, T), a right eigenvector v of (S, T) gives the right
  * eigenvector x = Z v of (A, B) for the same eigenvalue.  Computes X = Z V for
- * the m columns of V as pevc_solve writes them (one FP64 GEMM on the plan's
- * stream, cuBLAS), then, unless PEVC_NO_NORMALISE, scales every eigenvector
+ * the m columns of V as pevc_solve writes them, on the plan's stream, as
+ * exact BF16 slice products on the tensor cores: every row of Z and every
+ * column of V is split, per chunk of 256 along the inner dimension and
+ * relative to its own power-of-two bound in that chunk, into six 8-bit
+ * slices; the chunk's products sum exactly in FP32 per slice level and the
+ * chunks' values are summed in FP64, so each entry of X carries an error of
+ * at most about 2^-46 of sum over chunks of (the chunk's largest |Z_rk|) times
+ * sum |V_kc| plus (the chunk's largest |V_kc|) times sum |Z_rk| (chunks of V below a column's last
+ * non-zero row are skipped: V from a solve is quasi-triangular).  With
+ * PEVC_BT_CUBLAS or PEVC_BT_EMULATED it is cuBLAS's FP64 GEMM instead.  Then,
+ * unless PEVC_NO_NORMALISE, the call scales every eigenvector
  * (a real column, or the real and imaginary columns of a complex pair taken
  * as one complex vector) so that its entry of largest modulus is exactly 1
  * (the first such entry on ties; an all-zero vector stays zero).
@@ -267,11 +278,12 @@ int pevc_solve_static(const double *S, int lds, const double *T, int ldt, int n,
  *              pevc_solve (m must then equal that solve's column count)
  *   X, ldx     device, column-major n x m, ldx >= n, caller-allocated; must
  *              not overlap Z or V
- *   flags      PEVC_NO_NORMALISE | PEVC_BT_EMULATED (cuBLAS's fixed-point
- *              emulation of the FP64 GEMM on the tensor cores)
- * The first call allocates the plan's cuBLAS handle and, with kinds given,
- * a device copy of them (n_max bytes); the call synchronises the plan's
- * stream before returning.
+ *   flags      PEVC_NO_NORMALISE | PEVC_BT_CUBLAS | PEVC_BT_EMULATED (cuBLAS's
+ *              fixed-point emulation of the FP64 GEMM on the tensor cores)
+ * The first call allocates the split GEMM's workspace (about 24 n_max^2
+ * bytes) or, with the cuBLAS flags, the plan's cuBLAS handle, and, with kinds
+ * given, a device copy of them (n_max bytes); the call synchronises the
+ * plan's stream before returning.
  * Returns 0, -i (argument i invalid, counting the plan as argument 1),
  * PEVC_ERR_UNSUPPORTED (emulation not available), PEVC_ERR_NOMEM or
  * PEVC_ERR_CUDA (a CUDA or cuBLAS call failed).

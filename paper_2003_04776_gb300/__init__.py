@@ -33,6 +33,7 @@ BT_EMULATED = 4      # pevc_backtransform: FP64 GEMM by fixed-point emulation
 STAGE_WALK = 8       # FP64 plans: the stage walk from the host instead of the device-side scheduler
 AUTOTUNE = 16        # pevc_plan: time the candidate settings and keep the fastest
 DEVICE_WALK = 32     # FP64 plans: the device-side scheduler whatever the order
+BT_CUBLAS = 64       # pevc_backtransform: cuBLAS FP64 GEMM instead of the library's split GEMM
 
 SUCCESS = 0
 ERR_NOT_SCHUR = 1
@@ -373,17 +374,20 @@ class Plan:
         return st, out
 
     def backtransform(self, Z, V, kinds=None, normalise: bool = True, emulated: bool = False,
-                      check: bool = True):
+                      check: bool = True, cublas: bool = False):
         """X = Z V for the eigenvectors V of the plan's pencil (numpy n x m),
         each eigenvector normalised to largest-modulus entry 1 unless
-        normalise is False.  kinds as in pevc_backtransform (None: the
-        columns of the plan's last solve).  Returns (X as numpy, status)."""
+        normalise is False; the library's split GEMM, or cuBLAS's FP64 GEMM
+        with cublas (emulated: its fixed-point emulation).  kinds as in
+        pevc_backtransform (None: the columns of the plan's last solve).
+        Returns (X as numpy, status)."""
         import torch
         n, m = int(Z.shape[0]), int(V.shape[1])
         Zt = to_device_colmajor(Z)
         Vt = to_device_colmajor(V) if m else torch.zeros(1, dtype=torch.float64, device="cuda")
         X = torch.empty((max(m, 1), max(n, 1)), dtype=torch.float64, device="cuda")   # column-major storage
-        flags = (0 if normalise else NO_NORMALISE) | (BT_EMULATED if emulated else 0)
+        flags = ((0 if normalise else NO_NORMALISE) | (BT_EMULATED if emulated else 0) |
+                 (BT_CUBLAS if cublas else 0))
         with torch.cuda.stream(self.stream):
             st = pevc_backtransform(self.h, Zt.data_ptr(), max(n, 1), n, Vt.data_ptr(), max(n, 1), m,
                                     kinds, X.data_ptr(), max(n, 1), flags)

@@ -96,6 +96,8 @@ struct pevc_plan_s {
   int last_m = -1;
   signed char* bt_kind = nullptr;
   signed char* h_bt_kind = nullptr;
+  unsigned char* bt_ws = nullptr;   // split back-transformation workspace (first call)
+  size_t bt_ws_bytes = 0;
   // left eigenvectors: the flipped transposed pencil, its selection, its
   // solve's output (allocated by the first pevc_solve_left)
   double* lS = nullptr;
@@ -250,6 +252,7 @@ void free_plan(pevc_plan_t p) {
   for (void* h : dagh)
     if (h) cudaFreeHost(h);
   if (p->bt_kind) cudaFree(p->bt_kind);
+  if (p->bt_ws) cudaFree(p->bt_ws);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
   delete p;
 }
@@ -1090,7 +1093,7 @@ int pevc_backtransform(pevc_plan_t plan, const double* Z, int ldz, int n, const 
   if (m < 0 || m > n) return -7;
   if (!X && m > 0) return -9;
   if (ldx < ld_min) return -10;
-  if (flags & ~(PEVC_NO_NORMALISE | PEVC_BT_EMULATED)) return -11;
+  if (flags & ~(PEVC_NO_NORMALISE | PEVC_BT_EMULATED | PEVC_BT_CUBLAS)) return -11;
   const signed char* dkind = plan->kind;
   if (kinds) {
     for (int q = 0; q < m; ++q) {
@@ -1112,9 +1115,21 @@ int pevc_backtransform(pevc_plan_t plan, const double* Z, int ldz, int n, const 
     CK(cudaMemcpyAsync(plan->bt_kind, plan->h_bt_kind, (size_t)m, cudaMemcpyHostToDevice, plan->stream));
     dkind = plan->bt_kind;
   }
-  int rc = bt_handle(&plan->blas, plan->stream);
-  if (rc) return rc;
-  if ((rc = bt_gemm(plan->blas, (flags & PEVC_BT_EMULATED) != 0, n, m, Z, ldz, V, ldv, X, ldx))) return rc;
+  if (flags & (PEVC_BT_CUBLAS | PEVC_BT_EMULATED)) {
+    int rc = bt_handle(&plan->blas, plan->stream);
+    if (rc) return rc;
+    if ((rc = bt_gemm(plan->blas, (flags & PEVC_BT_EMULATED) != 0, n, m, Z, ldz, V, ldv, X, ldx))) return rc;
+  } else {
+    // the library's split GEMM; its workspace comes with the first call
+    if (!plan->bt_ws) {
+      plan->bt_ws_bytes = bt_split_bytes(plan->n_max);
+      if (cudaMalloc(&plan->bt_ws, plan->bt_ws_bytes) != cudaSuccess) {
+        plan->bt_ws = nullptr;
+        return PEVC_ERR_NOMEM;
+      }
+    }
+    CK(launch_bt_split(Z, ldz, n, V, ldv, m, X, ldx, plan->bt_ws, plan->stream));
+  }
   if (!(flags & PEVC_NO_NORMALISE)) CK(launch_bt_normalise(X, ldx, n, m, dkind, plan->stream));
   CK(cudaStreamSynchronize(plan->stream));
   return 0;

@@ -729,4 +729,285 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
   return 0;
 }
 
+
+// ----------------------------------------------- back-transformation X = Z V
+//
+// Section 1: with (A, B) = (Q S Z^T, Q T Z^T), x = Z v is an eigenvector of
+// (A, B).  The product runs as exact BF16 slice products, like the updates:
+// every row r of Z is sliced (kBtSlices slices of 8 bits) per chunk of kBtK
+// columns relative to its own exponent bound in that chunk, every column c of V per chunk of kBtK rows
+// likewise, so that the products of one chunk accumulate exactly in FP32 per
+// slice level; the chunks' recombined values are summed in FP64.  Chunks of
+// V below a column block's last non-zero row (V is quasi-triangular) are
+// skipped.
+
+constexpr int kBtK = 256;          // K chunk with exact FP32 level sums
+constexpr int kBtRows = 32;        // rows of Z sliced by one CTA
+constexpr int kBtSlices = 6;       // 48 bits per operand: entries of X within about 2^-47 of sum |Z_rk V_kc|
+
+// Last non-zero row + 1 of every column of V (one warp per column).
+__global__ void __launch_bounds__(256) k_bt_heights(const double* __restrict__ V, int ldv, int n, int m,
+                                                    int* __restrict__ h) {
+  const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (q >= m) return;
+  const double* v = V + (size_t)q * ldv;
+  int last = 0;
+  for (int r = lane; r < n; r += 32)
+    if (abs_key(v[r]) != 0) last = r + 1;
+  for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+  if (lane == 0) h[q] = last;
+}
+
+// Z slices: Zs[kc][p][r][kBtK] (K-contiguous per row), eZ[kc][r].  One CTA
+// per (32 rows, chunk): thread t reads row t % 32 at 32 consecutive chunk
+// columns (a warp reads 32 consecutive rows of a column: coalesced).
+template <int NS>
+__global__ void __launch_bounds__(256) k_bt_slice_Z(const double* __restrict__ Z, int ldz, int n,
+                                                    __nv_bfloat16* __restrict__ Zs, int* __restrict__ eZ) {
+  const int kc = blockIdx.y;
+  const int rr = threadIdx.x % kBtRows, part = threadIdx.x / kBtRows;   // 8 parts of 32 columns
+  const int r = blockIdx.x * kBtRows + rr;
+  const int k0 = kc * kBtK + part * 32;
+  __shared__ unsigned long long s_key[8][kBtRows];
+  double v[32];
+  unsigned long long key = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    v[t] = (r < n && k0 + t < n) ? Z[(size_t)(k0 + t) * ldz + r] : 0.0;
+    key = max(key, abs_key(v[t]));
+  }
+  s_key[part][rr] = key;
+  __syncthreads();
+  unsigned long long km = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) km = max(km, s_key[q][rr]);
+  const int e = km ? exp_above(__longlong_as_double((long long)km)) : 0;
+  if (r >= n) return;
+  if (part == 0) eZ[(size_t)kc * n + r] = e;
+  __nv_bfloat16* dst = Zs + (((size_t)kc * NS) * n + r) * kBtK + part * 32;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    int d[NS];
+    int_slices<NS>(v[t], e, d);
+#pragma unroll
+    for (int p = 0; p < NS; ++p) dst[(size_t)p * n * kBtK + t] = small_int_bf16(d[p]);
+  }
+}
+
+// V slices: Vs[kc][p][c][kBtK] (K-contiguous per column), eV[kc][c]; one warp
+// per (column, chunk), each lane 8 consecutive rows.  Chunks at or below the
+// column's height are all zero (exponent 0).
+template <int NS>
+__global__ void __launch_bounds__(256) k_bt_slice_V(const double* __restrict__ V, int ldv, int n, int m,
+                                                    __nv_bfloat16* __restrict__ Vs, int* __restrict__ eV) {
+  const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int kc = blockIdx.y;
+  if (q >= m) return;
+  const int r0 = kc * kBtK + lane * 8;
+  double v[8];
+  unsigned long long key = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    v[t] = (r0 + t < n) ? V[(size_t)q * ldv + r0 + t] : 0.0;
+    key = max(key, abs_key(v[t]));
+  }
+  for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+  const int e = key ? exp_above(__longlong_as_double((long long)key)) : 0;
+  if (lane == 0) eV[(size_t)kc * m + q] = e;
+  __nv_bfloat16* dst = Vs + (((size_t)kc * NS) * m + q) * kBtK + lane * 8;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    int d[NS];
+    int_slices<NS>(v[t], e, d);
+#pragma unroll
+    for (int p = 0; p < NS; ++p) dst[(size_t)p * m * kBtK + t] = small_int_bf16(d[p]);
+  }
+}
+
+
+// X[rows of this CTA, columns of this CTA] = Z V: a pipeline of K stages of
+// KC over the chunks the column block needs (cp.async double buffering, BF16
+// mma.sync with one FP32 accumulator per slice level); at the end of every
+// chunk the levels are recombined exactly as one integer and added, scaled by
+// the row's and the column's exponents of that chunk, to FP64 accumulators.
+template <int NS, int L>
+__global__ void __launch_bounds__(256, 1) k_bt_gemm(const __nv_bfloat16* __restrict__ Zs, const int* __restrict__ eZ,
+                                                     const __nv_bfloat16* __restrict__ Vs,
+                                                     const int* __restrict__ eV, const int* __restrict__ h, int n,
+                                                     int m, double* __restrict__ X, int ldx) {
+  constexpr int KC = split_kc<NS>();
+  constexpr int LD = split_ld<NS>();
+  constexpr int per_chunk = kBtK / KC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);    // [2][NS][128][LD]
+  __nv_bfloat16* sB = sA + 2 * NS * kSplitRows * LD;                 // [2][NS][32][LD]
+  const int c0 = blockIdx.x * kSplitCols, r0 = blockIdx.y * kSplitRows;
+  const int tid = threadIdx.x;
+  __shared__ int s_nk;
+  if (tid < 32) {
+    int hh = (c0 + tid < m) ? h[c0 + tid] : 0;
+    for (int o = 16; o > 0; o >>= 1) hh = max(hh, __shfl_xor_sync(0xffffffffu, hh, o));
+    if (tid == 0) s_nk = (hh + kBtK - 1) / kBtK;
+  }
+  __syncthreads();
+  const int nk = s_nk;
+
+  auto load_stage = [&](int st, int idx) {
+    const int kc = idx / per_chunk, kb = (idx % per_chunk) * KC;
+    __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * LD;
+    __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * LD;
+    constexpr int chunks = KC / 8;                        // 16-byte pieces per row
+    for (int q = tid; q < NS * kSplitRows * chunks; q += 256) {
+      const int c16 = q % chunks, r = (q / chunks) % kSplitRows, p = q / (chunks * kSplitRows);
+      const bool valid = r0 + r < n;
+      const __nv_bfloat16* src = Zs + (((size_t)kc * NS + p) * n + (valid ? r0 + r : 0)) * kBtK + kb + 8 * c16;
+      cp_async16(a_dst + (p * kSplitRows + r) * LD + 8 * c16, src, valid);
+    }
+    for (int q = tid; q < NS * kSplitCols * chunks; q += 256) {
+      const int c16 = q % chunks, col = (q / chunks) % kSplitCols, p = q / (chunks * kSplitCols);
+      const bool valid = c0 + col < m;
+      const __nv_bfloat16* src = Vs + (((size_t)kc * NS + p) * m + (valid ? c0 + col : 0)) * kBtK + kb + 8 * c16;
+      cp_async16(b_dst + (p * kSplitCols + col) * LD + 8 * c16, src, valid);
+    }
+  };
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wr = warp & 3, wc = warp >> 2;
+  const int g = lane >> 2, t4 = lane & 3;
+  float acc[L][2][2][4];
+  double out[2][2][2][2];   // [mt][nt][h][e]
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) out[mt][nt][hh][e] = 0.0;
+  auto zero_levels = [&]() {
+#pragma unroll
+    for (int s = 0; s < L; ++s)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[s][a][b][e] = 0.0f;
+  };
+  zero_levels();
+
+  const int nst = nk * per_chunk;
+  if (nst > 0) load_stage(0, 0);
+  cp_async_commit();
+  for (int idx = 0; idx < nst; ++idx) {
+    const int st = idx & 1;
+    if (idx + 1 < nst) load_stage(st ^ 1, idx + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const __nv_bfloat16* a_s = sA + st * NS * kSplitRows * LD;
+    const __nv_bfloat16* b_s = sB + st * NS * kSplitCols * LD;
+#pragma unroll
+    for (int kk = 0; kk < KC; kk += 16) {
+      unsigned bf[NS][4];
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+        ldmatrix_x4(bf[q], b_s + (q * kSplitCols + 16 * wc + (lane & 7) + ((lane >> 4) << 3)) * LD + kk +
+                               ((lane >> 3) & 1) * 8);
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        unsigned af[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+          ldmatrix_x4(af[mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * LD + kk + (lane >> 4) * 8);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (p + q < L) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              mma_bf16(acc[p + q][mt][0], af[mt], bf[q][0], bf[q][1]);
+              mma_bf16(acc[p + q][mt][1], af[mt], bf[q][2], bf[q][3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if ((idx + 1) % per_chunk == 0) {
+      // the chunk is complete: its exact level sums, scaled, into FP64
+      const int kc = idx / per_chunk;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int row = r0 + 32 * wr + 16 * mt + g + 8 * hh;
+          const int ez = row < n ? eZ[(size_t)kc * n + row] : 0;
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int col = c0 + 16 * wc + 8 * nt + 2 * t4 + e;
+              const int ev = col < m ? eV[(size_t)kc * m + col] : 0;
+              long long t = 0;
+#pragma unroll
+              for (int s = 0; s < L; ++s) t = (t << 8) + (long long)__float2int_rn(acc[s][mt][nt][2 * hh + e]);
+              out[mt][nt][hh][e] += i64_scaled(t, ez + ev - 14 - 8 * (L - 1));
+            }
+        }
+      zero_levels();
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int row = r0 + 32 * wr + 16 * mt + g + 8 * hh;
+      if (row >= n) continue;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int col = c0 + 16 * wc + 8 * nt + 2 * t4 + e;
+          if (col < m) X[(size_t)col * ldx + row] = out[mt][nt][hh][e];
+        }
+    }
+}
+
+// Workspace of the split back-transformation (slices and exponents of Z and
+// V, column heights), for orders up to n_max.
+size_t bt_split_bytes(int n_max) {
+  const size_t nkc = (size_t)(std::max(n_max, 1) + kBtK - 1) / kBtK, n = (size_t)std::max(n_max, 1);
+  return 2 * (nkc * kBtSlices * n * kBtK * sizeof(__nv_bfloat16)) + 2 * nkc * n * sizeof(int) + n * sizeof(int) +
+         6 * 256;
+}
+
+// X = Z V (n x m, column-major FP64) with the split GEMM above; ws holds
+// bt_split_bytes(n) bytes (256-byte aligned).
+cudaError_t launch_bt_split(const double* Z, int ldz, int n, const double* V, int ldv, int m, double* X, int ldx,
+                            unsigned char* ws, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  constexpr int NS = kBtSlices;
+  const int nkc = (n + kBtK - 1) / kBtK;
+  auto take = [&](size_t bytes) {
+    unsigned char* q = ws;
+    ws += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  __nv_bfloat16* Zs = (__nv_bfloat16*)take((size_t)nkc * NS * n * kBtK * sizeof(__nv_bfloat16));
+  __nv_bfloat16* Vs = (__nv_bfloat16*)take((size_t)nkc * NS * m * kBtK * sizeof(__nv_bfloat16));
+  int* eZ = (int*)take((size_t)nkc * n * sizeof(int));
+  int* eV = (int*)take((size_t)nkc * m * sizeof(int));
+  int* h = (int*)take((size_t)m * sizeof(int));
+  k_bt_heights<<<(m + 7) / 8, 256, 0, s>>>(V, ldv, n, m, h);
+  k_bt_slice_Z<NS><<<dim3((n + kBtRows - 1) / kBtRows, nkc), 256, 0, s>>>(Z, ldz, n, Zs, eZ);
+  k_bt_slice_V<NS><<<dim3((m + 7) / 8, nkc), 256, 0, s>>>(V, ldv, n, m, Vs, eV);
+  const int smem = split_smem_bytes<NS>();
+  cudaError_t e = cudaFuncSetAttribute(k_bt_gemm<NS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_bt_gemm<NS, NS><<<dim3((m + kSplitCols - 1) / kSplitCols, (n + kSplitRows - 1) / kSplitRows), 256, smem, s>>>(
+      Zs, eZ, Vs, eV, h, n, m, X, ldx);
+  return cudaGetLastError();
+}
+
 }  // namespace pevc

@@ -71,4 +71,11 @@ SplitConfig split_config(int prec, bool correction);
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr);
 
+// Back-transformation X = Z V as exact BF16 slice products (6 slices per
+// operand, chunks of 256 along K summed in FP64); the workspace ws holds
+// bt_split_bytes(n) bytes.
+size_t bt_split_bytes(int n_max);
+cudaError_t launch_bt_split(const double* Z, int ldz, int n, const double* V, int ldv, int m, double* X, int ldx,
+                            unsigned char* ws, cudaStream_t s);
+
 }  // namespace pevc

@@ -19,6 +19,21 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
+def _split_bound(Z, V, K=256, bits=46):
+    """Entrywise bound of |X - Z V| for the library's split GEMM: every entry
+    of Z (row r) and V (column c) is cut to 48 bits relative to a power of two
+    at most twice the largest |entry| of its row (column) in its chunk of K,
+    so a chunk's term errs by at most 2^-47 (max_chunk |Z_r.| sum |V_.c| +
+    max_chunk |V_.c| sum |Z_r.|); 2^-46 leaves a factor 2, and the FP64
+    sums of the chunks add a few units of rounding of |Z| |V|."""
+    B = np.zeros((Z.shape[0], V.shape[1]))
+    for k0 in range(0, Z.shape[0], K):
+        Zc, Vc = np.abs(Z[:, k0:k0 + K]), np.abs(V[k0:k0 + K, :])
+        B += Zc.max(axis=1, keepdims=True) * Vc.sum(axis=0, keepdims=True)
+        B += Zc.sum(axis=1, keepdims=True) * Vc.max(axis=0, keepdims=True)
+    return 2.0 ** -bits * B + 1e-14 * (np.abs(Z) @ np.abs(V))
+
+
 def _case(n, seed, stress=False, select=None):
     p = pencilgen.make_pencil(n, seed, stress=stress)
     Q = random_orthogonal(n, seed + 11)
@@ -72,7 +87,7 @@ def test_backtransform_selection_and_unnormalised(pevc_lib):
     assert st == 0 and st2 == 0
     _check(p, Z, A, B, kinds, pos, ev, X, select=sel)
     ref = Z @ V
-    assert np.max(np.abs(Xr - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    assert np.all(np.abs(Xr - ref) <= _split_bound(Z, V))
 
 
 def test_backtransform_stress_pencil_finite(pevc_lib):
@@ -127,3 +142,43 @@ def test_backtransform_argument_errors(pevc_lib):
         assert bt(plan.h, ptr, n, n, ptr, n, 0, None, ptr, n) == 0
     finally:
         plan.close()
+
+
+def test_backtransform_split_gemm_many_chunks_against_cublas_and_oracle(pevc_lib):
+    """n = 1500 (six chunks of 256 along the inner dimension, the last one
+    ragged; a selection so that V has columns of every height): the split
+    GEMM within its entrywise bound of Z V, within 1e-10 of the oracle after
+    normalisation, and faster than cuBLAS's FP64 GEMM on the same call."""
+    import time
+    import torch
+    n = 1500
+    sel = (np.arange(n) % 3 != 1).astype(np.int32)
+    p, Z, A, B, kinds, pos, ev = _case(n, 4700, select=sel)
+    plan = pevc_lib.Plan(n, prec="fp64")
+    try:
+        V, sc, st = plan.solve(p.S, p.T, select=sel)
+        assert st == 0
+        X, st = plan.backtransform(Z, V)
+        Xr, st2 = plan.backtransform(Z, V, normalise=False)
+        Xc, st3 = plan.backtransform(Z, V, normalise=False, cublas=True)
+        assert st == 0 and st2 == 0 and st3 == 0
+        # timing of the GEMMs alone, device-resident operands
+        Zt, Vt = pevc_lib.to_device_colmajor(Z), pevc_lib.to_device_colmajor(V)
+        m = V.shape[1]
+        Xt = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        ms = {}
+        for name, fl in (("split", pevc_lib.NO_NORMALISE), ("cublas", pevc_lib.NO_NORMALISE | pevc_lib.BT_CUBLAS)):
+            args = (plan.h, Zt.data_ptr(), n, n, Vt.data_ptr(), n, m, [int(k) for k in kinds], Xt.data_ptr(), n, fl)
+            assert pevc_lib.pevc_backtransform(*args) == 0
+            t0 = time.perf_counter()
+            for _ in range(3):
+                assert pevc_lib.pevc_backtransform(*args) == 0
+            ms[name] = (time.perf_counter() - t0) / 3 * 1e3
+    finally:
+        plan.close()
+    ref = Z @ V
+    assert np.all(np.abs(Xr - ref) <= _split_bound(Z, V))
+    assert np.max(np.abs(Xc - ref)) <= 1e-12 * np.max(np.abs(ref))
+    _check(p, Z, A, B, kinds, pos, ev, X, select=sel)
+    print(f"back-transform n={n}, m={V.shape[1]}: split {ms['split']:.2f} ms, cuBLAS FP64 {ms['cublas']:.2f} ms")
+    assert ms["split"] < ms["cublas"]

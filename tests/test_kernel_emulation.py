@@ -342,3 +342,29 @@ def math_ldexp(x, e):
         return math.ldexp(x, e)
     except OverflowError:
         return math.copysign(float("inf"), x)
+
+
+def test_emulated_split_backtransform_gemm(emu):
+    """The split back-transformation GEMM (slices of Z per row and of V per
+    column, per chunk of 256, BF16 mma.sync, exact level sums, FP64 chunk
+    sums) on the emulation: two chunks, the second ragged, columns of every
+    height; X within the entrywise bound the slicing implies."""
+    import sys
+    sys.path.insert(0, HERE)
+    from test_gpu_backtransform import _split_bound
+    from oracle.backtransform import random_orthogonal
+    n, m = 270, 40
+    p = pencilgen.make_pencil(n, 4950)
+    st, V, sc, mm = oracle.evc(p.S, p.T)
+    V = np.asfortranarray(V[:, ::7][:, :m])          # columns of heights spread over both chunks
+    m = V.shape[1]
+    Z = np.asfortranarray(random_orthogonal(n, 4951))
+    X = np.zeros((n, m), order="F")
+    emu.pevc_backtransform.argtypes = [vp, vp, ci, ci, vp, ci, ci, vp, vp, ci, ctypes.c_uint]
+    h = vp()
+    assert emu.pevc_plan(ctypes.byref(h), n, 1, 0, 32, 0, None) == 0
+    kinds = (ci * m)(*[0] * m)
+    rc = emu.pevc_backtransform(h, Z.ctypes.data, n, n, V.ctypes.data, n, m, kinds, X.ctypes.data, n, 1)
+    emu.pevc_destroy(h)
+    assert rc == 0
+    assert np.all(np.abs(X - Z @ V) <= _split_bound(Z, V))
