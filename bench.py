@@ -377,7 +377,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-arms", action="store_true")
     # "real" is the headline workload; "cplx" times the complex-pencil solve
     # (FP64) on its own, as a separate line
-    ap.add_argument("--workload", default="real", choices=["real", "cplx", "batched"])
+    ap.add_argument("--workload", default="real", choices=["real", "cplx", "batched", "backtransform"])
     return ap.parse_args(argv)
 
 
@@ -588,6 +588,72 @@ def run_batched(args):
     return 0
 
 
+def run_backtransform(args):
+    """Back-transformation X = Z V of all eigenvectors of the n x n benchmark
+    pencil (V from an FP64-accurate split solve, resident in HBM; Z dense,
+    N(0, 1/n) entries -- the GEMM's speed does not depend on Z being
+    orthogonal): the library's split GEMM against cuBLAS's FP64 GEMM, each
+    timed with CUDA events (normalisation included)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import pencilgen
+    import paper_2003_04776_gb300 as pevc
+    n = args.n
+    p = pencilgen.config_pencil(3, n=n)
+    stream = torch.cuda.current_stream()
+    St, Tt = pevc.to_device_colmajor(p.S), pevc.to_device_colmajor(p.T)
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    sc = torch.empty(n, dtype=torch.int32, device="cuda")
+    plan = pevc.Plan(n, prec="bf16x5", stream=stream)
+    st, m = plan.solve_colmajor(St, Tt, n, V, sc)
+    assert st == 0 and m == n
+    del St, Tt
+    g = torch.Generator(device="cuda").manual_seed(pencilgen.config_seed(3) + 77)
+    Z = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g) / n ** 0.5
+    X = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    res = {}
+    for name, fl, steps in (("split", 0, max(1, args.steps)), ("cublas", pevc.BT_CUBLAS, 1)):
+        call = lambda: pevc.pevc_backtransform(plan.h, Z.data_ptr(), n, n, V.data_ptr(), n, n, None, X.data_ptr(),
+                                               n, fl)
+        assert call() == 0                     # first use: workspace or handle
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                assert call() == 0
+            e1.record(stream)
+            torch.cuda.synchronize()
+        res[name] = (e0.elapsed_time(e1) / steps, clk.summary(), steps)
+        if name == "split":
+            Xs = X.clone()
+    # the two results against each other (normalised eigenvectors)
+    diff = float((Xs - X).abs().max().item())
+    plan.close()
+    F = 2.0 * n * n * n                       # nominal GEMM flops (the split GEMM skips V's zero chunks)
+    ms, clk, steps = res["split"]
+    peaks, src = load_peaks()
+    slice_flops = 21 * sum(2.0 * n * min(n, ((c + 2 + 255) // 256) * 256) for c in range(n))
+    line = {"metric": "back-transformation X = Z V of all eigenvectors, n=%d" % n,
+            "value": round(F / (ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s (2 n^3 nominal)", "n_gpus": 1,
+            "steps": steps, "warmup": 1, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split(6)+f64", "data": "synthetic",
+            "config": {"workload": f"X = Z V, V: the eigenvectors of the n={n} benchmark pencil, Z dense", "n": n},
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                         "achieved": round(slice_flops / (ms * 1e-3) / 1e12, 2),
+                         "peak": peaks.get("bf16_tflops_sustained"), "peak_source": f"{src} bf16 sustained",
+                         "frac": round(slice_flops / (ms * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained", 1.0), 4),
+                         "kernel": "k_bt_gemm (mma.sync BF16, 21 slice products per chunk; slicing included)"},
+            "cublas_fp64": {"ms_per_step": round(res["cublas"][0], 3),
+                            "value": round(F / (res["cublas"][0] * 1e-3) / 1e9, 2)},
+            "speedup_over_cublas_fp64": round(res["cublas"][0] / ms, 2),
+            "max_abs_diff_vs_cublas_normalised": diff, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def accuracy_of(St, Tt, V, pencil):
     """Accuracy of an all-eigenvector solve, outside any timed region: the
     residual of every column (GPU FP64 GEMMs) and the count of non-finite
@@ -649,6 +715,8 @@ def main():
         return run_complex(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "backtransform":
+        return run_backtransform(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -99,9 +99,8 @@ typedef struct pevc_plan_s *pevc_plan_t;
  *   flags      PEVC_NO_NORMALISE | PEVC_NO_CORRECTION | PEVC_STAGE_WALK |
  *              PEVC_DEVICE_WALK | PEVC_AUTOTUNE.  FP64 plans walk the task
  *              graph with the device-side scheduler (one persistent launch,
- *              Section 3 and Section 5.3) for batches and orders up to 4096,
- *              stage by stage from the host above; the walk flags force one
- *              (not both).  Split plans use the stage walk (their tcgen05
+ *              Section 3 and Section 5.3) for batches, stage by stage from the
+ *              host for single pencils; the walk flags force one (not both).  Split plans use the stage walk (their tcgen05
  *              update needs a whole SM per CTA).  With PEVC_AUTOTUNE the plan
  *              times one solve of
  *              each candidate setting on a synthetic pencil of order n_max

@@ -182,11 +182,12 @@ int choose_tile(int n_max, int prec) {
 }
 
 // Default walk of FP64 plans (PEVC_AUTOTUNE measures instead): the device-side
-// scheduler for batches and for orders up to 4096, where stages are short and
-// the per-stage barriers of the host walk cost most; the stage walk above,
-// where its 256-thread update kernel keeps the FP64 pipe busier (n = 20000:
-// 5.26 s against 5.81 s).
-bool default_dag(int n_max, int batch_max) { return batch_max > 1 || n_max <= 4096; }
+// scheduler for batches, where it runs every pencil's graph in one launch
+// (1210 against 903 pencils/s on the batched workload); the stage walk for
+// single pencils, where its 256-thread update kernel keeps the FP64 pipe
+// busier than the scheduler's 128-thread update tasks (n = 4000: 56 against
+// 67 ms; n = 20000: 5.26 against 5.81 s).
+bool default_dag(int, int batch_max) { return batch_max > 1; }
 
 template <typename Tp>
 int dalloc(Tp** p, size_t count) {

@@ -74,7 +74,7 @@ def test_dag_selection_and_empty_column_tiles(pevc_lib, monkeypatch):
 
 
 def test_scheduler_wait_runs_out_and_context_survives(pevc_lib):
-    plan = pevc_lib.Plan(200, prec="fp64")
+    plan = pevc_lib.Plan(200, prec="fp64", device_walk=True)
     try:
         h = plan.h
         assert pevc_lib.pevc_scheduler_selftest(h, 0, 2_000_000) == 0
