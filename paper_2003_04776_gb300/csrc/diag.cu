@@ -1,8 +1,6 @@
 // diag.cu -- diagonal-tile kernel launched once per stage: kernel 1 (tips)
 // and kernel 3 (the small solves S_ii Z D - T_ii Z B = Y_ij) of Section 3,
 // one CTA per (tile, column chunk), each running diag_tile (diag_tile.cuh).
-#include <cstdlib>
-
 #include "diag_tile.cuh"
 
 namespace pevc {
@@ -20,38 +18,11 @@ __global__ void __launch_bounds__(kMaxTile, 5) k_diag(Problem P, int i_row, int 
   diag_tile<CB>(P, i, j, chunk, mode, (int)(blockIdx.x + blockIdx.y) & 3, blockIdx.x == 0 && blockIdx.y == 0, sm);
 }
 
-// The warp-specialised variant: a fifth warp solves the next block while the
-// row owners apply the current one (diag_tile<CB, true>); four CTAs per SM.
-template <int CB>
-__global__ void __launch_bounds__(kMaxTile + 32, 4) k_diag_ws(Problem P, int i_row, int mode) {
-  __shared__ DiagSmemWS<CB> sm;
-  const bool tips = mode != kDiagSolve;
-  const int j = tips ? (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;
-  const int i = tips ? j : i_row;
-  const int chunk = P.dchunk_first[j] + (int)blockIdx.x;
-  if (chunk >= P.dchunk_first[j + 1]) return;
-  diag_tile<CB, true>(P, i, j, chunk, mode, 0, blockIdx.x == 0 && blockIdx.y == 0, sm);
-}
-
-namespace {
-// PEVC_DIAG_KERNEL=plain selects the four-warp kernel (for comparisons).
-bool diag_ws() {
-  static const bool ws = [] {
-    const char* e = getenv("PEVC_DIAG_KERNEL");
-    return !(e && e[0] == 'p');
-  }();
-  return ws;
-}
-}  // namespace
-
 cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s) {
   const int ntiles = (mode != kDiagSolve) ? P.M : (P.M - 1 - i);
   if (ntiles <= 0 || P.dchunk_max <= 0) return cudaSuccess;
   dim3 grid(P.dchunk_max, ntiles);
-  if (diag_ws())
-    k_diag_ws<kDiagChunk><<<grid, kMaxTile + 32, 0, s>>>(P, i, mode);
-  else
-    k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, i, mode);
+  k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, i, mode);
   return cudaGetLastError();
 }
 

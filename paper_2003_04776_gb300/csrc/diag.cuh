@@ -38,16 +38,6 @@ struct DiagSmem {
   unsigned char pf[kMaxTile][CB];    // 2x2 pivot position pi | pj << 1
 };
 
-// The warp-specialised diagonal solve (diag_tile<CB, true>): one extra warp
-// solves block b + 1 while the row-owner warps apply block b, so every
-// per-block result is double buffered (slot = block index & 1).
-template <int CB>
-struct DiagSmemWS : DiagSmem<CB> {
-  double2 wPQ[2][2][CB];
-  double wW[2][2][CB], wpiv[2][2][CB];
-  int wsh[2][CB], wany[2];
-};
-
 struct ColStep {
   double P[2][2];   // [block col][pair member]: beta * w
   double Q[2][2];   //                          : Re/Im of alpha * w

@@ -32,31 +32,14 @@
 
 namespace pevc {
 
-// Named barrier 1 of a warp-specialised diagonal solve: the row owners arrive
-// (without waiting), the solver warp waits for them.
-__device__ __forceinline__ void named_arrive(int id, int count) {
-  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(count) : "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
-}
-
 // One diagonal-tile task: tile (i, j) (i == j for the tips), column chunk
 // `chunk` (an index into the chunk lists), solved by the 128 threads of the
 // calling CTA in the shared memory sm.  pa_warp picks the warp of the block
 // solves; with prefetch the CTA also brings the diagonal tile's S and T
 // columns into L2 for the other chunks of the row.
-//
-// WS (warp specialisation, 160 threads, shared memory DiagSmemWS): warps 0-3
-// own the rows as above; warp 4 solves the blocks, one ahead.  In step b the
-// owners apply block b's scale and update to the rows of block b + 1 first,
-// publish them and arrive at named barrier 1, then update the rows above and
-// write block b's values; meanwhile warp 4, past barrier 1, solves block b + 1
-// into the other buffer.  A step then lasts about as long as the longer of the
-// two, instead of their sum and two barriers.
-template <int CB, bool WS = false, class Smem>
+template <int CB>
 __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int chunk, int mode, int pa_warp,
-                                          bool prefetch, Smem& sm) {
+                                          bool prefetch, DiagSmem<CB>& sm) {
   const bool tips = mode != kDiagSolve;
   const int cs = P.cstart[j];
   const int pos0 = P.dchunk_pos[chunk];
@@ -220,7 +203,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
   //      a step lasts as long as its busiest warp)
   constexpr int NG = kMaxTile / CB;
   const int t = lr % CB, g = lr / CB;
-  const bool tcol = lr < kMaxTile && t < nq;     // a row owner of a chunk column
+  const bool tcol = t < nq;
   double vals[CB];
 #pragma unroll
   for (int k = 0; k < CB; ++k) {
@@ -244,144 +227,50 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
   }
   __syncthreads();
 
-  if constexpr (!WS) {
-    for (int bidx = 0; bidx < nb; ++bidx) {
-      const int li0 = s_bs[bidx], sz = s_bz[bidx];
-      const int i0 = r0 + li0;
-      if (tcol) {
-  #pragma unroll
-        for (int k = 0; k < CB; ++k) {
-          const int r = g + NG * k;
-          if (r >= li0 && r < li0 + sz) s_piv[r - li0][t] = vals[k];
-        }
-      }
-      double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
-      const int ln = (bidx + 1 < nb) ? s_bs[bidx + 1] : 0, szn = (bidx + 1 < nb) ? s_bz[bidx + 1] : 1;
-      if (lr < ln) {
-        nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
-        nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
-        if (szn == 2) {
-          nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
-          nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
-        }
-      }
-      __syncthreads();
-      // ---- phase A: the block's solve for every unit; only the
-      //      right-hand-side-dependent arithmetic is left here (the 2x2
-      //      blocks of complex pairs in a right-hand-side solve take eight
-      //      lanes per unit, everything else one)
-      if ((lr >> 5) == pa_warp && mode == kDiagSolve && pairs && sz == 2) {
-        const bool anysh = pair2_step_warp<CB>(lr & 31, nu, li0, s_piv, s_pre + s_boff[bidx], s_ep[bidx],
-                                              s_pf[bidx], s_tn[bidx], s_a, s_b, s_beta, s_y, s_e, s_act, s_sh,
-                                              s_PQ, s_W);
-        if ((lr & 31) == 0) s_anysh = anysh ? 1 : 0;
-      } else if ((lr >> 5) == pa_warp) {
-        const int u = lr & 31;
-        int myshift = 0;
-        if (u < nu) {
-          const int t0c = pairs ? 2 * u : u;
-          const int tip = s_tip[u];
-          const bool has_above = li0 > 0;
-          const double a = s_a[u], b = s_b[u], beta = s_beta[u];
-          const double tn = s_tn[bidx][u];
-          double y = s_y[u];
-          bool active = s_act[u];
-          int e = s_e[u];
-          const ColStep st = unit_step<CB>(D, mode, tips, i0, tip, li0, sz, has_above, pairs, t0c, u, a, b, beta, tn,
-                                           s_ep[bidx][u], s_pre + s_boff[bidx], s_pf[bidx][u], s_piv, y, active, e);
-          s_e[u] = e;
-          s_act[u] = active;
-          s_y[u] = y;
-          myshift = st.shift;
-          const int ncols = pairs ? 2 : 1;
-  #pragma unroll
-          for (int mm = 0; mm < 2; ++mm) {
-            if (mm >= ncols) break;
-            s_sh[t0c + mm] = st.shift;
-  #pragma unroll
-            for (int x = 0; x < 2; ++x) {
-              s_PQ[x][t0c + mm] = make_double2(st.P[x][mm], st.Q[x][mm]);
-              s_W[x][t0c + mm] = st.W[x][mm];
-            }
-          }
-        }
-        const bool anysh = __any_sync(0xffffffffu, myshift != 0);
-        if (u == 0) s_anysh = anysh ? 1 : 0;
-      }
-      __syncthreads();
-      // ---- phase B: the scale and the rank update of the rows above, the
-      //      solved values into the block rows
-      if (tcol) {
-        if (s_anysh) {
-          const int sh = s_sh[t];
-          if (sh) {
-  #pragma unroll
-            for (int k = 0; k < CB; ++k) vals[k] = pow2_scale(vals[k], -sh);
-          }
-        }
-        // row steps k run while the warp's first row group is above the block
-        // (a warp-uniform exit, so no FP64 instruction is issued for a step
-        // without work); lanes past the block's first row keep their values
-        const double (*cn)[kMaxTile] = s_nc[bidx & 1];
-        const double2 pq0 = s_PQ[0][t];
-        const int wg = (lr >> 5) * (32 / CB);
-        if (sz == 1) {
-  #pragma unroll
-          for (int k = 0; k < CB; ++k) {
-            if (wg + NG * k >= li0) break;
-            const int r = g + NG * k;
-            const double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
-            vals[k] = r < li0 ? v : vals[k];
-          }
-        } else {
-          const double2 pq1 = s_PQ[1][t];
-  #pragma unroll
-          for (int k = 0; k < CB; ++k) {
-            if (wg + NG * k >= li0) break;
-            const int r = g + NG * k;
-            const double v = fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]))));
-            vals[k] = r < li0 ? v : vals[k];
-          }
-        }
-  #pragma unroll
-        for (int k = 0; k < CB; ++k) {
-          const int r = g + NG * k;
-          if (r >= li0 && r < li0 + sz) vals[k] = s_W[r - li0][t];
-        }
-      }
-      if (lr < ln) {
-        double (*cw)[kMaxTile] = s_nc[(bidx + 1) & 1];
-        cw[0][lr] = nS0;
-        cw[1][lr] = nT0;
-        cw[2][lr] = nS1;
-        cw[3][lr] = nT1;
+  for (int bidx = 0; bidx < nb; ++bidx) {
+    const int li0 = s_bs[bidx], sz = s_bz[bidx];
+    const int i0 = r0 + li0;
+    if (tcol) {
+#pragma unroll
+      for (int k = 0; k < CB; ++k) {
+        const int r = g + NG * k;
+        if (r >= li0 && r < li0 + sz) s_piv[r - li0][t] = vals[k];
       }
     }
-  } else {
-    const bool solver = lr >= kMaxTile;
-    const int sl = lr & 31;
-    // the solve of block bidx for every unit (solver warp), into buffer slot
-    auto solve_block = [&](int bidx, int slot) {
-      const int li0 = s_bs[bidx], sz = s_bz[bidx];
-      const int i0 = r0 + li0;
-      if (mode == kDiagSolve && pairs && sz == 2) {
-        const bool anysh = pair2_step_warp<CB>(sl, nu, li0, sm.wpiv[slot], s_pre + s_boff[bidx], s_ep[bidx],
-                                              s_pf[bidx], s_tn[bidx], s_a, s_b, s_beta, s_y, s_e, s_act,
-                                              sm.wsh[slot], sm.wPQ[slot], sm.wW[slot]);
-        if (sl == 0) sm.wany[slot] = anysh ? 1 : 0;
-        return;
+    double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
+    const int ln = (bidx + 1 < nb) ? s_bs[bidx + 1] : 0, szn = (bidx + 1 < nb) ? s_bz[bidx + 1] : 1;
+    if (lr < ln) {
+      nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
+      nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
+      if (szn == 2) {
+        nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
+        nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
       }
-      const int u = sl;
+    }
+    __syncthreads();
+    // ---- phase A: the block's solve for every unit; only the
+    //      right-hand-side-dependent arithmetic is left here (the 2x2
+    //      blocks of complex pairs in a right-hand-side solve take eight
+    //      lanes per unit, everything else one)
+    if ((lr >> 5) == pa_warp && mode == kDiagSolve && pairs && sz == 2) {
+      const bool anysh = pair2_step_warp<CB>(lr & 31, nu, li0, s_piv, s_pre + s_boff[bidx], s_ep[bidx],
+                                            s_pf[bidx], s_tn[bidx], s_a, s_b, s_beta, s_y, s_e, s_act, s_sh,
+                                            s_PQ, s_W);
+      if ((lr & 31) == 0) s_anysh = anysh ? 1 : 0;
+    } else if ((lr >> 5) == pa_warp) {
+      const int u = lr & 31;
       int myshift = 0;
       if (u < nu) {
         const int t0c = pairs ? 2 * u : u;
+        const int tip = s_tip[u];
+        const bool has_above = li0 > 0;
         const double a = s_a[u], b = s_b[u], beta = s_beta[u];
+        const double tn = s_tn[bidx][u];
         double y = s_y[u];
         bool active = s_act[u];
         int e = s_e[u];
-        const ColStep st = unit_step<CB>(D, mode, tips, i0, s_tip[u], li0, sz, li0 > 0, pairs, t0c, u, a, b, beta,
-                                         s_tn[bidx][u], s_ep[bidx][u], s_pre + s_boff[bidx], s_pf[bidx][u],
-                                         sm.wpiv[slot], y, active, e);
+        const ColStep st = unit_step<CB>(D, mode, tips, i0, tip, li0, sz, has_above, pairs, t0c, u, a, b, beta, tn,
+                                         s_ep[bidx][u], s_pre + s_boff[bidx], s_pf[bidx][u], s_piv, y, active, e);
         s_e[u] = e;
         s_act[u] = active;
         s_y[u] = y;
@@ -390,109 +279,64 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
 #pragma unroll
         for (int mm = 0; mm < 2; ++mm) {
           if (mm >= ncols) break;
-          sm.wsh[slot][t0c + mm] = st.shift;
+          s_sh[t0c + mm] = st.shift;
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
-            sm.wPQ[slot][x][t0c + mm] = make_double2(st.P[x][mm], st.Q[x][mm]);
-            sm.wW[slot][x][t0c + mm] = st.W[x][mm];
+            s_PQ[x][t0c + mm] = make_double2(st.P[x][mm], st.Q[x][mm]);
+            s_W[x][t0c + mm] = st.W[x][mm];
           }
         }
       }
       const bool anysh = __any_sync(0xffffffffu, myshift != 0);
-      if (u == 0) sm.wany[slot] = anysh ? 1 : 0;
-    };
-    // block 0: its rows as loaded, solved before the first step
+      if (u == 0) s_anysh = anysh ? 1 : 0;
+    }
+    __syncthreads();
+    // ---- phase B: the scale and the rank update of the rows above, the
+    //      solved values into the block rows
     if (tcol) {
-      const int li0 = s_bs[0], sz = s_bz[0];
+      if (s_anysh) {
+        const int sh = s_sh[t];
+        if (sh) {
+#pragma unroll
+          for (int k = 0; k < CB; ++k) vals[k] = pow2_scale(vals[k], -sh);
+        }
+      }
+      // row steps k run while the warp's first row group is above the block
+      // (a warp-uniform exit, so no FP64 instruction is issued for a step
+      // without work); lanes past the block's first row keep their values
+      const double (*cn)[kMaxTile] = s_nc[bidx & 1];
+      const double2 pq0 = s_PQ[0][t];
+      const int wg = (lr >> 5) * (32 / CB);
+      if (sz == 1) {
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          if (wg + NG * k >= li0) break;
+          const int r = g + NG * k;
+          const double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
+          vals[k] = r < li0 ? v : vals[k];
+        }
+      } else {
+        const double2 pq1 = s_PQ[1][t];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          if (wg + NG * k >= li0) break;
+          const int r = g + NG * k;
+          const double v = fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]))));
+          vals[k] = r < li0 ? v : vals[k];
+        }
+      }
 #pragma unroll
       for (int k = 0; k < CB; ++k) {
         const int r = g + NG * k;
-        if (r >= li0 && r < li0 + sz) sm.wpiv[0][r - li0][t] = vals[k];
+        if (r >= li0 && r < li0 + sz) vals[k] = s_W[r - li0][t];
       }
     }
-    __syncthreads();
-    if (solver) solve_block(0, 0);
-    __syncthreads();
-    constexpr int kNamed = kMaxTile + 32;
-    for (int bidx = 0; bidx < nb; ++bidx) {
-      const int slot = bidx & 1, nslot = slot ^ 1;
-      const int li0 = s_bs[bidx], sz = s_bz[bidx];
-      const bool more = bidx + 1 < nb;
-      const int ln = more ? s_bs[bidx + 1] : 0, szn = more ? s_bz[bidx + 1] : 1;
-      if (!solver) {
-        double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
-        if (lr < ln) {
-          nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
-          nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
-          if (szn == 2) {
-            nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
-            nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
-          }
-        }
-        const double (*cn)[kMaxTile] = s_nc[slot];
-        double2 pq0 = make_double2(0.0, 0.0), pq1 = make_double2(0.0, 0.0);
-        if (tcol) {
-          if (sm.wany[slot]) {
-            const int sh = sm.wsh[slot][t];
-            if (sh) {
-#pragma unroll
-              for (int k = 0; k < CB; ++k) vals[k] = pow2_scale(vals[k], -sh);
-            }
-          }
-          pq0 = sm.wPQ[slot][0][t];
-          if (sz == 2) pq1 = sm.wPQ[slot][1][t];
-          // the rows of block b + 1 first (they lie just above block b)
-#pragma unroll
-          for (int k = 0; k < CB; ++k) {
-            const int r = g + NG * k;
-            if (r >= ln && r < li0) {
-              double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
-              if (sz == 2) v = fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, v));
-              vals[k] = v;
-              sm.wpiv[nslot][r - ln][t] = v;
-            }
-          }
-        }
-        if (more) named_arrive(1, kNamed);
-        if (tcol) {
-          // then the rows above block b + 1 (a warp-uniform exit, as above)
-          const int wg = (lr >> 5) * (32 / CB);
-          if (sz == 1) {
-#pragma unroll
-            for (int k = 0; k < CB; ++k) {
-              if (wg + NG * k >= ln) break;
-              const int r = g + NG * k;
-              const double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
-              vals[k] = r < ln ? v : vals[k];
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < CB; ++k) {
-              if (wg + NG * k >= ln) break;
-              const int r = g + NG * k;
-              const double v =
-                  fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]))));
-              vals[k] = r < ln ? v : vals[k];
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < CB; ++k) {
-            const int r = g + NG * k;
-            if (r >= li0 && r < li0 + sz) vals[k] = sm.wW[slot][r - li0][t];
-          }
-        }
-        if (lr < ln) {
-          double (*cw)[kMaxTile] = s_nc[nslot];
-          cw[0][lr] = nS0;
-          cw[1][lr] = nT0;
-          cw[2][lr] = nS1;
-          cw[3][lr] = nT1;
-        }
-      } else if (more) {
-        named_sync(1, kNamed);
-        solve_block(bidx + 1, nslot);
-      }
-      __syncthreads();
+    if (lr < ln) {
+      double (*cw)[kMaxTile] = s_nc[(bidx + 1) & 1];
+      cw[0][lr] = nS0;
+      cw[1][lr] = nT0;
+      cw[2][lr] = nS1;
+      cw[3][lr] = nT1;
     }
   }
 

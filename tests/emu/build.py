@@ -61,21 +61,9 @@ def _replace_function(src: str, marker: str, new_def: str) -> str:
     raise RuntimeError(marker)
 
 
-# diag_tile.cuh's named barriers, replaced by the model in cuda_runtime.h
-DIAG_HELPERS = {
-    "void named_arrive(": "__device__ __forceinline__ void named_arrive(int id, int count) "
-                          "{ emu::named_bar(id, count, false); }",
-    "void named_sync(": "__device__ __forceinline__ void named_sync(int id, int count) "
-                        "{ emu::named_bar(id, count, true); }",
-}
-
-
 def _convert(src: str, name: str) -> str:
     if name == "split.cu":
         for marker, new_def in SPLIT_HELPERS.items():
-            src = _replace_function(src, marker, new_def)
-    if name == "diag_tile.cuh":
-        for marker, new_def in DIAG_HELPERS.items():
             src = _replace_function(src, marker, new_def)
     src = re.sub(r'#include "([\w.]+)"',
                  lambda m: f'#include "{BUILD if m.group(1) in HEADERS else CSRC}/{m.group(1)}"', src)

@@ -21,8 +21,6 @@
 #include <cfloat>
 #include <atomic>
 #include <barrier>
-#include <condition_variable>
-#include <mutex>
 #include <memory>
 #include <thread>
 #include <vector>
@@ -84,17 +82,8 @@ struct Warp {
   std::barrier<> bar{32};
   uint64_t slot[32];
 };
-// Named barriers (bar.arrive / bar.sync with a thread count): a generation
-// completes when `count` threads have arrived or synced; sync waits for it.
-struct NamedBar {
-  std::mutex m;
-  std::condition_variable cv;
-  int arrived = 0;
-  unsigned gen = 0;
-};
 struct Cta {
   std::barrier<>* bar;
-  NamedBar named[16];
 };
 inline thread_local uint3 tIdx, bIdx;
 inline thread_local dim3 bDim, gDim;
@@ -156,20 +145,6 @@ void launch(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t, A... arg
 #define gridDim emu::gDim
 
 inline void __syncthreads() { emu::cta->bar->arrive_and_wait(); }
-namespace emu {
-inline void named_bar(int id, int count, bool wait) {
-  NamedBar& b = cta->named[id];
-  std::unique_lock<std::mutex> lk(b.m);
-  const unsigned g = b.gen;
-  if (++b.arrived == count) {
-    b.arrived = 0;
-    ++b.gen;
-    b.cv.notify_all();
-    return;
-  }
-  if (wait) b.cv.wait(lk, [&] { return b.gen != g; });
-}
-}  // namespace emu
 template <class T>
 inline T __shfl_sync(unsigned, T v, int src) { return emu::shfl(v, src & 31); }
 template <class T>

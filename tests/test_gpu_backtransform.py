@@ -138,7 +138,7 @@ def test_backtransform_argument_errors(pevc_lib):
         assert bt(plan.h, ptr, n, n, ptr, n, n + 1, None, ptr, n) == -7
         assert bt(plan.h, ptr, n, n, ptr, n, m - 1, None, ptr, n) == -8     # not the last solve's count
         assert bt(plan.h, ptr, n, n, ptr, n, 2, [1, 0], ptr, n) == -8       # a pair without its second column
-        assert bt(plan.h, ptr, n, n, ptr, n, m, None, ptr, n, 64) == -11
+        assert bt(plan.h, ptr, n, n, ptr, n, m, None, ptr, n, 128) == -11
         assert bt(plan.h, ptr, n, n, ptr, n, 0, None, ptr, n) == 0
     finally:
         plan.close()
