@@ -40,15 +40,16 @@ def flops_all(n: int) -> float:
     return float((2.0 * c * c).sum())
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the launches of one n = 20000 solve) from the ncu captures summarised in
-# profiles/k_update_tc_bf16x5.md and profiles/k_diag_n8000.md, valid only for
-# the kernel sources they were taken on (their hash); any later change to them
-# reports null.
+# DRAM bytes per launch at n = 20000 (dram__bytes_read.sum + dram__bytes_write.sum)
+# from the ncu captures summarised in profiles/ (k_diag_n4000.md,
+# k_update_tc_bf16x5.md): small cases, scaled to the n = 20000 launches by
+# the units one launch processes (the diagonal kernel's CTAs; the update's
+# element updates); valid only for the kernel sources they were taken on
+# (their hash): any later change to them reports null.
 TRAFFIC = {
-    "k_diag": {"bytes_per_launch": 1.1207e7, "n": 20000, "prec": "bf16x5",
-               "sources": ("diag.cu", "diag.cuh", "common.cuh"),
-               "sha256_16": "c873c533c59ed5e8"},
+    "k_diag": {"bytes_per_launch": 1.2754e7, "n": 20000, "prec": "bf16x5",
+               "sources": ("diag.cu", "diag.cuh", "diag_tile.cuh", "common.cuh"),
+               "sha256_16": "40cc9a0f3b1b3b63"},
     "k_update_tc": {"bytes_per_launch": 1.2159e9, "n": 20000, "prec": "bf16x5",
                     "sources": ("update_tc.cu", "tc.cuh", "common.cuh", "split.cuh"),
                     "sha256_16": "5acffce1442da583"},
