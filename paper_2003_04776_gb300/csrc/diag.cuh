@@ -18,13 +18,21 @@ struct DiagSmem {
   double2 PQ[2][CB];                 // per block column, per column: (P, Q)
   double a[CB], b[CB], beta[CB], y[CB];   // per unit (eigenvector)
   double W[2][CB], piv[2][CB];
-  double Sd[kMaxTile][2], Td[kMaxTile][2], tcS[kMaxTile], tcT[kMaxTile];
+  // the diagonal tile's 1x1 / 2x2 blocks and column bounds, read by the
+  // up-front factors only (the complex tips are computed with them);
+  // afterwards the same memory holds the current block's S and T columns
+  union {
+    struct {
+      double Sd[kMaxTile][2], Td[kMaxTile][2], tcS[kMaxTile], tcT[kMaxTile];
+    } blk;
+    double nc[4][kMaxTile];
+  } ov;
+  double tipw[CB][4];                // a complex pair's tip: re, im of its two rows (tip mode)
   // right-hand-side-independent factors per (block, unit): 1x1 blocks the
   // inverted pivot (1 double real, 2 complex), 2x2 blocks the LU factors
   // (4 doubles real, 8 complex) -- at most 2 doubles per row and column
   double pre[2 * kMaxTile * CB];
   double tn[kMaxTile][CB];           // ProtectUpdate's t per (block, unit)
-  double nc[2][4][kMaxTile];         // the next block's S and T columns (double buffered)
   unsigned long long key[CB];        // column maxima
   int lc[CB];                        // local column of chunk column t
   int tip[CB], e[CB], act[CB];       // per unit
@@ -209,9 +217,10 @@ __device__ __forceinline__ void cplx_tip(const DiagBlocks& D, int li0, double a,
 // Phase A of one block step for one eigenvector (unit u): the right-hand-side-
 // dependent part of the robust 1x1 / 2x2 solve and its protection.  piv holds
 // the block rows' current values (the unit's columns t0c, t0c + 1); y, active
-// and e are the unit's running bound, activity and exponent (updated).
+// and e are the unit's running bound, activity and exponent (updated); tipw
+// is a complex pair's tip (cplx_tip, computed up front).
 template <int CB>
-__device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool tips, int i0, int tip, int li0,
+__device__ __forceinline__ ColStep unit_step(const double* tipw, int mode, bool tips, int i0, int tip, int li0,
                                              int sz, bool has_above, bool pairs, int t0c, int u, double a,
                                              double b, double beta, double tn, int ep, const double* f, int pf,
                                              const double (*piv)[CB], double& y, bool& active, int& e) {
@@ -226,7 +235,12 @@ __device__ __forceinline__ ColStep unit_step(const DiagBlocks& D, int mode, bool
     active = true;
     double w[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     if (!pairs) w[0][0] = 1.0;
-    else cplx_tip(D, li0, a, b, beta, w[0][0], w[0][1], w[1][0], w[1][1]);
+    else {
+      w[0][0] = tipw[0];
+      w[0][1] = tipw[1];
+      w[1][0] = tipw[2];
+      w[1][1] = tipw[3];
+    }
     const double x = fmax(cmag(w[0][0], w[0][1]), cmag(w[1][0], w[1][1]));
     const int ku = has_above ? protect_update(0.0, tn, x) : 0;
 #pragma unroll

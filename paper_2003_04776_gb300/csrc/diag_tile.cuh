@@ -70,16 +70,16 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
   auto& s_nb = sm.nb;
   auto& s_n1 = sm.n1;
   auto& s_bord = sm.bord;
-  auto& s_Sd = sm.Sd;
-  auto& s_Td = sm.Td;
-  auto& s_tcS = sm.tcS;
-  auto& s_tcT = sm.tcT;
+  auto& s_Sd = sm.ov.blk.Sd;
+  auto& s_Td = sm.ov.blk.Td;
+  auto& s_tcS = sm.ov.blk.tcS;
+  auto& s_tcT = sm.ov.blk.tcT;
   auto& s_pre = sm.pre;
   auto& s_tn = sm.tn;
   auto& s_ep = sm.ep;
   auto& s_pf = sm.pf;
   auto& s_key = sm.key;
-  auto& s_nc = sm.nc;
+  auto& s_nc = sm.ov.nc;
 
   // one CTA per launch brings the diagonal tile's S and T columns into L2:
   // every CTA of the launch walks the same columns, in step (prefetch
@@ -195,6 +195,13 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
     }
   }
 
+  // the complex tips (kernel 1 on a pair's own 2x2 block), from the staged
+  // blocks while they are still in shared memory
+  if (mode == kDiagTip && pairs && lr < nu) {
+    const int li = s_tip[lr] - r0;
+    cplx_tip(D, li, s_a[lr], s_b[lr], s_beta[lr], sm.tipw[lr][0], sm.tipw[lr][1], sm.tipw[lr][2], sm.tipw[lr][3]);
+  }
+
   // ---- element ownership: thread lr holds column t = lr % CB of the chunk at
   //      rows g + NG k (g = lr / CB, k < CB).  A warp then covers CB columns of
   //      32 / CB interleaved row groups, so the rows above a block -- the only
@@ -211,22 +218,26 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
     vals[k] = 0.0;
     if (mode != kDiagTip && tcol && r < h && s_act[pairs ? t / 2 : t]) vals[k] = Yt[(size_t)s_lc[t] * P.tb + r];
   }
-  // the next block's S and T columns are staged in shared memory (double
-  // buffered, s_nc): loaded into registers at the top of a step, stored after
-  // its rank update
+  // the current block's S and T columns (the rows above it) are staged in
+  // shared memory (s_nc, over the diagonal blocks' memory, free once the
+  // factors and tips above are computed): loaded into registers during the
+  // step before, stored after the step's first barrier (every thread has then
+  // finished the previous step's rank update, the only reader)
+  __syncthreads();
   {
     const int li0 = s_bs[0], sz = s_bz[0];
     if (lr < li0) {
-      s_nc[0][0][lr] = P.S[(size_t)(r0 + li0) * P.lds + r0 + lr];
-      s_nc[0][1][lr] = P.T[(size_t)(r0 + li0) * P.ldt + r0 + lr];
+      s_nc[0][lr] = P.S[(size_t)(r0 + li0) * P.lds + r0 + lr];
+      s_nc[1][lr] = P.T[(size_t)(r0 + li0) * P.ldt + r0 + lr];
       if (sz == 2) {
-        s_nc[0][2][lr] = P.S[(size_t)(r0 + li0 + 1) * P.lds + r0 + lr];
-        s_nc[0][3][lr] = P.T[(size_t)(r0 + li0 + 1) * P.ldt + r0 + lr];
+        s_nc[2][lr] = P.S[(size_t)(r0 + li0 + 1) * P.lds + r0 + lr];
+        s_nc[3][lr] = P.T[(size_t)(r0 + li0 + 1) * P.ldt + r0 + lr];
       }
     }
   }
   __syncthreads();
 
+  double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;   // the next block's columns, in flight
   for (int bidx = 0; bidx < nb; ++bidx) {
     const int li0 = s_bs[bidx], sz = s_bz[bidx];
     const int i0 = r0 + li0;
@@ -237,17 +248,24 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
         if (r >= li0 && r < li0 + sz) s_piv[r - li0][t] = vals[k];
       }
     }
-    double nS0 = 0.0, nT0 = 0.0, nS1 = 0.0, nT1 = 0.0;
+    __syncthreads();
+    if (bidx > 0 && lr < li0) {
+      s_nc[0][lr] = nS0;
+      s_nc[1][lr] = nT0;
+      s_nc[2][lr] = nS1;
+      s_nc[3][lr] = nT1;
+    }
     const int ln = (bidx + 1 < nb) ? s_bs[bidx + 1] : 0, szn = (bidx + 1 < nb) ? s_bz[bidx + 1] : 1;
     if (lr < ln) {
       nS0 = P.S[(size_t)(r0 + ln) * P.lds + r0 + lr];
       nT0 = P.T[(size_t)(r0 + ln) * P.ldt + r0 + lr];
+      nS1 = 0.0;
+      nT1 = 0.0;
       if (szn == 2) {
         nS1 = P.S[(size_t)(r0 + ln + 1) * P.lds + r0 + lr];
         nT1 = P.T[(size_t)(r0 + ln + 1) * P.ldt + r0 + lr];
       }
     }
-    __syncthreads();
     // ---- phase A: the block's solve for every unit; only the
     //      right-hand-side-dependent arithmetic is left here (the 2x2
     //      blocks of complex pairs in a right-hand-side solve take eight
@@ -269,7 +287,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
         double y = s_y[u];
         bool active = s_act[u];
         int e = s_e[u];
-        const ColStep st = unit_step<CB>(D, mode, tips, i0, tip, li0, sz, has_above, pairs, t0c, u, a, b, beta, tn,
+        const ColStep st = unit_step<CB>(sm.tipw[u], mode, tips, i0, tip, li0, sz, has_above, pairs, t0c, u, a, b, beta, tn,
                                          s_ep[bidx][u], s_pre + s_boff[bidx], s_pf[bidx][u], s_piv, y, active, e);
         s_e[u] = e;
         s_act[u] = active;
@@ -304,7 +322,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
       // row steps k run while the warp's first row group is above the block
       // (a warp-uniform exit, so no FP64 instruction is issued for a step
       // without work); lanes past the block's first row keep their values
-      const double (*cn)[kMaxTile] = s_nc[bidx & 1];
+      const double (*cn)[kMaxTile] = s_nc;
       const double2 pq0 = s_PQ[0][t];
       const int wg = (lr >> 5) * (32 / CB);
       if (sz == 1) {
@@ -330,13 +348,6 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
         const int r = g + NG * k;
         if (r >= li0 && r < li0 + sz) vals[k] = s_W[r - li0][t];
       }
-    }
-    if (lr < ln) {
-      double (*cw)[kMaxTile] = s_nc[(bidx + 1) & 1];
-      cw[0][lr] = nS0;
-      cw[1][lr] = nT0;
-      cw[2][lr] = nS1;
-      cw[3][lr] = nT1;
     }
   }
 
