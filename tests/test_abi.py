@@ -77,3 +77,77 @@ def test_watchdog_selftest_argument_checks_without_gpu():
     import paper_2003_04776_gb300 as pevc
     assert pevc.pevc_watchdog_selftest(None, 1, 1000) == -1
     assert pevc.ERR_TIMEOUT == 4
+
+
+def test_scheduler_autotune_and_flag_checks_without_gpu():
+    import paper_2003_04776_gb300 as pevc
+    assert pevc.pevc_scheduler_selftest(None, 1, 1000) == -1
+    assert pevc.pevc_autotune_log(None)[0] == -1
+    # flags are checked before any CUDA call: both walks at once, an unknown bit
+    assert pevc.pevc_plan(100, 1, pevc.FP64, 0, pevc.STAGE_WALK | pevc.DEVICE_WALK)[0] == -6
+    assert pevc.pevc_plan(100, 1, pevc.FP64, 0, 1 << 10)[0] == -6
+    assert pevc.pevc_plan(100, 1, pevc.FP64, 48, 0)[0] == -5
+    assert (pevc.STAGE_WALK, pevc.AUTOTUNE, pevc.DEVICE_WALK, pevc.BT_CUBLAS) == (8, 16, 32, 64)
+
+
+def test_dag_host_task_lists_are_topological():
+    """The scheduler's task list (built on the host by dag_stage_tasks, run
+    here through a tiny host harness compiled from the library's source) is a
+    topological order of Algorithm 1's task graph: every task's dependences
+    come before it, and the counts match the targets the device waits for."""
+    import subprocess
+    import tempfile
+    src = os.path.join(ROOT, "paper_2003_04776_gb300", "csrc")
+    harness = r'''
+#include <cstdio>
+#include <vector>
+#include <map>
+#include <tuple>
+#include "dag.cuh"
+using namespace pevc;
+int main() {
+  // M tiles; chunks per tile and sub-chunks per tile vary (zero for tile 2)
+  const int M = 6;
+  int dchunk_first[M + 1], sub_first[M + 1];
+  const int nch[M] = {3, 1, 0, 2, 4, 1}, nsub[M] = {2, 1, 0, 1, 3, 1};
+  dchunk_first[0] = sub_first[0] = 0;
+  for (int j = 0; j < M; ++j) { dchunk_first[j + 1] = dchunk_first[j] + nch[j]; sub_first[j + 1] = sub_first[j] + nsub[j]; }
+  std::vector<int4> t(100000);
+  int c = dag_stage_tasks(0, M, M, dchunk_first, sub_first, t.data(), 0, (int)t.size());
+  for (int i = M - 1; i >= 1; --i) c = dag_stage_tasks(0, M, i, dchunk_first, sub_first, t.data(), c, (int)t.size());
+  if (c < 0 || c > dag_task_bound(M, 128)) { printf("bad count %d\n", c); return 1; }
+  std::map<std::pair<int,int>, int> dcnt, utile;
+  std::map<std::tuple<int,int,int>, int> usub;
+  for (int q = 0; q < c; ++q) {
+    const int type = t[q].x >> 24, y = t[q].y, j = t[q].z;
+    if (type == kTaskDiag) {
+      if (utile[{y, j}] != (j - y) * nsub[j]) { printf("diag %d %d early\n", y, j); return 2; }
+      dcnt[{y, j}]++;
+    } else if (type == kTaskTip) {
+      dcnt[{j, j}]++;
+    } else {
+      const int i = t[q].w >> 8, s = t[q].w & 255;
+      if (dcnt[{i, j}] != nch[j] || usub[{y, j, s}] != j - i || !(y < i && i <= j)) { printf("upd early\n"); return 3; }
+      usub[{y, j, s}]++;
+      utile[{y, j}]++;
+    }
+  }
+  for (int i = 0; i < M; ++i)
+    for (int j = i; j < M; ++j)
+      if (dcnt[{i, j}] != nch[j] || (i < j && utile[{i, j}] != (j - i) * nsub[j])) { printf("incomplete %d %d\n", i, j); return 4; }
+  printf("ok %d\n", c);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        cpp = os.path.join(d, "h.cu")
+        with open(cpp, "w") as f:
+            f.write(harness)
+        exe = os.path.join(d, "h")
+        nvcc = "/usr/local/cuda/bin/nvcc"
+        r = subprocess.run([nvcc, "-std=c++17", "-I", src, "-I", os.path.join(ROOT, "include"), cpp,
+                            os.path.join(src, "dag.cu"), "-o", exe, "-gencode", "arch=compute_103a,code=sm_103a"],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out = subprocess.run([exe], capture_output=True, text=True)
+        assert out.returncode == 0 and out.stdout.startswith("ok"), out.stdout
