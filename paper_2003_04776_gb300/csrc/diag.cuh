@@ -32,7 +32,7 @@ struct DiagSmem {
   // inverted pivot (1 double real, 2 complex), 2x2 blocks the LU factors
   // (4 doubles real, 8 complex) -- at most 2 doubles per row and column
   double pre[2 * kMaxTile * CB];
-  double tn[kMaxTile][CB];           // ProtectUpdate's t per (block, unit)
+  short te[kMaxTile][CB];            // ProtectUpdate's t per (block, unit) as a power-of-two bound: t < 2^te
   unsigned long long key[CB];        // column maxima
   int lc[CB];                        // local column of chunk column t
   int tip[CB], e[CB], act[CB];       // per unit
@@ -63,6 +63,12 @@ struct DiagBlocks {
   const double* tcS;
   const double* tcT;
 };
+
+// 2^e for -1022 <= e <= 1023, assembled from the exponent field: the bound
+// ProtectUpdate's t is kept as (t < 2^e, stored as e in 16 bits).  With the
+// pre-scaling (|beta| max|S|, (|a| + |b|) max|T| <= 2^1000) t stays below
+// 2^1002, so 2^e is finite; it is at most twice t (times 2^-1022 for t = 0).
+__device__ __forceinline__ double pow2_bound(int e) { return __hiloint2double((e + 1023) << 20, 0); }
 
 __device__ __forceinline__ double upd_norm(const DiagBlocks& D, int li0, int sz, double beta, double amag) {
   double t = fabs(beta) * D.tcS[li0] + amag * D.tcT[li0];
@@ -370,7 +376,7 @@ __device__ __forceinline__ ColStep unit_step(const double* tipw, int mode, bool 
 template <int CB>
 __device__ __forceinline__ bool pair2_step_warp(int lane, int nu, int li0, const double (*piv)[CB],
                                                 const double* f, const short* ep_row, const unsigned char* pf_row,
-                                                const double* tn_row, const double* s_a, const double* s_b,
+                                                const short* te_row, const double* s_a, const double* s_b,
                                                 const double* s_beta, double* s_y, int* s_e, const int* s_act,
                                                 int* s_sh, double2 (*s_PQ)[CB], double (*s_W)[CB]) {
   const int u = lane >> 3, j = lane & 7, base = lane & ~7;
@@ -379,7 +385,7 @@ __device__ __forceinline__ bool pair2_step_warp(int lane, int nu, int li0, const
   const int t0c = 2 * uu;
   const bool has_above = li0 > 0;
   const double a = s_a[uu], b = s_b[uu], beta = s_beta[uu];
-  const double tn = tn_row[uu];
+  const double tn = pow2_bound(te_row[uu]);
   double y = s_y[uu];
   const int ep = ep_row[uu];
   const bool active = mine && s_act[uu];

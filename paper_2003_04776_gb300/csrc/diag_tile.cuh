@@ -75,7 +75,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
   auto& s_tcS = sm.ov.blk.tcS;
   auto& s_tcT = sm.ov.blk.tcT;
   auto& s_pre = sm.pre;
-  auto& s_tn = sm.tn;
+  auto& s_te = sm.te;
   auto& s_ep = sm.ep;
   auto& s_pf = sm.pf;
   auto& s_key = sm.key;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
     const double a = s_a[u], b = s_b[u], beta = s_beta[u];
     const double amag = fabs(a) + fabs(b);
     double* f = s_pre + s_boff[bidx];
-    s_tn[bidx][u] = upd_norm(D, li, one ? 1 : 2, beta, amag);
+    s_te[bidx][u] = (short)exp_ub(upd_norm(D, li, one ? 1 : 2, beta, amag));
     if (one) {
       const double s = s_Sd[li][0], t = s_Td[li][0];
       if (!pairs) {
@@ -272,7 +272,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
     //      lanes per unit, everything else one)
     if ((lr >> 5) == pa_warp && mode == kDiagSolve && pairs && sz == 2) {
       const bool anysh = pair2_step_warp<CB>(lr & 31, nu, li0, s_piv, s_pre + s_boff[bidx], s_ep[bidx],
-                                            s_pf[bidx], s_tn[bidx], s_a, s_b, s_beta, s_y, s_e, s_act, s_sh,
+                                            s_pf[bidx], s_te[bidx], s_a, s_b, s_beta, s_y, s_e, s_act, s_sh,
                                             s_PQ, s_W);
       if ((lr & 31) == 0) s_anysh = anysh ? 1 : 0;
     } else if ((lr >> 5) == pa_warp) {
@@ -283,7 +283,7 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
         const int tip = s_tip[u];
         const bool has_above = li0 > 0;
         const double a = s_a[u], b = s_b[u], beta = s_beta[u];
-        const double tn = s_tn[bidx][u];
+        const double tn = pow2_bound(s_te[bidx][u]);
         double y = s_y[u];
         bool active = s_act[u];
         int e = s_e[u];
