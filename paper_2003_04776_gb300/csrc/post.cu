@@ -19,7 +19,8 @@ namespace pevc {
 
 struct BestIdx {
   unsigned long long v;   // magnitude key: bits of |v| (real) or of |v|^2 (complex); non-negative doubles order like their bits
-  int i;
+  int i;                  // row
+  int k;                  // its row tile
 };
 
 __device__ __forceinline__ BestIdx better(BestIdx a, BestIdx b) {
@@ -59,22 +60,15 @@ __device__ __forceinline__ int col_tile(const Problem& P, int q) {
 constexpr int kPostTiles = 256;        // tiles of a column staged at once
 constexpr int kNoTile = INT32_MIN;     // a tile whose column segment is all zero
 
-// Per tile k in [kb, ke) of output column q: x = exponent shift to the
-// reference exponent (kNoTile for an all-zero segment), y = first row, z =
-// rows of the eigenvector's support in the tile.  Synchronises the CTA before
-// and after.
-__device__ __forceinline__ void stage_tiles(const Problem& P, int q, bool pair, int last, int eref, int kb, int ke,
-                                            int4* s_tile) {
-  __syncthreads();
-  for (int k = kb + (int)threadIdx.x; k < ke; k += blockDim.x) {
-    const long long idx = (long long)k * P.m + q;
-    const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
-    const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
-    s_tile[k - kb] = make_int4(abs_key(nv) ? P.ex[idx] - eref : kNoTile, r0, max(h, 0), 0);
-  }
-  __syncthreads();
-}
-
+// One CTA per output column (a pair's two columns together).  The column's
+// tiles are staged kPostTiles at a time (shift to the reference exponent,
+// first row, rows of the eigenvector's support, and whether the tile can
+// hold the entry of largest modulus); warps take tiles in turn and lanes
+// the rows of a tile, so every load and store is a contiguous run.  Y is
+// read once for the written column plus once for the few candidate tiles of
+// the argmax: the largest represented magnitude of the column is at least
+// 2^eref, so a tile whose own largest magnitude is below 2^(eref - 1) (times
+// sqrt 2 for the modulus of a pair) cannot hold it.
 __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V, int ldv,
                                               int32_t* __restrict__ scale, int normalise) {
   const int q = blockIdx.x;
@@ -86,11 +80,11 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   const int c0 = P.ccol[q];
   const int last = c0 + (pair ? 1 : 0);   // last row of the eigenvector's block
   const int m = P.m, tb = P.tb;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
   __shared__ int s_eref;
   __shared__ BestIdx s_red[8];
   __shared__ int s_ered[8];
-  __shared__ int4 s_tile[kPostTiles];
+  __shared__ int4 s_tile[kPostTiles];     // shift (kNoTile: all zero), first row, rows, candidate
 
   // 1. reference exponent: the largest represented magnitude over the tiles
   int eref = INT32_MIN;
@@ -100,66 +94,58 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
     if (abs_key(nv)) eref = max(eref, P.ex[idx] + ilogb_key(abs_key(nv)));
   }
   for (int o = 16; o > 0; o >>= 1) eref = max(eref, __shfl_xor_sync(0xffffffffu, eref, o));
-  if ((tid & 31) == 0) s_ered[tid >> 5] = eref;
+  if (lane == 0) s_ered[warp] = eref;
   __syncthreads();
   if (tid == 0) {
     int e = s_ered[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, s_ered[w]);
+    for (int w = 1; w < nw; ++w) e = max(e, s_ered[w]);
     s_eref = e;
   }
   __syncthreads();
   eref = s_eref;
 
-  // 2. the entry of largest modulus (first index on ties), and 3. the
-  //    written column(s).  Both passes run over the flattened (tile, row)
-  //    index space of the column in chunks of kPostTiles tiles, with the
-  //    per-tile shift and row range staged in shared memory, and four rows
-  //    per thread in flight.
-  BestIdx best{0ull, 0x7fffffff};
+  auto stage = [&](int kb, int ke) {
+    __syncthreads();
+    for (int k = kb + tid; k < ke; k += blockDim.x) {
+      const long long idx = (long long)k * m + q;
+      const double nv = pair ? max_nonneg(P.nrm[idx], P.nrm[idx + 1]) : P.nrm[idx];
+      const int r0 = P.toff[k], h = min(P.toff[k + 1], last + 1) - r0;
+      const bool nz = abs_key(nv) != 0;
+      const int top = nz ? P.ex[idx] + ilogb_key(abs_key(nv)) : INT32_MIN;
+      s_tile[k - kb] = make_int4(nz ? P.ex[idx] - eref : kNoTile, r0, max(h, 0), top >= eref - 1 ? 1 : 0);
+    }
+    __syncthreads();
+  };
+
+  // 2. the entry of largest modulus (first index on ties), over the
+  //    candidate tiles
+  BestIdx best{0ull, 0x7fffffff, 0};
   for (int kb = 0; kb <= j; kb += kPostTiles) {
     const int ke = min(j + 1, kb + kPostTiles);
-    stage_tiles(P, q, pair, last, eref, kb, ke, s_tile);
-    const int nflat = (ke - kb) * tb;
-    for (int f0 = tid; f0 < nflat; f0 += 4 * (int)blockDim.x) {
-      double vr[4], vi[4];
-      int row[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int f = f0 + u * (int)blockDim.x;
-        row[u] = -1;
-        vr[u] = vi[u] = 0.0;
-        if (f < nflat) {
-          const int kk = f / tb, r = f - kk * tb;
-          const int4 ti = s_tile[kk];
-          if (r < ti.z && ti.x != kNoTile) {
-            const double* Yt = tile_ptr(P, kb + kk, j);
-            vr[u] = Yt[(size_t)lq * tb + r];
-            if (pair) vi[u] = Yt[(size_t)(lq + 1) * tb + r];
-            row[u] = ti.y + r;
-            vr[u] = scale2(vr[u], ti.x);
-            if (pair) vi[u] = scale2(vi[u], ti.x);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (row[u] < 0) continue;
+    stage(kb, ke);
+    for (int kk = warp; kk < ke - kb; kk += nw) {
+      const int4 ti = s_tile[kk];
+      if (!ti.w) continue;
+      const double* Yt = tile_ptr(P, kb + kk, j);
+      for (int r = lane; r < ti.z; r += 32) {
+        const double vr = scale2(Yt[(size_t)lq * tb + r], ti.x);
+        const double vi = pair ? scale2(Yt[(size_t)(lq + 1) * tb + r], ti.x) : 0.0;
         // real columns compare |v| by its magnitude bits; pairs the squared modulus
-        const unsigned long long key = pair ? mag_key(fma(vr[u], vr[u], vi[u] * vi[u])) : mag_key(vr[u]);
-        best = better(best, BestIdx{key, row[u]});
+        const unsigned long long key = pair ? mag_key(fma(vr, vr, vi * vi)) : mag_key(vr);
+        best = better(best, BestIdx{key, ti.y + r, kb + kk});
       }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
     BestIdx other{(unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)best.v, o),
-                  __shfl_xor_sync(0xffffffffu, best.i, o)};
+                  __shfl_xor_sync(0xffffffffu, best.i, o), __shfl_xor_sync(0xffffffffu, best.k, o)};
     best = better(best, other);
   }
-  if ((tid & 31) == 0) s_red[tid >> 5] = best;
+  if (lane == 0) s_red[warp] = best;
   __syncthreads();
   if (tid == 0) {
     BestIdx b = s_red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = better(b, s_red[w]);
+    for (int w = 1; w < nw; ++w) b = better(b, s_red[w]);
     s_red[0] = b;
   }
   __syncthreads();
@@ -170,8 +156,7 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   // a real column, conj(d) / |d|^2 for a pair (|d| in [1, 2))
   double dr = 1.0, di = 0.0;
   if (best.v) {
-    int k = 0;
-    while (k < j && P.toff[k + 1] <= istar) ++k;
+    const int k = best.k;
     const long long idx = (long long)k * m + q;
     const int sh = P.ex[idx] - eref;
     const double* Yt = tile_ptr(P, k, j);
@@ -183,37 +168,22 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
   const double nr = pair ? dr * s2 : 1.0 / dr, ni = di * s2;
   const bool norm = normalise && best.v;
 
+  // 3. the written column(s)
   double* v0 = V + (size_t)q * ldv;
   double* v1 = pair ? V + (size_t)(q + 1) * ldv : nullptr;
   for (int kb = 0; kb <= j; kb += kPostTiles) {
     const int ke = min(j + 1, kb + kPostTiles);
-    stage_tiles(P, q, pair, last, eref, kb, ke, s_tile);
-    const int nflat = (ke - kb) * tb;
-    for (int f0 = tid; f0 < nflat; f0 += 4 * (int)blockDim.x) {
-      double vr[4], vi[4];
-      int row[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int f = f0 + u * (int)blockDim.x;
-        row[u] = -1;
-        vr[u] = vi[u] = 0.0;
-        if (f < nflat) {
-          const int kk = f / tb, r = f - kk * tb;
-          const int4 ti = s_tile[kk];
-          if (r < ti.z) {
-            row[u] = ti.y + r;
-            if (ti.x != kNoTile) {
-              const double* Yt = tile_ptr(P, kb + kk, j);
-              vr[u] = scale2(Yt[(size_t)lq * tb + r], ti.x);
-              if (pair) vi[u] = scale2(Yt[(size_t)(lq + 1) * tb + r], ti.x);
-            }
-          }
+    if (kb > 0) stage(kb, ke);
+    for (int kk = warp; kk < ke - kb; kk += nw) {
+      const int4 ti = s_tile[kk];
+      const double* Yt = tile_ptr(P, kb + kk, j);
+      for (int r = lane; r < ti.z; r += 32) {
+        double xr = 0.0, xi = 0.0;
+        if (ti.x != kNoTile) {
+          xr = scale2(Yt[(size_t)lq * tb + r], ti.x);
+          if (pair) xi = scale2(Yt[(size_t)(lq + 1) * tb + r], ti.x);
         }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (row[u] < 0) continue;
-        double xr = vr[u], xi = vi[u];
+        const int row = ti.y + r;
         if (norm) {
           if (pair) {
             const double zr = fma(xr, nr, xi * ni), zi = fma(xi, nr, -(xr * ni));
@@ -222,10 +192,10 @@ __global__ void __launch_bounds__(256) k_post(Problem P, double* __restrict__ V,
           } else {
             xr = xr * nr;
           }
-          if (row[u] == istar) { xr = 1.0; xi = 0.0; }
+          if (row == istar) { xr = 1.0; xi = 0.0; }
         }
-        v0[row[u]] = xr;
-        if (pair) v1[row[u]] = xi;
+        v0[row] = xr;
+        if (pair) v1[row] = xi;
       }
     }
   }

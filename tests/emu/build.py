@@ -71,7 +71,7 @@ def _convert(src: str, name: str) -> str:
                  r"\1* \2 = reinterpret_cast<\1*>(emu::dyn_smem);", src)
     src = re.sub(r"\b(k_\w+(?:<[^<>()]*>)?)<<<", r"emu::launch(\1, ", src)
     src = src.replace(">>>(", ", ")
-    src = re.sub(r'\s*asm volatile\("prefetch\.global\.L2[^;]*;', "", src)
+    src = re.sub(r'\s*asm volatile\("prefetch\.global\.L2[^"]*"[^;]*;', "", src)
     src = re.sub(r'asm volatile\("mma\.sync.*?"d"\(b\)\);', "emu::dmma_m8n8k4(c0, c1, a, b);", src, flags=re.S)
     if "asm" in src:
         raise RuntimeError(f"{name}: inline PTX the emulation does not model")

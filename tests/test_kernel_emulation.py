@@ -50,10 +50,10 @@ def emu():
     return L
 
 
-def _call(L, fn, S, T, dtype, tile=32, sel=None):
+def _call(L, fn, S, T, dtype, tile=32, sel=None, flags=0):
     n = S.shape[0]
     h = vp()
-    assert L.pevc_plan(ctypes.byref(h), n, 1, 0, tile, 0, None) == 0
+    assert L.pevc_plan(ctypes.byref(h), n, 1, 0, tile, flags, None) == 0
     S = np.asfortranarray(S, dtype=dtype)
     T = np.asfortranarray(T, dtype=dtype)
     V = np.zeros((n, n), dtype=dtype, order="F")
@@ -80,6 +80,25 @@ def test_emulated_fp64_real_solve_matches_oracle(emu):
         res = check.residuals(p.S, p.T, V, kinds, pos, a, b, beta).max() / (45 * check.U)
         assert V.shape == Vo.shape and err <= 1e-12 and res <= 100.0
         assert np.all(np.abs(sc.astype(np.int64) - sco.astype(np.int64)) <= 1)
+
+
+@pytest.mark.parametrize("n,tile,stress,every", [(70, 32, False, 1), (90, 64, True, 1), (140, 128, False, 3)])
+def test_emulated_stage_walk_matches_scheduler_bitwise(emu, n, tile, stress, every):
+    """The stage walk (one launch per stage kind, host-ordered) against the
+    device-side scheduler (one persistent launch, tasks taken by ticket and
+    ordered by ready counters): the updates land in every tile in the same
+    order and the kernels' arithmetic is shared, so the same bits, over real
+    and complex-pair columns, 1x1 and 2x2 blocks, ragged tiles, stress
+    scaling and a selection that leaves partial chunks."""
+    p = pencilgen.make_pencil(n, 9700 + n, stress=stress)
+    sel = None if every == 1 else (np.arange(n) % every != 1).astype(np.int32)
+    st1, V1, sc1 = _call(emu, "pevc_solve", p.S, p.T, np.float64, tile=tile, sel=sel, flags=8)    # PEVC_STAGE_WALK
+    st2, V2, sc2 = _call(emu, "pevc_solve", p.S, p.T, np.float64, tile=tile, sel=sel, flags=32)   # PEVC_DEVICE_WALK
+    assert st1 == 0 and st2 == 0
+    assert np.array_equal(V1, V2) and np.array_equal(sc1, sc2)
+    ost, Vo, sco, m = oracle.evc(p.S, p.T, select=sel)
+    kinds, _ = check.column_kinds(p.block, sel)
+    assert check.compare_normalised(Vo, V1, kinds)[0] <= (1e-6 if stress else 1e-12)
 
 
 def test_emulated_complex_solve_matches_oracle(emu):
