@@ -144,6 +144,33 @@ int pevc_solve(pevc_plan_t plan, const double *S, int lds, const double *T, int 
                const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
 
 /*
+ * pevc_solve_host -- pevc_solve on HOST memory: S, T (read), select (may be
+ * NULL), V_out and scale_out (written) are host arrays, with the leading
+ * dimensions and codes of pevc_solve.  The method reads only the tiles on and
+ * above the block diagonal of S and T (Section 3: the tiles (k, l), k <= l),
+ * and its bottom-up walk needs column block l of S and T only from stage l
+ * on; so the call copies, for every column block l from the last to the
+ * first, rows 0 .. (last row of block l) of its columns, on a copy stream of
+ * the plan's own, and stage l waits for block l alone: the copies overlap the
+ * solve, and the lower triangles are never copied.  The eigenvalues' pre-
+ * scaling (Section 4) takes the maximum of the blocks seen so far; if the
+ * final maximum would change a pre-scale (only for entries near 2^1000), the
+ * solve is run again on the copied data.  The first call allocates the
+ * device copies of S, T and V (3 n_max^2 doubles) and the copy stream; pinned
+ * host arrays give the fastest copies.  Ordered after the work on the plan's
+ * stream; synchronises on return.  Returns pevc_solve's codes.
+ */
+int pevc_solve_host(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
+                    const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
+
+/*
+ * pevc_last_host_bytes -- bytes the last pevc_solve_host call copied:
+ *   out  host long long[2]: {host to device, device to host}
+ * Returns 0, -1 (plan NULL) or -2 (out NULL).
+ */
+int pevc_last_host_bytes(pevc_plan_t plan, long long *out);
+
+/*
  * pevc_solve_batched -- count independent pencils of (possibly) different
  * orders, each as in pevc_solve.  Pointer arguments are host arrays of
  * length count holding device pointers (select[i] may be NULL, select itself

@@ -89,12 +89,16 @@ _lib.pevc_scheduler_selftest.argtypes = [_vp, _i, ctypes.c_longlong]
 _lib.pevc_scheduler_selftest.restype = _i
 _lib.pevc_autotune_log.argtypes = [_vp, _vp, _i]
 _lib.pevc_autotune_log.restype = _i
+_lib.pevc_solve_host.argtypes = [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, ctypes.POINTER(_i)]
+_lib.pevc_solve_host.restype = _i
+_lib.pevc_last_host_bytes.argtypes = [_vp, _vp]
+_lib.pevc_last_host_bytes.restype = _i
 
 EXPORTS = ("pevc_plan", "pevc_solve", "pevc_solve_batched", "pevc_destroy", "pevc_strerror",
            "pevc_plan_info", "pevc_last_stats", "pevc_set_profile", "pevc_kernel_profile",
            "pevc_solve_static", "pevc_backtransform", "pevc_solve_left", "pevc_solve_cplx",
            "pevc_solve_cplx_left", "pevc_backtransform_cplx", "pevc_watchdog_selftest",
-           "pevc_scheduler_selftest", "pevc_autotune_log")
+           "pevc_scheduler_selftest", "pevc_autotune_log", "pevc_solve_host", "pevc_last_host_bytes")
 
 
 # ----------------------------------------------------------- raw C ABI names
@@ -115,6 +119,22 @@ def pevc_solve(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, V:
     st = _lib.pevc_solve(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None,
                          _vp(V), ldv, _vp(scale), ctypes.byref(m))
     return st, m.value
+
+
+def pevc_solve_host(plan, S: int, lds: int, T: int, ldt: int, n: int, select: int, V: int, ldv: int,
+                    scale: int):
+    """Raw pointers (host addresses as ints).  Returns (status, m_out)."""
+    m = _i(0)
+    st = _lib.pevc_solve_host(plan, _vp(S), lds, _vp(T), ldt, n, _vp(select) if select else None,
+                              _vp(V), ldv, _vp(scale), ctypes.byref(m))
+    return st, m.value
+
+
+def pevc_last_host_bytes(plan):
+    """Bytes the last pevc_solve_host copied: (status, (host to device, device to host))."""
+    out = (ctypes.c_longlong * 2)()
+    st = _lib.pevc_last_host_bytes(plan, out)
+    return st, (int(out[0]), int(out[1]))
 
 
 def pevc_solve_batched(plan, count, S, lds, T, ldt, n, select, V, ldv, scale):
@@ -334,6 +354,35 @@ class Plan:
                            select.data_ptr() if select is not None else 0, V.data_ptr(),
                            ldv or max(n, 1), scale.data_ptr())
         return st, m
+
+    def solve_host(self, S, T, V, scale, select=None):
+        """Host arrays through pevc_solve_host (the copies stream behind the
+        solve).  S, T: n x n column-major host buffers -- numpy arrays in
+        Fortran order, or CPU torch tensors holding the transposes (row-major
+        storage of S^T is column-major storage of S), pinned for the fastest
+        copies; V: an n x n host buffer of the same kind for the output;
+        scale: int32[n].  Returns (status, m_out)."""
+        def ptr(x):
+            if isinstance(x, np.ndarray):
+                if x.ndim == 2 and not x.flags.f_contiguous:
+                    raise ValueError("solve_host: numpy matrices must be in Fortran (column-major) order")
+                return x.ctypes.data
+            if x.is_cuda or not x.is_contiguous():
+                raise ValueError("solve_host: torch tensors must be contiguous host tensors")
+            return x.data_ptr()
+        n = int(S.shape[0])
+        sel = None
+        if select is not None:
+            sel = np.ascontiguousarray(select, dtype=np.int32)
+        return pevc_solve_host(self.h, ptr(S), max(n, 1), ptr(T), max(n, 1), n,
+                               sel.ctypes.data if sel is not None else 0, ptr(V), max(n, 1), ptr(scale))
+
+    @property
+    def host_bytes(self):
+        st, b = pevc_last_host_bytes(self.h)
+        if st:
+            raise PevcError(st, "pevc_last_host_bytes")
+        return b
 
     def solve_batched(self, pencils, selects=None):
         """Several pencils [(S, T), ...] in one pevc_solve_batched call (the

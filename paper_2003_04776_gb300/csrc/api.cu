@@ -107,6 +107,21 @@ struct pevc_plan_s {
   int32_t* lsc = nullptr;
   // complex pencils (allocated by the first pevc_solve_cplx)
   CplxWork* cx = nullptr;
+  // solves from host memory (allocated by the first pevc_solve_host): device
+  // copies of S and T, the output and its scales (leading dimension n_max),
+  // the copy stream with one event per column block, the pre-scale record per
+  // column block (the maximum seen so far, the largest coefficient exponent)
+  // and the bytes the last call copied each way
+  double* hS = nullptr;
+  double* hT = nullptr;
+  double* hV = nullptr;
+  int32_t* hsc = nullptr;
+  cudaStream_t hstream = nullptr;
+  cudaEvent_t* hev = nullptr;
+  cudaEvent_t hstart = nullptr;
+  double* hspec = nullptr;
+  double* h_hspec = nullptr;
+  long long host_bytes[2] = {0, 0};
   // device-side task-graph scheduler (dag.cuh), the walk of FP64 plans:
   // the pencil record, the task list, the ready counters, the update
   // sub-chunks and the ticket / abort pair
@@ -252,6 +267,17 @@ void free_plan(pevc_plan_t p) {
   void* dagh[] = {p->h_pen, p->h_tasks, p->h_sub};
   for (void* h : dagh)
     if (h) cudaFreeHost(h);
+  void* hdev[] = {p->hS, p->hT, p->hV, p->hsc, p->hspec};
+  for (void* d : hdev)
+    if (d) cudaFree(d);
+  if (p->h_hspec) cudaFreeHost(p->h_hspec);
+  if (p->hev) {
+    for (int q = 0; q < p->Mmax; ++q)
+      if (p->hev[q]) cudaEventDestroy(p->hev[q]);
+    delete[] p->hev;
+  }
+  if (p->hstart) cudaEventDestroy(p->hstart);
+  if (p->hstream) cudaStreamDestroy(p->hstream);
   if (p->bt_kind) cudaFree(p->bt_kind);
   if (p->bt_ws) cudaFree(p->bt_ws);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
@@ -704,6 +730,229 @@ int check_args(int n_max, const double* S, int lds, const double* T, int ldt, in
   return 0;
 }
 
+// ---- solves from host memory, with the inputs streamed in by column blocks
+//
+// S and T are copied to the plan's device copies column block by column
+// block from the right (the order in which the bottom-up walk needs them),
+// each block's rows 0 .. (end of the block) only -- the tiles on and above the
+// diagonal, everything the method reads -- on a copy stream, one event per
+// block.  Stage i of the walk waits for block i, whose pre-pass (tile norms,
+// eigenvalues), slices and tips run on its arrival, so the copies overlap the
+// solve.  The eigenvalues' pre-scale (every (alpha, beta) scaled by a power of
+// two when max(|beta|, |a| + |b|) max|S, T| would exceed 2^1000) is taken from
+// the maximum of the blocks seen so far; once all have arrived the pre-scale
+// of every block is checked against the final maximum, and the rare solve
+// whose pre-scale would change is run again on the device copies.
+
+int host_alloc(pevc_plan_t p) {
+  if (p->hS) return 0;
+  const size_t nn = (size_t)p->n_max * p->n_max;
+  int rc = dalloc(&p->hS, nn);
+  rc = rc ? rc : dalloc(&p->hT, nn);
+  rc = rc ? rc : dalloc(&p->hV, nn);
+  rc = rc ? rc : dalloc(&p->hsc, (size_t)p->n_max);
+  rc = rc ? rc : dalloc(&p->hspec, 2 * (size_t)p->Mmax);
+  rc = rc ? rc : halloc(&p->h_hspec, 2 * (size_t)p->Mmax);
+  if (rc) return rc;
+  CK(cudaStreamCreateWithFlags(&p->hstream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->hstart, cudaEventDisableTiming));
+  p->hev = new (std::nothrow) cudaEvent_t[p->Mmax]();
+  if (!p->hev) return PEVC_ERR_NOMEM;
+  for (int q = 0; q < p->Mmax; ++q) CK(cudaEventCreateWithFlags(&p->hev[q], cudaEventDisableTiming));
+  return 0;
+}
+
+// Column block l's arrival: wait for its copy, then its pre-pass and tips.
+struct HostArrivals : Arrivals {
+  pevc_plan_t p;
+  const Problem& P;
+  HostArrivals(pevc_plan_t p_, const Problem& P_) : p(p_), P(P_) {}
+  cudaError_t arrive(int l, cudaStream_t s) override {
+    cudaError_t e = cudaStreamWaitEvent(s, p->hev[l], 0);
+    if (e != cudaSuccess) return e;
+    p->prof.begin(s);
+    e = launch_prepass_block(P, l, p->h_toff[l], p->h_toff[l + 1], p->hspec + 2 * l, s);
+    p->prof.end(s, 3, 0.0);
+    ++p->prof.launches;   // two kernels
+    if (e != cudaSuccess) return e;
+    p->prof.begin(s);
+    e = launch_diag_tile(P, l, kDiagTip, s);
+    p->prof.end(s, 1, 0.0);
+    return e;
+  }
+};
+
+int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n, const int32_t* sel,
+               double* V, int ldv, int32_t* scale, int* m_out) {
+  cudaStream_t s = p->stream;
+  *m_out = 0;
+  for (double& x : p->stats) x = 0.0;
+  p->host_bytes[0] = p->host_bytes[1] = 0;
+  if (n == 0) return 0;
+  int rc = host_alloc(p);
+  if (rc) return rc;
+  p->prof.reset();
+  CK(cudaEventRecord(p->ev[0], s));
+  // 1. block structure and selection, read on the host
+  for (int c = 0; c + 1 < n; ++c) p->h_subd[c] = S[(size_t)c * lds + c + 1];
+  if (sel) std::memcpy(p->h_sel, sel, (size_t)n * sizeof(int32_t));
+  Structure st;
+  if ((rc = analyse(p, n, sel != nullptr, st))) return rc;
+  *m_out = st.m;
+  p->last_m = st.m;
+  const int M = st.M, ldd = p->n_max;
+  // 2. the copies, column blocks from the right, after the plan's earlier
+  //    work (which may still read the device copies)
+  CK(cudaEventRecord(p->hstart, s));
+  CK(cudaStreamWaitEvent(p->hstream, p->hstart, 0));
+  for (int l = M - 1; l >= 0; --l) {
+    const int c0 = p->h_toff[l], c1 = p->h_toff[l + 1];
+    const size_t w = (size_t)c1 * sizeof(double);
+    CK(cudaMemcpy2DAsync(p->hS + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), S + (size_t)c0 * lds,
+                         (size_t)lds * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
+    CK(cudaMemcpy2DAsync(p->hT + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), T + (size_t)c0 * ldt,
+                         (size_t)ldt * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
+    CK(cudaEventRecord(p->hev[l], p->hstream));
+    p->host_bytes[0] += 2 * (long long)w * (c1 - c0);
+  }
+  // 3. the solve on the device copies, each stage after its column block
+  const bool streamed = !(p->prec != PEVC_FP64 && split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0).correction);
+  if (!streamed) {
+    // the correction sweep reads every block at the start: the whole copy first
+    for (int l = 0; l < M; ++l) CK(cudaStreamWaitEvent(s, p->hev[l], 0));
+    if ((rc = solve_enqueue(p, p->hS, ldd, p->hT, ldd, n, p->hV, ldd, p->hsc, st, false))) return rc;
+  } else {
+    cudaStream_t ss = s;
+    // structure to the device
+    CK(cudaMemcpyAsync(p->blk, p->h_blk, (size_t)n, cudaMemcpyHostToDevice, ss));
+    CK(cudaMemcpyAsync(p->toff, p->h_toff, (size_t)(M + 1) * sizeof(int), cudaMemcpyHostToDevice, ss));
+    CK(cudaMemcpyAsync(p->cstart, p->h_cstart, (size_t)(M + 1) * sizeof(int), cudaMemcpyHostToDevice, ss));
+    if (st.m > 0) {
+      CK(cudaMemcpyAsync(p->ccol, p->h_ccol, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, ss));
+      CK(cudaMemcpyAsync(p->kind, p->h_kind, (size_t)st.m, cudaMemcpyHostToDevice, ss));
+      CK(cudaMemcpyAsync(p->dperm, p->h_dperm, (size_t)st.m * sizeof(int), cudaMemcpyHostToDevice, ss));
+      CK(cudaMemcpyAsync(p->dcpos, p->h_dcpos, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, ss));
+      CK(cudaMemcpyAsync(p->dccnt, p->h_dccnt, (size_t)st.nchunks * sizeof(int), cudaMemcpyHostToDevice, ss));
+    }
+    CK(cudaMemcpyAsync(p->dcfirst, p->h_dcfirst, (size_t)(M + 1) * sizeof(int), cudaMemcpyHostToDevice, ss));
+    CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), ss));
+    CK(cudaMemsetAsync(p->gmax, 0, sizeof(double), ss));
+    for (int l = 0; l < M; ++l) {
+      p->h_hspec[2 * l] = 0.0;
+      const int lowest = INT32_MIN;
+      std::memcpy(&p->h_hspec[2 * l + 1], &lowest, sizeof(int));
+    }
+    CK(cudaMemcpyAsync(p->hspec, p->h_hspec, 2 * (size_t)M * sizeof(double), cudaMemcpyHostToDevice, ss));
+    Problem P = make_problem(p, p->hS, ldd, p->hT, ldd, n, st);
+    CK(cudaEventRecord(p->ev[1], ss));
+    if (st.m > 0) {
+      p->prof.begin(ss);
+      CK(launch_init_state(P, ss, 1));
+      p->prof.end(ss, 3, 0.0);
+      HostArrivals arr(p, P);
+      SchedContext sc{p->aux, p->sev, p->lookahead};
+      if (p->prec == PEVC_FP64) {
+        struct F64Streamed : StageOps {
+          const Problem& P;
+          pevc_plan_t p;
+          Arrivals& arr;
+          F64Streamed(const Problem& P_, pevc_plan_t p_, Arrivals& a_) : P(P_), p(p_), arr(a_) {}
+          cudaError_t arrive(int l, cudaStream_t st) override { return arr.arrive(l, st); }
+          cudaError_t tips(cudaStream_t) override { return cudaSuccess; }   // tile by tile, on arrival
+          cudaError_t diag(int i, cudaStream_t st) override {
+            p->prof.begin(st);
+            cudaError_t e = launch_diag(P, i, kDiagSolve, st);
+            p->prof.end(st, 1, 0.0);
+            return e;
+          }
+          cudaError_t prep(int, cudaStream_t) override { return cudaSuccess; }
+          cudaError_t update(int i, int k_lo, int k_hi, cudaStream_t st) override {
+            const double rows = p->h_toff[k_hi] - p->h_toff[k_lo], cols = P.m - p->h_cstart[i];
+            const double K = 2.0 * (p->h_toff[i + 1] - p->h_toff[i]);
+            p->prof.begin(st);
+            cudaError_t e = launch_update_f64(P, i, k_lo, k_hi, st);
+            p->prof.end(st, 0, 2.0 * rows * cols * K);
+            return e;
+          }
+        } ops(P, p, arr);
+        CK(walk_dag(M, ops, ss, sc.aux, sc.ev, sc.lookahead));
+        CK(cudaEventRecord(p->ev[2], ss));
+        CK(cudaEventRecord(p->ev[3], ss));
+      } else {
+        HostStructure hs{p->h_toff, p->h_cstart};
+        SplitConfig cfg = split_config(p->prec, false);
+        if ((rc = split_solve(p->split, P, hs, cfg, ss, sc, p->prof, p->ev[2], p->ev[3], &arr))) return rc;
+      }
+      // every eigenvalue is known now: the indefinite-eigenvalue check
+      p->prof.begin(ss);
+      CK(launch_init_state(P, ss, 2));
+      p->prof.end(ss, 3, 0.0);
+      p->prof.begin(ss);
+      CK(launch_post(P, p->hV, ldd, p->hsc, (p->flags & PEVC_NO_NORMALISE) == 0, ss));
+      p->prof.end(ss, 3, 0.0);
+    } else {
+      for (int l = 0; l < M; ++l) CK(cudaStreamWaitEvent(ss, p->hev[l], 0));
+      CK(cudaEventRecord(p->ev[2], ss));
+      CK(cudaEventRecord(p->ev[3], ss));
+    }
+    CK(cudaEventRecord(p->ev[4], ss));
+    // the pre-scale check: every block's pre-scale against the final maximum
+    CK(cudaMemcpyAsync(p->h_hspec, p->hspec, 2 * (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, ss));
+    CK(cudaMemcpyAsync(p->h_subd, p->gmax, sizeof(double), cudaMemcpyDeviceToHost, ss));
+    CK(cudaStreamSynchronize(ss));
+    const double gfin = p->h_subd[0];
+    bool redo = false;
+    for (int l = 0; l < M && st.m > 0; ++l) {
+      int ec = 0;
+      std::memcpy(&ec, &p->h_hspec[2 * l + 1], sizeof(int));
+      const double gu = p->h_hspec[2 * l];
+      if (ec == INT32_MIN || !(gfin > 0.0)) continue;
+      const int ef = std::ilogb(gfin) + 1, eu = gu > 0.0 ? std::ilogb(gu) + 1 : INT32_MIN / 2;
+      // the pre-scale of a pair is max(0, e_coef + e_max - 1000): it differs
+      // only where the final one is positive and the maxima differ
+      if (ef != eu && ec + ef - kPrescaleExp > 0) redo = true;
+    }
+    if (redo) {
+      if ((rc = solve_enqueue(p, p->hS, ldd, p->hT, ldd, n, p->hV, ldd, p->hsc, st, false))) return rc;
+    }
+  }
+  // 4. the result to the host
+  if (st.m > 0) {
+    CK(cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), p->hV, (size_t)ldd * sizeof(double),
+                         (size_t)n * sizeof(double), (size_t)st.m, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(scale, p->hsc, (size_t)st.m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    p->host_bytes[1] = (long long)st.m * n * (long long)sizeof(double) + (long long)st.m * sizeof(int32_t);
+  }
+  CK(cudaEventRecord(p->ev[5], s));
+  unsigned bits = 0;
+  if ((rc = read_status(p, &bits))) return rc;
+  float ms[4] = {0, 0, 0, 0};
+  cudaEventElapsedTime(&ms[0], p->ev[0], p->ev[5]);
+  cudaEventElapsedTime(&ms[1], p->ev[0], p->ev[1]);
+  cudaEventElapsedTime(&ms[2], p->ev[1], p->ev[2]);
+  cudaEventElapsedTime(&ms[3], p->ev[2], p->ev[3]);
+  p->stats[0] = ms[0];
+  p->stats[1] = ms[1];
+  p->stats[2] = ms[2];
+  p->stats[3] = ms[3];
+  float post = 0.0f;
+  cudaEventElapsedTime(&post, p->ev[3], p->ev[4]);
+  p->stats[4] = post;
+  p->stats[5] = M;
+  p->stats[6] = p->prof.launches;
+  p->stats[7] = 0.0;
+  for (double& x : p->kprof) x = 0.0;
+  for (int q = 0; q < p->prof.used; ++q) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, p->prof.ev[2 * q], p->prof.ev[2 * q + 1]);
+    const int k = p->prof.kind[q];
+    p->kprof[3 * k] += t;
+    p->kprof[3 * k + 1] += 1.0;
+    p->kprof[3 * k + 2] += p->prof.flops[q];
+  }
+  return status_from_bits(bits);
+}
+
 // A batch of an FP64 plan on the device scheduler: pencils are packed into
 // waves whose slices fit the pools (one wave for most batches); per wave the
 // host reads every pencil's block structure at once, builds one task list
@@ -1059,6 +1308,29 @@ int pevc_solve(pevc_plan_t plan, const double* S, int lds, const double* T, int 
   if (n > 0 && !scale_out) return -10;
   if (!m_out) return -11;
   return solve_one(plan, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out);
+}
+
+int pevc_solve_host(pevc_plan_t plan, const double* S, int lds, const double* T, int ldt, int n,
+                    const int32_t* select, double* V_out, int ldv, int32_t* scale_out, int* m_out) {
+  if (!plan) return -1;
+  if (n < 0 || n > plan->n_max) return -6;
+  if (n > 0 && !S) return -2;
+  if (lds < std::max(n, 1)) return -3;
+  if (n > 0 && !T) return -4;
+  if (ldt < std::max(n, 1)) return -5;
+  if (n > 0 && !V_out) return -8;
+  if (ldv < std::max(n, 1)) return -9;
+  if (n > 0 && !scale_out) return -10;
+  if (!m_out) return -11;
+  return solve_host(plan, S, lds, T, ldt, n, select, V_out, ldv, scale_out, m_out);
+}
+
+int pevc_last_host_bytes(pevc_plan_t plan, long long* out) {
+  if (!plan) return -1;
+  if (!out) return -2;
+  out[0] = plan->host_bytes[0];
+  out[1] = plan->host_bytes[1];
+  return 0;
 }
 
 int pevc_solve_batched(pevc_plan_t plan, int count, const double* const* S, const int* lds,

@@ -326,8 +326,14 @@ constexpr int kDiagTipCorr = 2;   // tiles (j, j) of a correction: zero tips, ri
 
 // ---- launchers (one translation unit each) ----
 cudaError_t launch_prepass(const Problem& P, cudaStream_t s);
-cudaError_t launch_init_state(const Problem& P, cudaStream_t s);
+// The pre-pass of one column block l (tiles (k, l), eigenvalues of the
+// diagonal positions [c_begin, c_end)), for a solve whose inputs arrive by
+// column blocks; spec: see k_eigpairs.
+cudaError_t launch_prepass_block(const Problem& P, int l, int c_begin, int c_end, double* spec, cudaStream_t s);
+cudaError_t launch_init_state(const Problem& P, cudaStream_t s, int what = 3);
 cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s);
+// The tips (mode kDiagTip) of one diagonal tile j.
+cudaError_t launch_diag_tile(const Problem& P, int j, int mode, cudaStream_t s);
 cudaError_t launch_update_f64(const Problem& P, int i, int k_lo, int k_hi, cudaStream_t s);
 cudaError_t launch_diag_residual_f64(const Problem& P, const double* Xsrc, const int* exX, const double* nrmX,
                                      cudaStream_t s);

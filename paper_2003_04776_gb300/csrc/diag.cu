@@ -8,8 +8,8 @@ namespace pevc {
 template <int CB>
 __global__ void __launch_bounds__(kMaxTile, 7) k_diag(Problem P, int i_row, int mode) {
   __shared__ DiagSmem<CB> sm;
-  const bool tips = mode != kDiagSolve;          // one CTA row per diagonal tile
-  const int j = tips ? (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;
+  const bool tips = mode != kDiagSolve;          // one CTA row per diagonal tile from i_row
+  const int j = tips ? i_row + (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;
   const int i = tips ? j : i_row;
   const int chunk = P.dchunk_first[j] + (int)blockIdx.x;
   if (chunk >= P.dchunk_first[j + 1]) return;
@@ -22,7 +22,14 @@ cudaError_t launch_diag(const Problem& P, int i, int mode, cudaStream_t s) {
   const int ntiles = (mode != kDiagSolve) ? P.M : (P.M - 1 - i);
   if (ntiles <= 0 || P.dchunk_max <= 0) return cudaSuccess;
   dim3 grid(P.dchunk_max, ntiles);
-  k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, i, mode);
+  k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, mode != kDiagSolve ? 0 : i, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_tile(const Problem& P, int j, int mode, cudaStream_t s) {
+  if (P.dchunk_max <= 0) return cudaSuccess;
+  dim3 grid(P.dchunk_max, 1);
+  k_diag<kDiagChunk><<<grid, kMaxTile, 0, s>>>(P, j, mode);
   return cudaGetLastError();
 }
 

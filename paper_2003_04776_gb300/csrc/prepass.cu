@@ -41,13 +41,17 @@ __device__ __forceinline__ double scaled_down32(unsigned long long key) {
 
 // One CTA per tile pair (k, l), k <= l.  Off-diagonal tiles: exponent bound
 // of ||[S_kl T_kl]||_inf.  Diagonal tiles: tcS/tcT column-segment maxima.
-__global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
+// lfix >= 0: the tiles (k, lfix) of one column block, k = blockIdx.x.
+__global__ void __launch_bounds__(128) k_tilenorms(Problem P, int lfix) {
   __shared__ double red[64];
   const long long x = blockIdx.x;
-  int l = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
-  while ((long long)l * (l + 1) / 2 > x) --l;
-  while ((long long)(l + 1) * (l + 2) / 2 <= x) ++l;
-  const int k = (int)(x - (long long)l * (l + 1) / 2);
+  int l = lfix, k = (int)x;
+  if (lfix < 0) {
+    l = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+    while ((long long)l * (l + 1) / 2 > x) --l;
+    while ((long long)(l + 1) * (l + 2) / 2 <= x) ++l;
+    k = (int)(x - (long long)l * (l + 1) / 2);
+  }
   const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
   const int cl0 = P.toff[l], hl = P.toff[l + 1] - cl0;
   const double* S = P.S;
@@ -112,11 +116,16 @@ __global__ void __launch_bounds__(128) k_tilenorms(Problem P) {
   }
 }
 
-// Eigenvalue pair of the block starting at each diagonal position, plus the
-// structural checks of a standardised real Schur form.
-__global__ void k_eigpairs(Problem P) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= P.n || P.blk[c] == 2) return;
+// Eigenvalue pair of the block starting at each diagonal position in
+// [c_begin, c_end), plus the structural checks of a standardised real Schur
+// form.  spec (may be null): the pre-scale was taken from the maximum of the
+// column blocks seen so far; spec[0] receives that maximum and spec[1] (an
+// int) the largest exponent bound of the pairs' coefficients, for the check
+// against the final maximum.
+__global__ void k_eigpairs(Problem P, int c_begin, int c_end, double* spec) {
+  const int c = c_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (spec && blockIdx.x == 0 && threadIdx.x == 0) spec[0] = *P.gmax;
+  if (c >= c_end || P.blk[c] == 2) return;
   const double* S = P.S;
   const double* T = P.T;
   const int lds = P.lds, ldt = P.ldt;
@@ -155,6 +164,7 @@ __global__ void k_eigpairs(Problem P) {
   // pre-scaling of the pair so that max(|beta|, |a|+|b|) * max|S,T| <= 2^1000
   const double coef = fmax(fabs(beta), fabs(a) + fabs(b));
   const double gm = *P.gmax;
+  if (spec && coef > 0.0) atomicMax(reinterpret_cast<int*>(spec + 1), exp_above(coef));
   if (coef > 0.0 && gm > 0.0) {
     const int k = exp_above(coef) + exp_above(gm) - kPrescaleExp;
     if (k > 0) { a = ldexp(a, -k); b = ldexp(b, -k); beta = ldexp(beta, -k); }
@@ -165,32 +175,41 @@ __global__ void k_eigpairs(Problem P) {
 
 cudaError_t launch_prepass(const Problem& P, cudaStream_t s) {
   const long long tiles = (long long)P.M * (P.M + 1) / 2;
-  if (tiles > 0) k_tilenorms<<<(unsigned)tiles, 128, 0, s>>>(P);
+  if (tiles > 0) k_tilenorms<<<(unsigned)tiles, 128, 0, s>>>(P, -1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (P.n > 0) k_eigpairs<<<(P.n + 127) / 128, 128, 0, s>>>(P);
+  if (P.n > 0) k_eigpairs<<<(P.n + 127) / 128, 128, 0, s>>>(P, 0, P.n, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepass_block(const Problem& P, int l, int c_begin, int c_end, double* spec, cudaStream_t s) {
+  k_tilenorms<<<(unsigned)(l + 1), 128, 0, s>>>(P, l);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (c_end > c_begin) k_eigpairs<<<(c_end - c_begin + 127) / 128, 128, 0, s>>>(P, c_begin, c_end, spec);
   return cudaGetLastError();
 }
 
 // Augmented state before the first task: every tile column is zero
-// (exponent kExpZero, norm 0); indefinite selected eigenvalues are flagged.
-__global__ void k_init_state(Problem P) {
+// (exponent kExpZero, norm 0) (what & 1); indefinite selected eigenvalues are
+// flagged (what & 2).
+__global__ void k_init_state(Problem P, int what) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)P.M * P.m;
-  if (idx < total) {
+  if ((what & 1) && idx < total) {
     P.ex[idx] = kExpZero;
     P.nrm[idx] = 0.0;
   }
-  if (idx < P.m) {
+  if ((what & 2) && idx < P.m) {
     const int c = P.ccol[idx];
     if (P.kind[idx] == 0 && P.ca[c] == 0.0 && P.cbeta[c] == 0.0) atomicOr(P.status, kStIndefinite);
   }
 }
 
-cudaError_t launch_init_state(const Problem& P, cudaStream_t s) {
+cudaError_t launch_init_state(const Problem& P, cudaStream_t s, int what) {
   const long long total = (long long)P.M * P.m > P.m ? (long long)P.M * P.m : P.m;
   if (total <= 0) return cudaSuccess;
-  k_init_state<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P);
+  k_init_state<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, what);
   return cudaGetLastError();
 }
 

@@ -87,9 +87,9 @@ constexpr int kSplitARows = 64;
 
 template <int NS>
 __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __restrict__ As,
-                                                 int* __restrict__ eA, int ns) {
-  int k, l;
-  tile_pair(blockIdx.x >> 1, k, l);
+                                                 int* __restrict__ eA, int ns, int lfix) {
+  int k = (int)(blockIdx.x >> 1), l = lfix;   // lfix >= 0: the tiles (k, lfix) of one column block
+  if (lfix < 0) tile_pair(blockIdx.x >> 1, k, l);
   const int tb = P.tb, K2 = 2 * tb;
   const int rbase = (int)(blockIdx.x & 1) * kSplitARows;   // first local row of this half
   const int rk0 = P.toff[k], hk = P.toff[k + 1] - rk0;
@@ -572,8 +572,14 @@ int products(int ns, int levels) {
 cudaError_t launch_split_A(const Problem& P, SplitWorkspace& w, int ns, cudaStream_t s) {
   const long long tiles = (long long)P.M * (P.M + 1) / 2;
   if (tiles <= 0) return cudaSuccess;
-  if (ns == 5) k_split_A<5><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns);
-  else k_split_A<3><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns);
+  if (ns == 5) k_split_A<5><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns, -1);
+  else k_split_A<3><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As, w.eA, w.ns, -1);
+  return cudaGetLastError();
+}
+
+cudaError_t split_A_block(const Problem& P, SplitWorkspace& w, int l, int ns, cudaStream_t s) {
+  if (ns == 5) k_split_A<5><<<(unsigned)(2 * (l + 1)), 256, 0, s>>>(P, w.As, w.eA, w.ns, l);
+  else k_split_A<3><<<(unsigned)(2 * (l + 1)), 256, 0, s>>>(P, w.As, w.eA, w.ns, l);
   return cudaGetLastError();
 }
 
@@ -652,9 +658,15 @@ struct SplitOps : StageOps {
 
 }  // namespace
 
+cudaError_t launch_split_A_block(const Problem& P, SplitWorkspace& w, int l, int ns, cudaStream_t s) {
+  return split_A_block(P, w, l, ns, s);
+}
+
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
-                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr) {
+                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
+                Arrivals* arr) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
+  if (arr && cfg.correction) return PEVC_ERR_UNSUPPORTED;
   if (w.use_tc && w.tc_ok) {
     // output column chunks (width 48 and 64) inside every column tile
     int* h48c = w.h_chunks;
@@ -677,11 +689,30 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     SCK(cudaMemcpyAsync(w.chunk_j_64, h64j, (size_t)n64 * sizeof(int), cudaMemcpyHostToDevice, s));
   }
   const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
-  prof.begin(s);
-  SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
-  prof.end(s, 3, 0.0);
-  {
+  if (!arr) {
+    prof.begin(s);
+    SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
+    prof.end(s, 3, 0.0);
     SplitOps ops(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, prof);
+    SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
+  } else {
+    // column block i: its arrival (pre-pass, tips), then its slices
+    struct StreamedOps : SplitOps {
+      Arrivals* arr;
+      int ns_a;
+      StreamedOps(const Problem& P_, SplitWorkspace& w_, const HostStructure& hs_, const SplitConfig& cfg_,
+                  Profiler& prof_, Arrivals* arr_, int ns_a_)
+          : SplitOps(P_, w_, hs_, kDiagTip, cfg_.ns1, cfg_.levels1, prof_), arr(arr_), ns_a(ns_a_) {}
+      cudaError_t tips(cudaStream_t) override { return cudaSuccess; }   // tile by tile, on arrival
+      cudaError_t arrive(int l, cudaStream_t st) override {
+        cudaError_t e = arr->arrive(l, st);
+        if (e != cudaSuccess) return e;
+        prof.begin(st);
+        e = launch_split_A_block(P, w, l, ns_a == 5 ? 5 : 3, st);
+        prof.end(st, 3, 0.0);
+        return e;
+      }
+    } ops(P, w, hs, cfg, prof, arr, ns_a);
     SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
   }
   SCK(cudaEventRecord(ev_dag, s));

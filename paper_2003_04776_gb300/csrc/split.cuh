@@ -68,8 +68,18 @@ cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, i
                              const double* nrmX, int ns, int levels, cudaStream_t s);
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
+// Inputs that arrive by column blocks (pevc_solve_host): arrive(i) orders
+// column block i after its copy and runs its pre-pass and tips.
+struct Arrivals {
+  virtual ~Arrivals() = default;
+  virtual cudaError_t arrive(int l, cudaStream_t s) = 0;
+};
+cudaError_t launch_split_A_block(const Problem& P, SplitWorkspace& w, int l, int ns, cudaStream_t s);
+// arr: null, or the arrivals of a streamed solve (no correction sweep): the
+// slicing of [S T] then runs by column block, after each block's arrival.
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
-                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr);
+                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
+                Arrivals* arr = nullptr);
 
 // Back-transformation X = Z V as exact BF16 slice products (6 slices per
 // operand, chunks of 256 along K summed in FP64); the workspace ws holds

@@ -55,6 +55,11 @@ inline cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t b, cudaMemcpyK
   memcpy(d, s, b);
   return 0;
 }
+inline cudaError_t cudaMemcpy2DAsync(void* d, size_t dp, const void* s, size_t sp, size_t w, size_t h,
+                                     cudaMemcpyKind, cudaStream_t) {
+  for (size_t r = 0; r < h; ++r) memcpy((char*)d + r * dp, (const char*)s + r * sp, w);
+  return 0;
+}
 inline cudaError_t cudaMemsetAsync(void* d, int v, size_t b, cudaStream_t) {
   memset(d, v, b);
   return 0;

@@ -101,6 +101,45 @@ def test_emulated_stage_walk_matches_scheduler_bitwise(emu, n, tile, stress, eve
     assert check.compare_normalised(Vo, V1, kinds)[0] <= (1e-6 if stress else 1e-12)
 
 
+@pytest.mark.parametrize("prec,n,tile,every", [(0, 70, 32, 1), (0, 90, 32, 3), (3, 45, 0, 1)])
+def test_emulated_host_solve_matches_device_solve_bitwise(emu, prec, n, tile, every):
+    """pevc_solve_host (S and T streamed in by column blocks from the right,
+    upper tiles only; each block's pre-pass, slices and tips on its arrival)
+    against pevc_solve on the same pencil: the same bits (FP64, and split
+    BF16x5 with its mma.sync update), the lower triangles of the host arrays
+    filled with garbage the method must not read, a selection, and the bytes
+    copied each way."""
+    emu.pevc_solve_host.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, vp, ctypes.POINTER(ci)]
+    emu.pevc_last_host_bytes.argtypes = [vp, vp]
+    p = pencilgen.make_pencil(n, 9800 + n)
+    sel = None if every == 1 else (np.arange(n) % every != 1).astype(np.int32)
+    h = vp()
+    assert emu.pevc_plan(ctypes.byref(h), n, 1, prec, tile, 0, None) == 0
+    S, T = np.asfortranarray(p.S), np.asfortranarray(p.T)
+    V1, V2 = np.zeros((n, n), order="F"), np.zeros((n, n), order="F")
+    sc1, sc2 = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+    m1, m2 = ci(0), ci(0)
+    s = None if sel is None else sel.ctypes.data
+    st1 = emu.pevc_solve(h, S.ctypes.data, n, T.ctypes.data, n, n, s, V1.ctypes.data, n, sc1.ctypes.data,
+                         ctypes.byref(m1))
+    # below the subdiagonal: entries the method never reads
+    Sg, Tg = S.copy(order="F"), T.copy(order="F")
+    low = np.tril(np.ones((n, n), dtype=bool), -2)
+    Sg[low] = 7.0e300
+    Tg[low] = -3.0e300
+    st2 = emu.pevc_solve_host(h, Sg.ctypes.data, n, Tg.ctypes.data, n, n, s, V2.ctypes.data, n, sc2.ctypes.data,
+                              ctypes.byref(m2))
+    nb = (ctypes.c_longlong * 2)()
+    assert emu.pevc_last_host_bytes(h, nb) == 0
+    emu.pevc_destroy(h)
+    assert st1 == 0 and st2 == 0 and m1.value == m2.value
+    m = m1.value
+    assert np.array_equal(V1[:, :m], V2[:, :m]) and np.array_equal(sc1[:m], sc2[:m])
+    # upper tiles only: between the upper triangle and the whole matrix, both S and T
+    assert n * (n + 1) * 8 <= nb[0] <= 2 * n * n * 8
+    assert nb[1] == m * n * 8 + m * 4
+
+
 def test_emulated_complex_solve_matches_oracle(emu):
     # two tiles of 64 (the second ragged), then a stress pencil in one tile
     for n, seed, stress in ((65, 9200, False), (40, 9201, True)):
