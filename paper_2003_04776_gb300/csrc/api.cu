@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "autotune.cuh"
@@ -117,8 +118,11 @@ struct pevc_plan_s {
   double* hV = nullptr;
   int32_t* hsc = nullptr;
   cudaStream_t hstream = nullptr;
-  cudaEvent_t* hev = nullptr;
+  cudaStream_t astream = nullptr;   // the blocks' arrival work (pre-pass, slices, tips)
+  cudaEvent_t* hev = nullptr;       // [Mmax] block l copied
+  cudaEvent_t* aev = nullptr;       // [Mmax] block l's arrival work done
   cudaEvent_t hstart = nullptr;
+  cudaEvent_t hinit = nullptr;
   double* hspec = nullptr;
   double* h_hspec = nullptr;
   long long host_bytes[2] = {0, 0};
@@ -271,13 +275,16 @@ void free_plan(pevc_plan_t p) {
   for (void* d : hdev)
     if (d) cudaFree(d);
   if (p->h_hspec) cudaFreeHost(p->h_hspec);
-  if (p->hev) {
+  for (cudaEvent_t* evs : {p->hev, p->aev}) {
+    if (!evs) continue;
     for (int q = 0; q < p->Mmax; ++q)
-      if (p->hev[q]) cudaEventDestroy(p->hev[q]);
-    delete[] p->hev;
+      if (evs[q]) cudaEventDestroy(evs[q]);
+    delete[] evs;
   }
   if (p->hstart) cudaEventDestroy(p->hstart);
+  if (p->hinit) cudaEventDestroy(p->hinit);
   if (p->hstream) cudaStreamDestroy(p->hstream);
+  if (p->astream) cudaStreamDestroy(p->astream);
   if (p->bt_kind) cudaFree(p->bt_kind);
   if (p->bt_ws) cudaFree(p->bt_ws);
   if (p->h_bt_kind) cudaFreeHost(p->h_bt_kind);
@@ -755,31 +762,53 @@ int host_alloc(pevc_plan_t p) {
   rc = rc ? rc : halloc(&p->h_hspec, 2 * (size_t)p->Mmax);
   if (rc) return rc;
   CK(cudaStreamCreateWithFlags(&p->hstream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&p->astream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->hstart, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&p->hinit, cudaEventDisableTiming));
   p->hev = new (std::nothrow) cudaEvent_t[p->Mmax]();
-  if (!p->hev) return PEVC_ERR_NOMEM;
-  for (int q = 0; q < p->Mmax; ++q) CK(cudaEventCreateWithFlags(&p->hev[q], cudaEventDisableTiming));
+  p->aev = new (std::nothrow) cudaEvent_t[p->Mmax]();
+  if (!p->hev || !p->aev) return PEVC_ERR_NOMEM;
+  for (int q = 0; q < p->Mmax; ++q) {
+    CK(cudaEventCreateWithFlags(&p->hev[q], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->aev[q], cudaEventDisableTiming));
+  }
   return 0;
 }
 
-// Column block l's arrival: wait for its copy, then its pre-pass and tips.
+// The arrival work of every column block, enqueued up front on the arrival
+// stream (after the zeroed state, hinit): per block, from the right, wait for
+// its copy, then its pre-pass (tile norms, eigenvalues), its slices (split
+// plans) and the tips of its diagonal tile; aev[l] marks it done.  The walk's
+// stage l waits for aev[l] alone, so the tips of the blocks to come run beside
+// the stages before them.  (Tiles and columns these write are not touched by
+// those stages: the tips write tile (l, l) and its columns' state, the stages
+// before l update tiles (k, j) with j > l.)
+int enqueue_arrivals(pevc_plan_t p, const Problem& P, int ns) {
+  cudaStream_t a = p->astream;
+  CK(cudaStreamWaitEvent(a, p->hinit, 0));
+  for (int l = P.M - 1; l >= 0; --l) {
+    CK(cudaStreamWaitEvent(a, p->hev[l], 0));
+    p->prof.begin(a);
+    CK(launch_prepass_block(P, l, p->h_toff[l], p->h_toff[l + 1], p->hspec + 2 * l, a));
+    p->prof.end(a, 3, 0.0);
+    ++p->prof.launches;   // two kernels
+    if (ns) {
+      p->prof.begin(a);
+      CK(launch_split_A_block(P, p->split, l, ns, a));
+      p->prof.end(a, 3, 0.0);
+    }
+    p->prof.begin(a);
+    CK(launch_diag_tile(P, l, kDiagTip, a));
+    p->prof.end(a, 1, 0.0);
+    CK(cudaEventRecord(p->aev[l], a));
+  }
+  return 0;
+}
+
 struct HostArrivals : Arrivals {
   pevc_plan_t p;
-  const Problem& P;
-  HostArrivals(pevc_plan_t p_, const Problem& P_) : p(p_), P(P_) {}
-  cudaError_t arrive(int l, cudaStream_t s) override {
-    cudaError_t e = cudaStreamWaitEvent(s, p->hev[l], 0);
-    if (e != cudaSuccess) return e;
-    p->prof.begin(s);
-    e = launch_prepass_block(P, l, p->h_toff[l], p->h_toff[l + 1], p->hspec + 2 * l, s);
-    p->prof.end(s, 3, 0.0);
-    ++p->prof.launches;   // two kernels
-    if (e != cudaSuccess) return e;
-    p->prof.begin(s);
-    e = launch_diag_tile(P, l, kDiagTip, s);
-    p->prof.end(s, 1, 0.0);
-    return e;
-  }
+  explicit HostArrivals(pevc_plan_t p_) : p(p_) {}
+  cudaError_t arrive(int l, cudaStream_t s) override { return cudaStreamWaitEvent(s, p->aev[l], 0); }
 };
 
 int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt, int n, const int32_t* sel,
@@ -801,6 +830,29 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
   *m_out = st.m;
   p->last_m = st.m;
   const int M = st.M, ldd = p->n_max;
+  // the rows of V below each column tile's last row are zero: host threads
+  // write them while the GPU works, and only the rows above come back
+  std::vector<std::thread> zero;
+  {
+    const int nt = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency() / 2));
+    const int m = st.m;
+    for (int t = 0; t < nt && m > 0; ++t)
+      zero.emplace_back([p, V, ldv, n, M, m, nt, t] {
+        int j = 0;
+        for (int q = (int)((long long)m * t / nt); q < (int)((long long)m * (t + 1) / nt); ++q) {
+          while (j + 1 < M && p->h_cstart[j + 1] <= q) ++j;
+          const int r0 = p->h_toff[j + 1];
+          if (r0 < n) std::memset(V + (size_t)q * ldv + r0, 0, (size_t)(n - r0) * sizeof(double));
+        }
+      });
+  }
+  struct Joiner {
+    std::vector<std::thread>& t;
+    ~Joiner() {
+      for (auto& x : t)
+        if (x.joinable()) x.join();
+    }
+  } joiner{zero};
   // 2. the copies, column blocks from the right, after the plan's earlier
   //    work (which may still read the device copies)
   CK(cudaEventRecord(p->hstart, s));
@@ -849,7 +901,11 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
       p->prof.begin(ss);
       CK(launch_init_state(P, ss, 1));
       p->prof.end(ss, 3, 0.0);
-      HostArrivals arr(p, P);
+      CK(cudaEventRecord(p->hinit, ss));
+      int ns = 0;
+      if (p->prec != PEVC_FP64) ns = split_config(p->prec, false).ns1 == 5 ? 5 : 3;
+      if ((rc = enqueue_arrivals(p, P, ns))) return rc;
+      HostArrivals arr(p);
       SchedContext sc{p->aux, p->sev, p->lookahead};
       if (p->prec == PEVC_FP64) {
         struct F64Streamed : StageOps {
@@ -916,12 +972,22 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
       if ((rc = solve_enqueue(p, p->hS, ldd, p->hT, ldd, n, p->hV, ldd, p->hsc, st, false))) return rc;
     }
   }
-  // 4. the result to the host
+  // 4. the result to the host: per column tile j the rows above the end of
+  //    row tile j (the zeros below are written by the host threads, joined
+  //    first so that no two writers share the buffer at once)
+  for (auto& x : zero) x.join();
   if (st.m > 0) {
-    CK(cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), p->hV, (size_t)ldd * sizeof(double),
-                         (size_t)n * sizeof(double), (size_t)st.m, cudaMemcpyDeviceToHost, s));
+    long long bytes = 0;
+    for (int j = 0; j < M; ++j) {
+      const int q0 = p->h_cstart[j], q1 = p->h_cstart[j + 1], rows = p->h_toff[j + 1];
+      if (q1 <= q0) continue;
+      CK(cudaMemcpy2DAsync(V + (size_t)q0 * ldv, (size_t)ldv * sizeof(double), p->hV + (size_t)q0 * ldd,
+                           (size_t)ldd * sizeof(double), (size_t)rows * sizeof(double), (size_t)(q1 - q0),
+                           cudaMemcpyDeviceToHost, s));
+      bytes += (long long)rows * (q1 - q0) * (long long)sizeof(double);
+    }
     CK(cudaMemcpyAsync(scale, p->hsc, (size_t)st.m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    p->host_bytes[1] = (long long)st.m * n * (long long)sizeof(double) + (long long)st.m * sizeof(int32_t);
+    p->host_bytes[1] = bytes + (long long)st.m * sizeof(int32_t);
   }
   CK(cudaEventRecord(p->ev[5], s));
   unsigned bits = 0;

@@ -696,23 +696,15 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     SplitOps ops(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, prof);
     SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
   } else {
-    // column block i: its arrival (pre-pass, tips), then its slices
+    // column block i's arrival work (pre-pass, slices, tips) is the caller's
     struct StreamedOps : SplitOps {
       Arrivals* arr;
-      int ns_a;
       StreamedOps(const Problem& P_, SplitWorkspace& w_, const HostStructure& hs_, const SplitConfig& cfg_,
-                  Profiler& prof_, Arrivals* arr_, int ns_a_)
-          : SplitOps(P_, w_, hs_, kDiagTip, cfg_.ns1, cfg_.levels1, prof_), arr(arr_), ns_a(ns_a_) {}
+                  Profiler& prof_, Arrivals* arr_)
+          : SplitOps(P_, w_, hs_, kDiagTip, cfg_.ns1, cfg_.levels1, prof_), arr(arr_) {}
       cudaError_t tips(cudaStream_t) override { return cudaSuccess; }   // tile by tile, on arrival
-      cudaError_t arrive(int l, cudaStream_t st) override {
-        cudaError_t e = arr->arrive(l, st);
-        if (e != cudaSuccess) return e;
-        prof.begin(st);
-        e = launch_split_A_block(P, w, l, ns_a == 5 ? 5 : 3, st);
-        prof.end(st, 3, 0.0);
-        return e;
-      }
-    } ops(P, w, hs, cfg, prof, arr, ns_a);
+      cudaError_t arrive(int l, cudaStream_t st) override { return arr->arrive(l, st); }
+    } ops(P, w, hs, cfg, prof, arr);
     SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
   }
   SCK(cudaEventRecord(ev_dag, s));

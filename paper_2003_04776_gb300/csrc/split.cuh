@@ -69,14 +69,15 @@ cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, i
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
 // Inputs that arrive by column blocks (pevc_solve_host): arrive(i) orders
-// column block i after its copy and runs its pre-pass and tips.
+// what follows after column block i's copy and arrival work (pre-pass,
+// slices of [S T], tips).
 struct Arrivals {
   virtual ~Arrivals() = default;
   virtual cudaError_t arrive(int l, cudaStream_t s) = 0;
 };
 cudaError_t launch_split_A_block(const Problem& P, SplitWorkspace& w, int l, int ns, cudaStream_t s);
-// arr: null, or the arrivals of a streamed solve (no correction sweep): the
-// slicing of [S T] then runs by column block, after each block's arrival.
+// arr: null, or the arrivals of a streamed solve (no correction sweep), which
+// then slice [S T] and run the tips block by block.
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
                 Arrivals* arr = nullptr);
