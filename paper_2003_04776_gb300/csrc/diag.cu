@@ -6,7 +6,7 @@
 namespace pevc {
 
 template <int CB>
-__global__ void __launch_bounds__(kMaxTile, 7) k_diag(Problem P, int i_row, int mode) {
+__global__ void __launch_bounds__(kMaxTile, 6) k_diag(Problem P, int i_row, int mode) {
   __shared__ DiagSmem<CB> sm;
   const bool tips = mode != kDiagSolve;          // one CTA row per diagonal tile from i_row
   const int j = tips ? i_row + (int)blockIdx.y : i_row + 1 + (int)blockIdx.y;

@@ -325,22 +325,37 @@ __device__ __forceinline__ void diag_tile(const Problem& P, int i, int j, int ch
       const double (*cn)[kMaxTile] = s_nc;
       const double2 pq0 = s_PQ[0][t];
       const int wg = (lr >> 5) * (32 / CB);
+      // the S, T entries of row step k + 1 are read from shared memory
+      // before the FMAs of step k (rows below 128 always: in bounds), so
+      // their latency hides behind the FP64 instructions
       if (sz == 1) {
+        double c0 = cn[0][g], c1 = cn[1][g];
 #pragma unroll
         for (int k = 0; k < CB; ++k) {
+          double d0 = 0.0, d1 = 0.0;
+          if (k + 1 < CB) { d0 = cn[0][g + NG * (k + 1)]; d1 = cn[1][g + NG * (k + 1)]; }
           if (wg + NG * k >= li0) break;
           const int r = g + NG * k;
-          const double v = fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]));
+          const double v = fma(c1, pq0.y, fma(-c0, pq0.x, vals[k]));
           vals[k] = r < li0 ? v : vals[k];
+          c0 = d0;
+          c1 = d1;
         }
       } else {
         const double2 pq1 = s_PQ[1][t];
+        double c0 = cn[0][g], c1 = cn[1][g], c2 = cn[2][g], c3 = cn[3][g];
 #pragma unroll
         for (int k = 0; k < CB; ++k) {
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+          if (k + 1 < CB) {
+            const int rn = g + NG * (k + 1);
+            d0 = cn[0][rn]; d1 = cn[1][rn]; d2 = cn[2][rn]; d3 = cn[3][rn];
+          }
           if (wg + NG * k >= li0) break;
           const int r = g + NG * k;
-          const double v = fma(cn[3][r], pq1.y, fma(-cn[2][r], pq1.x, fma(cn[1][r], pq0.y, fma(-cn[0][r], pq0.x, vals[k]))));
+          const double v = fma(c3, pq1.y, fma(-c2, pq1.x, fma(c1, pq0.y, fma(-c0, pq0.x, vals[k]))));
           vals[k] = r < li0 ? v : vals[k];
+          c0 = d0; c1 = d1; c2 = d2; c3 = d3;
         }
       }
 #pragma unroll
