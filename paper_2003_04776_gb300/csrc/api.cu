@@ -853,27 +853,11 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
         if (x.joinable()) x.join();
     }
   } joiner{zero};
-  // 2. the copies, column blocks from the right, after the plan's earlier
-  //    work (which may still read the device copies)
-  CK(cudaEventRecord(p->hstart, s));
-  CK(cudaStreamWaitEvent(p->hstream, p->hstart, 0));
-  for (int l = M - 1; l >= 0; --l) {
-    const int c0 = p->h_toff[l], c1 = p->h_toff[l + 1];
-    const size_t w = (size_t)c1 * sizeof(double);
-    CK(cudaMemcpy2DAsync(p->hS + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), S + (size_t)c0 * lds,
-                         (size_t)lds * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
-    CK(cudaMemcpy2DAsync(p->hT + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), T + (size_t)c0 * ldt,
-                         (size_t)ldt * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
-    CK(cudaEventRecord(p->hev[l], p->hstream));
-    p->host_bytes[0] += 2 * (long long)w * (c1 - c0);
-  }
-  // 3. the solve on the device copies, each stage after its column block
   const bool streamed = !(p->prec != PEVC_FP64 && split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0).correction);
-  if (!streamed) {
-    // the correction sweep reads every block at the start: the whole copy first
-    for (int l = 0; l < M; ++l) CK(cudaStreamWaitEvent(s, p->hev[l], 0));
-    if ((rc = solve_enqueue(p, p->hS, ldd, p->hT, ldd, n, p->hV, ldd, p->hsc, st, false))) return rc;
-  } else {
+  if (streamed) {
+    // the structure (and every other small host-to-device copy of the solve)
+    // first: the copy engine takes the copies in the order they are issued,
+    // so these must not queue behind the blocks of S and T
     cudaStream_t ss = s;
     // structure to the device
     CK(cudaMemcpyAsync(p->blk, p->h_blk, (size_t)n, cudaMemcpyHostToDevice, ss));
@@ -895,13 +879,42 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
       std::memcpy(&p->h_hspec[2 * l + 1], &lowest, sizeof(int));
     }
     CK(cudaMemcpyAsync(p->hspec, p->h_hspec, 2 * (size_t)M * sizeof(double), cudaMemcpyHostToDevice, ss));
-    Problem P = make_problem(p, p->hS, ldd, p->hT, ldd, n, st);
+    if (p->prec != PEVC_FP64 && st.m > 0) {
+      HostStructure hs{p->h_toff, p->h_cstart};
+      if ((rc = split_prepare(p->split, make_problem(p, p->hS, ldd, p->hT, ldd, n, st), hs, ss))) return rc;
+    }
+    // the zeroed augmented state, before the copies are issued
     CK(cudaEventRecord(p->ev[1], ss));
     if (st.m > 0) {
       p->prof.begin(ss);
-      CK(launch_init_state(P, ss, 1));
+      CK(launch_init_state(make_problem(p, p->hS, ldd, p->hT, ldd, n, st), ss, 1));
       p->prof.end(ss, 3, 0.0);
       CK(cudaEventRecord(p->hinit, ss));
+    }
+  }
+  // 2. the copies, column blocks from the right, after the plan's earlier
+  //    work (which may still read the device copies)
+  CK(cudaEventRecord(p->hstart, s));
+  CK(cudaStreamWaitEvent(p->hstream, p->hstart, 0));
+  for (int l = M - 1; l >= 0; --l) {
+    const int c0 = p->h_toff[l], c1 = p->h_toff[l + 1];
+    const size_t w = (size_t)c1 * sizeof(double);
+    CK(cudaMemcpy2DAsync(p->hS + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), S + (size_t)c0 * lds,
+                         (size_t)lds * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
+    CK(cudaMemcpy2DAsync(p->hT + (size_t)c0 * ldd, (size_t)ldd * sizeof(double), T + (size_t)c0 * ldt,
+                         (size_t)ldt * sizeof(double), w, (size_t)(c1 - c0), cudaMemcpyHostToDevice, p->hstream));
+    CK(cudaEventRecord(p->hev[l], p->hstream));
+    p->host_bytes[0] += 2 * (long long)w * (c1 - c0);
+  }
+  // 3. the solve on the device copies, each stage after its column block
+  if (!streamed) {
+    // the correction sweep reads every block at the start: the whole copy first
+    for (int l = 0; l < M; ++l) CK(cudaStreamWaitEvent(s, p->hev[l], 0));
+    if ((rc = solve_enqueue(p, p->hS, ldd, p->hT, ldd, n, p->hV, ldd, p->hsc, st, false))) return rc;
+  } else {
+    cudaStream_t ss = s;
+    Problem P = make_problem(p, p->hS, ldd, p->hT, ldd, n, st);
+    if (st.m > 0) {
       int ns = 0;
       if (p->prec != PEVC_FP64) ns = split_config(p->prec, false).ns1 == 5 ? 5 : 3;
       if ((rc = enqueue_arrivals(p, P, ns))) return rc;

@@ -662,11 +662,8 @@ cudaError_t launch_split_A_block(const Problem& P, SplitWorkspace& w, int l, int
   return split_A_block(P, w, l, ns, s);
 }
 
-int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
-                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
-                Arrivals* arr) {
+int split_prepare(SplitWorkspace& w, const Problem& P, const HostStructure& hs, cudaStream_t s) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
-  if (arr && cfg.correction) return PEVC_ERR_UNSUPPORTED;
   if (w.use_tc && w.tc_ok) {
     // output column chunks (width 48 and 64) inside every column tile
     int* h48c = w.h_chunks;
@@ -687,6 +684,18 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     SCK(cudaMemcpyAsync(w.chunk_j_48, h48j, (size_t)n48 * sizeof(int), cudaMemcpyHostToDevice, s));
     SCK(cudaMemcpyAsync(w.chunk_c0_64, h64c, (size_t)n64 * sizeof(int), cudaMemcpyHostToDevice, s));
     SCK(cudaMemcpyAsync(w.chunk_j_64, h64j, (size_t)n64 * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  return 0;
+}
+
+int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
+                cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
+                Arrivals* arr) {
+  if (!w.on) return PEVC_ERR_UNSUPPORTED;
+  if (arr && cfg.correction) return PEVC_ERR_UNSUPPORTED;
+  if (!arr) {
+    const int rc = split_prepare(w, P, hs, s);
+    if (rc) return rc;
   }
   const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
   if (!arr) {

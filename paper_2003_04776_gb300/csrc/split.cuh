@@ -76,8 +76,13 @@ struct Arrivals {
   virtual cudaError_t arrive(int l, cudaStream_t s) = 0;
 };
 cudaError_t launch_split_A_block(const Problem& P, SplitWorkspace& w, int l, int ns, cudaStream_t s);
+// The output column chunks of the tcgen05 update, built from the structure
+// and uploaded on s (small copies: a streamed solve issues them before its
+// blocks of S and T, which the copy engine would otherwise take first).
+int split_prepare(SplitWorkspace& w, const Problem& P, const HostStructure& hs, cudaStream_t s);
 // arr: null, or the arrivals of a streamed solve (no correction sweep), which
-// then slice [S T] and run the tips block by block.
+// then slice [S T] and run the tips block by block; the caller has run
+// split_prepare.
 int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, const SplitConfig& cfg,
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
                 Arrivals* arr = nullptr);
