@@ -49,7 +49,7 @@ def flops_all(n: int) -> float:
 TRAFFIC = {
     "k_diag": {"bytes_per_launch": 1.2826e+07, "n": 20000, "prec": "bf16x5",
                "sources": ("diag.cu", "diag.cuh", "diag_tile.cuh", "common.cuh"),
-               "sha256_16": "4d7b8222eac9945d"},
+               "sha256_16": "48a0fb1c5854b9b1"},
     "k_update_tc": {"bytes_per_launch": 9.067e8, "n": 20000, "prec": "bf16x5",
                     "sources": ("update_tc.cu", "tc.cuh", "common.cuh", "split.cuh"),
                     "sha256_16": "62ad274b08761267"},
