@@ -88,7 +88,9 @@ def rooflines(prof, ms, n, prec, tile, peaks, peak_src, nsm, tc_kernel=True):
         pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         upd = {"bound": "tensor", "unit": "TFLOP/s",
                "achieved": upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms else None,
-               "peak": pk, "peak_source": f"{peak_src} bf16 sustained",
+               "peak": pk, "peak_source": f"{peak_src} bf16 sustained" +
+                                          (" (E4M3 products counted at half weight, the nominal FP8:BF16 "
+                                           "rate ratio of 2)" if prec == "fp8x4" else ""),
                "kernel": "k_update_tc" if tc_kernel else "k_update_split"}
     clock = float(peaks.get("sm_max_mhz") or 2070.0) * 1e6
     dg = {"bound": "alu", "unit": "TFLOP/s",
@@ -808,10 +810,11 @@ def main():
     if rank == 0:
         line["accuracy"] = accuracy_of(St, Tt, V, seed_pencil)
 
-    # the comparison the target turns on: the plain FP64-DMMA path and the
-    # 3-slice split path with its correction sweep, timed the same way
+    # the comparison the target turns on: the plain FP64-DMMA path, and the
+    # 3-slice BF16 and 4-slice FP8 split paths with their correction sweeps,
+    # timed the same way
     if extra:
-        for prec, key, steps in (("fp64", "fp64_path", 2), ("bf16x3", "bf16x3_path", 3)):
+        for prec, key, steps in (("fp64", "fp64_path", 2), ("bf16x3", "bf16x3_path", 3), ("fp8x4", "fp8x4_path", 3)):
             if prec == args.prec:
                 continue
             Va = torch.empty((n, n), dtype=torch.float64, device="cuda")

@@ -56,7 +56,7 @@ typedef struct pevc_plan_s *pevc_plan_t;
 /* Arithmetic of the bulk updates (kernel 2 of Section 3). */
 #define PEVC_FP64 0          /* FP64 tensor-core updates (DMMA)                      */
 #define PEVC_SPLIT_BF16X3 1  /* BF16 x3 slice products + FP64 residual correction   */
-#define PEVC_SPLIT_FP8X4 2   /* FP8 E4M3 x4 slice products + FP64 residual correction */
+#define PEVC_SPLIT_FP8X4 2   /* FP8 E4M3 x4 slice products + residual corrections   */
 #define PEVC_SPLIT_BF16X5 3  /* BF16 x5 slice products in one pass (no correction)   */
 
 /* Plan / solve flags. */
@@ -107,8 +107,8 @@ typedef struct pevc_plan_s *pevc_plan_t;
  *              (made on the device: 2x2 blocks on two thirds of the diagonal,
  *              uniform off-diagonal entries) and keeps the fastest: for the
  *              split precisions the split depth (BF16x5 in one pass, or
- *              BF16x3 plus the correction sweep), whichever of the two prec
- *              names, at tile order 128 (or the given one); for FP64 the tile
+ *              BF16x3 or FP8x4 plus the correction sweep), whichever of the
+ *              three prec names, at tile order 128 (or the given one); for FP64 the tile
  *              order among 64, 96 and 128 (32 too up to order 512) when tile
  *              is 0, and the walk; FP64 plans time orders above 8192 on a
  *              pencil of order 8192.  The
@@ -199,7 +199,8 @@ const char *pevc_strerror(int code);
 /*
  * pevc_plan_info -- the plan's resolved settings (after autotuning).
  *   info  host int[8]: {tile, prec, n_max, batch_max, flags, device SM count,
- *                       slices per operand (0 for FP64), correction sweeps}
+ *                       slices per operand (0 for FP64), correction sweeps
+ *                       (the most: FP8x4 repeats them until they converge)}
  */
 int pevc_plan_info(pevc_plan_t plan, int *info);
 
@@ -216,9 +217,10 @@ int pevc_autotune_log(pevc_plan_t plan, double *out, int cap);
 /*
  * pevc_last_stats -- host double[8] timing/work figures of the last solve on
  * this plan: {total ms (device, CUDA events), prepass ms, first-pass ms,
- * correction ms, postpass ms, tiles M, kernel launches, scheduler (1: the
- * task graph walked on the device by one persistent launch, 0: stage by
- * stage from the host)}.
+ * correction ms, postpass ms, tiles M, kernel launches, and for FP64 plans
+ * the scheduler (1: the task graph walked on the device by one persistent
+ * launch, 0: stage by stage from the host), for split plans the correction
+ * sweeps the solve ran}.
  */
 int pevc_last_stats(pevc_plan_t plan, double *stats);
 

@@ -710,7 +710,7 @@ int solve_one(pevc_plan_t p, const double* S, int lds, const double* T, int ldt,
   p->stats[4] = post;
   p->stats[5] = st.M;
   p->stats[6] = p->prof.launches;
-  p->stats[7] = (p->dag && p->prec == PEVC_FP64) ? 1.0 : 0.0;
+  p->stats[7] = p->prec == PEVC_FP64 ? (p->dag ? 1.0 : 0.0) : (double)p->split.last_sweeps;
   for (double& x : p->kprof) x = 0.0;
   for (int q = 0; q < p->prof.used; ++q) {
     float t = 0.0f;
@@ -853,7 +853,10 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
         if (x.joinable()) x.join();
     }
   } joiner{zero};
-  const bool streamed = !(p->prec != PEVC_FP64 && split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0).correction);
+  // split plans with the correction sweep (which reads every block at once) or
+  // FP8 slices take the whole copy first
+  const SplitConfig scfg = split_config(p->prec, (p->flags & PEVC_NO_CORRECTION) == 0);
+  const bool streamed = p->prec == PEVC_FP64 || !(scfg.correction || scfg.fp8);
   if (streamed) {
     // the structure (and every other small host-to-device copy of the solve)
     // first: the copy engine takes the copies in the order they are issued,
@@ -1019,7 +1022,7 @@ int solve_host(pevc_plan_t p, const double* S, int lds, const double* T, int ldt
   p->stats[4] = post;
   p->stats[5] = M;
   p->stats[6] = p->prof.launches;
-  p->stats[7] = 0.0;
+  p->stats[7] = p->prec == PEVC_FP64 ? 0.0 : (double)p->split.last_sweeps;
   for (double& x : p->kprof) x = 0.0;
   for (int q = 0; q < p->prof.used; ++q) {
     float t = 0.0f;
@@ -1210,7 +1213,6 @@ int pevc_plan(pevc_plan_t* plan, int n_max, int batch_max, int prec, int tile, u
   if (batch_max < 1) return -3;
   if (prec != PEVC_FP64 && prec != PEVC_SPLIT_BF16X3 && prec != PEVC_SPLIT_FP8X4 && prec != PEVC_SPLIT_BF16X5)
     return -4;
-  if (prec == PEVC_SPLIT_FP8X4) return PEVC_ERR_UNSUPPORTED;
   if (tile != 0 && tile != 32 && tile != 64 && tile != 96 && tile != 128) return -5;
   if (flags & ~(PEVC_NO_NORMALISE | PEVC_NO_CORRECTION | PEVC_STAGE_WALK | PEVC_DEVICE_WALK | PEVC_AUTOTUNE))
     return -6;
@@ -1662,7 +1664,10 @@ int pevc_plan_info(pevc_plan_t plan, int* info) {
   info[4] = (int)plan->flags;
   info[5] = plan->nsm;
   info[6] = plan->prec == PEVC_FP64 ? 0 : (plan->prec == PEVC_SPLIT_BF16X5 ? 5 : (plan->prec == PEVC_SPLIT_BF16X3 ? 3 : 4));
-  info[7] = (plan->prec == PEVC_SPLIT_BF16X3 && !(plan->flags & PEVC_NO_CORRECTION)) ? 1 : 0;
+  {
+    const SplitConfig c = split_config(plan->prec, (plan->flags & PEVC_NO_CORRECTION) == 0);
+    info[7] = (plan->prec != PEVC_FP64 && c.correction) ? c.sweeps : 0;
+  }
   return 0;
 }
 

@@ -107,7 +107,7 @@ int autotune_pick(int n_max, int prec, int tile, unsigned flags, void* stream, i
   } else if (flags & PEVC_NO_CORRECTION) {
     modes = {{prec, 0u}};                         // without the sweep only the caller's depth is accurate
   } else {
-    modes = {{PEVC_SPLIT_BF16X5, 0u}, {PEVC_SPLIT_BF16X3, 0u}};
+    modes = {{PEVC_SPLIT_BF16X5, 0u}, {PEVC_SPLIT_BF16X3, 0u}, {PEVC_SPLIT_FP8X4, 0u}};
   }
   // the synthetic pencil: the plan's order (FP64 plans: at most 8192, where
   // one solve already takes a good part of a second)

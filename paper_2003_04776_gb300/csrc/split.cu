@@ -43,13 +43,16 @@ __device__ __forceinline__ int col_tile_of(const Problem& P, int q) {
   return lo;
 }
 
-// Slices of v relative to 2^e (|v| < 2^e): the balanced base-256 digits of
-// the integer round(v 2^(B - e)), B = 7 + 8 (NS - 1), so that
-//   v 2^-e = sum_p d_p 2^(-7 - 8p) + O(2^-B-1),   |d_p| <= 128.
-// Integer arithmetic on the binary64 fields only (exact).
-template <int NS>
+// Slices of v relative to 2^e (|v| < 2^e): the balanced base-2^DB digits of
+// the integer round(v 2^(B - e)), B = (DB - 1) + DB (NS - 1), so that
+//   v 2^-e = sum_p d_p 2^(-(DB - 1) - DB p) + O(2^-B-1),   |d_p| <= 2^(DB - 1):
+// DB = 8 for BF16 slices (|d| <= 128, 8 significant bits), DB = 4 for FP8
+// E4M3 slices (|d| <= 8, 4 significant bits).  Integer arithmetic on the
+// binary64 fields only (exact).
+template <int NS, int DB = 8>
 __device__ __forceinline__ void int_slices(double v, int e, int (&d)[NS]) {
-  constexpr int B = 7 + 8 * (NS - 1);
+  constexpr int B = (DB - 1) + DB * (NS - 1);
+  constexpr long long R = 1ll << DB, H = R / 2;
   const long long bits = __double_as_longlong(v);
   const int E = (int)((bits >> 52) & 0x7ff);
   long long mant = bits & ((1ll << 52) - 1);
@@ -70,14 +73,41 @@ __device__ __forceinline__ void int_slices(double v, int e, int (&d)[NS]) {
   if (bits < 0) q = -q;
 #pragma unroll
   for (int p = NS - 1; p >= 1; --p) {
-    const int dp = (int)(((q + 128) & 255) - 128);
+    const int dp = (int)(((q + H) & (R - 1)) - H);
     d[p] = dp;
-    q = (q - dp) >> 8;
+    q = (q - dp) >> DB;
   }
   d[0] = (int)q;
 }
 
 __device__ __forceinline__ __nv_bfloat16 small_int_bf16(int x) { return __float2bfloat16_rn((float)x); }
+
+// The FP8 E4M3 byte of an integer |x| <= 15 (exact: 4 significant bits),
+// assembled from the fields: sign, biased exponent (bias 7), 3 mantissa bits.
+__device__ __forceinline__ unsigned char small_int_e4m3(int x) {
+  const unsigned a = (unsigned)(x < 0 ? -x : x);
+  if (a == 0) return 0;
+  const int E = 31 - __clz((int)a);                   // floor(log2 a), 0..3
+  const unsigned m = (a << (3 - E)) & 7u;
+  return (unsigned char)(((x < 0) ? 0x80u : 0u) | ((unsigned)(E + 7) << 3) | m);
+}
+
+// The slice storage of the two formats: BF16 (8-bit digits) or FP8 E4M3
+// (4-bit digits).
+template <bool FP8>
+struct Slice;
+template <>
+struct Slice<false> {
+  using T = __nv_bfloat16;
+  static constexpr int DB = 8;
+  __device__ static T enc(int x) { return small_int_bf16(x); }
+};
+template <>
+struct Slice<true> {
+  using T = unsigned char;
+  static constexpr int DB = 4;
+  __device__ static T enc(int x) { return small_int_e4m3(x); }
+};
 
 // ---------------------------------------------------------------- A slices
 
@@ -85,9 +115,10 @@ __device__ __forceinline__ __nv_bfloat16 small_int_bf16(int x) { return __float2
 // resident CTAs hold between the row maxima and the slicing stay in L2.
 constexpr int kSplitARows = 64;
 
-template <int NS>
-__global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __restrict__ As,
+template <int NS, bool FP8 = false>
+__global__ void __launch_bounds__(256) k_split_A(Problem P, typename Slice<FP8>::T* __restrict__ As,
                                                  int* __restrict__ eA, int ns, int lfix) {
+  using E = typename Slice<FP8>::T;
   int k = (int)(blockIdx.x >> 1), l = lfix;   // lfix >= 0: the tiles (k, lfix) of one column block
   if (lfix < 0) tile_pair(blockIdx.x >> 1, k, l);
   const int tb = P.tb, K2 = 2 * tb;
@@ -146,15 +177,16 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
         if (k == l) ok = isT ? (gc >= gr) : (gc >= gr || (gc == gr - 1 && P.blk[gr] == 2));
         if (ok) v = isT ? T[(size_t)gc * P.ldt + gr] : S[(size_t)gc * P.lds + gr];
       }
-      int_slices<NS>(v, s_e[rr], sl[u]);
+      int_slices<NS, Slice<FP8>::DB>(v, s_e[rr], sl[u]);
     }
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-      __align__(16) __nv_bfloat16 pk[8];
+      __align__(16) E pk[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) pk[u] = small_int_bf16(sl[u][p]);
-      __nv_bfloat16* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
+      for (int u = 0; u < 8; ++u) pk[u] = Slice<FP8>::enc(sl[u][p]);
+      E* dst = As + ((tri * ns + p) * tb + r) * (long long)K2 + 8 * g;
+      if (FP8) *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(pk);
+      else *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
     }
   }
 }
@@ -163,10 +195,12 @@ __global__ void __launch_bounds__(256) k_split_A(Problem P, __nv_bfloat16* __res
 
 // X'' = [beta x ; -(alpha x)] of tile row i for output columns q >= q_begin,
 // from the augmented tiles (Ysrc, exsrc, nrmsrc).  One warp per column.
-template <int NS>
+template <int NS, bool FP8 = false>
 __global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, const double* __restrict__ Ysrc,
-                                                 const double* __restrict__ nrmsrc, __nv_bfloat16* __restrict__ Xs,
-                                                 int* __restrict__ F, int ns, int mstride) {
+                                                 const double* __restrict__ nrmsrc,
+                                                 typename Slice<FP8>::T* __restrict__ Xs, int* __restrict__ F, int ns,
+                                                 int mstride) {
+  using T = typename Slice<FP8>::T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = q_begin + blockIdx.x * 8 + warp;
   if (q >= P.m) return;
@@ -211,13 +245,13 @@ __global__ void __launch_bounds__(256) k_split_X(Problem P, int i, int q_begin, 
     const int kap = lane + 32 * u;
     if (kap >= tb) continue;
     int st[NS], sb[NS];
-    int_slices<NS>(top[u], f, st);
-    int_slices<NS>(bot[u], f, sb);
+    int_slices<NS, Slice<FP8>::DB>(top[u], f, st);
+    int_slices<NS, Slice<FP8>::DB>(bot[u], f, sb);
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-      __nv_bfloat16* xrow = Xs + ((long long)p * mstride + q) * K2;
-      xrow[kap] = small_int_bf16(st[p]);
-      xrow[tb + kap] = small_int_bf16(sb[p]);
+      T* xrow = Xs + ((long long)p * mstride + q) * K2;
+      xrow[kap] = Slice<FP8>::enc(st[p]);
+      xrow[tb + kap] = Slice<FP8>::enc(sb[p]);
     }
   }
 }
@@ -248,34 +282,52 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// D = A B + C for a 16x32 E4M3 A (row) and a 32x8 E4M3 B (col), FP32
+// accumulators: four E4M3 values per register, the fragment layout of
+// mma.m16n8k16 with each 16-bit element replaced by two consecutive 8-bit
+// ones (so ldmatrix of the bytes as 16-bit pairs gives the fragments).
+__device__ __forceinline__ void mma_fp8(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 constexpr int kSplitRows = 128;
 constexpr int kSplitCols = 32;
 
-// K chunk per pipeline stage: 32 for up to 3 slices, 16 for 5 (so that two
-// CTAs fit in shared memory and one CTA's epilogue overlaps the other's MMAs).
-template <int NS>
-__host__ __device__ constexpr int split_kc() { return NS >= 5 ? 16 : 32; }
-template <int NS>
-__host__ __device__ constexpr int split_ld() { return split_kc<NS>() + 8; }   // padded smem row (bf16): conflict-free ldmatrix
+// K chunk per pipeline stage (elements): BF16 32 for up to 3 slices, 16 for 5
+// (so that two CTAs fit in shared memory and one CTA's epilogue overlaps the
+// other's MMAs); FP8 32 (one K step of the m16n8k32 MMA).
+template <int NS, bool FP8 = false>
+__host__ __device__ constexpr int split_kc() { return FP8 ? 32 : (NS >= 5 ? 16 : 32); }
+// padded smem row (elements): 16 bytes more, so ldmatrix is conflict-free
+template <int NS, bool FP8 = false>
+__host__ __device__ constexpr int split_ld() { return split_kc<NS, FP8>() + (FP8 ? 16 : 8); }
 
-template <int NS>
+template <int NS, bool FP8 = false>
 constexpr int split_smem_bytes() {
-  return 2 * NS * (kSplitRows + kSplitCols) * split_ld<NS>() * 2;
+  return 2 * NS * (kSplitRows + kSplitCols) * split_ld<NS, FP8>() * (FP8 ? 1 : 2);
 }
 
 // Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij for k_lo <= k < k_lo + gridDim.y, j >= i.
-template <int NS, int L>
+template <int NS, int L, bool FP8 = false>
 __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k_lo, const int* __restrict__ exX,
                                                          const double* __restrict__ nrmX,
-                                                         const __nv_bfloat16* __restrict__ As,
+                                                         const typename Slice<FP8>::T* __restrict__ As,
                                                          const int* __restrict__ eA,
-                                                         const __nv_bfloat16* __restrict__ Xs,
+                                                         const typename Slice<FP8>::T* __restrict__ Xs,
                                                          const int* __restrict__ F, int ns, int mstride) {
-  constexpr int KC = split_kc<NS>();
-  constexpr int LD = split_ld<NS>();
+  using T = typename Slice<FP8>::T;
+  constexpr int DB = Slice<FP8>::DB;                  // bits per digit
+  constexpr int E16 = 16 / (int)sizeof(T);            // elements per 16 bytes
+  constexpr int KSTEP = FP8 ? 32 : 16;                // K of one mma.sync
+  constexpr int KC = split_kc<NS, FP8>();
+  constexpr int LD = split_ld<NS, FP8>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);    // [2][NS][128][LD]
-  __nv_bfloat16* sB = sA + 2 * NS * kSplitRows * LD;                 // [2][NS][32][LD]
+  T* sA = reinterpret_cast<T*>(smem_raw);             // [2][NS][128][LD]
+  T* sB = sA + 2 * NS * kSplitRows * LD;              // [2][NS][32][LD]
   const int tb = P.tb, K2 = 2 * tb;
   const int nsub = tb / kSplitCols;
   const int j = i + (int)blockIdx.x / nsub;
@@ -303,7 +355,7 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
       const int q = c0 + tid;
       on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
       if (on && F[q] == kExpZero) on = 0;
-      s_sc[tid] = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
+      s_sc[tid] = on ? F[q] - 2 * (DB - 1) - DB * (L - 1) + sX : 0;
     }
     s_on[tid] = on;
     s_sY[tid] = sY;
@@ -317,22 +369,22 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
   if (!s_any) return;
 
   // slices are stored K-contiguous: [slice][row or column][K]
-  const __nv_bfloat16* Abase = As + tri * ns * (long long)tb * K2;
+  const T* Abase = As + tri * ns * (long long)tb * K2;
   auto load_stage = [&](int st, int kb) {
-    __nv_bfloat16* a_dst = sA + st * NS * kSplitRows * LD;
-    __nv_bfloat16* b_dst = sB + st * NS * kSplitCols * LD;
-    constexpr int chunks = KC / 8;                        // 16-byte pieces per row
+    T* a_dst = sA + st * NS * kSplitRows * LD;
+    T* b_dst = sB + st * NS * kSplitCols * LD;
+    constexpr int chunks = KC / E16;                      // 16-byte pieces per row
     for (int idx = tid; idx < NS * kSplitRows * chunks; idx += 256) {
       const int c16 = idx % chunks, r = (idx / chunks) % kSplitRows, p = idx / (chunks * kSplitRows);
       const bool valid = r < tb;
-      const __nv_bfloat16* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + 8 * c16;
-      cp_async16(a_dst + (p * kSplitRows + r) * LD + 8 * c16, src, valid);
+      const T* src = Abase + ((long long)p * tb + (valid ? r : 0)) * K2 + kb + E16 * c16;
+      cp_async16(a_dst + (p * kSplitRows + r) * LD + E16 * c16, src, valid);
     }
     for (int idx = tid; idx < NS * kSplitCols * chunks; idx += 256) {
       const int c16 = idx % chunks, col = (idx / chunks) % kSplitCols, p = idx / (chunks * kSplitCols);
       const bool valid = col < nc;
-      const __nv_bfloat16* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + 8 * c16;
-      cp_async16(b_dst + (p * kSplitCols + col) * LD + 8 * c16, src, valid);
+      const T* src = Xs + ((long long)p * mstride + c0 + (valid ? col : 0)) * K2 + kb + E16 * c16;
+      cp_async16(b_dst + (p * kSplitCols + col) * LD + E16 * c16, src, valid);
     }
   };
 
@@ -357,28 +409,33 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    const __nv_bfloat16* a_s = sA + st * NS * kSplitRows * LD;
-    const __nv_bfloat16* b_s = sB + st * NS * kSplitCols * LD;
+    const T* a_s = sA + st * NS * kSplitRows * LD;
+    const T* b_s = sB + st * NS * kSplitCols * LD;
 #pragma unroll
-    for (int kk = 0; kk < KC; kk += 16) {
+    for (int kk = 0; kk < KC; kk += KSTEP) {
       unsigned bf[NS][4];
 #pragma unroll
       for (int q = 0; q < NS; ++q)
         ldmatrix_x4(bf[q], b_s + (q * kSplitCols + 16 * wc + (lane & 7) + ((lane >> 4) << 3)) * LD + kk +
-                               ((lane >> 3) & 1) * 8);
+                               ((lane >> 3) & 1) * E16);
 #pragma unroll
       for (int p = 0; p < NS; ++p) {
         unsigned af[2][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
-          ldmatrix_x4(af[mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * LD + kk + (lane >> 4) * 8);
+          ldmatrix_x4(af[mt], a_s + (p * kSplitRows + 32 * wr + 16 * mt + (lane & 15)) * LD + kk + (lane >> 4) * E16);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
           if (p + q < L) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-              mma_bf16(acc[p + q][mt][0], af[mt], bf[q][0], bf[q][1]);
-              mma_bf16(acc[p + q][mt][1], af[mt], bf[q][2], bf[q][3]);
+              if (FP8) {
+                mma_fp8(acc[p + q][mt][0], af[mt], bf[q][0], bf[q][1]);
+                mma_fp8(acc[p + q][mt][1], af[mt], bf[q][2], bf[q][3]);
+              } else {
+                mma_bf16(acc[p + q][mt][0], af[mt], bf[q][0], bf[q][1]);
+                mma_bf16(acc[p + q][mt][1], af[mt], bf[q][2], bf[q][3]);
+              }
             }
           }
         }
@@ -411,7 +468,7 @@ __global__ void __launch_bounds__(256, 2) k_update_split(Problem P, int i, int k
             if (row < hk) {
               long long t = 0;
 #pragma unroll
-              for (int s = 0; s < L; ++s) t = (t << 8) + (long long)__float2int_rn(acc[s][mt][nt][2 * h + e]);
+              for (int s = 0; s < L; ++s) t = (t << DB) + (long long)__float2int_rn(acc[s][mt][nt][2 * h + e]);
               const double prod = i64_scaled(t, s_eA[row] + sc);
               const double yold = yz ? 0.0 : pow2_scale(ycol[row], sY);
               const double ynew = yold - prod;
@@ -470,10 +527,36 @@ __global__ void __launch_bounds__(256) k_combine(Problem P, const double* __rest
   }
 }
 
+constexpr int kSweepNoV = 1 << 20;   // a correction in a column whose V is zero
+
+// Convergence of the correction sweeps: for every column, the largest power
+// of two of the correction just added (its tiles' maxima at their exponents)
+// against the largest of V, as the difference of the two binary exponents;
+// the maximum over columns into *out (which starts below any difference).
+// One warp per column.
+__global__ void __launch_bounds__(256) k_sweep_size(Problem P, const int* __restrict__ ex2,
+                                                    const double* __restrict__ nrm2, int* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * 8 + warp;
+  if (q >= P.m) return;
+  const int j = col_tile_of(P, q);
+  int eV = INT32_MIN, eD = INT32_MIN;
+  for (int k = lane; k <= j; k += 32) {
+    const long long idx = (long long)k * P.m + q;
+    const unsigned long long kv = abs_key(P.nrm[idx]), kd = abs_key(nrm2[idx]);
+    if (kv) eV = max(eV, P.ex[idx] + ilogb_key(kv));
+    if (kd) eD = max(eD, ex2[idx] + ilogb_key(kd));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    eV = max(eV, __shfl_xor_sync(0xffffffffu, eV, o));
+    eD = max(eD, __shfl_xor_sync(0xffffffffu, eD, o));
+  }
+  if (lane == 0 && eD != INT32_MIN) atomicMax(out, eV != INT32_MIN ? eD - eV : kSweepNoV);
+}
+
 // ------------------------------------------------------------------ host
 
 int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
-  (void)prec;
   w.tb = tb;
   w.n_max = std::max(n_max, 1);
   w.Mmax = Mmax;
@@ -485,9 +568,19 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
   if (e == cudaSuccess) e = al((void**)&w.eA, w.tiles * (size_t)tb * sizeof(int));
   if (e == cudaSuccess) e = al((void**)&w.Xs, (size_t)w.ns * w.n_max * 2 * tb * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = al((void**)&w.F, (size_t)w.n_max * sizeof(int));
+  if (e == cudaSuccess) e = al((void**)&w.d_sweep, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w.h_sweep, sizeof(int));
   if (e == cudaSuccess) e = al((void**)&w.Y2, w.tiles * (size_t)tb * tb * sizeof(double));
   if (e == cudaSuccess) e = al((void**)&w.ex2, (size_t)Mmax * w.n_max * sizeof(int));
   if (e == cudaSuccess) e = al((void**)&w.nrm2, (size_t)Mmax * w.n_max * sizeof(double));
+  w.fp8 = prec == PEVC_SPLIT_FP8X4;
+  if (w.fp8) {
+    if (e == cudaSuccess) e = al((void**)&w.As8, w.tiles * 4 * (size_t)tb * 2 * tb);
+    if (e == cudaSuccess) e = al((void**)&w.Xs8, (size_t)4 * w.n_max * 2 * tb);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_update_split<4, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               split_smem_bytes<4, true>());
+  }
   if (e == cudaSuccess) {
     cudaError_t a1 = cudaFuncSetAttribute(k_update_split<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           split_smem_bytes<3>());
@@ -525,15 +618,19 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec) {
 }
 
 void split_free(SplitWorkspace& w) {
-  void* ptrs[] = {w.As, w.eA, w.Xs, w.F, w.Y2, w.ex2, w.nrm2, w.chunk_c0_48, w.chunk_j_48, w.chunk_c0_64, w.chunk_j_64};
+  void* ptrs[] = {w.As, w.eA, w.Xs, w.F, w.d_sweep, w.Y2, w.ex2, w.nrm2, w.chunk_c0_48, w.chunk_j_48, w.chunk_c0_64, w.chunk_j_64,
+                  w.As8, w.Xs8};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* hp[] = {w.h_chunk_first48, w.h_chunk_first64, w.h_chunks};
+  void* hp[] = {w.h_chunk_first48, w.h_chunk_first64, w.h_chunks, w.h_sweep};
   for (void* p : hp)
     if (p) cudaFreeHost(p);
   w.chunk_c0_48 = w.chunk_j_48 = w.chunk_c0_64 = w.chunk_j_64 = nullptr;
   w.h_chunk_first48 = w.h_chunk_first64 = w.h_chunks = nullptr;
+  w.d_sweep = w.h_sweep = nullptr;
   w.As = nullptr;
+  w.As8 = nullptr;
+  w.Xs8 = nullptr;
   w.eA = nullptr;
   w.Xs = nullptr;
   w.F = nullptr;
@@ -543,12 +640,29 @@ void split_free(SplitWorkspace& w) {
   w.on = false;
 }
 
+constexpr int kMaxSweeps = 6;      // adaptive correction sweeps: at most
+constexpr int kSweepTarget = -30;  // stop once the predicted error is below 2^-30 of V
+
 SplitConfig split_config(int prec, bool correction) {
   SplitConfig c;
   if (prec == PEVC_SPLIT_BF16X5) {
     c.ns1 = 5;
     c.levels1 = 5;
     c.correction = false;
+  } else if (prec == PEVC_SPLIT_FP8X4) {
+    // four FP8 E4M3 slices of 4-bit digits (about 15 bits) and the levels
+    // p + q < 4 (10 products); the residual of the correction sweeps in
+    // BF16x5.  A sweep multiplies the error by about the pass's own relative
+    // error (2^-15 times the substitution's growth, measured 1/30 to 1/200),
+    // so one sweep leaves errors up to 1e-5 on pencils of order 1000: the
+    // sweeps repeat (iterative refinement) until the predicted error is
+    // below 2^kSweepTarget, at most kMaxSweeps times
+    c.ns1 = 4;
+    c.levels1 = 4;
+    c.fp8 = true;
+    c.correction = correction;
+    c.sweeps = kMaxSweeps;
+    c.adaptive = true;
   } else {
     c.ns1 = 3;
     c.levels1 = 3;
@@ -556,6 +670,11 @@ SplitConfig split_config(int prec, bool correction) {
   }
   c.ns_res = 5;
   c.levels_res = 5;
+  // tuning override: a fixed sweep count (1 to kMaxSweeps)
+  if (const char* sw = getenv("PEVC_SWEEPS")) {
+    c.sweeps = std::min(std::max(atoi(sw), 1), kMaxSweeps);
+    c.adaptive = false;
+  }
   return c;
 }
 
@@ -593,10 +712,39 @@ cudaError_t launch_split_X(const Problem& P, SplitWorkspace& w, int i, int q_beg
   return cudaGetLastError();
 }
 
+// The FP8 E4M3 slices (four 4-bit digits) of [S T] and of X'', and the
+// update from them: tcgen05 kind::f8f6f4 for tiles of order 128, else
+// mma.sync m16n8k32.
+cudaError_t launch_split_A8(const Problem& P, SplitWorkspace& w, cudaStream_t s) {
+  const long long tiles = (long long)P.M * (P.M + 1) / 2;
+  if (tiles <= 0) return cudaSuccess;
+  k_split_A<4, true><<<(unsigned)(2 * tiles), 256, 0, s>>>(P, w.As8, w.eA, 4, -1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_X8(const Problem& P, SplitWorkspace& w, int i, int q_begin, const double* Ysrc,
+                            const double* nrmsrc, cudaStream_t s) {
+  const int cols = P.m - q_begin;
+  if (cols <= 0) return cudaSuccess;
+  k_split_X<4, true><<<(unsigned)((cols + 7) / 8), 256, 0, s>>>(P, i, q_begin, Ysrc, nrmsrc, w.Xs8, w.F, 4, w.n_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_split8(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
+                                 const double* nrmX, cudaStream_t s) {
+  if (k_hi <= k_lo) return cudaSuccess;
+  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, 4, 4, true, s);
+  const int nsub = P.tb / kSplitCols;
+  dim3 grid((P.M - i) * nsub, k_hi - k_lo);
+  k_update_split<4, 4, true><<<grid, 256, split_smem_bytes<4, true>(), s>>>(P, i, k_lo, exX, nrmX, w.As8, w.eA,
+                                                                            w.Xs8, w.F, 4, w.n_max);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
                                 const double* nrmX, int ns, int levels, cudaStream_t s) {
   if (k_hi <= k_lo) return cudaSuccess;
-  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, s);
+  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, false, s);
   const int nsub = P.tb / kSplitCols;
   dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   if (ns == 5 && levels == 5)
@@ -618,10 +766,11 @@ struct SplitOps : StageOps {
   const HostStructure& hs;
   int tip_mode, ns, levels, prods;
   Profiler& prof;
+  bool fp8;   // FP8 E4M3 slices (four 4-bit digits), else BF16
   SplitOps(const Problem& P_, SplitWorkspace& w_, const HostStructure& hs_, int tip_mode_, int ns_, int levels_,
-           Profiler& prof_)
+           Profiler& prof_, bool fp8_ = false)
       : P(P_), w(w_), hs(hs_), tip_mode(tip_mode_), ns(ns_), levels(levels_), prods(products(ns_, levels_)),
-        prof(prof_) {}
+        prof(prof_), fp8(fp8_) {}
   cudaError_t tips(cudaStream_t s) override {
     prof.begin(s);
     cudaError_t e = launch_diag(P, 0, tip_mode, s);
@@ -636,7 +785,8 @@ struct SplitOps : StageOps {
   }
   cudaError_t prep(int i, cudaStream_t s) override {
     prof.begin(s);
-    cudaError_t e = launch_split_X(P, w, i, hs.cstart[i], P.Y, P.nrm, ns, s);
+    cudaError_t e = fp8 ? launch_split_X8(P, w, i, hs.cstart[i], P.Y, P.nrm, s)
+                        : launch_split_X(P, w, i, hs.cstart[i], P.Y, P.nrm, ns, s);
     prof.end(s, 2, 0.0);
     return e;
   }
@@ -644,8 +794,11 @@ struct SplitOps : StageOps {
     const double rows = hs.toff[k_hi] - hs.toff[k_lo], cols = P.m - hs.cstart[i];
     const double K = 2.0 * (hs.toff[i + 1] - hs.toff[i]);
     prof.begin(s);
-    cudaError_t e = launch_update_split(P, w, i, k_lo, k_hi, P.ex, P.nrm, ns, levels, s);
-    prof.end(s, 0, 2.0 * rows * cols * K * prods);
+    cudaError_t e = fp8 ? launch_update_split8(P, w, i, k_lo, k_hi, P.ex, P.nrm, s)
+                        : launch_update_split(P, w, i, k_lo, k_hi, P.ex, P.nrm, ns, levels, s);
+    // E4M3 products at half weight: the tensor cores' FP8 rate is twice
+    // their BF16 rate, so every pass is counted in BF16-equivalent flops
+    prof.end(s, 0, 2.0 * rows * cols * K * prods * (fp8 ? 0.5 : 1.0));
     return e;
   }
 };
@@ -692,17 +845,27 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
                 cudaStream_t s, const SchedContext& sc, Profiler& prof, cudaEvent_t ev_dag, cudaEvent_t ev_corr,
                 Arrivals* arr) {
   if (!w.on) return PEVC_ERR_UNSUPPORTED;
-  if (arr && cfg.correction) return PEVC_ERR_UNSUPPORTED;
+  if (arr && (cfg.correction || cfg.fp8)) return PEVC_ERR_UNSUPPORTED;
   if (!arr) {
     const int rc = split_prepare(w, P, hs, s);
     if (rc) return rc;
   }
-  const int ns_a = cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1;
+  // BF16 slices of [S T] for the solve passes (BF16 plans) and the residual
+  // (5 slices); FP8 slices for the solve passes of FP8 plans
+  const int ns_a = cfg.fp8 ? cfg.ns_res : (cfg.correction ? std::max(cfg.ns1, cfg.ns_res) : cfg.ns1);
   if (!arr) {
-    prof.begin(s);
-    SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
-    prof.end(s, 3, 0.0);
-    SplitOps ops(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, prof);
+    if (cfg.fp8) {
+      if (!w.fp8) return PEVC_ERR_UNSUPPORTED;
+      prof.begin(s);
+      SCK(launch_split_A8(P, w, s));
+      prof.end(s, 3, 0.0);
+    }
+    if (!cfg.fp8 || cfg.correction) {
+      prof.begin(s);
+      SCK(launch_split_A(P, w, ns_a == 5 ? 5 : 3, s));
+      prof.end(s, 3, 0.0);
+    }
+    SplitOps ops(P, w, hs, kDiagTip, cfg.ns1, cfg.levels1, prof, cfg.fp8);
     SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
   } else {
     // column block i's arrival work (pre-pass, slices, tips) is the caller's
@@ -717,9 +880,12 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
   }
   SCK(cudaEventRecord(ev_dag, s));
-  if (cfg.correction) {
-    // residual R = (S V D - T V B) of the first pass, accumulated tile row by
-    // tile row into the correction tiles as -R (including the diagonal tiles)
+  w.last_sweeps = 0;
+  int prev = 0;   // the previous sweep's size (adaptive sweeps)
+  for (int sweep = 0; cfg.correction && sweep < cfg.sweeps; ++sweep) {
+    // residual R = (S V D - T V B) of the current V (the first pass, or the
+    // previous sweep's sum), accumulated tile row by tile row into the
+    // correction tiles as -R (including the diagonal tiles)
     Problem P2 = P;
     P2.Y = w.Y2;
     P2.ex = w.ex2;
@@ -748,7 +914,7 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     }
     // the correction: same graph, zero tips, right-hand side -R
     {
-      SplitOps ops(P2, w, hs, kDiagTipCorr, cfg.ns1, cfg.levels1, prof);
+      SplitOps ops(P2, w, hs, kDiagTipCorr, cfg.ns1, cfg.levels1, prof, cfg.fp8);
       SCK(walk_dag(P.M, ops, s, sc.aux, sc.ev, sc.lookahead));
     }
     prof.begin(s);
@@ -756,6 +922,24 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     k_combine<<<grid, 256, 0, s>>>(P, w.Y2, w.ex2, w.nrm2);
     SCK(cudaGetLastError());
     prof.end(s, 3, 0.0);
+    ++w.last_sweeps;
+    if (cfg.adaptive && sweep + 1 < cfg.sweeps) {
+      // r = log2 of the largest correction relative to its column of V,
+      // about the error V had before this sweep; the error after it is about
+      // r times the contraction, estimated from the last two sweeps (the host
+      // waits for the sweep to finish to read r)
+      prof.begin(s);
+      SCK(cudaMemsetAsync(w.d_sweep, 0x80, sizeof(int), s));
+      k_sweep_size<<<(unsigned)((P.m + 7) / 8), 256, 0, s>>>(P, w.ex2, w.nrm2, w.d_sweep);
+      SCK(cudaGetLastError());
+      prof.end(s, 3, 0.0);
+      SCK(cudaMemcpyAsync(w.h_sweep, w.d_sweep, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCK(cudaStreamSynchronize(s));
+      const int r = *w.h_sweep;
+      const int predicted = sweep > 0 ? r + std::min(0, r - prev) : r;
+      if (predicted <= kSweepTarget) break;
+      prev = r;
+    }
   }
   SCK(cudaEventRecord(ev_corr, s));
   return 0;

@@ -16,6 +16,10 @@ struct SplitConfig {
   int ns1 = 3, levels1 = 3;      // slices / levels of the solve passes
   int ns_res = 5, levels_res = 5;  // slices / levels of the residual
   bool correction = true;
+  int sweeps = 1;                  // correction sweeps (iterative refinement) when correction is on:
+                                   // the count, or with `adaptive` the most
+  bool adaptive = false;           // stop once the correction has converged
+  bool fp8 = false;                // solve passes on FP8 E4M3 slices (4-bit digits)
 };
 
 struct SplitWorkspace {
@@ -25,7 +29,13 @@ struct SplitWorkspace {
   __nv_bfloat16* As = nullptr;   // [tile (k<=l)][slice][tb][2 tb]   row slices of [S_kl T_kl]
   int* eA = nullptr;             // [tile (k<=l)][tb]                row exponents
   __nv_bfloat16* Xs = nullptr;   // [slice][n_max][2 tb]             column slices of X''
+  bool fp8 = false;              // FP8 plans: the E4M3 slices below
+  unsigned char* As8 = nullptr;  // [tile (k<=l)][4][tb][2 tb]       E4M3 row slices of [S_kl T_kl]
+  unsigned char* Xs8 = nullptr;  // [4][n_max][2 tb]                 E4M3 column slices of X''
   int* F = nullptr;              // [n_max]                          column exponents of X''
+  int* d_sweep = nullptr;        // device int: size of the last correction (log2, relative to V)
+  int* h_sweep = nullptr;        // pinned host copy of it
+  int last_sweeps = 0;           // correction sweeps the last solve ran
   double* Y2 = nullptr;          // correction tiles
   int* ex2 = nullptr;
   double* nrm2 = nullptr;
@@ -38,6 +48,9 @@ struct SplitWorkspace {
   alignas(64) unsigned char tmA3[128];
   alignas(64) unsigned char tmB48[128];
   alignas(64) unsigned char tmB64[128];
+  // FP8 plans: E4M3 A boxes of 4 slices, X'' boxes of 64 columns x 4 slices
+  alignas(64) unsigned char tmA8[128];
+  alignas(64) unsigned char tmB64_8[128];
   // output column chunks of width 48 / 64 inside each column tile (per solve)
   int* chunk_c0_48 = nullptr;
   int* chunk_j_48 = nullptr;
@@ -65,7 +78,7 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
 int update_tc_setup();
 int make_tensor_maps(SplitWorkspace& w);
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                             const double* nrmX, int ns, int levels, cudaStream_t s);
+                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s);
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
 // Inputs that arrive by column blocks (pevc_solve_host): arrive(i) orders

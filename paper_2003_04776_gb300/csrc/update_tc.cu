@@ -1,18 +1,21 @@
 // update_tc.cu -- the split-precision update (Section 3, kernel 2) on the
 // fifth-generation tensor cores, fed by TMA:
 //     Y_kj <- 2^sY Y_kj - 2^sX [S_ki T_ki] X''_ij,   k in [k_lo, k_hi), j >= i,
-// with [S_ki T_ki] and X'' given as exact BF16 slices (split.cu).
+// with [S_ki T_ki] and X'' given as exact integer slices (split.cu): BF16
+// (8-bit digits) or FP8 E4M3 (4-bit digits).
 //
 // Persistent CTA (one per SM) of nineteen warps:
-//   warp 0     TMA producer: per K block of 64 one 3-D box with every slice of
+//   warp 0     TMA producer: per K block of 128 bytes (64 BF16 or 128 E4M3
+//              elements) one 3-D box with every slice of
 //              the A row tile and one with every slice of the X'' column
 //              chunk (rows of 128 bytes, 128-byte swizzle), landing directly
 //              in the K-major layout the MMA reads; a ring of shared-memory
 //              stages with full / empty mbarriers;
 //   warp 1     tensor-memory owner and MMA issuer: the slice products p x q
 //              with p + q < L of one A slice p are one tcgen05.mma (M = 128,
-//              N = (L - p) NCOL over the stacked X'' slices, K = 16, BF16 in,
-//              FP32 out) whose consecutive NCOL-column blocks are the level
+//              N = (L - p) NCOL over the stacked X'' slices, K = 32 bytes:
+//              16 BF16 (kind::f16) or 32 E4M3 (kind::f8f6f4), FP32 out)
+//              whose consecutive NCOL-column blocks are the level
 //              accumulators p .. L - 1;
 //              the level accumulators of an output tile live in one of two
 //              tensor-memory buffers;
@@ -43,7 +46,7 @@
 namespace pevc {
 
 constexpr int kTcRows = 128;                 // M of every MMA: one row tile
-constexpr int kTcK = 64;                     // K per pipeline stage: one 128-byte swizzle row
+constexpr int kTcRowBytes = 128;             // K per pipeline stage: one 128-byte swizzle row
 constexpr long long kTcWait = 4000000000LL;  // bounded waits: about 2 s of SM clock
 constexpr int kTcEpiWarps = 8;               // warps per epilogue group: two per lane quarter
 constexpr int kTcColBlock = 4;               // columns per epilogue step
@@ -55,8 +58,8 @@ constexpr int kTcRing = 4;                              // column-scale slots (o
 
 template <int NS, int NCOL>
 struct TcGeom {
-  static constexpr int a_slice = kTcRows * kTcK * 2;   // bytes of one A slice per stage (1024-multiple)
-  static constexpr int b_slice = NCOL * kTcK * 2;      // bytes of one X'' slice per stage (1024-multiple)
+  static constexpr int a_slice = kTcRows * kTcRowBytes;   // bytes of one A slice per stage (1024-multiple)
+  static constexpr int b_slice = NCOL * kTcRowBytes;      // bytes of one X'' slice per stage (1024-multiple)
   static constexpr int stage = NS * (a_slice + b_slice);
   static constexpr int stages = (225 * 1024) / stage < 4 ? (225 * 1024) / stage : 4;
   static constexpr int smem = stages * stage + 1024 + 256;   // + alignment slack, mbarriers, TMEM address
@@ -97,7 +100,7 @@ struct TmTiles {
 // Per-column data of an output tile: x = shift of the stored Y, y = shift of
 // the product (without the row exponent), z = flags (1 = column updated,
 // 2 = Y still zero), w = the column's new exponent.
-template <int L, int NCOL>
+template <int L, int NCOL, int DB>
 __device__ __forceinline__ void tile_scales(const Problem& P, int i, const TmTiles& tt, int t, const int* exX,
                                             const double* nrmX, const int* F, int col, int4* out) {
   const int k = tt.k_lo + t / tt.nchunks;
@@ -111,7 +114,7 @@ __device__ __forceinline__ void tile_scales(const Problem& P, int i, const TmTil
     const int q = c0 + col;
     on = update_scales(P, exX, nrmX, k, i, q, sY, sX, en, yz) ? 1 : 0;
     if (on && F[q] == kExpZero) on = 0;
-    sc = on ? F[q] - 14 - 8 * (L - 1) + sX : 0;
+    sc = on ? F[q] - 2 * (DB - 1) - DB * (L - 1) + sX : 0;
   }
   *out = make_int4(sY, sc, on | (yz ? 2 : 0), en);
 }
@@ -136,7 +139,7 @@ __device__ __forceinline__ unsigned key32(double x) {
   return (unsigned)((abs_key(x) + 0xffffffffull) >> 32);
 }
 
-template <int NS, int L, int NCOL>
+template <int NS, int L, int NCOL, bool FP8 = false>
 __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
                                                              const double* __restrict__ nrmX,
                                                              const int* __restrict__ eA, const int* __restrict__ F,
@@ -145,6 +148,8 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
   static_assert(NCOL % 16 == 0 && 2 * L * NCOL <= 512, "two level-accumulator buffers must fit tensor memory");
   static_assert(NS >= L && L <= 5 && L * NCOL <= 256, "one MMA per A slice covers at most N = 256 columns");
   using G = TcGeom<NS, NCOL>;
+  constexpr int DB = FP8 ? 4 : 8;                 // bits per slice digit
+  constexpr int KE = FP8 ? 128 : 64;              // K elements per stage (one 128-byte row)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // swizzle atoms need 1024-byte aligned stage bases
   unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -163,7 +168,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tb = P.tb;
-  const int nks = 2 * tb / kTcK;
+  const int nks = 2 * tb / KE;
   const int total = tt.nk * tt.nchunks;
   constexpr uint32_t kCols = 512;
   constexpr uint32_t kTx = (uint32_t)G::stage;
@@ -198,8 +203,8 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           if (!mbar_wait_cycles(&empty[s], ph ^ 1u, kTcWait)) { *fail = 1; break; }
           mbar_expect_tx(&full[s], kTx);
           unsigned char* dst = smem + s * G::stage;
-          tma_load_3d(dst, &tmA, kk * kTcK, 0, a_plane, &full[s]);
-          tma_load_3d(dst + NS * G::a_slice, &tmB, kk * kTcK, c0, 0, &full[s]);
+          tma_load_3d(dst, &tmA, kk * KE, 0, a_plane, &full[s]);
+          tma_load_3d(dst + NS * G::a_slice, &tmB, kk * KE, c0, 0, &full[s]);
           used |= 1u << s;
           last_ph = (last_ph & ~(1u << s)) | (ph << s);
           if (++s == G::stages) { s = 0; ph ^= 1u; }
@@ -232,15 +237,20 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
           // NCOL-row blocks of the stage and the level accumulators
           // consecutive NCOL-column blocks of the buffer, so A_p times the
           // stacked slices lands every product p x q in level p + q
+          // K steps of 32 bytes inside the swizzled row
 #pragma unroll
-          for (int k16 = 0; k16 < kTcK / 16; ++k16)
+          for (int k32 = 0; k32 < kTcRowBytes / 32; ++k32)
 #pragma unroll
             for (int p = 0; p < NS && p < L; ++p) {
               constexpr int kNq[5] = {NS < L ? NS : L, NS < L - 1 ? NS : L - 1, NS < L - 2 ? NS : L - 2,
                                       NS < L - 3 ? NS : L - 3, NS < L - 4 ? NS : L - 4};
-              tc_mma_bf16(acc + (uint32_t)(p * NCOL), ad + (uint64_t)((p * G::a_slice + 32 * k16) >> 4),
-                          bd + (uint64_t)((32 * k16) >> 4), idesc_bf16_f32(kTcRows, kNq[p] * NCOL),
-                          (kk | k16 | p) ? 1u : 0u);
+              const uint64_t a_p = ad + (uint64_t)((p * G::a_slice + 32 * k32) >> 4);
+              const uint64_t b_k = bd + (uint64_t)((32 * k32) >> 4);
+              const uint32_t accum = (kk | k32 | p) ? 1u : 0u;
+              if constexpr (FP8)
+                tc_mma_e4m3(acc + (uint32_t)(p * NCOL), a_p, b_k, idesc_e4m3_f32(kTcRows, kNq[p] * NCOL), accum);
+              else
+                tc_mma_bf16(acc + (uint32_t)(p * NCOL), a_p, b_k, idesc_bf16_f32(kTcRows, kNq[p] * NCOL), accum);
             }
           tc_commit(&empty[s]);             // frees the stage once these MMAs completed
           if (++s == G::stages) { s = 0; ph ^= 1u; }
@@ -268,7 +278,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
         *fail = 1;
         break;
       }
-      for (int c = lane; c < NCOL; c += 32) tile_scales<L, NCOL>(P, i, tt, t, exX, nrmX, F, c, &s_col[rs][c]);
+      for (int c = lane; c < NCOL; c += 32) tile_scales<L, NCOL, DB>(P, i, tt, t, exX, nrmX, F, c, &s_col[rs][c]);
       if (lane == 0) {
         const double* yp;
         uint32_t yb;
@@ -363,7 +373,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             long long tv = 0;
 #pragma unroll
             for (int s = 0; s < L; ++s)
-              tv += (long long)__float2int_rn(__uint_as_float(lv[s][u])) * (1ll << (8 * (L - 1 - s)));
+              tv += (long long)__float2int_rn(__uint_as_float(lv[s][u])) * (1ll << (DB * (L - 1 - s)));
             bool sl = false;
             // half the elements convert on the FP64 pipe, half by integer
             // assembly of the binary64 fields (the same rounded value), so
@@ -382,7 +392,7 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
               const int4 cd = scol[cb + u];
               long long tv = 0;
 #pragma unroll
-              for (int s = 0; s < L; ++s) tv = (tv << 8) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
+              for (int s = 0; s < L; ++s) tv = (tv << DB) + (long long)__float2int_rn(__uint_as_float(lv[s][u]));
               const double prod = pow2_scale((double)tv, erow + cd.y);
               const double yold = (cd.z & 2) ? 0.0 : pow2_scale(yv[u], cd.x);
               if (act[u]) ynew[u] = yold - prod;
@@ -453,13 +463,18 @@ int update_tc_setup() {
                                        TcGeom<5, 48>::smem);
   cudaError_t b = cudaFuncSetAttribute(k_update_tc<3, 3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TcGeom<3, 64>::smem);
-  return (a == cudaSuccess && b == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
+  cudaError_t c = cudaFuncSetAttribute(k_update_tc<4, 4, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcGeom<4, 64>::smem);
+  return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
 }
 
-// Tensor maps over the K-contiguous slice buffers (one K block of 64 = one
-// 128-byte swizzle row per box row, every slice of the operand in one box):
+// Tensor maps over the K-contiguous slice buffers (one K block of 128 bytes =
+// one 128-byte swizzle row per box row, every slice of the operand in one box):
 //   A: [tile * ns + slice][row][2 tb]  -> dims {2tb, tb, tiles*ns}, box {64, 128, NS}
 //   B: [slice][column][2 tb]           -> dims {2tb, n_max, ns},    box {64, NCOL, NS}
+// and, for FP8 plans, over the E4M3 slices (four, bytes):
+//   A: [tile * 4 + slice][row][2 tb]   -> dims {2tb, tb, tiles*4},  box {128, 128, 4}
+//   B: [slice][column][2 tb]           -> dims {2tb, n_max, 4},     box {128, 64, 4}
 int make_tensor_maps(SplitWorkspace& w) {
   w.tc_ok = false;
   EncodeTiledFn enc = encode_fn();
@@ -471,7 +486,7 @@ int make_tensor_maps(SplitWorkspace& w) {
     const cuuint32_t nsl = v == 0 ? 5 : 3;
     cuuint64_t dims[3] = {K2, tb, (cuuint64_t)(w.tiles * w.ns)};
     cuuint64_t strides[2] = {K2 * 2, tb * K2 * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kTcK, (cuuint32_t)kTcRows, nsl};
+    cuuint32_t box[3] = {(cuuint32_t)(kTcRowBytes / 2), (cuuint32_t)kTcRows, nsl};
     if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmA : w.tmA3), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.As, dims,
             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -481,10 +496,26 @@ int make_tensor_maps(SplitWorkspace& w) {
     const cuuint32_t ncol = v == 0 ? 48 : 64, nsl = v == 0 ? 5 : 3;
     cuuint64_t dims[3] = {K2, (cuuint64_t)w.n_max, (cuuint64_t)w.ns};
     cuuint64_t strides[2] = {K2 * 2, (cuuint64_t)w.n_max * K2 * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kTcK, ncol, nsl};
+    cuuint32_t box[3] = {(cuuint32_t)(kTcRowBytes / 2), ncol, nsl};
     if (enc(reinterpret_cast<CUtensorMap*>(v == 0 ? w.tmB48 : w.tmB64), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, w.Xs,
             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PEVC_ERR_CUDA;
+  }
+  if (w.fp8) {
+    cuuint64_t adims[3] = {K2, tb, (cuuint64_t)(w.tiles * 4)};
+    cuuint64_t astrides[2] = {K2, tb * K2};
+    cuuint32_t abox[3] = {(cuuint32_t)kTcRowBytes, (cuuint32_t)kTcRows, 4};
+    if (enc(reinterpret_cast<CUtensorMap*>(w.tmA8), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, w.As8, adims, astrides, abox,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PEVC_ERR_CUDA;
+    cuuint64_t bdims[3] = {K2, (cuuint64_t)w.n_max, 4};
+    cuuint64_t bstrides[2] = {K2, (cuuint64_t)w.n_max * K2};
+    cuuint32_t bbox[3] = {(cuuint32_t)kTcRowBytes, 64, 4};
+    if (enc(reinterpret_cast<CUtensorMap*>(w.tmB64_8), CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, w.Xs8, bdims, bstrides,
+            bbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PEVC_ERR_CUDA;
   }
   w.tc_ok = true;
@@ -492,9 +523,9 @@ int make_tensor_maps(SplitWorkspace& w) {
 }
 
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                             const double* nrmX, int ns, int levels, cudaStream_t s) {
+                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s) {
   if (k_hi <= k_lo) return cudaSuccess;
-  const bool five = (ns == 5 && levels == 5);
+  const bool five = !fp8 && ns == 5 && levels == 5;
   const int* first = five ? w.h_chunk_first48 : w.h_chunk_first64;
   TmTiles tt;
   tt.chunk_c0 = five ? w.chunk_c0_48 : w.chunk_c0_64;
@@ -506,7 +537,12 @@ cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, i
   const int total = tt.nk * tt.nchunks;
   if (total <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)(total < w.nsm ? total : w.nsm);
-  if (five) {
+  if (fp8) {
+    const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA8);
+    const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB64_8);
+    k_update_tc<4, 4, 64, true><<<grid, kTcThreads, TcGeom<4, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, 4, mA,
+                                                                             mB);
+  } else if (five) {
     const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB48);
     k_update_tc<5, 5, 48><<<grid, kTcThreads, TcGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);

@@ -7,7 +7,7 @@ the split-precision path with its mma.sync update, post-pass, left flips) and
 the complex-pencil path are preprocessed from the library's CUDA sources into
 host C++ (launch syntax into emu::launch calls, dynamic shared memory onto the
 emulated block's buffer, the L2 prefetch hint dropped, the PTX of the FP64 and
-BF16 mma.sync, ldmatrix and cp.async onto their models) and compiled with g++
+BF16 and E4M3 mma.sync, ldmatrix and cp.async onto their models) and compiled with g++
 against the cuda_runtime.h stand-in beside this file.  The tcgen05 update and
 the cuBLAS pieces are stubbed out (without tensor maps the split path takes
 its mma.sync update); the back-transform normalisation kernels and the
@@ -40,6 +40,8 @@ SPLIT_HELPERS = {
                          "{ emu::ldmatrix_x4(r, smem); }",
     "void mma_bf16(": "__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, "
                       "unsigned b1) { emu::mma_bf16(c, a, b0, b1); }",
+    "void mma_fp8(": "__device__ __forceinline__ void mma_fp8(float (&c)[4], const unsigned (&a)[4], unsigned b0, "
+                     "unsigned b1) { emu::mma_e4m3(c, a, b0, b1); }",
 }
 
 
@@ -88,7 +90,7 @@ namespace pevc {{
 // path takes its mma.sync update at every tile order
 int update_tc_setup() {{ return 0; }}
 int make_tensor_maps(SplitWorkspace& w) {{ w.tc_ok = false; return 0; }}
-cudaError_t launch_update_tc(const Problem&, const SplitWorkspace&, int, int, int, const int*, const double*, int, int,
+cudaError_t launch_update_tc(const Problem&, const SplitWorkspace&, int, int, int, const int*, const double*, int, int, bool,
                              cudaStream_t) {{ return 1; }}
 int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
 void bt_handle_destroy(void*) {{}}

@@ -178,6 +178,7 @@ inline double __hiloint2double(int hi, int lo) {
   return __longlong_as_double((long long)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo));
 }
 inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
+inline int __clz(int x) { return x ? __builtin_clz((unsigned)x) : 32; }
 template <class T>
 inline T max(T a, T b) { return a > b ? a : b; }
 template <class T>
@@ -272,6 +273,7 @@ inline long long clock64() {
 
 // ---- the split path's PTX: cp.async, ldmatrix.x4 and mma.sync m16n8k16 bf16 ----
 struct uint4 { unsigned x, y, z, w; };
+struct uint2 { unsigned x, y; };
 inline size_t __cvta_generic_to_shared(const void* p) { return (size_t)p; }
 inline int __float2int_rn(float f) { return (int)lrintf(f); }
 namespace emu {
@@ -327,6 +329,47 @@ inline void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigne
     const int row = g + 8 * (e >> 1), col = 2 * t + (e & 1);
     float acc = c[e];
     for (int k = 0; k < 16; ++k) acc += a_el(row, k) * b_el(k, col);
+    c[e] = acc;
+  }
+}
+// E4M3 byte to float: sign, 4-bit exponent (bias 7; 0 = subnormal), 3-bit
+// mantissa (exponent 15 with mantissa 7 is NaN, never produced by the slices).
+inline float e4m3_value(unsigned b) {
+  const int sgn = (b >> 7) & 1, E = (b >> 3) & 15, m = b & 7;
+  const float mag = E ? std::ldexp(1.0f + m / 8.0f, E - 7) : std::ldexp(m / 8.0f, -6);
+  return sgn ? -mag : mag;
+}
+// mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 (g = lane / 4, t = lane % 4),
+// four bytes per register, element k of a register at byte k % 4:
+//   A regs (row, k quad): {g, 4t}, {g+8, 4t}, {g, 4t+16}, {g+8, 4t+16};
+//   B regs (k quad, col): {4t, g}, {4t+16, g};  C as m16n8k16.
+inline void mma_e4m3(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  unsigned A[32][4], B[32][2];
+  for (int q = 0; q < 4; ++q) {
+    warp->slot[lane] = a[q];
+    warp->bar.arrive_and_wait();
+    for (int l = 0; l < 32; ++l) A[l][q] = (unsigned)warp->slot[l];
+    warp->bar.arrive_and_wait();
+  }
+  for (int q = 0; q < 2; ++q) {
+    warp->slot[lane] = q ? b1 : b0;
+    warp->bar.arrive_and_wait();
+    for (int l = 0; l < 32; ++l) B[l][q] = (unsigned)warp->slot[l];
+    warp->bar.arrive_and_wait();
+  }
+  auto a_el = [&](int row, int k) {
+    const int l = (row % 8) * 4 + (k % 16) / 4, q = row / 8 + 2 * (k / 16);
+    return e4m3_value((A[l][q] >> (8 * (k % 4))) & 0xffu);
+  };
+  auto b_el = [&](int k, int col) {
+    const int l = col * 4 + (k % 16) / 4, q = k / 16;
+    return e4m3_value((B[l][q] >> (8 * (k % 4))) & 0xffu);
+  };
+  const int g = lane >> 2, t = lane & 3;
+  for (int e = 0; e < 4; ++e) {
+    const int row = g + 8 * (e >> 1), col = 2 * t + (e & 1);
+    float acc = c[e];
+    for (int k = 0; k < 32; ++k) acc += a_el(row, k) * b_el(k, col);
     c[e] = acc;
   }
 }

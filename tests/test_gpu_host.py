@@ -65,6 +65,7 @@ def _host_solve(pevc, p, prec, tile, sel=None, pinned=True):
     ("bf16x5", 128, 1030, False, 1, True),
     ("bf16x5", 128, 2000, True, 1, True),
     ("bf16x5", 128, 513, False, 4, False),
+    ("fp8x4", 128, 700, False, 1, True),       # the correction sweep: copied whole, then solved
 ])
 def test_host_solve_matches_device_solve_bitwise(pevc_lib, prec, tile, n, stress, every, pinned):
     p = pencilgen.make_pencil(n, 9900 + n + tile, stress=stress)

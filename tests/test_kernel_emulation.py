@@ -303,14 +303,17 @@ def test_emulated_real_left_static_and_batched_entry_points(emu):
         _check_real(q, Vq[:, :mq], sq[:mq])
 
 
-@pytest.mark.parametrize("prec,n", [(3, 45), (1, 36)])    # PEVC_SPLIT_BF16X5, PEVC_SPLIT_BF16X3 (+ correction)
-def test_emulated_split_solve_matches_oracle(emu, prec, n):
-    """The split-precision path with its mma.sync update (BF16 slices, FP32
-    level accumulators, FP64 recombination), the slicing kernels it shares with
-    the tcgen05 update, and the correction sweep of BF16x3."""
+# PEVC_SPLIT_BF16X5; PEVC_SPLIT_BF16X3 and PEVC_SPLIT_FP8X4 (+ correction);
+# PEVC_SPLIT_FP8X4 with PEVC_NO_CORRECTION (about 15 bits)
+@pytest.mark.parametrize("prec,n,flags,tol", [(3, 45, 0, 1e-8), (1, 36, 0, 1e-8), (2, 40, 0, 1e-8), (2, 40, 2, 1e-5)])
+def test_emulated_split_solve_matches_oracle(emu, prec, n, flags, tol):
+    """The split-precision path with its mma.sync update (BF16 or E4M3 slices,
+    FP32 level accumulators, FP64 recombination), the slicing kernels it
+    shares with the tcgen05 update, and the correction sweep of BF16x3 and
+    FP8x4 (residual in BF16x5)."""
     p = pencilgen.make_pencil(n, 9800 + n)
     h = vp()
-    assert emu.pevc_plan(ctypes.byref(h), n, 1, prec, 32, 0, None) == 0
+    assert emu.pevc_plan(ctypes.byref(h), n, 1, prec, 32, flags, None) == 0
     S, T = np.asfortranarray(p.S), np.asfortranarray(p.T)
     V = np.zeros((n, n), order="F")
     sc = np.zeros(n, dtype=np.int32)
@@ -324,7 +327,8 @@ def test_emulated_split_solve_matches_oracle(emu, prec, n):
     kinds, pos = check.column_kinds(blk)
     err, _ = check.compare_normalised(Vo, V[:, :m.value], kinds)
     res = check.residuals(p.S, p.T, V[:, :m.value], kinds, pos, a, b, beta).max() / (n * check.U)
-    assert err <= 1e-8 and res <= 100.0
+    print(f"emulated split prec {prec} flags {flags}: err {err:.3e} resid/(nu) {res:.3e}")
+    assert err <= tol and (res <= 100.0 or flags)
 
 
 def test_epilogue_and_protection_helpers(emu):
