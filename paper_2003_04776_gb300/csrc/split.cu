@@ -527,31 +527,101 @@ __global__ void __launch_bounds__(256) k_combine(Problem P, const double* __rest
   }
 }
 
-constexpr int kSweepNoV = 1 << 20;   // a correction in a column whose V is zero
+constexpr int kSweepBig = 1 << 20;   // a sweep that changed a column beyond measure
 
-// Convergence of the correction sweeps: for every column, the largest power
-// of two of the correction just added (its tiles' maxima at their exponents)
-// against the largest of V, as the difference of the two binary exponents;
-// the maximum over columns into *out (which starts below any difference).
-// One warp per column.
-__global__ void __launch_bounds__(256) k_sweep_size(Problem P, const int* __restrict__ ex2,
-                                                    const double* __restrict__ nrm2, int* __restrict__ out) {
+// Convergence of the correction sweeps: how much the sweep just made
+// (V <- V + delta) changed each eigenvector as returned, i.e. normalised by
+// its largest entry V(m).  To first order that change is
+//     (delta - g V) / V(m),   g = delta(m) / V(m),
+// so the part of delta along V itself -- large when an error made near the
+// bottom of a column grew upward with the eigenvector's own growth -- does
+// not count, as it does not change the normalised vector.  A pair's complex
+// vector is measured as one (complex g).  Values are taken relative to 2^E,
+// E the binary exponent of the column's largest tile maximum; the maximum
+// over columns of floor(log2 max_i |change(i)|) into *out (which starts below
+// any value).  One warp per real eigenvector or pair.
+__global__ void __launch_bounds__(256) k_sweep_change(Problem P, const double* __restrict__ Y2,
+                                                      const int* __restrict__ ex2, int* __restrict__ out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.x * 8 + warp;
   if (q >= P.m) return;
+  const int kd = P.kind[q];
+  if (kd == 2) return;                       // the pair's first column measures both
+  const bool pr = kd == 1;
   const int j = col_tile_of(P, q);
-  int eV = INT32_MIN, eD = INT32_MIN;
+  const int lq = q - P.cstart[j], tb = P.tb, m = P.m;
+  // the tile with the largest entry (per-tile maxima at their exponents)
+  int E = INT32_MIN, ks = 0;
   for (int k = lane; k <= j; k += 32) {
-    const long long idx = (long long)k * P.m + q;
-    const unsigned long long kv = abs_key(P.nrm[idx]), kd = abs_key(nrm2[idx]);
-    if (kv) eV = max(eV, P.ex[idx] + ilogb_key(kv));
-    if (kd) eD = max(eD, ex2[idx] + ilogb_key(kd));
+    const long long idx = (long long)k * m + q;
+    const unsigned long long k0 = abs_key(P.nrm[idx]), k1 = pr ? abs_key(P.nrm[idx + 1]) : 0ull;
+    int e = INT32_MIN;
+    if (k0) e = P.ex[idx] + ilogb_key(k0);
+    if (k1) e = max(e, P.ex[idx + 1] + ilogb_key(k1));
+    if (e > E) { E = e; ks = k; }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    eV = max(eV, __shfl_xor_sync(0xffffffffu, eV, o));
-    eD = max(eD, __shfl_xor_sync(0xffffffffu, eD, o));
+    const int e2 = __shfl_xor_sync(0xffffffffu, E, o), k2 = __shfl_xor_sync(0xffffffffu, ks, o);
+    if (e2 > E || (e2 == E && k2 < ks)) { E = e2; ks = k2; }
   }
-  if (lane == 0 && eD != INT32_MIN) atomicMax(out, eV != INT32_MIN ? eD - eV : kSweepNoV);
+  if (E == INT32_MIN) return;                // V is zero: nothing to measure
+  // V and delta of column c at tile k, row r, relative to 2^E
+  auto vat = [&](int c, int k, int r) {
+    return pow2_scale(tile_ptr(P, k, j)[(size_t)(lq + c) * tb + r], P.ex[(long long)k * m + q + c] - E);
+  };
+  auto dat = [&](int c, int k, int r) {
+    const double* Dt = Y2 + tri_index(k, j) * (long long)tb * tb;
+    return pow2_scale(Dt[(size_t)(lq + c) * tb + r], ex2[(long long)k * m + q + c] - E);
+  };
+  // the largest entry of that tile (modulus bound |Re| + |Im| for a pair)
+  const int hs = P.toff[ks + 1] - P.toff[ks];
+  unsigned long long best = 0;
+  int rm = 0;
+  for (int r = lane; r < hs; r += 32) {
+    const double x = pr ? cmag(vat(0, ks, r), vat(1, ks, r)) : fabs(vat(0, ks, r));
+    const unsigned long long kx = abs_key(x);
+    if (kx > best) { best = kx; rm = r; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int r2 = __shfl_xor_sync(0xffffffffu, rm, o);
+    if (b2 > best || (b2 == best && r2 < rm)) { best = b2; rm = r2; }
+  }
+  if (!best) return;
+  // g = delta(m) / V(m)
+  double gr, gi = 0.0;
+  double vmr = vat(0, ks, rm), vmi = pr ? vat(1, ks, rm) : 0.0;
+  const double dmr = dat(0, ks, rm), dmi = pr ? dat(1, ks, rm) : 0.0;
+  if (!pr) {
+    gr = dmr / vmr;
+  } else {
+    const double den = vmr * vmr + vmi * vmi;
+    gr = (dmr * vmr + dmi * vmi) / den;
+    gi = (dmi * vmr - dmr * vmi) / den;
+  }
+  // max_i |delta(i) - g V(i)| over the column's tiles, relative to |V(m)|
+  double mx = 0.0;
+  for (int k = 0; k <= j; ++k) {
+    const int h = P.toff[k + 1] - P.toff[k];
+    for (int r = lane; r < h; r += 32) {
+      const double vr = vat(0, k, r), dr = dat(0, k, r);
+      double c;
+      if (!pr) {
+        c = fabs(fma(-gr, vr, dr));
+      } else {
+        const double vi = vat(1, k, r), di = dat(1, k, r);
+        c = cmag(dr - (gr * vr - gi * vi), di - (gr * vi + gi * vr));
+      }
+      mx = fmax(mx, c);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.0) {
+    const double vm = pr ? cmag(vmr, vmi) : fabs(vmr);
+    const double rel = mx / vm;
+    const unsigned long long kr = abs_key(rel);
+    atomicMax(out, (rel < 0x1p1000) ? ilogb_key(kr) : kSweepBig);   // NaN or huge: count as large
+  }
 }
 
 // ------------------------------------------------------------------ host
@@ -924,13 +994,13 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
     prof.end(s, 3, 0.0);
     ++w.last_sweeps;
     if (cfg.adaptive && sweep + 1 < cfg.sweeps) {
-      // r = log2 of the largest correction relative to its column of V,
-      // about the error V had before this sweep; the error after it is about
-      // r times the contraction, estimated from the last two sweeps (the host
-      // waits for the sweep to finish to read r)
+      // r = log2 of the largest change this sweep made to a normalised
+      // eigenvector, about the error it had before the sweep; the error
+      // after it is about r times the contraction, estimated from the last
+      // two sweeps (the host waits for the sweep to finish to read r)
       prof.begin(s);
       SCK(cudaMemsetAsync(w.d_sweep, 0x80, sizeof(int), s));
-      k_sweep_size<<<(unsigned)((P.m + 7) / 8), 256, 0, s>>>(P, w.ex2, w.nrm2, w.d_sweep);
+      k_sweep_change<<<(unsigned)((P.m + 7) / 8), 256, 0, s>>>(P, w.Y2, w.ex2, w.d_sweep);
       SCK(cudaGetLastError());
       prof.end(s, 3, 0.0);
       SCK(cudaMemcpyAsync(w.h_sweep, w.d_sweep, sizeof(int), cudaMemcpyDeviceToHost, s));
