@@ -26,7 +26,7 @@ def _bad_pencil(n=20, seed=7):
     return S, p.T.copy()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x5", 1e-8)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x5", 1e-8), ("fp8x4", 1e-8)])
 def test_batched_matches_single_solves_and_oracle(pevc_lib, prec, tol):
     orders = [1, 7, 40, 100, 0, 257, 300, 129, 64, 513, 33, 200]
     pencils, selects, metas = [], [], []

@@ -37,7 +37,7 @@ def _compare(p, U, select, tol):
 
 @pytest.mark.parametrize("prec,n,tile,tol", [("fp64", 1, 32, 1e-10), ("fp64", 5, 32, 1e-10),
                                              ("fp64", 300, 32, 1e-10), ("fp64", 257, 64, 1e-10),
-                                             ("bf16x5", 700, 128, 1e-8)])
+                                             ("bf16x5", 700, 128, 1e-8), ("fp8x4", 500, 96, 1e-8)])
 def test_left_matches_oracle(pevc_lib, prec, n, tile, tol):
     p = pencilgen.make_pencil(n, 6100 + n)
     plan = pevc_lib.Plan(n, prec=prec, tile=tile)

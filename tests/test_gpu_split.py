@@ -57,7 +57,8 @@ def _errors(p, V, select=None):
 
 
 @pytest.mark.parametrize("prec", ["bf16x5", "bf16x3", "fp8x4"])
-@pytest.mark.parametrize("n,tile", [(1, 32), (5, 32), (64, 32), (100, 32), (257, 32), (300, 64), (513, 128)])
+@pytest.mark.parametrize("n,tile", [(1, 32), (5, 32), (64, 32), (100, 32), (257, 32), (300, 64), (500, 96),
+                                    (513, 128)])
 def test_split_matches_oracle(pevc_lib, prec, n, tile):
     p = pencilgen.make_pencil(n, 2000 + n + tile)
     V, sc, st, stats = _run(pevc_lib, p.S, p.T, prec, tile=tile)
