@@ -61,7 +61,7 @@ typedef struct pevc_plan_s *pevc_plan_t;
 
 /* Plan / solve flags. */
 #define PEVC_NO_NORMALISE 1u   /* return consolidated columns and exponents      */
-#define PEVC_NO_CORRECTION 2u  /* split precisions: skip the correction sweep    */
+#define PEVC_NO_CORRECTION 2u  /* split precisions: skip the correction sweeps   */
 #define PEVC_BT_EMULATED 4u    /* pevc_backtransform: FP64 GEMM by fixed-point emulation */
 #define PEVC_STAGE_WALK 8u     /* FP64 plans: walk the task graph stage by stage from the host
                                   instead of the device-side scheduler                    */
