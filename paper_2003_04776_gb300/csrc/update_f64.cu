@@ -133,6 +133,15 @@ __global__ void __launch_bounds__(256) k_update_f64(Problem P, int i_stage, int 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kUpdK; kk += 4) {
+      // mode 1: [S_kk T_kk] is quasi-triangular (S_rc = 0 for c < r - 1,
+      // T_rc = 0 for c < r), so a K step whose four columns all lie left of
+      // the warp's first row (32 wr) minus one multiplies zeros only: the
+      // warp skips it (warp-uniform; the same sums, without the zero terms)
+      if (mode == 1) {
+        const int kap = kb + kk + 3;                          // the step's last K index
+        const int c = kap < hi ? kap : kap - hi;              // its local column in S or T
+        if (kap < K && (kap < hi ? c < 32 * wr - 1 : (kb + kk >= hi && c < 32 * wr - 1))) continue;
+      }
       double af[4], bf[2];
 #pragma unroll
       for (int a = 0; a < 4; ++a) af[a] = As[kk + t4][32 * wr + 8 * a + g];
