@@ -52,7 +52,7 @@ TRAFFIC = {
                "sha256_16": "48a0fb1c5854b9b1"},
     "k_update_tc": {"bytes_per_launch": 9.570e8, "n": 20000, "prec": "bf16x5",
                     "sources": ("update_tc.cu", "tc.cuh", "common.cuh", "split.cuh"),
-                    "sha256_16": "c71908596b5568aa"},
+                    "sha256_16": "66320edc2040f95c"},
 }
 
 

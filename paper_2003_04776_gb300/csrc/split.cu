@@ -800,10 +800,12 @@ cudaError_t launch_split_X8(const Problem& P, SplitWorkspace& w, int i, int q_be
   return cudaGetLastError();
 }
 
+// ftz: a correction sweep's update (products below the normal range flushed,
+// see update_tc.cu)
 cudaError_t launch_update_split8(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                                 const double* nrmX, cudaStream_t s) {
+                                 const double* nrmX, cudaStream_t s, bool ftz = false) {
   if (k_hi <= k_lo) return cudaSuccess;
-  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, 4, 4, true, s);
+  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, 4, 4, true, s, ftz);
   const int nsub = P.tb / kSplitCols;
   dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   k_update_split<4, 4, true><<<grid, 256, split_smem_bytes<4, true>(), s>>>(P, i, k_lo, exX, nrmX, w.As8, w.eA,
@@ -812,9 +814,9 @@ cudaError_t launch_update_split8(const Problem& P, SplitWorkspace& w, int i, int
 }
 
 cudaError_t launch_update_split(const Problem& P, SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                                const double* nrmX, int ns, int levels, cudaStream_t s) {
+                                const double* nrmX, int ns, int levels, cudaStream_t s, bool ftz = false) {
   if (k_hi <= k_lo) return cudaSuccess;
-  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, false, s);
+  if (w.use_tc && w.tc_ok) return launch_update_tc(P, w, i, k_lo, k_hi, exX, nrmX, ns, levels, false, s, ftz);
   const int nsub = P.tb / kSplitCols;
   dim3 grid((P.M - i) * nsub, k_hi - k_lo);
   if (ns == 5 && levels == 5)
@@ -864,8 +866,9 @@ struct SplitOps : StageOps {
     const double rows = hs.toff[k_hi] - hs.toff[k_lo], cols = P.m - hs.cstart[i];
     const double K = 2.0 * (hs.toff[i + 1] - hs.toff[i]);
     prof.begin(s);
-    cudaError_t e = fp8 ? launch_update_split8(P, w, i, k_lo, k_hi, P.ex, P.nrm, s)
-                        : launch_update_split(P, w, i, k_lo, k_hi, P.ex, P.nrm, ns, levels, s);
+    const bool ftz = tip_mode == kDiagTipCorr;   // the correction pass of a sweep
+    cudaError_t e = fp8 ? launch_update_split8(P, w, i, k_lo, k_hi, P.ex, P.nrm, s, ftz)
+                        : launch_update_split(P, w, i, k_lo, k_hi, P.ex, P.nrm, ns, levels, s, ftz);
     // E4M3 products at half weight: the tensor cores' FP8 rate is twice
     // their BF16 rate, so every pass is counted in BF16-equivalent flops
     prof.end(s, 0, 2.0 * rows * cols * K * prods * (fp8 ? 0.5 : 1.0));
@@ -979,7 +982,7 @@ int split_solve(SplitWorkspace& w, const Problem& P, const HostStructure& hs, co
       prof.end(s, 2, 0.0);
       const double rows = hs.toff[l], cols = P.m - hs.cstart[l], K = 2.0 * (hs.toff[l + 1] - hs.toff[l]);
       prof.begin(s);
-      SCK(launch_update_split(P2, w, l, 0, l, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s));
+      SCK(launch_update_split(P2, w, l, 0, l, P.ex, P.nrm, cfg.ns_res, cfg.levels_res, s, true));
       prof.end(s, 0, 2.0 * rows * cols * K * prods);
     }
     // the correction: same graph, zero tips, right-hand side -R

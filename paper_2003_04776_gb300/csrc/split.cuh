@@ -78,7 +78,7 @@ int split_alloc(SplitWorkspace& w, int n_max, int tb, int Mmax, int prec);
 int update_tc_setup();
 int make_tensor_maps(SplitWorkspace& w);
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s);
+                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s, bool ftz = false);
 void split_free(SplitWorkspace& w);
 SplitConfig split_config(int prec, bool correction);
 // Inputs that arrive by column blocks (pevc_solve_host): arrive(i) orders

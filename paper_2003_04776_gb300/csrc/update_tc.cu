@@ -132,6 +132,38 @@ __device__ __forceinline__ void tile_y_range(const Problem& P, const TmTiles& tt
   bytes = (uint32_t)(nc * P.tb * sizeof(double));
 }
 
+// The scaled product t * 2^e of an update, as i64_scaled_fast and
+// pow2_scale_fast form it, except that a product whose stored magnitude falls
+// below the normal range is flushed to a zero of its sign instead of sending
+// the block to the exact path.  Such products arise in the correction pass,
+// where a tile Y2(k) holds the residual of row k at the scale of that row's
+// own terms, while the corrections of rows i far below k are smaller by the
+// eigenvector's growth over i - k tiles; below 2^-1022 of the tile's scale
+// they cannot change a stored value of the tile.  Overflow still takes the
+// exact path.  Used by the correction sweeps' updates (template flag FTZ); the
+// first pass keeps the plain fast paths (its products never underflow: every
+// update into a tile is at least as large as the tile's stored values).
+__device__ __forceinline__ double i64_scaled_ftz(long long t, int e, bool& slow) {
+  const unsigned long long sgn = (unsigned long long)t & (1ull << 63);
+  const unsigned long long mag = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)(mag | 1ull));
+  const int E = 1086 - lz + e;                 // before rounding; rounding adds at most one
+  bool sl = false;
+  const double r = i64_scaled_fast(t, e, sl);
+  slow |= sl & (E > 0);
+  return (mag != 0 && E <= 0) ? __longlong_as_double((long long)sgn) : r;
+}
+// y * 2^s for y = (double)t (a normal number or zero), flushed like i64_scaled_ftz
+__device__ __forceinline__ double pow2_scale_ftz(double y, int sh, bool& slow) {
+  const int hi = __double2hiint(y);
+  const int E = (hi >> 20) & 0x7ff;
+  const bool under = E != 0 && E + sh <= 0;
+  bool sl = false;
+  const double r = pow2_scale_fast(y, sh, sl);
+  slow |= sl & !under;
+  return under ? __hiloint2double(hi & (int)0x80000000, 0) : r;
+}
+
 // Upper 32 bits of |x|'s bit pattern, rounded up: non-negative doubles order
 // like these keys, and the double they stand for is an upper bound of |x|
 // (within 2^-20 relative), which is all the norm bookkeeping needs.
@@ -139,7 +171,7 @@ __device__ __forceinline__ unsigned key32(double x) {
   return (unsigned)((abs_key(x) + 0xffffffffull) >> 32);
 }
 
-template <int NS, int L, int NCOL, bool FP8 = false>
+template <int NS, int L, int NCOL, bool FP8 = false, bool FTZ = false>
 __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const int* __restrict__ exX,
                                                              const double* __restrict__ nrmX,
                                                              const int* __restrict__ eA, const int* __restrict__ F,
@@ -378,8 +410,11 @@ __global__ void __maxnreg__(96) k_update_tc(Problem P, int i, TmTiles tt, const 
             // half the elements convert on the FP64 pipe, half by integer
             // assembly of the binary64 fields (the same rounded value), so
             // that neither pipe alone bounds the block
-            const double prod = (u & 2) ? i64_scaled_fast(tv, erow + cd.y, sl)
-                                        : pow2_scale_fast((double)tv, erow + cd.y, sl);
+            double prod;
+            if constexpr (FTZ)
+              prod = (u & 2) ? i64_scaled_ftz(tv, erow + cd.y, sl) : pow2_scale_ftz((double)tv, erow + cd.y, sl);
+            else
+              prod = (u & 2) ? i64_scaled_fast(tv, erow + cd.y, sl) : pow2_scale_fast((double)tv, erow + cd.y, sl);
             double yold = yv[u];
             if (shy) yold = pow2_scale_fast(yv[u], cd.x, sl);
             if (cd.z & 2) yold = 0.0;
@@ -465,7 +500,17 @@ int update_tc_setup() {
                                        TcGeom<3, 64>::smem);
   cudaError_t c = cudaFuncSetAttribute(k_update_tc<4, 4, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TcGeom<4, 64>::smem);
-  return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess && encode_fn()) ? 0 : PEVC_ERR_CUDA;
+  // the correction sweeps' instantiations (underflowing products flushed)
+  cudaError_t d = cudaFuncSetAttribute(k_update_tc<5, 5, 48, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcGeom<5, 48>::smem);
+  cudaError_t e = cudaFuncSetAttribute(k_update_tc<3, 3, 64, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcGeom<3, 64>::smem);
+  cudaError_t f = cudaFuncSetAttribute(k_update_tc<4, 4, 64, true, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcGeom<4, 64>::smem);
+  return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess && d == cudaSuccess && e == cudaSuccess &&
+          f == cudaSuccess && encode_fn())
+             ? 0
+             : PEVC_ERR_CUDA;
 }
 
 // Tensor maps over the K-contiguous slice buffers (one K block of 128 bytes =
@@ -523,7 +568,7 @@ int make_tensor_maps(SplitWorkspace& w) {
 }
 
 cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, int k_lo, int k_hi, const int* exX,
-                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s) {
+                             const double* nrmX, int ns, int levels, bool fp8, cudaStream_t s, bool ftz) {
   if (k_hi <= k_lo) return cudaSuccess;
   const bool five = !fp8 && ns == 5 && levels == 5;
   const int* first = five ? w.h_chunk_first48 : w.h_chunk_first64;
@@ -540,16 +585,28 @@ cudaError_t launch_update_tc(const Problem& P, const SplitWorkspace& w, int i, i
   if (fp8) {
     const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA8);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB64_8);
-    k_update_tc<4, 4, 64, true><<<grid, kTcThreads, TcGeom<4, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, 4, mA,
-                                                                             mB);
+    if (ftz)
+      k_update_tc<4, 4, 64, true, true><<<grid, kTcThreads, TcGeom<4, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F,
+                                                                                     4, mA, mB);
+    else
+      k_update_tc<4, 4, 64, true><<<grid, kTcThreads, TcGeom<4, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, 4, mA,
+                                                                               mB);
   } else if (five) {
     const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB48);
-    k_update_tc<5, 5, 48><<<grid, kTcThreads, TcGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+    if (ftz)
+      k_update_tc<5, 5, 48, false, true><<<grid, kTcThreads, TcGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F,
+                                                                                      w.ns, mA, mB);
+    else
+      k_update_tc<5, 5, 48><<<grid, kTcThreads, TcGeom<5, 48>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
   } else {
     const CUtensorMap& mA = *reinterpret_cast<const CUtensorMap*>(w.tmA3);
     const CUtensorMap& mB = *reinterpret_cast<const CUtensorMap*>(w.tmB64);
-    k_update_tc<3, 3, 64><<<grid, kTcThreads, TcGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
+    if (ftz)
+      k_update_tc<3, 3, 64, false, true><<<grid, kTcThreads, TcGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F,
+                                                                                      w.ns, mA, mB);
+    else
+      k_update_tc<3, 3, 64><<<grid, kTcThreads, TcGeom<3, 64>::smem, s>>>(P, i, tt, exX, nrmX, w.eA, w.F, w.ns, mA, mB);
   }
   return cudaGetLastError();
 }

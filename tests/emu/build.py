@@ -91,7 +91,7 @@ namespace pevc {{
 int update_tc_setup() {{ return 0; }}
 int make_tensor_maps(SplitWorkspace& w) {{ w.tc_ok = false; return 0; }}
 cudaError_t launch_update_tc(const Problem&, const SplitWorkspace&, int, int, int, const int*, const double*, int, int, bool,
-                             cudaStream_t) {{ return 1; }}
+                             cudaStream_t, bool) {{ return 1; }}
 int bt_handle(void**, cudaStream_t) {{ return PEVC_ERR_UNSUPPORTED; }}
 void bt_handle_destroy(void*) {{}}
 int bt_gemm(void*, bool, int, int, const double*, int, const double*, int, double*, int) {{ return PEVC_ERR_UNSUPPORTED; }}
