@@ -10,8 +10,8 @@ emulated block's buffer, the L2 prefetch hint dropped, the PTX of the FP64 and
 BF16 and E4M3 mma.sync, ldmatrix and cp.async onto their models) and compiled with g++
 against the cuda_runtime.h stand-in beside this file.  The tcgen05 update and
 the cuBLAS pieces are stubbed out (without tensor maps the split path takes
-its mma.sync update); the back-transform normalisation kernels and the
-bounded-wait self-test are compiled on their own.  The result goes to tests/emu/_build/libpevc_emu.so.
+its mma.sync update); the back-transform normalisation kernels, the
+bounded-wait self-test and the epilogue's flushing helpers are compiled on their own.  The result goes to tests/emu/_build/libpevc_emu.so.
 """
 from __future__ import annotations
 
@@ -146,6 +146,18 @@ def _bt_source() -> str:
             "{ pevc::launch_bt_normalise_c(X, ldx, n, m, nullptr); }\n")
 
 
+def _ftz_source() -> str:
+    """The flushing product helpers of update_tc.cu's epilogue (the correction
+    sweeps'), compiled as host code and exported for unit tests."""
+    src = open(os.path.join(CSRC, "update_tc.cu")).read()
+    body = src[src.index("__device__ __forceinline__ double i64_scaled_ftz"):src.index("// Upper 32 bits of |x|'s bit pattern")]
+    return (f'#include "{CSRC}/common.cuh"\nnamespace pevc {{\n{body}\n}}\n'
+            'extern "C" double emu_i64_scaled_ftz(long long t, int e, int* slow) {\n'
+            "  bool s = false;\n  const double r = pevc::i64_scaled_ftz(t, e, s);\n  *slow = s;\n  return r;\n}\n"
+            'extern "C" double emu_pow2_scale_ftz(double y, int sh, int* slow) {\n'
+            "  bool s = false;\n  const double r = pevc::pow2_scale_ftz(y, sh, s);\n  *slow = s;\n  return r;\n}\n")
+
+
 def _watchdog_source() -> str:
     """watchdog.cu with its mbarrier PTX replaced by the model in cuda_runtime.h
     (the wait helper of tc.cuh restated on the modelled try_wait)."""
@@ -184,7 +196,8 @@ def build() -> str:
             fh.write(_convert(open(os.path.join(CSRC, f)).read(), f))
         srcs.append(out)
     for name, text in (("stubs.cpp", STUBS.format(csrc=CSRC)), ("bt.cpp", _bt_source()),
-                       ("watchdog.cpp", _watchdog_source()), ("helpers.cpp", HELPERS.format(csrc=CSRC))):
+                       ("watchdog.cpp", _watchdog_source()), ("helpers.cpp", HELPERS.format(csrc=CSRC)),
+                       ("ftz.cpp", _ftz_source())):
         out = os.path.join(BUILD, name)
         with open(out, "w") as fh:
             fh.write(text)

@@ -13,6 +13,7 @@ self-test are covered; the tcgen05 / TMA update is not.
 Sizes are small, since every warp exchange is a host barrier.
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -405,6 +406,50 @@ def math_ldexp(x, e):
         return math.ldexp(x, e)
     except OverflowError:
         return math.copysign(float("inf"), x)
+
+
+def test_epilogue_flush_helpers(emu):
+    """The correction sweeps' product helpers (update_tc.cu): a scaled product
+    t 2^e in the normal range is the correctly rounded value, as on the fast
+    path; one whose magnitude is below 2^-1022 becomes a zero of its sign
+    without the exact path; overflow still asks for the exact path."""
+    from fractions import Fraction
+    cd, cll = ctypes.c_double, ctypes.c_longlong
+    emu.emu_i64_scaled_ftz.argtypes = [cll, ci, ctypes.POINTER(ci)]
+    emu.emu_i64_scaled_ftz.restype = cd
+    emu.emu_pow2_scale_ftz.argtypes = [cd, ci, ctypes.POINTER(ci)]
+    emu.emu_pow2_scale_ftz.restype = cd
+    rng = np.random.default_rng(9960)
+    slow = ci(0)
+    tiny, huge = Fraction(2) ** -1022, Fraction(2) ** 1024
+    ts = [int(x) for x in (rng.integers(-2 ** 62, 2 ** 62, 2000) >> rng.integers(0, 62, 2000))] + [0, 1, -1, 2 ** 53 + 1]
+    seen = {"normal": 0, "flushed": 0, "overflow": 0}
+    for t in ts:
+        for e in (int(rng.integers(-1140, 1040)), int(rng.integers(-1100, -1000)), int(rng.integers(-60, 60))):
+            exact = Fraction(t) * Fraction(2) ** e
+            r = emu.emu_i64_scaled_ftz(t, e, ctypes.byref(slow))
+            if t != 0 and abs(exact) < tiny:
+                assert r == 0.0 and math.copysign(1.0, r) == math.copysign(1.0, t) and slow.value == 0, (t, e)
+                seen["flushed"] += 1
+            elif abs(exact) >= huge:
+                assert slow.value == 1, (t, e)
+                seen["overflow"] += 1
+            elif slow.value == 0:
+                assert r == float(exact), (t, e)         # correctly rounded, as the fast path
+                seen["normal"] += 1
+            else:
+                assert abs(exact) >= Fraction(2) ** 1023   # rounds up into overflow
+            if t != 0:
+                y = float(t)
+                ey = Fraction(y) * Fraction(2) ** e
+                ry = emu.emu_pow2_scale_ftz(y, e, ctypes.byref(slow))
+                if abs(ey) < tiny:
+                    assert ry == 0.0 and math.copysign(1.0, ry) == math.copysign(1.0, y) and slow.value == 0
+                elif abs(ey) >= huge:
+                    assert slow.value == 1
+                else:
+                    assert ry == float(ey) and slow.value == 0
+    assert min(seen.values()) > 20, seen
 
 
 def test_emulated_split_backtransform_gemm(emu):
