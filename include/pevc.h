@@ -137,8 +137,9 @@ int pevc_plan(pevc_plan_t *plan, int n_max, int batch_max, int prec, int tile,
  *   m_out      host: number of columns written
  * Stream-ordered on the plan's stream; the call reads the block structure
  * back to the host once and synchronises on return (m_out and the status are
- * final when it returns).  Deterministic: equal inputs give bitwise-equal
- * outputs.
+ * final when it returns); PEVC_SPLIT_FP8X4 plans also wait after each
+ * correction sweep, to read how much it changed the eigenvectors.
+ * Deterministic: equal inputs give bitwise-equal outputs.
  */
 int pevc_solve(pevc_plan_t plan, const double *S, int lds, const double *T, int ldt, int n,
                const int32_t *select, double *V_out, int ldv, int32_t *scale_out, int *m_out);
